@@ -1,0 +1,186 @@
+/*
+ * wavelet.h -- C ABI of the GB300 wavelet-tree / wavelet-matrix library.
+ *
+ * Builds the level bitmaps of wavelet trees and wavelet matrices on one GPU
+ * (Shun, "Improved Parallel Construction of Wavelet Trees and Rank/Select
+ * Structures"), plus rank/select directories on every level, and answers
+ * access / rank / select queries in batches.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  * Pointers named d_* are device pointers (CUDA global memory of the
+ *    current device); h_* are host pointers.  Sizes are element counts.
+ *  * `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Every call only enqueues work on it and returns; results are
+ *    final once the stream is synchronised.  Device-side errors found during
+ *    a build (a symbol >= sigma, a bounded wait that ran out) are reported by
+ *    wt_sync() or by the next call on the handle.
+ *  * Symbol sequences are contiguous arrays of width_bytes = 1, 2 or 4
+ *    (little-endian unsigned), read-only, borrowed for the duration of the
+ *    call and never retained.
+ *  * A build returns WT_OK and a handle in *out, or an error status and
+ *    leaves *out == NULL.  The handle owns every array it exports (except
+ *    the caller's bitvector for rs_build) until wt_free().
+ *  * Level l of a binary structure uses bit L-1-l of the symbol (most
+ *    significant first), L = ceil(log2 sigma) and L = 1 for sigma = 1.  Level
+ *    bitmaps are u64 words, bit i at word i/64, bit i%64, zero-padded to a
+ *    multiple of 2048 bits, levels stored back to back.
+ *  * Query semantics (Section 2 of the paper): access(i) = S[i];
+ *    rank(c, i) = number of c in S[0..i] (inclusive); select(c, k) = position
+ *    of the k-th occurrence of c, k >= 1.  An invalid argument (i >= n,
+ *    c >= sigma, k == 0, k > count of c) yields UINT64_MAX in that slot and
+ *    does not fail the batch.
+ *  * Thread safety: distinct handles may be used from distinct threads;
+ *    one handle must not be built/freed concurrently with its own use.
+ */
+#ifndef GB300_WAVELET_H
+#define GB300_WAVELET_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  WT_OK = 0,
+  WT_ERR_INVALID_ARG = 1,      /* bad size, width, sigma, NULL pointer, option */
+  WT_ERR_SYMBOL_GE_SIGMA = 2,  /* the sequence holds a symbol >= sigma */
+  WT_ERR_NO_MEMORY = 3,        /* device allocation failed */
+  WT_ERR_CUDA = 4,             /* a CUDA runtime call failed */
+  WT_ERR_TIMEOUT = 5,          /* a bounded device-side wait ran out */
+  WT_ERR_UNSUPPORTED = 6       /* valid but not supported (e.g. sigma too large) */
+} wt_status;
+
+typedef struct wt_struct* wt_handle;
+typedef void* wt_stream;
+
+/* Build options; a zero field means "choose automatically".
+ *  tau           levels per partition pass (1..8); the paper's tau (Sections 3, 4.1).
+ *  tile_symbols  symbols per tile; the paper's sub-sequence size n/K (Section 4.2).
+ *  ctas_per_sm   resident CTAs per SM for the persistent partition kernel.
+ *  k_chunks      number of tiles K; overrides tile_symbols when set.
+ *  select_sample sampling period of the select directory; only 4096 is supported.
+ *  flags         WT_FLAG_* below. */
+typedef struct {
+  uint32_t tau, tile_symbols, ctas_per_sm, k_chunks, select_sample, flags;
+} wt_build_opts;
+
+#define WT_FLAG_NO_DIRECTORY 1u  /* skip rank/select directories (timing of the bitmap build) */
+
+enum { WT_KIND_WT = 0, WT_KIND_WM = 1, WT_KIND_HUFF = 2, WT_KIND_MULTI = 3, WT_KIND_RS = 4 };
+
+/* Everything a handle holds, for parity checks and export.  Device arrays:
+ * bits, dir, samp.  Host arrays (owned by the handle, valid until wt_free):
+ * the offset tables, zeros, code_len, code.  For kind MULTI the "levels" are
+ * digit levels with bits_per_elem = 2 and dir records of 8 u64. */
+typedef struct {
+  uint32_t kind;
+  uint32_t levels;          /* binary levels, or digit levels (MULTI) */
+  uint64_t n;               /* sequence length (bits for RS) */
+  uint32_t sigma;
+  uint32_t bits_per_elem;   /* 1, or 2 for MULTI */
+  uint32_t dir_words_per_rec; /* 2 (binary) or 8 (MULTI) */
+  uint32_t max_code_len;    /* HUFF only */
+  const uint64_t* bits;     /* device */
+  const uint64_t* dir;      /* device */
+  const uint64_t* samp;     /* device (binary kinds) */
+  const uint64_t* level_len;  /* host [levels]: elements on each level */
+  const uint64_t* level_off;  /* host [levels+1]: word offset of each level in bits */
+  const uint64_t* dir_off;    /* host [levels+1]: u64 offset of each level in dir */
+  const uint64_t* samp_off;   /* host [2*levels+1]: u64 offsets into samp; level l
+                                 holds ceil(zeros_l/4096) zero samples from
+                                 samp_off[2l] and ceil(ones_l/4096) one samples
+                                 from samp_off[2l+1] (offsets are capacities) */
+  const uint64_t* zeros;      /* host [levels]: 0 bits per level (binary kinds) */
+  const uint8_t* code_len;    /* host [sigma] (HUFF) */
+  const uint32_t* code;       /* host [sigma] (HUFF) */
+} wt_export_view;
+
+/* Balanced binary wavelet tree, levelwise and pointer-free (paper Section 2,
+ * definition of the tree; Section 4.1 integer-sort construction; Section 4.2
+ * domain decomposition).  sigma in [1, 2^24]. */
+wt_status wt_build(const void* d_seq, uint64_t n, uint32_t sigma, uint32_t width_bytes,
+                   const wt_build_opts* opts, wt_stream stream, wt_handle* out);
+
+/* Wavelet matrix (Section 4.3, wavelet-matrix paragraph): level l holds bit
+ * l (from the top) of T_l, T_{l+1} = zeros of T_l then ones, order kept;
+ * zeros per level exported.  One pass handles tau levels by a stable
+ * partition on the reversed tau-bit digit.  sigma in [1, 2^32-1]. */
+wt_status wm_build(const void* d_seq, uint64_t n, uint32_t sigma, uint32_t width_bytes,
+                   const wt_build_opts* opts, wt_stream stream, wt_handle* out);
+
+/* Huffman-shaped binary wavelet tree (Section 4.3, arbitrarily-shaped
+ * trees).  h_code_len: sigma code lengths (0 = absent symbol), or NULL to
+ * derive Huffman lengths from the sequence's histogram, limited to 32 bits.
+ * Codes are canonical.  Level l holds the elements with code length > l,
+ * ordered by their l-bit code prefix; its bit is code bit l.  This call
+ * synchronises the stream once (the code is built on the host from the
+ * histogram).  sigma in [1, 2^24]. */
+wt_status huff_wt_build(const void* d_seq, uint64_t n, uint32_t sigma, uint32_t width_bytes,
+                        const uint8_t* h_code_len, const wt_build_opts* opts,
+                        wt_stream stream, wt_handle* out);
+
+/* Multiary wavelet tree of degree 4 (Section 4.3, multiary trees; Section
+ * 5.2 generalized rank): digit level beta keeps binary level 2*beta and
+ * stores the 2-bit digit below it (1 bit on the last level when L is odd),
+ * 32 digits per u64.  Per-digit-value rank directory per 1024 digits.
+ * degree must be 4 (WT_ERR_UNSUPPORTED otherwise).  sigma in [1, 2^24]. */
+wt_status multiary_build(const void* d_seq, uint64_t n, uint32_t sigma, uint32_t width_bytes,
+                         uint32_t degree, const wt_build_opts* opts, wt_stream stream,
+                         wt_handle* out);
+
+/* Rank/select directory over a caller bitvector (Section 5.1): d_bits holds
+ * nbits bits LSB-first in u64 words; bits at positions >= nbits inside the
+ * last word must be zero.  The handle keeps a reference to d_bits, which
+ * must stay alive and unchanged until wt_free().  Queries use c in {0,1}. */
+wt_status rs_build(const uint64_t* d_bits, uint64_t nbits, const wt_build_opts* opts,
+                   wt_stream stream, wt_handle* out);
+
+/* Batched queries (definitions of Section 2).  q queries; d_i / d_c / d_k /
+ * d_out are device arrays of q entries owned by the caller. */
+wt_status wt_access(wt_handle h, const uint64_t* d_i, uint64_t q, uint64_t* d_out,
+                    wt_stream stream);
+wt_status wt_rank(wt_handle h, const uint32_t* d_c, const uint64_t* d_i, uint64_t q,
+                  uint64_t* d_out, wt_stream stream);
+wt_status wt_select(wt_handle h, const uint32_t* d_c, const uint64_t* d_k, uint64_t q,
+                    uint64_t* d_out, wt_stream stream);
+
+/* Waits for the handle's build stream and returns its deferred status. */
+wt_status wt_sync(wt_handle h);
+
+/* Fills *out with views of the handle's arrays (synchronises the stream). */
+wt_status wt_export(wt_handle h, wt_export_view* out);
+
+/* Frees the handle and every array it owns (after its stream's work). */
+wt_status wt_free(wt_handle h);
+
+/* Number of symbol levels the structure represents (sum of level lengths). */
+uint64_t wt_symbol_levels(wt_handle h);
+
+const char* wt_status_str(wt_status s);
+
+/* Copies `bytes` from device memory d_src to host memory h_dst (synchronous;
+ * a utility for reading exported arrays). */
+wt_status wt_memcpy_d2h(void* h_dst, const void* d_src, uint64_t bytes);
+
+/* Measurement hooks (process-wide, not thread-safe): wt_prof_enable(1)
+ * starts counting every kernel this library launches and recording CUDA
+ * events around each partition-pass launch on its stream; wt_prof_read()
+ * waits for those events and returns the kernel count, the number of pass
+ * launches and their summed device time in milliseconds, then clears them. */
+void wt_prof_enable(int on);
+wt_status wt_prof_read(uint64_t* launches, uint64_t* pass_launches, double* pass_ms);
+
+/* Host-side helpers (no GPU needed): Huffman code lengths (heap keyed by
+ * (weight, id), leaf id = symbol, internal id = sigma + creation order;
+ * package-merge when longer than cap) and canonical codes.  Return the
+ * longest length.  Used by huff_wt_build; exported for testing. */
+uint32_t wt_huffman_lengths(const uint64_t* h_hist, uint32_t sigma, uint32_t cap,
+                            uint8_t* h_len);
+void wt_canonical_codes(const uint8_t* h_len, uint32_t sigma, uint32_t* h_code);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,349 @@
+"""GB300-native levelwise wavelet-tree / wavelet-matrix construction.
+
+Thin Python binding over the C ABI in ``include/wavelet.h`` (the shared
+library ``libwavelet.so`` built from ``csrc/`` for sm_103a).  The binding only
+marshals arguments: every step of a build or a query runs in the library's
+CUDA kernels.  PyTorch supplies device memory and streams.  There is no CPU
+fallback: if the library cannot be loaded, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libwavelet.so")
+
+WT_OK = 0
+STATUS = {0: "ok", 1: "invalid argument", 2: "symbol >= sigma", 3: "out of device memory",
+          4: "CUDA error", 5: "bounded device wait ran out", 6: "unsupported"}
+KIND_WT, KIND_WM, KIND_HUFF, KIND_MULTI, KIND_RS = range(5)
+FLAG_NO_DIRECTORY = 1
+
+#: every entry point declared in include/wavelet.h
+ABI_SYMBOLS = ("wt_build", "wm_build", "huff_wt_build", "multiary_build", "rs_build",
+               "wt_access", "wt_rank", "wt_select", "wt_sync", "wt_export", "wt_free",
+               "wt_symbol_levels", "wt_status_str", "wt_memcpy_d2h", "wt_huffman_lengths",
+               "wt_canonical_codes", "wt_prof_enable", "wt_prof_read")
+
+
+class WaveletError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        super().__init__(f"{what}: {STATUS.get(status, status)}")
+        self.status = status
+
+
+class BuildOpts(ctypes.Structure):
+    _fields_ = [("tau", ctypes.c_uint32), ("tile_symbols", ctypes.c_uint32),
+                ("ctas_per_sm", ctypes.c_uint32), ("k_chunks", ctypes.c_uint32),
+                ("select_sample", ctypes.c_uint32), ("flags", ctypes.c_uint32)]
+
+
+class ExportView(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_uint32), ("levels", ctypes.c_uint32), ("n", ctypes.c_uint64),
+                ("sigma", ctypes.c_uint32), ("bits_per_elem", ctypes.c_uint32),
+                ("dir_words_per_rec", ctypes.c_uint32), ("max_code_len", ctypes.c_uint32),
+                ("bits", ctypes.c_void_p), ("dir", ctypes.c_void_p), ("samp", ctypes.c_void_p),
+                ("level_len", ctypes.POINTER(ctypes.c_uint64)),
+                ("level_off", ctypes.POINTER(ctypes.c_uint64)),
+                ("dir_off", ctypes.POINTER(ctypes.c_uint64)),
+                ("samp_off", ctypes.POINTER(ctypes.c_uint64)),
+                ("zeros", ctypes.POINTER(ctypes.c_uint64)),
+                ("code_len", ctypes.POINTER(ctypes.c_uint8)),
+                ("code", ctypes.POINTER(ctypes.c_uint32))]
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libwavelet.so; raises if it was not built (no fallback exists)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"{path} is missing: run __graft_entry__.build() (no CPU fallback)")
+    lib = ctypes.CDLL(path)
+    c = ctypes
+    vp, u64, u32 = c.c_void_p, c.c_uint64, c.c_uint32
+    hp = c.POINTER(c.c_void_p)
+    for name in ("wt_build", "wm_build"):
+        f = getattr(lib, name)
+        f.restype = c.c_int
+        f.argtypes = [vp, u64, u32, u32, c.POINTER(BuildOpts), vp, hp]
+    lib.huff_wt_build.restype = c.c_int
+    lib.huff_wt_build.argtypes = [vp, u64, u32, u32, vp, c.POINTER(BuildOpts), vp, hp]
+    lib.multiary_build.restype = c.c_int
+    lib.multiary_build.argtypes = [vp, u64, u32, u32, u32, c.POINTER(BuildOpts), vp, hp]
+    lib.rs_build.restype = c.c_int
+    lib.rs_build.argtypes = [vp, u64, c.POINTER(BuildOpts), vp, hp]
+    lib.wt_access.restype = c.c_int
+    lib.wt_access.argtypes = [vp, vp, u64, vp, vp]
+    lib.wt_rank.restype = c.c_int
+    lib.wt_rank.argtypes = [vp, vp, vp, u64, vp, vp]
+    lib.wt_select.restype = c.c_int
+    lib.wt_select.argtypes = [vp, vp, vp, u64, vp, vp]
+    lib.wt_sync.restype = c.c_int
+    lib.wt_sync.argtypes = [vp]
+    lib.wt_export.restype = c.c_int
+    lib.wt_export.argtypes = [vp, c.POINTER(ExportView)]
+    lib.wt_free.restype = c.c_int
+    lib.wt_free.argtypes = [vp]
+    lib.wt_symbol_levels.restype = u64
+    lib.wt_symbol_levels.argtypes = [vp]
+    lib.wt_status_str.restype = c.c_char_p
+    lib.wt_status_str.argtypes = [c.c_int]
+    lib.wt_memcpy_d2h.restype = c.c_int
+    lib.wt_memcpy_d2h.argtypes = [vp, vp, u64]
+    lib.wt_huffman_lengths.restype = u32
+    lib.wt_huffman_lengths.argtypes = [vp, u32, u32, vp]
+    lib.wt_canonical_codes.restype = None
+    lib.wt_canonical_codes.argtypes = [vp, u32, vp]
+    lib.wt_prof_enable.restype = None
+    lib.wt_prof_enable.argtypes = [c.c_int]
+    lib.wt_prof_read.restype = c.c_int
+    lib.wt_prof_read.argtypes = [c.POINTER(u64), c.POINTER(u64), c.POINTER(c.c_double)]
+    _lib = lib
+    return lib
+
+
+def _check(status: int, what: str):
+    if status != WT_OK:
+        raise WaveletError(status, what)
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        import torch
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _opts(tau=0, ctas_per_sm=0, flags=0):
+    o = BuildOpts()
+    o.tau, o.ctas_per_sm, o.flags = tau, ctas_per_sm, flags
+    return o
+
+
+def _ptr(x) -> int:
+    return x if isinstance(x, int) else x.data_ptr()
+
+
+def d2h(dptr: int, nbytes: int, dtype=np.uint64) -> np.ndarray:
+    """Copy device memory (an exported array) to a new numpy array."""
+    itemsize = np.dtype(dtype).itemsize
+    out = np.empty(max(nbytes // itemsize, 0), dtype=dtype)
+    if nbytes:
+        _check(load_library().wt_memcpy_d2h(out.ctypes.data, dptr, nbytes), "wt_memcpy_d2h")
+    return out
+
+
+@dataclass
+class Exported:
+    kind: int
+    levels: int
+    n: int
+    sigma: int
+    bits_per_elem: int
+    max_code_len: int
+    level_len: np.ndarray
+    level_off: np.ndarray
+    dir_off: np.ndarray
+    samp_off: np.ndarray
+    zeros: np.ndarray
+    bits: np.ndarray
+    dir: np.ndarray
+    samp: np.ndarray
+    code_len: np.ndarray | None
+    code: np.ndarray | None
+
+    def level(self, l: int) -> np.ndarray:
+        return self.bits[int(self.level_off[l]):int(self.level_off[l + 1])]
+
+    def level_dir(self, l: int) -> np.ndarray:
+        w = 8 if self.bits_per_elem == 2 else 2
+        return self.dir[int(self.dir_off[l]):int(self.dir_off[l + 1])].reshape(-1, w)
+
+    def samples(self, l: int, b: int) -> np.ndarray:
+        n = int(self.level_len[l])
+        z = int(self.zeros[l])
+        cnt = z if b == 0 else n - z
+        s = int(self.samp_off[2 * l + b])
+        return self.samp[s:s + (cnt + 4095) // 4096]
+
+
+class Handle:
+    """A built structure; owns its device arrays until ``free()``."""
+
+    def __init__(self, raw: ctypes.c_void_p, keep=None):
+        self._h = raw
+        self._keep = keep  # caller buffer that must outlive the handle (rs_build)
+
+    @property
+    def raw(self):
+        return self._h
+
+    def _live(self):
+        if not self._h:
+            raise WaveletError(1, "handle already freed")
+        return self._h
+
+    def sync(self):
+        _check(load_library().wt_sync(self._live()), "wt_sync")
+
+    def symbol_levels(self) -> int:
+        return int(load_library().wt_symbol_levels(self._live()))
+
+    def access(self, i, out, q=None, stream=None):
+        q = i.numel() if q is None else q
+        _check(load_library().wt_access(self._live(), _ptr(i), q, _ptr(out), _stream_ptr(stream)),
+               "wt_access")
+        return out
+
+    def rank(self, c, i, out, q=None, stream=None):
+        q = i.numel() if q is None else q
+        _check(load_library().wt_rank(self._live(), _ptr(c), _ptr(i), q, _ptr(out),
+                                      _stream_ptr(stream)), "wt_rank")
+        return out
+
+    def select(self, c, k, out, q=None, stream=None):
+        q = k.numel() if q is None else q
+        _check(load_library().wt_select(self._live(), _ptr(c), _ptr(k), q, _ptr(out),
+                                        _stream_ptr(stream)), "wt_select")
+        return out
+
+    def export(self) -> Exported:
+        v = ExportView()
+        _check(load_library().wt_export(self._live(), ctypes.byref(v)), "wt_export")
+        L = v.levels
+
+        def host(p, n, dt=np.uint64):
+            if n == 0 or not p:
+                return np.zeros(0, dtype=dt)
+            return np.ctypeslib.as_array(p, shape=(n,)).astype(dt).copy()
+
+        level_len = host(v.level_len, L)
+        level_off = host(v.level_off, L + 1)
+        dir_off = host(v.dir_off, L + 1)
+        samp_off = host(v.samp_off, 2 * L + 1)
+        zeros = host(v.zeros, L)
+        nw = int(level_off[-1]) if L else 0
+        bits = d2h(v.bits, nw * 8) if nw else np.zeros(0, np.uint64)
+        nd = int(dir_off[-1]) if L else 0
+        dirs = d2h(v.dir, nd * 8) if nd else np.zeros(0, np.uint64)
+        ns = int(samp_off[-1]) if L else 0
+        samp = d2h(v.samp, ns * 8) if ns else np.zeros(0, np.uint64)
+        code_len = host(v.code_len, v.sigma, np.uint8) if v.code_len else None
+        code = host(v.code, v.sigma, np.uint32) if v.code else None
+        return Exported(v.kind, L, v.n, v.sigma, v.bits_per_elem, v.max_code_len, level_len,
+                        level_off, dir_off, samp_off, zeros, bits, dirs, samp, code_len, code)
+
+    def free(self):
+        if self._h:
+            _check(load_library().wt_free(self._h), "wt_free")
+            self._h = None
+            self._keep = None
+
+    def __del__(self):
+        try:
+            if self._h and _lib is not None:
+                _lib.wt_free(self._h)
+        except Exception:
+            pass
+
+
+def _width(seq) -> int:
+    return seq.element_size()
+
+
+def _build(fn, what, *args):
+    h = ctypes.c_void_p()
+    _check(fn(*args, ctypes.byref(h)), what)
+    return Handle(h)
+
+
+def wm_build(seq, sigma: int, n: int | None = None, tau: int = 0, ctas_per_sm: int = 0,
+             flags: int = 0, stream=None) -> Handle:
+    """Wavelet matrix of a device tensor of uint8/int16/int32 symbols."""
+    n = seq.numel() if n is None else n
+    o = _opts(tau, ctas_per_sm, flags)
+    return _build(load_library().wm_build, "wm_build", _ptr(seq), n, sigma, _width(seq),
+                  ctypes.byref(o), _stream_ptr(stream))
+
+
+def wt_build(seq, sigma: int, n: int | None = None, tau: int = 0, ctas_per_sm: int = 0,
+             flags: int = 0, stream=None) -> Handle:
+    """Balanced levelwise wavelet tree."""
+    n = seq.numel() if n is None else n
+    o = _opts(tau, ctas_per_sm, flags)
+    return _build(load_library().wt_build, "wt_build", _ptr(seq), n, sigma, _width(seq),
+                  ctypes.byref(o), _stream_ptr(stream))
+
+
+def huff_wt_build(seq, sigma: int, code_len: np.ndarray | None = None, n: int | None = None,
+                  tau: int = 0, flags: int = 0, stream=None) -> Handle:
+    """Huffman-shaped wavelet tree (lengths from the histogram when code_len is None)."""
+    n = seq.numel() if n is None else n
+    o = _opts(tau, 0, flags)
+    cl = None
+    if code_len is not None:
+        cl = np.ascontiguousarray(code_len, dtype=np.uint8)
+    h = ctypes.c_void_p()
+    _check(load_library().huff_wt_build(_ptr(seq), n, sigma, _width(seq),
+                                         cl.ctypes.data if cl is not None else None,
+                                         ctypes.byref(o), _stream_ptr(stream), ctypes.byref(h)),
+           "huff_wt_build")
+    return Handle(h)
+
+
+def multiary_build(seq, sigma: int, degree: int = 4, n: int | None = None, tau: int = 0,
+                   flags: int = 0, stream=None) -> Handle:
+    """4-ary wavelet tree (2-bit digit levels)."""
+    n = seq.numel() if n is None else n
+    o = _opts(tau, 0, flags)
+    h = ctypes.c_void_p()
+    _check(load_library().multiary_build(_ptr(seq), n, sigma, _width(seq), degree,
+                                          ctypes.byref(o), _stream_ptr(stream), ctypes.byref(h)),
+           "multiary_build")
+    return Handle(h)
+
+
+def rs_build(bits, nbits: int, stream=None) -> Handle:
+    """Rank/select directory over a device bitvector (kept referenced by the handle)."""
+    o = _opts()
+    h = ctypes.c_void_p()
+    _check(load_library().rs_build(_ptr(bits), nbits, ctypes.byref(o), _stream_ptr(stream),
+                                    ctypes.byref(h)), "rs_build")
+    return Handle(h, keep=bits)
+
+
+def prof_enable(on: bool = True):
+    """Count kernel launches and time partition-pass launches (CUDA events)."""
+    load_library().wt_prof_enable(1 if on else 0)
+
+
+def prof_read():
+    """(kernel launches, pass launches, summed pass milliseconds) since prof_enable."""
+    a, b, ms = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_double()
+    _check(load_library().wt_prof_read(ctypes.byref(a), ctypes.byref(b), ctypes.byref(ms)),
+           "wt_prof_read")
+    return int(a.value), int(b.value), float(ms.value)
+
+
+def huffman_lengths(hist: np.ndarray, cap: int = 32):
+    h = np.ascontiguousarray(hist, dtype=np.uint64)
+    ln = np.zeros(h.size, dtype=np.uint8)
+    mx = load_library().wt_huffman_lengths(h.ctypes.data, h.size, cap, ln.ctypes.data)
+    return ln, int(mx)
+
+
+def canonical_codes(lengths: np.ndarray) -> np.ndarray:
+    ln = np.ascontiguousarray(lengths, dtype=np.uint8)
+    code = np.zeros(ln.size, dtype=np.uint32)
+    load_library().wt_canonical_codes(ln.ctypes.data, ln.size, code.ctypes.data)
+    return code

@@ -1,0 +1,305 @@
+// api.cu -- the C ABI (include/wavelet.h): argument checks, handle lifetime,
+// export.  Every computational step runs in the kernels of build.cu and
+// dirq.cu.
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "wt_host.h"
+#include "wt_internal.cuh"
+
+using namespace wtk;
+
+namespace {
+
+bool valid_width(uint32_t w) { return w == 1 || w == 2 || w == 4; }
+
+bool sigma_fits_width(uint32_t sigma, uint32_t w) {
+  return w == 4 || (uint64_t)sigma <= ((uint64_t)1 << (8 * w));
+}
+
+wt_status check_opts(const wt_build_opts* o) {
+  if (!o) return WT_OK;
+  if (o->tau > 8) return WT_ERR_INVALID_ARG;
+  if (o->select_sample != 0 && o->select_sample != 4096) return WT_ERR_UNSUPPORTED;
+  if (o->tile_symbols != 0 && o->tile_symbols != 8192) return WT_ERR_UNSUPPORTED;
+  if (o->k_chunks != 0) return WT_ERR_UNSUPPORTED;
+  return WT_OK;
+}
+
+void free_arrays(wt_struct* h) {
+  cudaStream_t st = h->stream;
+  dfree(h->d_bits, st);
+  dfree(h->d_dir, st);
+  dfree(h->d_samp, st);
+  dfree(h->d_zeros, st);
+  dfree(h->d_err, st);
+  dfree(h->d_abort, st);
+  dfree(h->d_meta, st);
+  dfree(h->d_code, st);
+  dfree(h->d_len, st);
+  dfree(h->d_sym_by_rank, st);
+  dfree(h->d_len_tab, st);
+  dfree(h->d_node, st);
+  dfree(h->d_node_lvl, st);
+}
+
+wt_status new_handle(wt_stream stream, uint64_t n, uint32_t sigma, wt_struct** out) {
+  wt_struct* h = new (std::nothrow) wt_struct();
+  if (!h) return WT_ERR_NO_MEMORY;
+  h->stream = (cudaStream_t)stream;
+  h->n = n;
+  h->sigma = sigma;
+  cudaGetDevice(&h->device);
+  if (dmalloc((void**)&h->d_err, 8, h->stream) != cudaSuccess ||
+      dmalloc((void**)&h->d_abort, 8, h->stream) != cudaSuccess) {
+    free_arrays(h);
+    delete h;
+    return WT_ERR_NO_MEMORY;
+  }
+  cudaMemsetAsync(h->d_err, 0, 8, h->stream);
+  cudaMemsetAsync(h->d_abort, 0, 8, h->stream);
+  *out = h;
+  return WT_OK;
+}
+
+wt_status finish(wt_struct* h, wt_status s, wt_handle* out) {
+  if (s == WT_OK) {
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) s = WT_ERR_CUDA;
+  }
+  if (s != WT_OK) {
+    cudaStreamSynchronize(h->stream);
+    free_arrays(h);
+    cudaStreamSynchronize(h->stream);
+    delete h;
+    *out = nullptr;
+    return s;
+  }
+  *out = h;
+  return WT_OK;
+}
+
+wt_status sync_handle(wt_struct* h) {
+  if (h->deferred != WT_OK) return h->deferred;
+  cudaError_t e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return h->deferred = WT_ERR_CUDA;
+  uint32_t err = 0;
+  e = cudaMemcpy(&err, h->d_err, 4, cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return h->deferred = WT_ERR_CUDA;
+  if (err & ERR_SYMBOL) return h->deferred = WT_ERR_SYMBOL_GE_SIGMA;
+  if (err & ERR_TIMEOUT) return h->deferred = WT_ERR_TIMEOUT;
+  if (err) return h->deferred = WT_ERR_CUDA;
+  if (!h->zeros_valid) {
+    h->zeros.assign(h->levels, 0);
+    if (h->levels && h->bpe == 1) {
+      e = cudaMemcpy(h->zeros.data(), h->d_zeros, h->levels * 8, cudaMemcpyDeviceToHost);
+      if (e != cudaSuccess) return h->deferred = WT_ERR_CUDA;
+    }
+    h->zeros_valid = true;
+  }
+  return WT_OK;
+}
+
+wt_status seq_build(int kind, const void* d_seq, uint64_t n, uint32_t sigma, uint32_t width,
+                    const uint8_t* h_len, uint32_t degree, const wt_build_opts* opts,
+                    wt_stream stream, wt_handle* out) {
+  if (!out) return WT_ERR_INVALID_ARG;
+  *out = nullptr;
+  if ((!d_seq && n) || sigma == 0 || !valid_width(width)) return WT_ERR_INVALID_ARG;
+  if (!sigma_fits_width(sigma, width) && width < 4) {
+    // symbols >= sigma cannot be stored anyway; sigma above the width range is allowed
+  }
+  wt_status s = check_opts(opts);
+  if (s != WT_OK) return s;
+  if (kind == WT_KIND_MULTI && degree != 4) return WT_ERR_UNSUPPORTED;
+  if ((kind == WT_KIND_WT || kind == WT_KIND_MULTI || kind == WT_KIND_HUFF) && sigma > (1u << 24))
+    return WT_ERR_UNSUPPORTED;
+  wt_struct* h = nullptr;
+  s = new_handle(stream, n, sigma, &h);
+  if (s != WT_OK) return s;
+  switch (kind) {
+    case WT_KIND_WM: s = build_wm(d_seq, n, sigma, (int)width, opts, h); break;
+    case WT_KIND_WT: s = build_wt(d_seq, n, sigma, (int)width, opts, h, false); break;
+    case WT_KIND_MULTI: s = build_wt(d_seq, n, sigma, (int)width, opts, h, true); break;
+    default: s = build_huff(d_seq, n, sigma, (int)width, h_len, opts, h); break;
+  }
+  return finish(h, s, out);
+}
+
+}  // namespace
+
+extern "C" {
+
+wt_status wt_build(const void* d_seq, uint64_t n, uint32_t sigma, uint32_t width_bytes,
+                   const wt_build_opts* opts, wt_stream stream, wt_handle* out) {
+  return seq_build(WT_KIND_WT, d_seq, n, sigma, width_bytes, nullptr, 2, opts, stream, out);
+}
+
+wt_status wm_build(const void* d_seq, uint64_t n, uint32_t sigma, uint32_t width_bytes,
+                   const wt_build_opts* opts, wt_stream stream, wt_handle* out) {
+  return seq_build(WT_KIND_WM, d_seq, n, sigma, width_bytes, nullptr, 2, opts, stream, out);
+}
+
+wt_status huff_wt_build(const void* d_seq, uint64_t n, uint32_t sigma, uint32_t width_bytes,
+                        const uint8_t* h_code_len, const wt_build_opts* opts, wt_stream stream,
+                        wt_handle* out) {
+  return seq_build(WT_KIND_HUFF, d_seq, n, sigma, width_bytes, h_code_len, 2, opts, stream, out);
+}
+
+wt_status multiary_build(const void* d_seq, uint64_t n, uint32_t sigma, uint32_t width_bytes,
+                         uint32_t degree, const wt_build_opts* opts, wt_stream stream,
+                         wt_handle* out) {
+  return seq_build(WT_KIND_MULTI, d_seq, n, sigma, width_bytes, nullptr, degree, opts, stream,
+                   out);
+}
+
+wt_status rs_build(const uint64_t* d_bits, uint64_t nbits, const wt_build_opts* opts,
+                   wt_stream stream, wt_handle* out) {
+  if (!out) return WT_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (!d_bits && nbits) return WT_ERR_INVALID_ARG;
+  wt_status s = check_opts(opts);
+  if (s != WT_OK) return s;
+  wt_struct* h = nullptr;
+  s = new_handle(stream, nbits, 2, &h);
+  if (s != WT_OK) return s;
+  h->kind = WT_KIND_RS;
+  h->levels = h->L = 1;
+  h->bpe = 1;
+  h->d_bits_ro = d_bits;
+  h->level_len.assign(1, nbits);
+  h->level_off.assign(2, 0);
+  h->level_off[1] = ((nbits + 2047) / 2048) * 32;
+  if (dmalloc((void**)&h->d_zeros, 8, h->stream) != cudaSuccess) s = WT_ERR_NO_MEMORY;
+  if (s == WT_OK) s = build_directories(h);
+  return finish(h, s, out);
+}
+
+wt_status wt_access(wt_handle h, const uint64_t* d_i, uint64_t q, uint64_t* d_out,
+                    wt_stream stream) {
+  if (!h || (q && (!d_i || !d_out))) return WT_ERR_INVALID_ARG;
+  if (h->deferred != WT_OK) return h->deferred;
+  return launch_query(h, 0, nullptr, d_i, q, d_out, (cudaStream_t)stream);
+}
+
+wt_status wt_rank(wt_handle h, const uint32_t* d_c, const uint64_t* d_i, uint64_t q,
+                  uint64_t* d_out, wt_stream stream) {
+  if (!h || (q && (!d_c || !d_i || !d_out))) return WT_ERR_INVALID_ARG;
+  if (h->deferred != WT_OK) return h->deferred;
+  return launch_query(h, 1, d_c, d_i, q, d_out, (cudaStream_t)stream);
+}
+
+wt_status wt_select(wt_handle h, const uint32_t* d_c, const uint64_t* d_k, uint64_t q,
+                    uint64_t* d_out, wt_stream stream) {
+  if (!h || (q && (!d_c || !d_k || !d_out))) return WT_ERR_INVALID_ARG;
+  if (h->deferred != WT_OK) return h->deferred;
+  return launch_query(h, 2, d_c, d_k, q, d_out, (cudaStream_t)stream);
+}
+
+wt_status wt_sync(wt_handle h) {
+  if (!h) return WT_ERR_INVALID_ARG;
+  return sync_handle(h);
+}
+
+wt_status wt_export(wt_handle h, wt_export_view* out) {
+  if (!h || !out) return WT_ERR_INVALID_ARG;
+  wt_status s = sync_handle(h);
+  if (s != WT_OK) return s;
+  memset(out, 0, sizeof(*out));
+  out->kind = (uint32_t)h->kind;
+  out->levels = h->levels;
+  out->n = h->n;
+  out->sigma = h->sigma;
+  out->bits_per_elem = h->bpe;
+  out->dir_words_per_rec = h->bpe == 2 ? 8 : 2;
+  out->max_code_len = h->max_code_len;
+  out->bits = h->d_bits_ro;
+  out->dir = h->d_dir;
+  out->samp = h->d_samp;
+  out->level_len = h->level_len.data();
+  out->level_off = h->level_off.data();
+  out->dir_off = h->dir_off.data();
+  out->samp_off = h->samp_off.data();
+  out->zeros = h->zeros.data();
+  out->code_len = h->code_len.empty() ? nullptr : h->code_len.data();
+  out->code = h->code.empty() ? nullptr : h->code.data();
+  return WT_OK;
+}
+
+wt_status wt_free(wt_handle h) {
+  if (!h) return WT_ERR_INVALID_ARG;
+  cudaStreamSynchronize(h->stream);
+  free_arrays(h);
+  cudaError_t e = cudaStreamSynchronize(h->stream);
+  delete h;
+  return e == cudaSuccess ? WT_OK : WT_ERR_CUDA;
+}
+
+uint64_t wt_symbol_levels(wt_handle h) {
+  if (!h) return 0;
+  uint64_t s = 0;
+  for (uint64_t v : h->level_len) s += v;
+  return h->bpe == 2 ? s * 2 : s;
+}
+
+const char* wt_status_str(wt_status s) {
+  switch (s) {
+    case WT_OK: return "ok";
+    case WT_ERR_INVALID_ARG: return "invalid argument";
+    case WT_ERR_SYMBOL_GE_SIGMA: return "symbol >= sigma";
+    case WT_ERR_NO_MEMORY: return "out of device memory";
+    case WT_ERR_CUDA: return "CUDA error";
+    case WT_ERR_TIMEOUT: return "bounded device wait ran out";
+    case WT_ERR_UNSUPPORTED: return "unsupported";
+  }
+  return "unknown status";
+}
+
+wt_status wt_memcpy_d2h(void* h_dst, const void* d_src, uint64_t bytes) {
+  if (!bytes) return WT_OK;
+  if (!h_dst || !d_src) return WT_ERR_INVALID_ARG;
+  return cudaMemcpy(h_dst, d_src, bytes, cudaMemcpyDeviceToHost) == cudaSuccess ? WT_OK
+                                                                                : WT_ERR_CUDA;
+}
+
+void wt_prof_enable(int on) {
+  Prof& p = prof();
+  p.on = on != 0;
+  p.launches = 0;
+  p.pass_launches = 0;
+  for (cudaEvent_t e : p.ev) cudaEventDestroy(e);
+  p.ev.clear();
+}
+
+wt_status wt_prof_read(uint64_t* launches, uint64_t* pass_launches, double* pass_ms) {
+  Prof& p = prof();
+  double ms = 0;
+  wt_status s = WT_OK;
+  for (size_t i = 0; i + 1 < p.ev.size(); i += 2) {
+    if (cudaEventSynchronize(p.ev[i + 1]) != cudaSuccess) s = WT_ERR_CUDA;
+    float f = 0;
+    if (cudaEventElapsedTime(&f, p.ev[i], p.ev[i + 1]) == cudaSuccess) ms += f;
+  }
+  if (launches) *launches = p.launches;
+  if (pass_launches) *pass_launches = p.pass_launches;
+  if (pass_ms) *pass_ms = ms;
+  for (cudaEvent_t e : p.ev) cudaEventDestroy(e);
+  p.ev.clear();
+  p.launches = 0;
+  p.pass_launches = 0;
+  return s;
+}
+
+uint32_t wt_huffman_lengths(const uint64_t* h_hist, uint32_t sigma, uint32_t cap,
+                            uint8_t* h_len) {
+  if (!h_hist || !h_len || cap == 0 || cap > 64) return 0;
+  return huffman_lengths(h_hist, sigma, cap, h_len);
+}
+
+void wt_canonical_codes(const uint8_t* h_len, uint32_t sigma, uint32_t* h_code) {
+  if (!h_len || !h_code) return;
+  canonical_codes(h_len, sigma, h_code);
+}
+
+}  // extern "C"

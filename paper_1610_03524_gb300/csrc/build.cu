@@ -1,0 +1,986 @@
+// build.cu -- construction of wavelet matrices, balanced / Huffman-shaped /
+// 4-ary wavelet trees on one GPU.
+//
+// Pipeline of one build (all on one stream, no host synchronisation except
+// the Huffman code construction):
+//   1. histogram + validation pass over S (Section 4.1: counting for the
+//      integer sort; for the wavelet matrix one digit histogram per pass,
+//      since a histogram does not depend on the order of the elements);
+//   2. plan: node/class start offsets of every level by prefix sums
+//      (Section 4.2), zero counts z_l (Section 4.3), zeroing of the words
+//      that straddle two nodes, look-back reset;
+//   3. one partition pass per tau levels (k_pass.cuh);
+//   4. rank/select directories on every level (dirq.cu).
+#include <algorithm>
+#include <cmath>
+#include <type_traits>
+#include <atomic>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "k_pass.cuh"
+#include "wt_host.h"
+
+namespace wtk {
+
+static std::atomic<uint64_t> g_seq{1};
+constexpr uint32_t RING_SLOTS = 2048;
+constexpr uint64_t SPIN_LIMIT = 1ull << 24;
+
+#define CK(x)                                                   \
+  do {                                                          \
+    cudaError_t e_ = (x);                                       \
+    if (e_ != cudaSuccess) {                                    \
+      fprintf(stderr, "wavelet: %s -> %s\n", #x, cudaGetErrorString(e_)); \
+      return e_ == cudaErrorMemoryAllocation ? WT_ERR_NO_MEMORY : WT_ERR_CUDA; \
+    }                                                           \
+  } while (0)
+
+cudaError_t dmalloc(void** p, size_t bytes, cudaStream_t s) {
+  if (bytes == 0) bytes = 16;
+  return cudaMallocAsync(p, bytes, s);
+}
+void dfree(void* p, cudaStream_t s) {
+  if (p) cudaFreeAsync(p, s);
+}
+
+Prof& prof() {
+  static Prof p;
+  return p;
+}
+
+uint32_t num_sms() {
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms <= 0) sms = 1;
+  }
+  return (uint32_t)sms;
+}
+
+static uint32_t levels_of(uint32_t sigma) {
+  uint32_t L = 0;
+  while (L < 32 && ((uint64_t)1 << L) < (uint64_t)sigma) L++;
+  return L == 0 ? 1 : L;
+}
+static uint64_t level_words(uint64_t nbits) { return ((nbits + 2047) / 2048) * 32; }
+static int width_for_bits(int b) { return b <= 8 ? 1 : (b <= 16 ? 2 : 4); }
+
+// ---------------------------------------------------------------------------
+// 1. histogram / validation
+// ---------------------------------------------------------------------------
+template <int WB, typename F>
+__device__ __forceinline__ void for_each_symbol(const void* seq, uint64_t n, uint64_t gtid,
+                                                uint64_t gstride, F&& f) {
+  using T = typename std::conditional<WB == 1, uint8_t,
+                                      typename std::conditional<WB == 2, uint16_t, uint32_t>::type>::type;
+  const T* s = (const T*)seq;
+  constexpr int PER = 16 / WB;
+  const bool aligned = (((uintptr_t)seq) & 15) == 0;
+  uint64_t nvec = aligned ? n / PER : 0;
+  const uint4* v = (const uint4*)seq;
+  for (uint64_t i = gtid; i < nvec; i += gstride) {
+    const uint4 q = __ldcs(v + i);
+    const uint32_t w[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+      if (WB == 1) {
+#pragma unroll
+        for (int b = 0; b < 4; b++) f((w[k] >> (8 * b)) & 0xffu);
+      } else if (WB == 2) {
+        f(w[k] & 0xffffu);
+        f(w[k] >> 16);
+      } else {
+        f(w[k]);
+      }
+    }
+  }
+  for (uint64_t i = nvec * PER + gtid; i < n; i += gstride) f((uint32_t)s[i]);
+}
+
+// Per-pass reversed-digit histograms (wavelet matrix).  Pass g covers levels
+// a = g*tau .. a+t-1; its digit is the t bits below level a read with the
+// level-a bit as the least significant one (Section 4.3: sort on the
+// reverse of the tau bits).
+template <int WB>
+__global__ void k_hist_digits(const void* seq, uint64_t n, uint32_t sigma, int L, int tau,
+                              int G, uint64_t* hist, uint32_t* err) {
+  // at most 1024 bins in total: G passes of 2^t bins, G*2^tau <= 1024 for tau <= 8
+  __shared__ uint32_t sh[1024];
+  __shared__ int off[33], tt[32], shf[32];
+  if (threadIdx.x == 0) {
+    int o = 0;
+    for (int g = 0; g < G; g++) {
+      const int a = g * tau;
+      tt[g] = min(tau, L - a);
+      shf[g] = L - a - tt[g];
+      off[g] = o;
+      o += 1 << tt[g];
+    }
+    off[G] = o;
+  }
+  __syncthreads();
+  const int o = off[G];
+  for (int i = threadIdx.x; i < o; i += blockDim.x) sh[i] = 0;
+  __syncthreads();
+  bool bad = false;
+  for_each_symbol<WB>(seq, n, (uint64_t)blockIdx.x * blockDim.x + threadIdx.x,
+                      (uint64_t)gridDim.x * blockDim.x, [&](uint32_t x) {
+                        bad |= x >= sigma;
+                        for (int g = 0; g < G; g++) {
+                          const uint32_t d = (x >> shf[g]) & ((1u << tt[g]) - 1u);
+                          atomicAdd(&sh[off[g] + rev_bits(d, tt[g])], 1u);
+                        }
+                      });
+  if (bad) atomicOr(err, ERR_SYMBOL);
+  __syncthreads();
+  for (int i = threadIdx.x; i < o; i += blockDim.x)
+    if (sh[i]) atomicAdd((unsigned long long*)&hist[i], (unsigned long long)sh[i]);
+}
+
+// Full symbol histogram (balanced / Huffman / 4-ary trees).
+template <int WB>
+__global__ void k_hist_full(const void* seq, uint64_t n, uint32_t sigma, uint64_t* hist,
+                            uint32_t* err, int use_smem) {
+  extern __shared__ uint32_t shh[];
+  if (use_smem) {
+    for (uint32_t i = threadIdx.x; i < sigma; i += blockDim.x) shh[i] = 0;
+    __syncthreads();
+  }
+  bool bad = false;
+  const int lane = threadIdx.x & 31;
+  for_each_symbol<WB>(seq, n, (uint64_t)blockIdx.x * blockDim.x + threadIdx.x,
+                      (uint64_t)gridDim.x * blockDim.x, [&](uint32_t x) {
+                        const bool ok = x < sigma;
+                        bad |= !ok;
+                        if (use_smem) {
+                          if (ok) atomicAdd(&shh[x], 1u);
+                        } else if (ok) {
+                          atomicAdd((unsigned long long*)&hist[x], 1ull);
+                        }
+                      });
+  (void)lane;
+  if (bad) atomicOr(err, ERR_SYMBOL);
+  if (use_smem) {
+    __syncthreads();
+    for (uint32_t i = threadIdx.x; i < sigma; i += blockDim.x)
+      if (shh[i]) atomicAdd((unsigned long long*)&hist[i], (unsigned long long)shh[i]);
+  }
+}
+
+static wt_status launch_hist_full(const void* seq, int w, uint64_t n, uint32_t sigma,
+                                  uint64_t* hist, uint32_t* err, cudaStream_t st) {
+  if (n == 0) return WT_OK;
+  const int use_smem = sigma <= 12288;
+  const size_t shb = use_smem ? sigma * 4 : 0;
+  const uint32_t blocks = std::min<uint64_t>(num_sms() * 4, (n + 4095) / 4096 + 1);
+  if (w == 1) k_hist_full<1><<<blocks, 512, shb, st>>>(seq, n, sigma, hist, err, use_smem);
+  else if (w == 2) k_hist_full<2><<<blocks, 512, shb, st>>>(seq, n, sigma, hist, err, use_smem);
+  else k_hist_full<4><<<blocks, 512, shb, st>>>(seq, n, sigma, hist, err, use_smem);
+  count_launch();
+  CK(cudaGetLastError());
+  return WT_OK;
+}
+
+// ---------------------------------------------------------------------------
+// exclusive scan of u64 (n entries -> n+1 outputs); reduce, scan, add
+// ---------------------------------------------------------------------------
+constexpr int SCAN_BT = 1024, SCAN_PER = 4, SCAN_CH = SCAN_BT * SCAN_PER;
+
+__device__ uint64_t block_scan_excl_u64(uint64_t v, uint64_t* total) {
+  __shared__ uint64_t ws[32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint64_t x = v;
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint64_t y = __shfl_up_sync(FULL, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) ws[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    const int nw = blockDim.x >> 5;
+    uint64_t s = lane < nw ? ws[lane] : 0;
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint64_t y = __shfl_up_sync(FULL, s, o);
+      if (lane >= o) s += y;
+    }
+    if (lane < nw) ws[lane] = s;
+  }
+  __syncthreads();
+  const uint64_t base = warp ? ws[warp - 1] : 0;
+  if (total) *total = ws[(blockDim.x >> 5) - 1];
+  __syncthreads();
+  return base + x - v;
+}
+
+__global__ void k_scan_reduce(const uint64_t* in, uint64_t n, uint64_t* bsum) {
+  const uint64_t b0 = (uint64_t)blockIdx.x * SCAN_CH;
+  uint64_t s = 0;
+  for (int k = 0; k < SCAN_PER; k++) {
+    const uint64_t i = b0 + (uint64_t)k * SCAN_BT + threadIdx.x;
+    if (i < n) s += in[i];
+  }
+  uint64_t tot;
+  block_scan_excl_u64(s, &tot);
+  if (threadIdx.x == 0) bsum[blockIdx.x] = tot;
+}
+
+__global__ void k_scan_top(uint64_t* bsum, uint64_t nb) {
+  __shared__ uint64_t carry;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  for (uint64_t c0 = 0; c0 < nb; c0 += blockDim.x) {
+    const uint64_t i = c0 + threadIdx.x;
+    const uint64_t v = i < nb ? bsum[i] : 0;
+    uint64_t tot;
+    const uint64_t ex = block_scan_excl_u64(v, &tot);
+    if (i < nb) bsum[i] = carry + ex;
+    __syncthreads();
+    if (threadIdx.x == 0) carry += tot;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) bsum[nb] = carry;
+}
+
+__global__ void k_scan_down(const uint64_t* in, uint64_t n, const uint64_t* bsum, uint64_t* out) {
+  const uint64_t b0 = (uint64_t)blockIdx.x * SCAN_CH;
+  const uint64_t i0 = b0 + (uint64_t)threadIdx.x * SCAN_PER;
+  uint64_t v[SCAN_PER], s = 0;
+  for (int k = 0; k < SCAN_PER; k++) {
+    v[k] = (i0 + k < n) ? in[i0 + k] : 0;
+    s += v[k];
+  }
+  uint64_t ex = block_scan_excl_u64(s, nullptr) + bsum[blockIdx.x];
+  for (int k = 0; k < SCAN_PER; k++) {
+    if (i0 + k < n) out[i0 + k] = ex;
+    ex += v[k];
+  }
+  if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) out[n] = bsum[gridDim.x];
+}
+
+// out[0..n] = exclusive prefix of in[0..n); scratch >= n/4096 + 2 entries
+static wt_status scan_excl_u64(const uint64_t* in, uint64_t* out, uint64_t n, uint64_t* scratch,
+                               cudaStream_t st) {
+  const uint64_t nb = (n + SCAN_CH - 1) / SCAN_CH;
+  if (nb == 0) {
+    CK(cudaMemsetAsync(out, 0, sizeof(uint64_t), st));
+    return WT_OK;
+  }
+  k_scan_reduce<<<(unsigned)nb, SCAN_BT, 0, st>>>(in, n, scratch);
+  count_launch();
+  k_scan_top<<<1, SCAN_BT, 0, st>>>(scratch, nb);
+  count_launch();
+  k_scan_down<<<(unsigned)nb, SCAN_BT, 0, st>>>(in, n, scratch, out);
+  count_launch();
+  CK(cudaGetLastError());
+  return WT_OK;
+}
+static uint64_t scan_scratch(uint64_t n) { return n / SCAN_CH + 2; }
+
+// ---------------------------------------------------------------------------
+// 2. plans
+// ---------------------------------------------------------------------------
+struct PassGeom {
+  int a, t, rbits, in_w, out_w;
+  bool wide;  // 32-bit working elements
+};
+
+static std::vector<PassGeom> make_passes(int L, int tau, int first_w) {
+  std::vector<PassGeom> ps;
+  for (int a = 0; a < L; a += tau) {
+    PassGeom p;
+    p.a = a;
+    p.t = std::min(tau, L - a);
+    p.rbits = L - a;
+    p.in_w = a == 0 ? first_w : width_for_bits(L - a);
+    p.out_w = (a + p.t < L) ? width_for_bits(L - a - p.t) : 0;
+    p.wide = p.rbits > 16;
+    ps.push_back(p);
+  }
+  return ps;
+}
+
+// Wavelet-matrix plan, one block: class starts of every level of every pass
+// (classes of level a+j are the values of the low j bits of the reversed
+// digit), zero counts, zeroing of node-boundary words and of the padding,
+// reset of the look-back ring and tickets.
+__global__ void k_plan_wm(const uint64_t* hist, uint64_t n, int L, int tau, int G,
+                          uint64_t* cls, uint64_t* zeros, uint64_t* bits, uint64_t W,
+                          uint64_t* ring, uint32_t ring_slots, uint32_t* tickets,
+                          uint32_t* abort_flag) {
+  __shared__ uint64_t cnt[512];
+  __shared__ uint64_t st[512];
+  int hoff = 0, coff = 0;
+  for (int g = 0; g < G; g++) {
+    const int a = g * tau, t = min(tau, L - a);
+    for (int j = 0; j <= t; j++) {
+      const int nk = 1 << j;
+      for (int k = threadIdx.x; k < nk; k += blockDim.x) {
+        uint64_t s = 0;
+        for (int r = k; r < (1 << t); r += nk) s += hist[hoff + r];
+        cnt[k] = s;
+      }
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        uint64_t acc = 0;
+        for (int k = 0; k < nk; k++) {
+          st[k] = acc;
+          acc += cnt[k];
+        }
+        st[nk] = acc;
+      }
+      __syncthreads();
+      uint64_t* c = cls + coff + (nk - 1 + j);
+      for (int k = threadIdx.x; k <= nk; k += blockDim.x) c[k] = st[k];
+      if (j >= 1 && j < t) {
+        uint64_t* lb = bits + (uint64_t)(a + j) * W;
+        for (int k = 1 + threadIdx.x; k < nk; k += blockDim.x) {
+          const uint64_t s = st[k];
+          if ((s & 63) && s < n) lb[s >> 6] = 0;
+        }
+      }
+      if (j >= 1 && threadIdx.x == 0) zeros[a + j - 1] = st[nk >> 1];
+      __syncthreads();
+    }
+    hoff += 1 << t;
+    coff += (2 << t) + t + 1;
+  }
+  // padding words of every level
+  const uint64_t used = (n + 63) >> 6;
+  for (int l = 0; l < L; l++)
+    for (uint64_t w = used + threadIdx.x; w < W; w += blockDim.x) bits[(uint64_t)l * W + w] = 0;
+  for (uint32_t i = threadIdx.x; i < ring_slots; i += blockDim.x) ring[(uint64_t)i * SLOT_U64] = 0;
+  for (int g = threadIdx.x; g < 32; g += blockDim.x) tickets[g] = 0;
+  if (threadIdx.x == 0) *abort_flag = 0;
+}
+
+// Balanced-tree helpers over C (C[v] = number of symbols < v, v in [0, 2^L]).
+// Zero counts: z_l = sum over nodes q of level l of the size of the left child.
+__global__ void k_wt_zeros(const uint64_t* C, int L, uint64_t* zeros) {
+  // one block per level
+  const int l = blockIdx.x;
+  const int sh = L - l - 1;
+  uint64_t s = 0;
+  for (uint64_t q = threadIdx.x; q < ((uint64_t)1 << l); q += blockDim.x)
+    s += C[(2 * q + 1) << sh] - C[(2 * q) << sh];
+  uint64_t tot;
+  block_scan_excl_u64(s, &tot);
+  if (threadIdx.x == 0) zeros[l] = tot;
+}
+
+// Zero the words that hold the start of a node (not word aligned) on every
+// output level; and the padding words.  digits: only even binary levels are
+// output (digit level l/2), 2 bits per element.
+__global__ void k_wt_zero_words(const uint64_t* C, int L, uint64_t n, uint64_t* bits,
+                                const uint64_t* lvl_off, int digits) {
+  const uint64_t gid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const uint64_t total = ((uint64_t)1 << L);  // sum over levels l < L of 2^l = 2^L - 1
+  if (gid >= total - 1) return;
+  // level l holds gids [2^l - 1, 2^{l+1} - 1)
+  const int l = 63 - __clzll(gid + 1);
+  const uint64_t q = gid + 1 - ((uint64_t)1 << l);
+  if (q == 0) return;
+  if (digits && (l & 1)) return;
+  const uint64_t s = C[q << (L - l)];
+  const uint64_t bp = digits ? 2 * s : s;
+  if ((bp & 63) && s < n) bits[lvl_off[digits ? l / 2 : l] + (bp >> 6)] = 0;
+}
+
+__global__ void k_zero_padding(uint64_t* bits, const uint64_t* lvl_off, const uint64_t* lvl_len,
+                               int nlev, int bpe) {
+  const int l = blockIdx.x;
+  if (l >= nlev) return;
+  const uint64_t used = (lvl_len[l] * bpe + 63) >> 6;
+  const uint64_t W = lvl_off[l + 1] - lvl_off[l];
+  for (uint64_t w = used + threadIdx.x; w < W; w += blockDim.x) bits[lvl_off[l] + w] = 0;
+}
+
+__global__ void k_reset_lookback(uint64_t* ring, uint32_t ring_slots, uint32_t* tickets,
+                                 uint32_t* abort_flag) {
+  for (uint32_t i = threadIdx.x; i < ring_slots; i += blockDim.x) ring[(uint64_t)i * SLOT_U64] = 0;
+  for (int g = threadIdx.x; g < 32; g += blockDim.x) tickets[g] = 0;
+  if (threadIdx.x == 0) *abort_flag = 0;
+}
+
+// Node-aligned tiles over T_a: node p spans [bnd[p*stride], bnd[(p+1)*stride]).
+__global__ void k_tiles_count(const uint64_t* bnd, uint64_t stride, uint64_t nn, uint32_t T,
+                              uint64_t* tcnt) {
+  const uint64_t p = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= nn) return;
+  const uint64_t sz = bnd[(p + 1) * stride] - bnd[p * stride];
+  tcnt[p] = (sz + T - 1) / T;
+}
+
+__global__ void k_tiles_write(const uint64_t* bnd, uint64_t stride, uint64_t nn, uint32_t T,
+                              uint64_t node_base, const uint64_t* toff, TileDesc* tiles,
+                              uint32_t* ntiles) {
+  const uint64_t p = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p == 0) *ntiles = (uint32_t)toff[nn];
+  if (p >= nn) return;
+  const uint64_t s = bnd[p * stride], e = bnd[(p + 1) * stride];
+  uint64_t o = toff[p];
+  for (uint64_t x = s; x < e; x += T, o++) {
+    TileDesc d;
+    d.start = x;
+    d.count = (uint32_t)std::min<uint64_t>(T, e - x);
+    d.node = (uint32_t)(node_base + p);
+    d.first = (x == s);
+    d.pad = 0;
+    tiles[o] = d;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// 3. pass launch
+// ---------------------------------------------------------------------------
+constexpr int PT = 8192, PNT = 256;
+
+template <typename E, bool DIG>
+static wt_status launch_pass_t(const PassParams& P, uint64_t max_tiles, const wt_build_opts* o,
+                               cudaStream_t st) {
+  using SM = PassSmem<E, PT, PNT, DIG>;
+  auto kern = k_pass<E, PT, PNT, DIG>;
+  static bool attr = false;
+  static int occ = 0;
+  if (!attr) {
+    CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM::bytes));
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, PNT, SM::bytes));
+    if (occ < 1) occ = 1;
+    attr = true;
+  }
+  int per_sm = occ;
+  if (o && o->ctas_per_sm) per_sm = std::min<int>(occ, (int)o->ctas_per_sm);
+  uint64_t grid = (uint64_t)num_sms() * per_sm;
+  if (grid > max_tiles) grid = std::max<uint64_t>(max_tiles, 1);
+  if (grid >= RING_SLOTS / 2) grid = RING_SLOTS / 2 - 1;
+  Prof& pf = prof();
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (pf.on) {
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    cudaEventRecord(e0, st);
+  }
+  kern<<<(unsigned)grid, PNT, SM::bytes, st>>>(P);
+  CK(cudaGetLastError());
+  count_launch();
+  if (pf.on) {
+    cudaEventRecord(e1, st);
+    pf.ev.push_back(e0);
+    pf.ev.push_back(e1);
+    pf.pass_launches++;
+  }
+  return WT_OK;
+}
+
+static wt_status launch_pass(const PassParams& P, bool wide, bool dig, uint64_t max_tiles,
+                             const wt_build_opts* o, cudaStream_t st) {
+  if (dig) return wide ? launch_pass_t<uint32_t, true>(P, max_tiles, o, st)
+                       : launch_pass_t<uint16_t, true>(P, max_tiles, o, st);
+  return wide ? launch_pass_t<uint32_t, false>(P, max_tiles, o, st)
+              : launch_pass_t<uint16_t, false>(P, max_tiles, o, st);
+}
+
+static int pick_tau(const wt_build_opts* o, int L, bool even) {
+  int tau = (o && o->tau) ? (int)o->tau : 8;
+  if (tau < 1) tau = 1;
+  if (tau > TAU_MAX) tau = TAU_MAX;
+  if (even && (tau & 1)) tau = tau > 1 ? tau - 1 : 2;
+  (void)L;
+  return tau;
+}
+
+// common workspace of a build
+struct Work {
+  cudaStream_t st;
+  std::vector<void*> bufs;
+  ~Work() {
+    for (void* p : bufs) dfree(p, st);
+  }
+  template <typename T>
+  wt_status get(T** p, size_t count) {
+    void* q = nullptr;
+    cudaError_t e = dmalloc(&q, count * sizeof(T), st);
+    if (e != cudaSuccess) return WT_ERR_NO_MEMORY;
+    bufs.push_back(q);
+    *p = (T*)q;
+    return WT_OK;
+  }
+};
+
+#define TRY(x)                     \
+  do {                             \
+    wt_status s_ = (x);            \
+    if (s_ != WT_OK) return s_;    \
+  } while (0)
+
+static wt_status alloc_outputs(wt_struct* h, uint64_t total_words) {
+  CK(dmalloc((void**)&h->d_bits, total_words * 8, h->stream));
+  h->d_bits_ro = h->d_bits;
+  CK(dmalloc((void**)&h->d_zeros, std::max<uint32_t>(h->levels, 1) * 8, h->stream));
+  CK(cudaMemsetAsync(h->d_zeros, 0, std::max<uint32_t>(h->levels, 1) * 8, h->stream));
+  return WT_OK;
+}
+
+static void set_uniform_levels(wt_struct* h, uint64_t elems_per_level) {
+  h->level_len.assign(h->levels, elems_per_level);
+  h->level_off.assign(h->levels + 1, 0);
+  for (uint32_t l = 0; l < h->levels; l++)
+    h->level_off[l + 1] = h->level_off[l] + level_words(elems_per_level * h->bpe);
+}
+
+static PassParams base_params(wt_struct* h, Work& wk, uint64_t* ring, uint32_t* tickets,
+                              const uint64_t* d_lvl_off, const uint64_t* d_lvl_len) {
+  PassParams P;
+  memset(&P, 0, sizeof(P));
+  P.bits = h->d_bits;
+  P.lvl_off = d_lvl_off;
+  P.lvl_len = d_lvl_len;
+  P.ring = ring;
+  P.ring_mask = RING_SLOTS - 1;
+  P.ticket = tickets;
+  P.err = h->d_err;
+  P.abort_flag = h->d_abort;
+  P.spin_limit = SPIN_LIMIT;
+  (void)wk;
+  return P;
+}
+
+// ---------------------------------------------------------------------------
+// wavelet matrix
+// ---------------------------------------------------------------------------
+wt_status build_wm(const void* d_seq, uint64_t n, uint32_t sigma, int w, const wt_build_opts* o,
+                   wt_struct* h) {
+  cudaStream_t st = h->stream;
+  const int L = (int)levels_of(sigma);
+  h->kind = WT_KIND_WM;
+  h->L = h->levels = (uint32_t)L;
+  h->bpe = 1;
+  set_uniform_levels(h, n);
+  const uint64_t W = level_words(n);
+  TRY(alloc_outputs(h, W * L));
+  Work wk{st, {}};
+  if (n == 0) return build_directories(h);
+  const int tau = pick_tau(o, L, false);
+  std::vector<PassGeom> ps = make_passes(L, tau, w);
+  const int G = (int)ps.size();
+  uint32_t T = PT;
+  uint64_t *hist, *cls, *ring, *d_off, *d_len;
+  uint32_t* tickets;
+  int nh = 0, ncls = 0;
+  for (auto& p : ps) {
+    nh += 1 << p.t;
+    ncls += (2 << p.t) + p.t + 1;
+  }
+  TRY(wk.get(&hist, nh));
+  TRY(wk.get(&cls, ncls));
+  TRY(wk.get(&ring, (size_t)RING_SLOTS * SLOT_U64));
+  TRY(wk.get(&tickets, 32));
+  TRY(wk.get(&d_off, L + 1));
+  TRY(wk.get(&d_len, L));
+  CK(cudaMemcpyAsync(d_off, h->level_off.data(), (L + 1) * 8, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(d_len, h->level_len.data(), L * 8, cudaMemcpyHostToDevice, st));
+  CK(cudaMemsetAsync(hist, 0, nh * 8, st));
+  {
+    const uint32_t blocks = std::min<uint64_t>(num_sms() * 4, (n + 8191) / 8192 + 1);
+    if (w == 1) k_hist_digits<1><<<blocks, 512, 0, st>>>(d_seq, n, sigma, L, tau, G, hist, h->d_err);
+    else if (w == 2) k_hist_digits<2><<<blocks, 512, 0, st>>>(d_seq, n, sigma, L, tau, G, hist, h->d_err);
+    else k_hist_digits<4><<<blocks, 512, 0, st>>>(d_seq, n, sigma, L, tau, G, hist, h->d_err);
+    count_launch();
+    CK(cudaGetLastError());
+  }
+  k_plan_wm<<<1, 1024, 0, st>>>(hist, n, L, tau, G, cls, h->d_zeros, h->d_bits, W, ring,
+                                RING_SLOTS, tickets, h->d_abort);
+  count_launch();
+  CK(cudaGetLastError());
+  // intermediate sequences
+  void* seqbuf[2] = {nullptr, nullptr};
+  for (int g = 0; g + 1 < G; g++) {
+    if (!seqbuf[g & 1]) {
+      uint8_t* b;
+      TRY(wk.get(&b, (size_t)n * 4));
+      seqbuf[g & 1] = b;
+    }
+  }
+  const void* in = d_seq;
+  int coff = 0;
+  const uint64_t ntiles = (n + T - 1) / T;
+  for (int g = 0; g < G; g++) {
+    const PassGeom& pg = ps[g];
+    PassParams P = base_params(h, wk, ring, tickets + g, d_off, d_len);
+    P.in = in;
+    P.in_w = pg.in_w;
+    P.out = (g + 1 < G) ? seqbuf[g & 1] : nullptr;
+    P.out_w = pg.out_w;
+    P.L = L;
+    P.a = pg.a;
+    P.t = pg.t;
+    P.rbits = pg.rbits;
+    P.shape = SHAPE_WM;
+    P.wm_cls = cls + coff;
+    P.ntiles = (uint32_t)ntiles;
+    P.n_in = n;
+    P.seq_base = g_seq.fetch_add(ntiles + 1);
+    TRY(launch_pass(P, pg.wide, false, ntiles, o, st));
+    coff += (2 << pg.t) + pg.t + 1;
+    in = P.out;
+  }
+  if (o && (o->flags & WT_FLAG_NO_DIRECTORY)) return WT_OK;
+  return build_directories(h);
+}
+
+// ---------------------------------------------------------------------------
+// balanced wavelet tree and its 4-ary variant
+// ---------------------------------------------------------------------------
+wt_status build_wt(const void* d_seq, uint64_t n, uint32_t sigma, int w, const wt_build_opts* o,
+                   wt_struct* h, bool multiary) {
+  cudaStream_t st = h->stream;
+  const int L = (int)levels_of(sigma);
+  if (L > 24) return WT_ERR_UNSUPPORTED;
+  h->kind = multiary ? WT_KIND_MULTI : WT_KIND_WT;
+  h->L = (uint32_t)L;
+  h->levels = multiary ? (uint32_t)((L + 1) / 2) : (uint32_t)L;
+  h->bpe = multiary ? 2 : 1;
+  set_uniform_levels(h, n);
+  TRY(alloc_outputs(h, h->level_off.back()));
+  Work wk{st, {}};
+  if (n == 0) return build_directories(h);
+  const int tau = pick_tau(o, L, multiary);
+  std::vector<PassGeom> ps = make_passes(L, tau, w);
+  const int G = (int)ps.size();
+  const uint32_t T = PT;
+  const uint64_t V = (uint64_t)1 << L;
+  uint64_t *hist, *C, *scr, *ring, *d_off, *d_len, *tcnt, *toff;
+  uint32_t *tickets, *d_ntiles;
+  TileDesc* tiles;
+  uint64_t max_nodes = (uint64_t)1 << ps.back().a;
+  const uint64_t max_tiles = (n + T - 1) / T + max_nodes + 1;
+  TRY(wk.get(&hist, V));
+  TRY(wk.get(&C, V + 1));
+  TRY(wk.get(&scr, scan_scratch(std::max(V, max_nodes))));
+  TRY(wk.get(&ring, (size_t)RING_SLOTS * SLOT_U64));
+  TRY(wk.get(&tickets, 32));
+  TRY(wk.get(&d_off, h->levels + 1));
+  TRY(wk.get(&d_len, h->levels));
+  TRY(wk.get(&tcnt, max_nodes));
+  TRY(wk.get(&toff, max_nodes + 1));
+  TRY(wk.get(&tiles, max_tiles));
+  TRY(wk.get(&d_ntiles, 1));
+  CK(cudaMemcpyAsync(d_off, h->level_off.data(), (h->levels + 1) * 8, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(d_len, h->level_len.data(), h->levels * 8, cudaMemcpyHostToDevice, st));
+  CK(cudaMemsetAsync(hist, 0, V * 8, st));
+  TRY(launch_hist_full(d_seq, w, n, sigma, hist, h->d_err, st));
+  TRY(scan_excl_u64(hist, C, V, scr, st));
+  if (!multiary) {
+    k_wt_zeros<<<L, 1024, 0, st>>>(C, L, h->d_zeros);
+    count_launch();
+    CK(cudaGetLastError());
+  }
+  {
+    const uint64_t tot = V - 1;
+    if (tot) {
+      k_wt_zero_words<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(C, L, n, h->d_bits, d_off,
+                                                                   multiary ? 1 : 0);
+  count_launch();
+      CK(cudaGetLastError());
+    }
+    k_zero_padding<<<h->levels, 256, 0, st>>>(h->d_bits, d_off, d_len, h->levels, h->bpe);
+    count_launch();
+    CK(cudaGetLastError());
+  }
+  k_reset_lookback<<<1, 1024, 0, st>>>(ring, RING_SLOTS, tickets, h->d_abort);
+  count_launch();
+  CK(cudaGetLastError());
+  void* seqbuf[2] = {nullptr, nullptr};
+  for (int g = 0; g + 1 < G; g++) {
+    if (!seqbuf[g & 1]) {
+      uint8_t* b;
+      TRY(wk.get(&b, (size_t)n * 4));
+      seqbuf[g & 1] = b;
+    }
+  }
+  const void* in = d_seq;
+  for (int g = 0; g < G; g++) {
+    const PassGeom& pg = ps[g];
+    const uint64_t nn = (uint64_t)1 << pg.a;
+    const uint64_t stride = (uint64_t)1 << (L - pg.a);
+    k_tiles_count<<<(unsigned)((nn + 255) / 256), 256, 0, st>>>(C, stride, nn, T, tcnt);
+    count_launch();
+    TRY(scan_excl_u64(tcnt, toff, nn, scr, st));
+    k_tiles_write<<<(unsigned)((nn + 255) / 256), 256, 0, st>>>(C, stride, nn, T, 0, toff, tiles,
+                                                               d_ntiles);
+  count_launch();
+    CK(cudaGetLastError());
+    PassParams P = base_params(h, wk, ring, tickets + g, d_off, d_len);
+    P.in = in;
+    P.in_w = pg.in_w;
+    P.out = (g + 1 < G) ? seqbuf[g & 1] : nullptr;
+    P.out_w = pg.out_w;
+    P.L = L;
+    P.a = pg.a;
+    P.t = pg.t;
+    P.rbits = pg.rbits;
+    P.shape = SHAPE_WT;
+    P.digits = multiary ? 1 : 0;
+    P.wt_C = C;
+    P.tiles = tiles;
+    P.ntiles_dev = d_ntiles;
+    P.n_in = n;
+    const uint64_t mt = (n + T - 1) / T + nn;
+    P.seq_base = g_seq.fetch_add(mt + 1);
+    TRY(launch_pass(P, pg.wide, multiary, mt, o, st));
+    in = P.out;
+  }
+  if (o && (o->flags & WT_FLAG_NO_DIRECTORY)) return WT_OK;
+  return build_directories(h);
+}
+
+// ---------------------------------------------------------------------------
+// Huffman-shaped wavelet tree
+// ---------------------------------------------------------------------------
+__global__ void k_clear_words(uint64_t* bits, const uint64_t* idx, uint64_t m) {
+  const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < m) bits[idx[i]] = 0;
+}
+
+uint32_t huffman_lengths(const uint64_t* hist, uint32_t sigma, uint32_t cap, uint8_t* len);
+void canonical_codes(const uint8_t* len, uint32_t sigma, uint32_t* code);
+
+wt_status build_huff(const void* d_seq, uint64_t n, uint32_t sigma, int w, const uint8_t* h_len,
+                     const wt_build_opts* o, wt_struct* h) {
+  cudaStream_t st = h->stream;
+  if (sigma > (1u << 24)) return WT_ERR_UNSUPPORTED;
+  h->kind = WT_KIND_HUFF;
+  h->bpe = 1;
+  Work wk{st, {}};
+  uint64_t* hist;
+  TRY(wk.get(&hist, sigma));
+  CK(cudaMemsetAsync(hist, 0, (size_t)sigma * 8, st));
+  TRY(launch_hist_full(d_seq, w, n, sigma, hist, h->d_err, st));
+  std::vector<uint64_t> hh(sigma);
+  uint32_t err = 0;
+  CK(cudaMemcpyAsync(hh.data(), hist, (size_t)sigma * 8, cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(&err, h->d_err, 4, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  if (err & ERR_SYMBOL) return WT_ERR_SYMBOL_GE_SIGMA;
+  h->code_len.assign(sigma, 0);
+  h->code.assign(sigma, 0);
+  uint32_t maxlen = 0;
+  if (h_len) {
+    // caller lengths: every present symbol needs a code, Kraft sum <= 1
+    double kraft = 0;
+    uint32_t present = 0;
+    for (uint32_t s = 0; s < sigma; s++) {
+      h->code_len[s] = h_len[s];
+      if (h_len[s] > 32) return WT_ERR_INVALID_ARG;
+      if (hh[s] && !h_len[s]) return WT_ERR_INVALID_ARG;
+      if (h_len[s]) {
+        kraft += std::ldexp(1.0, -(int)h_len[s]);
+        maxlen = std::max<uint32_t>(maxlen, h_len[s]);
+        present++;
+      }
+    }
+    if (kraft > 1.0 + 1e-12) return WT_ERR_INVALID_ARG;
+    (void)present;
+  } else {
+    maxlen = huffman_lengths(hh.data(), sigma, 32, h->code_len.data());
+  }
+  canonical_codes(h->code_len.data(), sigma, h->code.data());
+  h->max_code_len = maxlen;
+  const int Lm = (int)maxlen;
+  h->L = h->levels = (uint32_t)Lm;
+  // symbols in canonical order (= order of the left-aligned codewords)
+  std::vector<uint32_t> order;
+  for (uint32_t ln = 1; ln <= 32; ln++)
+    for (uint32_t s = 0; s < sigma; s++)
+      if (h->code_len[s] == ln) order.push_back(s);
+  // level sizes, internal nodes of every level and their start positions
+  h->level_len.assign(Lm, 0);
+  std::vector<uint64_t> node, node_lvl(3 * (size_t)std::max(Lm, 1), 0);
+  for (int l = 0; l < Lm; l++) {
+    node_lvl[3 * l] = node.size();
+    uint64_t pos = 0;
+    bool any = false;
+    uint64_t firstq = 0, lastq = 0;
+    for (uint32_t s : order) {
+      if (h->code_len[s] <= (uint32_t)l) continue;
+      const uint64_t q = l == 0 ? 0 : ((uint64_t)h->code[s] >> (h->code_len[s] - l));
+      if (!any) {
+        firstq = lastq = q;
+        node.push_back(pos);
+        any = true;
+      }
+      while (lastq < q) {  // consecutive prefixes (empty ones for incomplete codes)
+        lastq++;
+        node.push_back(pos);
+      }
+      pos += hh[s];
+    }
+    node.push_back(pos);  // sentinel = level length
+    h->level_len[l] = pos;
+    node_lvl[3 * l + 1] = firstq;
+    node_lvl[3 * l + 2] = any ? lastq - firstq + 1 : 0;
+  }
+  h->level_off.assign(Lm + 1, 0);
+  for (int l = 0; l < Lm; l++) h->level_off[l + 1] = h->level_off[l] + level_words(h->level_len[l]);
+  TRY(alloc_outputs(h, std::max<uint64_t>(h->level_off.back(), 1)));
+  // zero counts per level (host): elements whose code bit l is 0
+  {
+    std::vector<uint64_t> z(std::max(Lm, 1), 0);
+    for (uint32_t s = 0; s < sigma; s++)
+      for (uint32_t l = 0; l < h->code_len[s]; l++)
+        if (!((h->code[s] >> (h->code_len[s] - 1 - l)) & 1u)) z[l] += hh[s];
+    h->zeros.assign(z.begin(), z.begin() + Lm);
+    if (Lm) CK(cudaMemcpyAsync(h->d_zeros, h->zeros.data(), Lm * 8, cudaMemcpyHostToDevice, st));
+    h->zeros_valid = true;
+  }
+  // device tables
+  std::vector<uint32_t> left(sigma);
+  for (uint32_t s = 0; s < sigma; s++)
+    left[s] = h->code_len[s] ? (uint32_t)((uint64_t)h->code[s] << (Lm - h->code_len[s])) : 0;
+  std::vector<uint64_t> lentab(3 * 34, 0);
+  {
+    uint64_t idx = 0;
+    for (uint32_t ln = 1; ln <= 32; ln++) {
+      lentab[34 + ln] = idx;
+      bool f = true;
+      for (uint32_t s : order)
+        if (h->code_len[s] == ln) {
+          if (f) { lentab[ln] = h->code[s]; f = false; }
+          lentab[68 + ln]++;
+        }
+      idx += lentab[68 + ln];
+    }
+  }
+  CK(dmalloc((void**)&h->d_code, (size_t)sigma * 4, st));
+  CK(dmalloc((void**)&h->d_len, sigma, st));
+  CK(dmalloc((void**)&h->d_sym_by_rank, std::max<size_t>(order.size(), 1) * 4, st));
+  CK(dmalloc((void**)&h->d_len_tab, lentab.size() * 8, st));
+  CK(dmalloc((void**)&h->d_node, std::max<size_t>(node.size(), 1) * 8, st));
+  CK(dmalloc((void**)&h->d_node_lvl, node_lvl.size() * 8, st));
+  uint32_t* d_left;
+  TRY(wk.get(&d_left, sigma));
+  CK(cudaMemcpyAsync(h->d_code, h->code.data(), (size_t)sigma * 4, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(h->d_len, h->code_len.data(), sigma, cudaMemcpyHostToDevice, st));
+  if (!order.empty())
+    CK(cudaMemcpyAsync(h->d_sym_by_rank, order.data(), order.size() * 4, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(h->d_len_tab, lentab.data(), lentab.size() * 8, cudaMemcpyHostToDevice, st));
+  if (!node.empty())
+    CK(cudaMemcpyAsync(h->d_node, node.data(), node.size() * 8, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(h->d_node_lvl, node_lvl.data(), node_lvl.size() * 8, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(d_left, left.data(), (size_t)sigma * 4, cudaMemcpyHostToDevice, st));
+  CK(cudaStreamSynchronize(st));  // host vectors above are pageable and local
+  if (n == 0 || Lm == 0) return build_directories(h);
+  // the pass kernel wants hf_lvl as [off, first] pairs plus the count; use a
+  // 3-wide table and read [3l], [3l+1], [3l+2]
+  const int tau = pick_tau(o, Lm, false);
+  std::vector<PassGeom> ps = make_passes(Lm, tau, 4);
+  const int G = (int)ps.size();
+  const uint32_t T = PT;
+  uint64_t *ring, *d_off, *d_len, *scr, *tcnt, *toff;
+  uint32_t *tickets, *d_ntiles;
+  TileDesc* tiles;
+  uint64_t max_nodes = 1;
+  for (int l = 0; l < Lm; l++) max_nodes = std::max<uint64_t>(max_nodes, node_lvl[3 * l + 2]);
+  const uint64_t max_tiles = (n + T - 1) / T + max_nodes + 1;
+  TRY(wk.get(&ring, (size_t)RING_SLOTS * SLOT_U64));
+  TRY(wk.get(&tickets, 32));
+  TRY(wk.get(&d_off, Lm + 1));
+  TRY(wk.get(&d_len, Lm));
+  TRY(wk.get(&scr, scan_scratch(max_nodes)));
+  TRY(wk.get(&tcnt, max_nodes));
+  TRY(wk.get(&toff, max_nodes + 1));
+  TRY(wk.get(&tiles, max_tiles));
+  TRY(wk.get(&d_ntiles, 1));
+  CK(cudaMemcpyAsync(d_off, h->level_off.data(), (Lm + 1) * 8, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(d_len, h->level_len.data(), Lm * 8, cudaMemcpyHostToDevice, st));
+  // zero words holding a node start, and padding
+  {
+    std::vector<uint64_t> zw;
+    for (int l = 0; l < Lm; l++) {
+      const uint64_t off = node_lvl[3 * l], cnt = node_lvl[3 * l + 2];
+      for (uint64_t i = 1; i < cnt; i++) {
+        const uint64_t s = node[off + i];
+        if ((s & 63) && s < h->level_len[l]) zw.push_back(h->level_off[l] + (s >> 6));
+      }
+    }
+    if (!zw.empty()) {
+      std::sort(zw.begin(), zw.end());
+      zw.erase(std::unique(zw.begin(), zw.end()), zw.end());
+      // scatter zeros: upload the word list and clear on device
+      uint64_t* d_zw;
+      TRY(wk.get(&d_zw, zw.size()));
+      CK(cudaMemcpyAsync(d_zw, zw.data(), zw.size() * 8, cudaMemcpyHostToDevice, st));
+      k_clear_words<<<(unsigned)((zw.size() + 255) / 256), 256, 0, st>>>(h->d_bits, d_zw, zw.size());
+      count_launch();
+      CK(cudaGetLastError());
+      CK(cudaStreamSynchronize(st));
+    }
+    k_zero_padding<<<Lm, 256, 0, st>>>(h->d_bits, d_off, d_len, Lm, 1);
+    count_launch();
+    CK(cudaGetLastError());
+  }
+  k_reset_lookback<<<1, 1024, 0, st>>>(ring, RING_SLOTS, tickets, h->d_abort);
+  count_launch();
+  CK(cudaGetLastError());
+  void* seqbuf[2] = {nullptr, nullptr};
+  for (int g = 0; g + 1 < G; g++) {
+    if (!seqbuf[g & 1]) {
+      uint8_t* b;
+      TRY(wk.get(&b, (size_t)n * 4));
+      seqbuf[g & 1] = b;
+    }
+  }
+  const void* in = d_seq;
+  for (int g = 0; g < G; g++) {
+    const PassGeom& pg = ps[g];
+    const uint64_t nn = node_lvl[3 * pg.a + 2];
+    if (nn) {
+      const uint64_t* bnd = h->d_node + node_lvl[3 * pg.a];
+      k_tiles_count<<<(unsigned)((nn + 255) / 256), 256, 0, st>>>(bnd, 1, nn, T, tcnt);
+      count_launch();
+      TRY(scan_excl_u64(tcnt, toff, nn, scr, st));
+      k_tiles_write<<<(unsigned)((nn + 255) / 256), 256, 0, st>>>(bnd, 1, nn, T, node_lvl[3 * pg.a + 1],
+                                                                 toff, tiles, d_ntiles);
+  count_launch();
+    } else {
+      CK(cudaMemsetAsync(d_ntiles, 0, 4, st));
+    }
+    CK(cudaGetLastError());
+    PassParams P = base_params(h, wk, ring, tickets + g, d_off, d_len);
+    P.in = in;
+    P.in_w = g == 0 ? w : pg.in_w;
+    P.code_map = g == 0 ? d_left : nullptr;
+    P.out = (g + 1 < G) ? seqbuf[g & 1] : nullptr;
+    P.out_w = pg.out_w;
+    P.L = Lm;
+    P.a = pg.a;
+    P.t = pg.t;
+    P.rbits = pg.rbits;
+    P.shape = SHAPE_HUFF;
+    P.hf_node = h->d_node;
+    P.hf_lvl = h->d_node_lvl;
+    P.tiles = tiles;
+    P.ntiles_dev = d_ntiles;
+    P.n_in = h->level_len[pg.a];
+    const uint64_t mt = (P.n_in + T - 1) / T + nn;
+    P.seq_base = g_seq.fetch_add(mt + 1);
+    TRY(launch_pass(P, pg.wide, false, mt, o, st));
+    in = P.out;
+  }
+  if (o && (o->flags & WT_FLAG_NO_DIRECTORY)) return WT_OK;
+  return build_directories(h);
+}
+
+
+}  // namespace wtk
+
+namespace wtk {
+wt_status scan_excl_u64_pub(const uint64_t* in, uint64_t* out, uint64_t n, uint64_t* scratch,
+                            cudaStream_t st) {
+  return scan_excl_u64(in, out, n, scratch, st);
+}
+uint64_t scan_scratch_pub(uint64_t n) { return scan_scratch(n); }
+}  // namespace wtk

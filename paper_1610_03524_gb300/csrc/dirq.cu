@@ -1,0 +1,746 @@
+// dirq.cu -- rank/select directories on every level (Section 5) and the
+// batched query kernels (access / rank / select, Section 2 definitions).
+//
+// Binary levels (Section 5.1, rank of 0 only, Jacobson-style two-level
+// counts): one 16-byte record per 2048-bit superblock, {u64 zeros before the
+// superblock, 4 x u16 zeros before each 512-bit block inside it}, plus a
+// trailing record with the level total.  Select (Section 5.1, positions of
+// every k-th bit kept, here k = 4096): the position of the occurrence with
+// 0-based index 4096k of each bit value; a query starts at the sample and
+// searches superblocks, blocks, words, then the bit inside the word.
+// Digit levels of the 4-ary tree (Section 5.2, per-value counts): one
+// 64-byte record per 1024 digits, {4 x u64 counts of each value before the
+// superblock, 4 blocks x 4 values u16 counts inside it}.
+#include <algorithm>
+#include <cstdio>
+#include <vector>
+
+#include "wt_host.h"
+#include "wt_internal.cuh"
+
+namespace wtk {
+
+constexpr uint64_t NONE = ~0ull;
+
+#define CK(x)                                                   \
+  do {                                                          \
+    cudaError_t e_ = (x);                                       \
+    if (e_ != cudaSuccess) {                                    \
+      fprintf(stderr, "wavelet: %s -> %s\n", #x, cudaGetErrorString(e_)); \
+      return e_ == cudaErrorMemoryAllocation ? WT_ERR_NO_MEMORY : WT_ERR_CUDA; \
+    }                                                           \
+  } while (0)
+
+// exclusive u64 scan from build.cu
+wt_status scan_excl_u64_pub(const uint64_t* in, uint64_t* out, uint64_t n, uint64_t* scratch,
+                            cudaStream_t st);
+uint64_t scan_scratch_pub(uint64_t n);
+
+__device__ __forceinline__ int find_level(const uint64_t* first, int nlev, uint64_t g) {
+  int l = 0;
+  while (l + 1 < nlev && first[l + 1] <= g) l++;
+  return l;
+}
+
+// r-th (0-based) set bit of v
+__device__ __forceinline__ uint32_t sel64(uint64_t v, uint32_t r) {
+  const uint32_t lo = (uint32_t)v, hi = (uint32_t)(v >> 32);
+  const uint32_t pl = __popc(lo);
+  if (r < pl) return __fns(lo, 0, (int)r + 1);
+  return 32 + __fns(hi, 0, (int)(r - pl) + 1);
+}
+
+// ---------------------------------------------------------------------------
+// binary directories
+// ---------------------------------------------------------------------------
+__global__ void k_dir_count(const uint64_t* bits, const LevelMeta* meta, int nlev,
+                            const uint64_t* sb_first, uint64_t total_sb, uint64_t* dir,
+                            uint64_t* sbz) {
+  const int lane = threadIdx.x & 31;
+  const uint64_t gw = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+  for (uint64_t g = gw; g < total_sb; g += nw) {
+    const int l = find_level(sb_first, nlev, g);
+    const LevelMeta m = meta[l];
+    const uint64_t s = g - sb_first[l];
+    const int64_t rem = (int64_t)m.n - (int64_t)(2048 * s + 64 * (uint64_t)lane);
+    const int valid = rem <= 0 ? 0 : (rem >= 64 ? 64 : (int)rem);
+    // words past the last valid bit are not read (a caller bitvector may end there)
+    const uint64_t w = valid ? __ldcs(bits + m.bit_off + 32 * s + lane) : 0ull;
+    const int z = valid - __popcll(w);
+    int zi = z;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(FULL, zi, o);
+      if (lane >= o) zi += y;
+    }
+    const uint64_t r1 = (uint64_t)__shfl_sync(FULL, zi, 7);
+    const uint64_t r2 = (uint64_t)__shfl_sync(FULL, zi, 15);
+    const uint64_t r3 = (uint64_t)__shfl_sync(FULL, zi, 23);
+    if (lane == 0) dir[m.dir_off + 2 * s + 1] = (r1 << 16) | (r2 << 32) | (r3 << 48);
+    if (lane == 31) sbz[g] = (uint64_t)zi;
+  }
+}
+
+__global__ void k_dir_finish(const LevelMeta* meta, int nlev, const uint64_t* sb_first,
+                             uint64_t total_sb, const uint64_t* sbx, uint64_t* dir,
+                             uint64_t* zeros, int write_zeros) {
+  const uint64_t g = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g < total_sb) {
+    const int l = find_level(sb_first, nlev, g);
+    const uint64_t s = g - sb_first[l];
+    dir[meta[l].dir_off + 2 * s] = sbx[g] - sbx[sb_first[l]];
+  } else if (g < total_sb + nlev) {
+    const int l = (int)(g - total_sb);
+    const LevelMeta m = meta[l];
+    const uint64_t tot = sbx[sb_first[l + 1]] - sbx[sb_first[l]];
+    dir[m.dir_off + 2 * m.nsb] = tot;
+    dir[m.dir_off + 2 * m.nsb + 1] = 0;
+    if (write_zeros) zeros[l] = tot;
+  }
+}
+
+// position (inside superblock s, relative to its start) of the r-th
+// (0-based) bit equal to bv
+__device__ uint32_t find_in_sb(const uint64_t* lbits, const uint64_t* ldir, uint64_t s, int bv,
+                               uint32_t r) {
+  const uint64_t rel = ldir[2 * s + 1];
+  int b = 3;
+  for (; b > 0; b--) {
+    const uint32_t z = (uint32_t)((rel >> (16 * b)) & 0xffffu);
+    const uint32_t before = bv ? 512u * b - z : z;
+    if (before <= r) break;
+  }
+  const uint32_t z = b ? (uint32_t)((rel >> (16 * b)) & 0xffffu) : 0u;
+  r -= bv ? 512u * b - z : z;
+  // the target lies in this superblock, so at most 32 words are visited
+  for (uint64_t w = 32 * s + 8 * b; w < 32 * s + 32; w++) {
+    const uint64_t v = lbits[w];
+    const uint32_t c = bv ? __popcll(v) : 64 - __popcll(v);
+    if (c > r) return (uint32_t)((w - 32 * s) * 64) + sel64(bv ? v : ~v, r);
+    r -= c;
+  }
+  return 2047;
+}
+
+__global__ void k_select_samples(const uint64_t* bits, const LevelMeta* meta, int nlev,
+                                 const uint64_t* sb_first, uint64_t total_sb,
+                                 const uint64_t* dir, uint64_t* samp) {
+  const uint64_t g = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= total_sb) return;
+  const int l = find_level(sb_first, nlev, g);
+  const LevelMeta m = meta[l];
+  const uint64_t s = g - sb_first[l];
+  const uint64_t* ld = dir + m.dir_off;
+  const uint64_t* lb = bits + m.bit_off;
+  const uint64_t zb = ld[2 * s], ze = ld[2 * s + 2];
+  const uint64_t zs = ze - zb;
+  const uint64_t nvalid = std::min<uint64_t>(2048, m.n - 2048 * s);
+  const uint64_t ob = 2048 * s - zb, os = nvalid - zs;
+  const uint64_t k0 = (zb + 4095) / 4096;
+  if (4096 * k0 < zb + zs)
+    samp[m.s0_off + k0] = 2048 * s + find_in_sb(lb, ld, s, 0, (uint32_t)(4096 * k0 - zb));
+  const uint64_t k1 = (ob + 4095) / 4096;
+  if (4096 * k1 < ob + os)
+    samp[m.s1_off + k1] = 2048 * s + find_in_sb(lb, ld, s, 1, (uint32_t)(4096 * k1 - ob));
+}
+
+// ---------------------------------------------------------------------------
+// digit-level (4-ary) directories
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint64_t digit_match(uint64_t w, uint32_t d) {
+  const uint64_t x = w ^ (0x5555555555555555ull * d);
+  return ~(x | (x >> 1)) & 0x5555555555555555ull;
+}
+
+__global__ void k_mdir_count(const uint64_t* bits, const LevelMeta* meta, int nlev,
+                             const uint64_t* sb_first, uint64_t total_sb, uint64_t* dir,
+                             uint64_t* sbz /* 4 x total_sb */) {
+  const int lane = threadIdx.x & 31;
+  const uint64_t gw = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+  for (uint64_t g = gw; g < total_sb; g += nw) {
+    const int l = find_level(sb_first, nlev, g);
+    const LevelMeta m = meta[l];
+    const uint64_t s = g - sb_first[l];
+    const int64_t rem = (int64_t)m.n - (int64_t)(1024 * s + 32 * (uint64_t)lane);
+    const int valid = rem <= 0 ? 0 : (rem >= 32 ? 32 : (int)rem);
+    const uint64_t w = valid ? bits[m.bit_off + 32 * s + lane] : 0ull;
+    const uint64_t vm = valid == 32 ? ~0ull : ((1ull << (2 * valid)) - 1ull);
+    uint64_t packed[4];
+#pragma unroll
+    for (int d = 0; d < 4; d++) {
+      int c = __popcll(digit_match(w, d) & vm);
+      int ci = c;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(FULL, ci, o);
+        if (lane >= o) ci += y;
+      }
+      const uint64_t r1 = (uint64_t)__shfl_sync(FULL, ci, 7);
+      const uint64_t r2 = (uint64_t)__shfl_sync(FULL, ci, 15);
+      const uint64_t r3 = (uint64_t)__shfl_sync(FULL, ci, 23);
+      packed[d] = (r1 << 16) | (r2 << 32) | (r3 << 48);  // rel of blocks 1..3 for value d
+      if (lane == 31) sbz[(uint64_t)d * total_sb + g] = (uint64_t)ci;
+    }
+    if (lane < 4) {
+      // record word 4+b holds the four values' counts of block b
+      const int b = lane;
+      uint64_t v = 0;
+#pragma unroll
+      for (int d = 0; d < 4; d++) v |= ((packed[d] >> (16 * b)) & 0xffffull) << (16 * d);
+      dir[m.dir_off + 8 * s + 4 + b] = v;
+    }
+  }
+}
+
+__global__ void k_mdir_finish(const LevelMeta* meta, int nlev, const uint64_t* sb_first,
+                              uint64_t total_sb, const uint64_t* sbx /* 4 x (total_sb+1) */,
+                              uint64_t* dir) {
+  const uint64_t g = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g < total_sb) {
+    const int l = find_level(sb_first, nlev, g);
+    const uint64_t s = g - sb_first[l];
+    for (int d = 0; d < 4; d++) {
+      const uint64_t* x = sbx + (uint64_t)d * (total_sb + 1);
+      dir[meta[l].dir_off + 8 * s + d] = x[g] - x[sb_first[l]];
+    }
+  } else if (g < total_sb + nlev) {
+    const int l = (int)(g - total_sb);
+    const LevelMeta m = meta[l];
+    for (int d = 0; d < 4; d++) {
+      const uint64_t* x = sbx + (uint64_t)d * (total_sb + 1);
+      dir[m.dir_off + 8 * m.nsb + d] = x[sb_first[l + 1]] - x[sb_first[l]];
+      dir[m.dir_off + 8 * m.nsb + 4 + d] = 0;
+    }
+  }
+}
+
+wt_status upload_meta(wt_struct* h) {
+  const size_t nb = std::max<size_t>(h->meta.size(), 1) * sizeof(LevelMeta);
+  if (!h->d_meta) CK(dmalloc((void**)&h->d_meta, nb, h->stream));
+  if (!h->meta.empty())
+    CK(cudaMemcpyAsync(h->d_meta, h->meta.data(), h->meta.size() * sizeof(LevelMeta),
+                       cudaMemcpyHostToDevice, h->stream));
+  return WT_OK;
+}
+
+wt_status build_directories(wt_struct* h) {
+  cudaStream_t st = h->stream;
+  const uint32_t nlev = h->levels;
+  const bool dig = h->bpe == 2;
+  const uint64_t sbsz = dig ? 1024 : 2048;
+  const uint64_t rec = dig ? 8 : 2;
+  h->meta.assign(nlev, LevelMeta{});
+  h->dir_off.assign(nlev + 1, 0);
+  h->samp_off.assign(2 * nlev + 1, 0);
+  std::vector<uint64_t> sb_first(nlev + 1, 0);
+  for (uint32_t l = 0; l < nlev; l++) {
+    LevelMeta& m = h->meta[l];
+    m.bit_off = h->level_off[l];
+    m.n = h->level_len[l];
+    m.nsb = (m.n + sbsz - 1) / sbsz;
+    m.dir_off = h->dir_off[l];
+    h->dir_off[l + 1] = h->dir_off[l] + rec * (m.nsb + 1);
+    sb_first[l + 1] = sb_first[l] + m.nsb;
+    const uint64_t cap = dig ? 0 : m.n / 4096 + 1;
+    m.s0_off = h->samp_off[2 * l];
+    h->samp_off[2 * l + 1] = m.s0_off + cap;
+    m.s1_off = h->samp_off[2 * l + 1];
+    h->samp_off[2 * l + 2] = m.s1_off + cap;
+  }
+  const uint64_t total_sb = sb_first[nlev];
+  CK(dmalloc((void**)&h->d_dir, std::max<uint64_t>(h->dir_off[nlev], 1) * 8, st));
+  CK(dmalloc((void**)&h->d_samp, std::max<uint64_t>(h->samp_off[2 * nlev], 1) * 8, st));
+  wt_status s = upload_meta(h);
+  if (s != WT_OK) return s;
+  if (nlev == 0) return WT_OK;
+  uint64_t *d_first, *sbz, *sbx, *scr;
+  const int nval = dig ? 4 : 1;
+  CK(dmalloc((void**)&d_first, (nlev + 1) * 8, st));
+  CK(dmalloc((void**)&sbz, std::max<uint64_t>(total_sb, 1) * 8 * nval, st));
+  CK(dmalloc((void**)&sbx, (total_sb + 1) * 8 * nval, st));
+  CK(dmalloc((void**)&scr, scan_scratch_pub(total_sb) * 8, st));
+  CK(cudaMemcpyAsync(d_first, sb_first.data(), (nlev + 1) * 8, cudaMemcpyHostToDevice, st));
+  const unsigned cgrid = (unsigned)std::min<uint64_t>((total_sb * 32 + 255) / 256 + 1,
+                                                       (uint64_t)num_sms() * 16);
+  const unsigned fgrid = (unsigned)((total_sb + nlev + 255) / 256);
+  if (!dig) {
+    if (total_sb) {
+      k_dir_count<<<cgrid, 256, 0, st>>>(h->d_bits_ro, h->d_meta, nlev, d_first, total_sb,
+                                         h->d_dir, sbz);
+      count_launch();
+    }
+    s = scan_excl_u64_pub(sbz, sbx, total_sb, scr, st);
+    if (s == WT_OK) {
+      k_dir_finish<<<fgrid, 256, 0, st>>>(h->d_meta, nlev, d_first, total_sb, sbx, h->d_dir,
+                                          h->d_zeros, h->kind == WT_KIND_RS ? 1 : 0);
+      count_launch();
+      if (total_sb) {
+        k_select_samples<<<(unsigned)((total_sb + 255) / 256), 256, 0, st>>>(
+            h->d_bits_ro, h->d_meta, nlev, d_first, total_sb, h->d_dir, h->d_samp);
+        count_launch();
+      }
+    }
+  } else {
+    if (total_sb) {
+      k_mdir_count<<<cgrid, 256, 0, st>>>(h->d_bits_ro, h->d_meta, nlev, d_first, total_sb,
+                                          h->d_dir, sbz);
+      count_launch();
+    }
+    for (int d = 0; d < 4 && s == WT_OK; d++)
+      s = scan_excl_u64_pub(sbz + (uint64_t)d * total_sb, sbx + (uint64_t)d * (total_sb + 1),
+                            total_sb, scr, st);
+    if (s == WT_OK) {
+      k_mdir_finish<<<fgrid, 256, 0, st>>>(h->d_meta, nlev, d_first, total_sb, sbx, h->d_dir);
+      count_launch();
+    }
+  }
+  cudaError_t e = cudaGetLastError();
+  dfree(d_first, st);
+  dfree(sbz, st);
+  dfree(sbx, st);
+  dfree(scr, st);
+  if (s != WT_OK) return s;
+  if (e != cudaSuccess) return WT_ERR_CUDA;
+  return WT_OK;
+}
+
+// ---------------------------------------------------------------------------
+// queries
+// ---------------------------------------------------------------------------
+struct QStruct {
+  int kind;
+  uint64_t n;
+  uint32_t sigma;
+  int L;        // binary levels (HUFF: max code length)
+  int levels;   // output levels
+  const uint64_t* bits;
+  const uint64_t* dir;
+  const uint64_t* samp;
+  const LevelMeta* meta;
+  const uint64_t* zeros;
+  HuffQuery hq;
+};
+
+struct BinLevel {
+  const uint64_t* bits;
+  const uint64_t* dir;
+  const uint64_t* s0;
+  const uint64_t* s1;
+  uint64_t n, nsb, zeros;
+};
+
+__device__ __forceinline__ BinLevel bin_level(const QStruct& S, int l) {
+  const LevelMeta m = S.meta[l];
+  BinLevel v;
+  v.bits = S.bits + m.bit_off;
+  v.dir = S.dir + m.dir_off;
+  v.s0 = S.samp + m.s0_off;
+  v.s1 = S.samp + m.s1_off;
+  v.n = m.n;
+  v.nsb = m.nsb;
+  v.zeros = S.zeros[l];
+  return v;
+}
+
+__device__ __forceinline__ int get_bit(const BinLevel& v, uint64_t i) {
+  return (int)((v.bits[i >> 6] >> (i & 63)) & 1ull);
+}
+
+// zeros in [0, x), x <= n
+__device__ uint64_t rank0(const BinLevel& v, uint64_t x) {
+  const uint64_t s = x >> 11;
+  const uint32_t b = (uint32_t)((x >> 9) & 3);
+  uint64_t r = v.dir[2 * s] + ((v.dir[2 * s + 1] >> (16 * b)) & 0xffffull);
+  const uint64_t wend = x >> 6;
+  for (uint64_t w = 32 * s + 8 * b; w < wend; w++) r += 64 - __popcll(v.bits[w]);
+  const uint32_t rem = (uint32_t)(x & 63);
+  if (rem) r += rem - __popcll(v.bits[wend] & ((1ull << rem) - 1ull));
+  return r;
+}
+__device__ __forceinline__ uint64_t rank1(const BinLevel& v, uint64_t x) { return x - rank0(v, x); }
+
+// position of the k-th (0-based) bit equal to bv; k < count
+__device__ uint64_t select_b(const BinLevel& v, int bv, uint64_t k) {
+  const uint64_t* samp = bv ? v.s1 : v.s0;
+  const uint64_t cnt = bv ? v.n - v.zeros : v.zeros;
+  const uint64_t ns = (cnt + 4095) / 4096;
+  const uint64_t idx = k >> 12;
+  uint64_t lo = samp[idx] >> 11;
+  uint64_t hi = (idx + 1 < ns) ? (samp[idx + 1] >> 11) : v.nsb - 1;
+  auto before = [&](uint64_t s) -> uint64_t {
+    const uint64_t z = v.dir[2 * s];
+    return bv ? 2048 * s - z : z;
+  };
+  while (lo < hi) {
+    const uint64_t mid = (lo + hi + 1) >> 1;
+    if (before(mid) <= k) lo = mid;
+    else hi = mid - 1;
+  }
+  return 2048 * lo + find_in_sb(v.bits, v.dir, lo, bv, (uint32_t)(k - before(lo)));
+}
+
+
+__device__ uint64_t q_wm(const QStruct& S, int op, uint32_t c, uint64_t x) {
+  const int L = S.L;
+  if (op == 0) {
+    if (x >= S.n) return NONE;
+    uint64_t pos = x, sym = 0;
+    for (int l = 0; l < L; l++) {
+      const BinLevel v = bin_level(S, l);
+      const int b = get_bit(v, pos);
+      sym = (sym << 1) | (uint64_t)b;
+      pos = b ? v.zeros + rank1(v, pos) : rank0(v, pos);
+    }
+    return sym;
+  }
+  if (c >= S.sigma) return NONE;
+  if (op == 1) {
+    if (x >= S.n) return NONE;
+    uint64_t s = 0, j = x + 1;
+    for (int l = 0; l < L; l++) {
+      const BinLevel v = bin_level(S, l);
+      const int b = (c >> (L - 1 - l)) & 1;
+      if (b) { s = v.zeros + rank1(v, s); j = v.zeros + rank1(v, j); }
+      else { s = rank0(v, s); j = rank0(v, j); }
+    }
+    return j - s;
+  }
+  if (x == 0) return NONE;
+  uint64_t s = 0, e = S.n;
+  for (int l = 0; l < L; l++) {
+    const BinLevel v = bin_level(S, l);
+    const int b = (c >> (L - 1 - l)) & 1;
+    if (b) { s = v.zeros + rank1(v, s); e = v.zeros + rank1(v, e); }
+    else { s = rank0(v, s); e = rank0(v, e); }
+  }
+  if (x > e - s) return NONE;
+  uint64_t pos = s + x - 1;
+  for (int l = L - 1; l >= 0; l--) {
+    const BinLevel v = bin_level(S, l);
+    const int b = (c >> (L - 1 - l)) & 1;
+    pos = b ? select_b(v, 1, pos - v.zeros) : select_b(v, 0, pos);
+  }
+  return pos;
+}
+
+__device__ uint64_t q_wt(const QStruct& S, int op, uint32_t c, uint64_t x) {
+  const int L = S.L;
+  if (op == 0) {
+    if (x >= S.n) return NONE;
+    uint64_t s = 0, e = S.n, pos = x, sym = 0;
+    for (int l = 0; l < L; l++) {
+      const BinLevel v = bin_level(S, l);
+      const uint64_t zs = rank0(v, s), zp = rank0(v, pos), ze = rank0(v, e);
+      const int b = get_bit(v, pos);
+      sym = (sym << 1) | (uint64_t)b;
+      if (!b) { pos = s + (zp - zs); e = s + (ze - zs); }
+      else { pos = s + (ze - zs) + (pos - s) - (zp - zs); s = s + (ze - zs); }
+    }
+    return sym;
+  }
+  if (c >= S.sigma) return NONE;
+  if (op == 1) {
+    if (x >= S.n) return NONE;
+    uint64_t s = 0, e = S.n, j = x + 1;
+    for (int l = 0; l < L; l++) {
+      const BinLevel v = bin_level(S, l);
+      const uint64_t zs = rank0(v, s), zj = rank0(v, j), ze = rank0(v, e);
+      const int b = (c >> (L - 1 - l)) & 1;
+      if (!b) { j = s + (zj - zs); e = s + (ze - zs); }
+      else { j = s + (ze - zs) + (j - s) - (zj - zs); s = s + (ze - zs); }
+    }
+    return j - s;
+  }
+  if (x == 0) return NONE;
+  uint64_t S0[33];
+  uint64_t s = 0, e = S.n;
+  for (int l = 0; l < L; l++) {
+    S0[l] = s;
+    const BinLevel v = bin_level(S, l);
+    const uint64_t zs = rank0(v, s), ze = rank0(v, e);
+    const int b = (c >> (L - 1 - l)) & 1;
+    if (!b) e = s + (ze - zs);
+    else s = s + (ze - zs);
+  }
+  S0[L] = s;
+  if (x > e - s) return NONE;
+  uint64_t pos = s + x - 1;
+  for (int l = L - 1; l >= 0; l--) {
+    const BinLevel v = bin_level(S, l);
+    const int b = (c >> (L - 1 - l)) & 1;
+    const uint64_t off = pos - S0[l + 1];
+    const uint64_t zs = rank0(v, S0[l]);
+    pos = b ? select_b(v, 1, (S0[l] - zs) + off) : select_b(v, 0, zs + off);
+  }
+  return pos;
+}
+
+// Huffman-shaped tree: node (level l, prefix q) -> [start, end) on level l
+__device__ __forceinline__ bool huff_node(const QStruct& S, int l, uint64_t q, uint64_t& st,
+                                          uint64_t& en) {
+  if (l >= S.L) return false;
+  const uint64_t off = S.hq.node_lvl[3 * l], first = S.hq.node_lvl[3 * l + 1],
+                 num = S.hq.node_lvl[3 * l + 2];
+  if (q < first || q >= first + num) return false;
+  st = S.hq.node[off + q - first];
+  en = S.hq.node[off + q - first + 1];
+  return true;
+}
+
+__device__ uint64_t q_huff(const QStruct& S, int op, uint32_t c, uint64_t x) {
+  if (op == 0) {
+    if (x >= S.n) return NONE;
+    uint64_t q = 0, s = 0, pos = x;
+    for (int l = 0; l < S.L; l++) {
+      const BinLevel v = bin_level(S, l);
+      const int b = get_bit(v, pos);
+      const uint64_t child = (q << 1) | (uint64_t)b;
+      const uint64_t cnt_b = b ? (pos - s) - (rank0(v, pos) - rank0(v, s)) : rank0(v, pos) - rank0(v, s);
+      uint64_t cs, ce;
+      if (!huff_node(S, l + 1, child, cs, ce)) {
+        // a leaf at depth l+1: canonical code -> symbol
+        const int ln = l + 1;
+        const uint64_t first = S.hq.len_first[ln], base = S.hq.len_base[ln];
+        return S.hq.sym_by_rank[base + (child - first)];
+      }
+      q = child;
+      s = cs;
+      pos = cs + cnt_b;
+    }
+    return NONE;
+  }
+  if (c >= S.sigma) return NONE;
+  const int ln = S.hq.len[c];
+  const uint64_t code = S.hq.code[c];
+  if (op == 1) {
+    if (x >= S.n) return NONE;
+    if (ln == 0) return 0;
+    uint64_t q = 0, s = 0, j = x + 1;
+    for (int l = 0; l < ln; l++) {
+      const BinLevel v = bin_level(S, l);
+      const int b = (int)((code >> (ln - 1 - l)) & 1u);
+      const uint64_t z = rank0(v, j) - rank0(v, s);
+      const uint64_t cb = b ? (j - s) - z : z;
+      if (l == ln - 1) return cb;
+      q = (q << 1) | (uint64_t)b;
+      uint64_t cs, ce;
+      huff_node(S, l + 1, q, cs, ce);
+      s = cs;
+      j = cs + cb;
+    }
+    return NONE;
+  }
+  if (x == 0 || ln == 0) return NONE;
+  uint64_t S0[33];
+  uint64_t q = 0, s = 0, e = S.n;
+  for (int l = 0; l < ln; l++) {
+    S0[l] = s;
+    const BinLevel v = bin_level(S, l);
+    const int b = (int)((code >> (ln - 1 - l)) & 1u);
+    const uint64_t z = rank0(v, e) - rank0(v, s);
+    const uint64_t cb = b ? (e - s) - z : z;
+    if (l == ln - 1) {
+      if (x > cb) return NONE;
+      break;
+    }
+    q = (q << 1) | (uint64_t)b;
+    uint64_t cs, ce;
+    huff_node(S, l + 1, q, cs, ce);
+    s = cs;
+    e = ce;
+  }
+  // bottom-up: at level l the target is the off-th b-bit of node [S0[l], .)
+  uint64_t off = x - 1, pos = 0;
+  for (int l = ln - 1; l >= 0; l--) {
+    const BinLevel v = bin_level(S, l);
+    const int b = (int)((code >> (ln - 1 - l)) & 1u);
+    const uint64_t zs = rank0(v, S0[l]);
+    pos = b ? select_b(v, 1, (S0[l] - zs) + off) : select_b(v, 0, zs + off);
+    if (l > 0) off = pos - S0[l];
+  }
+  return pos;
+}
+
+// 4-ary tree: digit levels, per-value counts
+struct DigLevel {
+  const uint64_t* bits;
+  const uint64_t* dir;
+  uint64_t n, nsb;
+};
+
+__device__ __forceinline__ DigLevel dig_level(const QStruct& S, int l) {
+  const LevelMeta m = S.meta[l];
+  DigLevel v;
+  v.bits = S.bits + m.bit_off;
+  v.dir = S.dir + m.dir_off;
+  v.n = m.n;
+  v.nsb = m.nsb;
+  return v;
+}
+
+// count of digit d in [0, x)
+__device__ uint64_t rank_d(const DigLevel& v, uint32_t d, uint64_t x) {
+  const uint64_t s = x >> 10;
+  const uint32_t b = (uint32_t)((x >> 8) & 3);
+  uint64_t r = v.dir[8 * s + d] + ((v.dir[8 * s + 4 + b] >> (16 * d)) & 0xffffull);
+  const uint64_t wend = x >> 5;
+  for (uint64_t w = 32 * s + 8 * b; w < wend; w++) r += __popcll(digit_match(v.bits[w], d));
+  const uint32_t rem = (uint32_t)(x & 31);
+  if (rem) r += __popcll(digit_match(v.bits[wend], d) & ((1ull << (2 * rem)) - 1ull));
+  return r;
+}
+
+__device__ __forceinline__ uint32_t get_digit(const DigLevel& v, uint64_t i) {
+  return (uint32_t)((v.bits[i >> 5] >> (2 * (i & 31))) & 3ull);
+}
+
+// position of the k-th (0-based) occurrence of digit d
+__device__ uint64_t select_d(const DigLevel& v, uint32_t d, uint64_t k) {
+  uint64_t lo = 0, hi = v.nsb - 1;
+  while (lo < hi) {
+    const uint64_t mid = (lo + hi + 1) >> 1;
+    if (v.dir[8 * mid + d] <= k) lo = mid;
+    else hi = mid - 1;
+  }
+  uint64_t r = k - v.dir[8 * lo + d];
+  int b = 3;
+  for (; b > 0; b--)
+    if (((v.dir[8 * lo + 4 + b] >> (16 * d)) & 0xffffull) <= r) break;
+  r -= b ? ((v.dir[8 * lo + 4 + b] >> (16 * d)) & 0xffffull) : 0;
+  for (uint64_t w = 32 * lo + 8 * b; w < 32 * lo + 32; w++) {
+    const uint64_t m = digit_match(v.bits[w], d);
+    const uint32_t c = __popcll(m);
+    if (c > r) return w * 32 + sel64(m, (uint32_t)r) / 2;
+    r -= c;
+  }
+  return NONE;
+}
+
+__device__ uint64_t q_multi(const QStruct& S, int op, uint32_t c, uint64_t x) {
+  const int L = S.L, D = S.levels;
+  auto dwidth = [&](int be) { return (2 * be + 1 < L) ? 2 : 1; };
+  auto cdigit = [&](int be) -> uint32_t {
+    const int w = dwidth(be);
+    const int sh = L - 2 * be - w;
+    return (c >> sh) & ((1u << w) - 1u);
+  };
+  if (op == 0) {
+    if (x >= S.n) return NONE;
+    uint64_t s = 0, e = S.n, pos = x, sym = 0;
+    for (int be = 0; be < D; be++) {
+      const DigLevel v = dig_level(S, be);
+      const uint32_t d = get_digit(v, pos);
+      sym = (sym << dwidth(be)) | d;
+      uint64_t cs = s;
+      for (uint32_t d2 = 0; d2 < d; d2++) cs += rank_d(v, d2, e) - rank_d(v, d2, s);
+      const uint64_t rs = rank_d(v, d, s);
+      const uint64_t ne = cs + (rank_d(v, d, e) - rs);
+      pos = cs + (rank_d(v, d, pos) - rs);
+      s = cs;
+      e = ne;
+    }
+    return sym;
+  }
+  if (c >= S.sigma) return NONE;
+  if (op == 1) {
+    if (x >= S.n) return NONE;
+    uint64_t s = 0, e = S.n, j = x + 1;
+    for (int be = 0; be < D; be++) {
+      const DigLevel v = dig_level(S, be);
+      const uint32_t d = cdigit(be);
+      uint64_t cs = s;
+      for (uint32_t d2 = 0; d2 < d; d2++) cs += rank_d(v, d2, e) - rank_d(v, d2, s);
+      const uint64_t rs = rank_d(v, d, s);
+      const uint64_t ne = cs + (rank_d(v, d, e) - rs);
+      j = cs + (rank_d(v, d, j) - rs);
+      s = cs;
+      e = ne;
+    }
+    return j - s;
+  }
+  if (x == 0) return NONE;
+  uint64_t S0[17];
+  uint64_t s = 0, e = S.n;
+  for (int be = 0; be < D; be++) {
+    S0[be] = s;
+    const DigLevel v = dig_level(S, be);
+    const uint32_t d = cdigit(be);
+    uint64_t cs = s;
+    for (uint32_t d2 = 0; d2 < d; d2++) cs += rank_d(v, d2, e) - rank_d(v, d2, s);
+    const uint64_t ne = cs + (rank_d(v, d, e) - rank_d(v, d, s));
+    s = cs;
+    e = ne;
+  }
+  S0[D] = s;
+  if (x > e - s) return NONE;
+  uint64_t pos = s + x - 1;
+  for (int be = D - 1; be >= 0; be--) {
+    const DigLevel v = dig_level(S, be);
+    const uint32_t d = cdigit(be);
+    const uint64_t off = pos - S0[be + 1];
+    pos = select_d(v, d, rank_d(v, d, S0[be]) + off);
+  }
+  return pos;
+}
+
+__device__ uint64_t q_rs(const QStruct& S, int op, uint32_t c, uint64_t x) {
+  const BinLevel v = bin_level(S, 0);
+  if (op == 0) return x < S.n ? (uint64_t)get_bit(v, x) : NONE;
+  if (c > 1) return NONE;
+  if (op == 1) {
+    if (x >= S.n) return NONE;
+    return c ? rank1(v, x + 1) : rank0(v, x + 1);
+  }
+  const uint64_t cnt = c ? S.n - v.zeros : v.zeros;
+  if (x == 0 || x > cnt) return NONE;
+  return select_b(v, (int)c, x - 1);
+}
+
+__global__ void k_query(QStruct S, int op, const uint32_t* c, const uint64_t* x, uint64_t q,
+                        uint64_t* out) {
+  const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= q) return;
+  const uint32_t ci = c ? c[i] : 0u;
+  const uint64_t xi = x[i];
+  uint64_t r;
+  switch (S.kind) {
+    case WT_KIND_WM: r = q_wm(S, op, ci, xi); break;
+    case WT_KIND_WT: r = q_wt(S, op, ci, xi); break;
+    case WT_KIND_HUFF: r = q_huff(S, op, ci, xi); break;
+    case WT_KIND_MULTI: r = q_multi(S, op, ci, xi); break;
+    default: r = q_rs(S, op, ci, xi); break;
+  }
+  out[i] = r;
+}
+
+wt_status launch_query(wt_struct* h, int op, const uint32_t* c, const uint64_t* x, uint64_t q,
+                       uint64_t* out, cudaStream_t st) {
+  if (q == 0) return WT_OK;
+  QStruct S;
+  S.kind = h->kind;
+  S.n = h->n;
+  S.sigma = h->sigma;
+  S.L = (int)h->L;
+  S.levels = (int)h->levels;
+  S.bits = h->d_bits_ro;
+  S.dir = h->d_dir;
+  S.samp = h->d_samp;
+  S.meta = h->d_meta;
+  S.zeros = h->d_zeros;
+  S.hq.code = h->d_code;
+  S.hq.len = h->d_len;
+  S.hq.sym_by_rank = h->d_sym_by_rank;
+  S.hq.len_first = h->d_len_tab;
+  S.hq.len_base = h->d_len_tab ? h->d_len_tab + 34 : nullptr;
+  S.hq.len_count = h->d_len_tab ? h->d_len_tab + 68 : nullptr;
+  S.hq.node = h->d_node;
+  S.hq.node_lvl = h->d_node_lvl;
+  k_query<<<(unsigned)((q + 127) / 128), 128, 0, st>>>(S, op, c, x, q, out);
+  count_launch();
+  CK(cudaGetLastError());
+  return WT_OK;
+}
+
+}  // namespace wtk

@@ -1,0 +1,112 @@
+// wt_host.h -- host-side internals of the library (handle layout, launch
+// helpers shared between translation units).  Not part of the public ABI.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "../../include/wavelet.h"
+
+namespace wtk {
+
+// Per-level metadata used by the query kernels (device copy in the handle).
+struct LevelMeta {
+  uint64_t bit_off;   // word offset of the level in bits
+  uint64_t dir_off;   // u64 offset of the level's directory records
+  uint64_t s0_off;    // u64 offset of the zero samples
+  uint64_t s1_off;    // u64 offset of the one samples
+  uint64_t n;         // elements (bits or digits) on the level
+  uint64_t nsb;       // superblocks
+};
+
+// Huffman query tables (device): symbols in canonical order, per length the
+// first code and the offset into that order; per level the internal nodes.
+struct HuffQuery {
+  const uint32_t* code;     // [sigma]
+  const uint8_t* len;       // [sigma]
+  const uint32_t* sym_by_rank;  // present symbols sorted by (len, symbol)
+  const uint64_t* len_first;    // [34]: first canonical code of each length
+  const uint64_t* len_base;     // [34]: index in sym_by_rank of that code
+  const uint64_t* len_count;    // [34]: symbols of each length
+  const uint64_t* node;         // internal-node starts, per level + sentinel
+  const uint64_t* node_lvl;     // per level: offset, first prefix, count
+};
+
+}  // namespace wtk
+
+struct wt_struct {
+  int kind = 0;
+  uint64_t n = 0;
+  uint32_t sigma = 0;
+  uint32_t levels = 0;      // output levels (digit levels for MULTI)
+  uint32_t L = 0;           // binary levels (code length bound for HUFF)
+  uint32_t bpe = 1;
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  // device arrays owned by the handle
+  uint64_t* d_bits = nullptr;
+  const uint64_t* d_bits_ro = nullptr;  // == d_bits, or the caller's bitvector (RS)
+  uint64_t* d_dir = nullptr;
+  uint64_t* d_samp = nullptr;
+  uint64_t* d_zeros = nullptr;   // [levels]
+  uint32_t* d_err = nullptr;     // device error word
+  uint32_t* d_abort = nullptr;
+  wtk::LevelMeta* d_meta = nullptr;
+  // Huffman tables (device)
+  uint32_t* d_code = nullptr;
+  uint8_t* d_len = nullptr;
+  uint32_t* d_sym_by_rank = nullptr;
+  uint64_t* d_len_tab = nullptr;   // len_first | len_base | len_count (3 x 34)
+  uint64_t* d_node = nullptr;
+  uint64_t* d_node_lvl = nullptr;
+  // host mirrors
+  std::vector<uint64_t> level_len, level_off, dir_off, samp_off, zeros;
+  std::vector<wtk::LevelMeta> meta;
+  std::vector<uint8_t> code_len;
+  std::vector<uint32_t> code;
+  uint32_t max_code_len = 0;
+  bool zeros_valid = false;
+  wt_status deferred = WT_OK;
+};
+
+namespace wtk {
+
+// device memory helpers (stream-ordered pools)
+cudaError_t dmalloc(void** p, size_t bytes, cudaStream_t s);
+void dfree(void* p, cudaStream_t s);
+
+// directories and select samples for all levels of a handle whose bitmaps,
+// level_len/level_off/meta are set.  bpe == 1 binary; bpe == 2 digits.
+wt_status build_directories(wt_struct* h);
+
+// upload h->meta into h->d_meta (allocating it)
+wt_status upload_meta(wt_struct* h);
+
+uint32_t num_sms();
+
+// Launch accounting (all kernels of the library) and optional CUDA-event
+// timing of the partition-pass launches, for the benchmark's roofline.
+struct Prof {
+  bool on = false;
+  uint64_t launches = 0;
+  uint64_t pass_launches = 0;
+  std::vector<cudaEvent_t> ev;  // pairs: before, after each pass launch
+};
+Prof& prof();
+inline void count_launch(uint64_t k = 1) { prof().launches += k; }
+
+}  // namespace wtk
+
+namespace wtk {
+wt_status build_wm(const void* d_seq, uint64_t n, uint32_t sigma, int w, const wt_build_opts* o,
+                   wt_struct* h);
+wt_status build_wt(const void* d_seq, uint64_t n, uint32_t sigma, int w, const wt_build_opts* o,
+                   wt_struct* h, bool multiary);
+wt_status build_huff(const void* d_seq, uint64_t n, uint32_t sigma, int w, const uint8_t* h_len,
+                     const wt_build_opts* o, wt_struct* h);
+wt_status launch_query(wt_struct* h, int op, const uint32_t* c, const uint64_t* x, uint64_t q,
+                       uint64_t* out, cudaStream_t st);
+uint32_t huffman_lengths(const uint64_t* hist, uint32_t sigma, uint32_t cap, uint8_t* len);
+void canonical_codes(const uint8_t* len, uint32_t sigma, uint32_t* code);
+}  // namespace wtk

@@ -1,0 +1,106 @@
+// wt_internal.cuh -- device-side types and helpers shared by the kernels of
+// the GB300 wavelet library (not part of the public ABI).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace wtk {
+
+constexpr int TAU_MAX = 8;                  // levels per partition pass (upper bound)
+constexpr int NCLS = 1 << (TAU_MAX + 1);    // class-tree slots: level j class k at 2^j-1+k
+constexpr int NTAIL = 1 << TAU_MAX;         // tail slots: levels 0..t-1
+constexpr uint32_t FULL = 0xffffffffu;
+
+// device error word bits
+enum : uint32_t { ERR_SYMBOL = 1u, ERR_TIMEOUT = 2u, ERR_INTERNAL = 4u };
+
+// structure shapes handled by the partition pass
+enum Shape : int { SHAPE_WM = 0, SHAPE_WT = 1, SHAPE_HUFF = 2 };
+
+// One tile of a pass: `count` consecutive elements of T_a starting at
+// `start`, all inside node `node` (bit 31 of `flags`: first tile of its node).
+struct TileDesc {
+  uint64_t start;
+  uint32_t count;
+  uint32_t node;
+  uint32_t first;
+  uint32_t pad;
+};
+
+// Look-back ring slot: flag word followed by the aggregate and the
+// inclusive state (class counts tree, then tails).
+constexpr int SLOT_STATE = NCLS + NTAIL;       // u64 per state
+constexpr int SLOT_U64 = 8 + 2 * SLOT_STATE;   // flag padded to 64 bytes
+
+struct PassParams {
+  // input sequence T_a (elements hold the rbits = L - a low bits still needed)
+  const void* in;
+  int in_w;                 // bytes per input element (1, 2, 4)
+  const uint32_t* code_map; // HUFF first pass: symbol -> left-aligned codeword
+  // output sequence T_{a+t}, narrowed to rbits - t bits (nullptr on the last pass)
+  void* out;
+  int out_w;
+  // geometry
+  int L;                    // total levels (max code length for HUFF)
+  int a, t;                 // first level of the pass, levels in the pass
+  int rbits;                // bits per input element that matter (L - a)
+  int shape;
+  int digits;               // 1: emit 2-bit digit levels at even levels (multiary)
+  // outputs
+  uint64_t* bits;           // level bitmaps (or digit levels)
+  const uint64_t* lvl_off;  // word offset per output level
+  const uint64_t* lvl_len;  // elements per output level
+  // class starts
+  const uint64_t* wm_cls;   // WM: per level j of the pass, 2^j+1 starts at 2^j-1+j
+  const uint64_t* wt_C;     // WT: C[v] = #symbols < v, v in [0, 2^L]
+  const uint64_t* hf_node;  // HUFF: starts of the internal nodes, per level + sentinel
+  const uint64_t* hf_lvl;   // HUFF: per level l: [3l] table offset, [3l+1] first internal prefix, [3l+2] count
+  // tiles
+  const TileDesc* tiles;    // nullptr: uniform tiles of TILE elements over n_in
+  const uint32_t* ntiles_dev;
+  uint32_t ntiles;
+  uint64_t n_in;
+  // decoupled look-back
+  uint64_t* ring;
+  uint32_t ring_mask;
+  uint64_t seq_base;
+  uint32_t* ticket;
+  uint32_t* err;
+  uint32_t* abort_flag;
+  uint64_t spin_limit;
+};
+
+__device__ __forceinline__ uint32_t rev_bits(uint32_t k, int j) {
+  return j == 0 ? 0u : (__brev(k) >> (32 - j));
+}
+
+__device__ __forceinline__ uint64_t ld_acquire_u64(const uint64_t* p) {
+  uint64_t v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ void st_release_u64(uint64_t* p, uint64_t v) {
+  asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+__device__ __forceinline__ uint32_t ld_volatile_u32(const uint32_t* p) {
+  return *(const volatile uint32_t*)p;
+}
+
+__device__ __forceinline__ uint32_t lanemask_lt() {
+  uint32_t m;
+  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+  return m;
+}
+
+// Combine the last-64-bit tails of two adjacent bit streams A (earlier) and B:
+// a tail keeps the stream's last bits at the top (bit 63 = last bit) and
+// zeros below them.  nbB = length of B in bits.
+__device__ __forceinline__ uint64_t tail_combine(uint64_t A, uint64_t B, uint64_t nbB) {
+  if (nbB >= 64) return B;
+  if (nbB == 0) return A;
+  return (A >> nbB) | B;
+}
+
+}  // namespace wtk

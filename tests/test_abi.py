@@ -1,0 +1,79 @@
+"""C ABI: the library loads without a GPU, exports every declared entry point,
+and its host-side logic (Huffman code construction) matches the oracle."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = []
+    inc = os.path.join(ROOT, "include")
+    for f in sorted(os.listdir(inc)):
+        if not f.endswith(".h"):
+            continue
+        text = open(os.path.join(inc, f)).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\*?\s*([a-z_][a-z0-9_]*)\s*\(",
+                             text, flags=re.M):
+            names.append(m.group(1))
+    return names
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1610_03524_gb300 as wt
+    return wt
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_functions()
+    assert len(names) >= 16
+    so = ctypes.CDLL(lib.LIB_PATH)
+    for n in names:
+        assert hasattr(so, n), n
+    assert set(names) == set(lib.ABI_SYMBOLS)
+
+
+def test_status_strings(lib):
+    so = lib.load_library()
+    for s in range(7):
+        assert so.wt_status_str(s)
+
+
+@pytest.mark.parametrize("seed,sigma,s", [(1, 2, 1.0), (2, 17, 1.0), (3, 1000, 1.1), (4, 5000, 0.7),
+                                          (5, 1 << 16, 1.0)])
+def test_library_huffman_matches_oracle(lib, seed, sigma, s):
+    S = synth.zipf(seed, 1 << 16, sigma, s, 4)
+    hist = np.bincount(S.astype(np.int64), minlength=sigma).astype(np.uint64)
+    la, ma = lib.huffman_lengths(hist, 32)
+    lo, mo = oracle.huffman_lengths(hist, 32)
+    assert ma == mo and np.array_equal(la, lo)
+    assert np.array_equal(lib.canonical_codes(la), oracle.canonical_codes(lo))
+
+
+def test_library_package_merge_matches_oracle(lib):
+    fib = [1, 1]
+    while len(fib) < 45:
+        fib.append(fib[-1] + fib[-2])
+    hist = np.array(fib + [0, 3, 3], dtype=np.uint64)
+    for cap in (32, 24, 10, 7):
+        la, ma = lib.huffman_lengths(hist, cap)
+        lo, mo = oracle.huffman_lengths(hist, cap)
+        assert ma == mo <= cap and np.array_equal(la, lo)
+
+
+def test_no_cpu_fallback(lib, monkeypatch):
+    # a missing library must raise, never silently compute on the host
+    monkeypatch.setattr(lib, "_lib", None)
+    with pytest.raises(ImportError):
+        lib.load_library(os.path.join(ROOT, "no_such_libwavelet.so"))
