@@ -137,6 +137,25 @@ wt_status multiary_build(const void* d_seq, uint64_t n, uint32_t sigma, uint32_t
 wt_status rs_build(const uint64_t* d_bits, uint64_t nbits, const wt_build_opts* opts,
                    wt_stream stream, wt_handle* out);
 
+/* Rank/select directory of a bitvector that allocates no device memory.
+ * The paper has no counterpart: this entry point exists for callers that
+ * cannot call cudaMalloc when they need the directory (a component that owns
+ * all device memory through its own manager, paths that must not wait on an
+ * allocation, runtimes that forbid allocation after start-up).  The build's
+ * scratch lives in a static device array of about 4 MiB that every GPU
+ * loading this library keeps until the process exits.
+ * d_bits: nbits bits LSB-first (bits >= nbits in the last word zero).
+ * Outputs, allocated by the caller: d_dir, 2*(ceil(nbits/2048)+1) u64 in the
+ * rs_build record layout; d_samp0 / d_samp1, nbits/4096+1 u64 each, receiving
+ * the positions of the 0-based 4096k-th zero / one (as rs_build's samples).
+ * nbits must be <= 2^30; larger sizes return WT_ERR_UNSUPPORTED.  The first
+ * call on a device looks up the array's device address; issue that first call
+ * before any stream capture.  All calls share the scratch array, so calls
+ * whose kernels overlap on the GPU race: order them (e.g. one stream).
+ * Asynchronous on `stream` like every other call. */
+wt_status rs_dir_build_static(const uint64_t* d_bits, uint64_t nbits, uint64_t* d_dir,
+                              uint64_t* d_samp0, uint64_t* d_samp1, wt_stream stream);
+
 /* Batched queries (definitions of Section 2).  q queries; d_i / d_c / d_k /
  * d_out are device arrays of q entries owned by the caller. */
 wt_status wt_access(wt_handle h, const uint64_t* d_i, uint64_t q, uint64_t* d_out,

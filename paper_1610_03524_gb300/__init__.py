@@ -27,7 +27,7 @@ FLAG_NO_DIRECTORY = 1
 ABI_SYMBOLS = ("wt_build", "wm_build", "huff_wt_build", "multiary_build", "rs_build",
                "wt_access", "wt_rank", "wt_select", "wt_sync", "wt_export", "wt_free",
                "wt_symbol_levels", "wt_status_str", "wt_memcpy_d2h", "wt_huffman_lengths",
-               "wt_canonical_codes", "wt_prof_enable", "wt_prof_read")
+               "wt_canonical_codes", "wt_prof_enable", "wt_prof_read", "rs_dir_build_static")
 
 
 class WaveletError(RuntimeError):
@@ -102,6 +102,8 @@ def load_library(path: str = LIB_PATH):
     lib.wt_huffman_lengths.argtypes = [vp, u32, u32, vp]
     lib.wt_canonical_codes.restype = None
     lib.wt_canonical_codes.argtypes = [vp, u32, vp]
+    lib.rs_dir_build_static.restype = c.c_int
+    lib.rs_dir_build_static.argtypes = [vp, u64, vp, vp, vp, vp]
     lib.wt_prof_enable.restype = None
     lib.wt_prof_enable.argtypes = [c.c_int]
     lib.wt_prof_read.restype = c.c_int
@@ -320,6 +322,15 @@ def rs_build(bits, nbits: int, stream=None) -> Handle:
     _check(load_library().rs_build(_ptr(bits), nbits, ctypes.byref(o), _stream_ptr(stream),
                                     ctypes.byref(h)), "rs_build")
     return Handle(h, keep=bits)
+
+
+def rs_dir_build_static(bits, nbits: int, dir_out, samp0_out, samp1_out, stream=None):
+    """Rank directory and select samples of a device bitvector into caller
+    buffers, with no device allocation (scratch in a static device array;
+    nbits <= 2^30; calls must not overlap on the GPU)."""
+    _check(load_library().rs_dir_build_static(_ptr(bits), nbits, _ptr(dir_out), _ptr(samp0_out),
+                                               _ptr(samp1_out), _stream_ptr(stream)),
+           "rs_dir_build_static")
 
 
 def prof_enable(on: bool = True):
