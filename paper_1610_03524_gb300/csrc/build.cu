@@ -25,7 +25,7 @@
 namespace wtk {
 
 static std::atomic<uint64_t> g_seq{1};
-constexpr uint32_t RING_SLOTS = 2048;
+constexpr uint32_t RING_SLOTS = 4096;
 constexpr uint64_t SPIN_LIMIT = 1ull << 24;
 
 #define CK(x)                                                   \
@@ -335,23 +335,12 @@ __global__ void k_plan_wm(const uint64_t* hist, uint64_t n, int L, int tau, int 
       __syncthreads();
       uint64_t* c = cls + coff + (nk - 1 + j);
       for (int k = threadIdx.x; k <= nk; k += blockDim.x) c[k] = st[k];
-      if (j >= 1 && j < t) {
-        uint64_t* lb = bits + (uint64_t)(a + j) * W;
-        for (int k = 1 + threadIdx.x; k < nk; k += blockDim.x) {
-          const uint64_t s = st[k];
-          if ((s & 63) && s < n) lb[s >> 6] = 0;
-        }
-      }
       if (j >= 1 && threadIdx.x == 0) zeros[a + j - 1] = st[nk >> 1];
       __syncthreads();
     }
     hoff += 1 << t;
     coff += (2 << t) + t + 1;
   }
-  // padding words of every level
-  const uint64_t used = (n + 63) >> 6;
-  for (int l = 0; l < L; l++)
-    for (uint64_t w = used + threadIdx.x; w < W; w += blockDim.x) bits[(uint64_t)l * W + w] = 0;
   for (uint32_t i = threadIdx.x; i < ring_slots; i += blockDim.x) ring[(uint64_t)i * SLOT_U64] = 0;
   for (int g = threadIdx.x; g < 32; g += blockDim.x) tickets[g] = 0;
   if (threadIdx.x == 0) *abort_flag = 0;
@@ -436,7 +425,7 @@ __global__ void k_tiles_write(const uint64_t* bnd, uint64_t stride, uint64_t nn,
 // ---------------------------------------------------------------------------
 // 3. pass launch
 // ---------------------------------------------------------------------------
-constexpr int PT = 8192, PNT = 256;
+constexpr int PT = 4096, PNT = 256;
 
 template <typename E, bool DIG>
 static wt_status launch_pass_t(const PassParams& P, uint64_t max_tiles, const wt_build_opts* o,
@@ -447,7 +436,7 @@ static wt_status launch_pass_t(const PassParams& P, uint64_t max_tiles, const wt
   static int occ = 0;
   if (!attr) {
     CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM::bytes));
-    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, PNT, SM::bytes));
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, PNT + 32, SM::bytes));
     if (occ < 1) occ = 1;
     attr = true;
   }
@@ -455,7 +444,9 @@ static wt_status launch_pass_t(const PassParams& P, uint64_t max_tiles, const wt
   if (o && o->ctas_per_sm) per_sm = std::min<int>(occ, (int)o->ctas_per_sm);
   uint64_t grid = (uint64_t)num_sms() * per_sm;
   if (grid > max_tiles) grid = std::max<uint64_t>(max_tiles, 1);
-  if (grid >= RING_SLOTS / 2) grid = RING_SLOTS / 2 - 1;
+  if (grid >= RING_SLOTS / 4) grid = RING_SLOTS / 4 - 1;
+  // per-digit look-back words carry no pass tag: clear them for this pass
+  CK(cudaMemsetAsync(P.ring, 0, (size_t)RING_SLOTS * SLOT_U64 * 8, st));
   Prof& pf = prof();
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (pf.on) {
@@ -463,7 +454,7 @@ static wt_status launch_pass_t(const PassParams& P, uint64_t max_tiles, const wt
     cudaEventCreate(&e1);
     cudaEventRecord(e0, st);
   }
-  kern<<<(unsigned)grid, PNT, SM::bytes, st>>>(P);
+  kern<<<(unsigned)grid, PNT + 32, SM::bytes, st>>>(P);
   CK(cudaGetLastError());
   count_launch();
   if (pf.on) {
@@ -519,6 +510,9 @@ struct Work {
 static wt_status alloc_outputs(wt_struct* h, uint64_t total_words) {
   CK(dmalloc((void**)&h->d_bits, total_words * 8, h->stream));
   h->d_bits_ro = h->d_bits;
+  // the partition passes store whole words and OR the words shared by
+  // several tiles or nodes, so the level buffer starts at zero
+  CK(cudaMemsetAsync(h->d_bits, 0, total_words * 8, h->stream));
   CK(dmalloc((void**)&h->d_zeros, std::max<uint32_t>(h->levels, 1) * 8, h->stream));
   CK(cudaMemsetAsync(h->d_zeros, 0, std::max<uint32_t>(h->levels, 1) * 8, h->stream));
   return WT_OK;
@@ -675,18 +669,6 @@ wt_status build_wt(const void* d_seq, uint64_t n, uint32_t sigma, int w, const w
   TRY(scan_excl_u64(hist, C, V, scr, st));
   if (!multiary) {
     k_wt_zeros<<<L, 1024, 0, st>>>(C, L, h->d_zeros);
-    count_launch();
-    CK(cudaGetLastError());
-  }
-  {
-    const uint64_t tot = V - 1;
-    if (tot) {
-      k_wt_zero_words<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(C, L, n, h->d_bits, d_off,
-                                                                   multiary ? 1 : 0);
-  count_launch();
-      CK(cudaGetLastError());
-    }
-    k_zero_padding<<<h->levels, 256, 0, st>>>(h->d_bits, d_off, d_len, h->levels, h->bpe);
     count_launch();
     CK(cudaGetLastError());
   }
@@ -896,32 +878,6 @@ wt_status build_huff(const void* d_seq, uint64_t n, uint32_t sigma, int w, const
   TRY(wk.get(&d_ntiles, 1));
   CK(cudaMemcpyAsync(d_off, h->level_off.data(), (Lm + 1) * 8, cudaMemcpyHostToDevice, st));
   CK(cudaMemcpyAsync(d_len, h->level_len.data(), Lm * 8, cudaMemcpyHostToDevice, st));
-  // zero words holding a node start, and padding
-  {
-    std::vector<uint64_t> zw;
-    for (int l = 0; l < Lm; l++) {
-      const uint64_t off = node_lvl[3 * l], cnt = node_lvl[3 * l + 2];
-      for (uint64_t i = 1; i < cnt; i++) {
-        const uint64_t s = node[off + i];
-        if ((s & 63) && s < h->level_len[l]) zw.push_back(h->level_off[l] + (s >> 6));
-      }
-    }
-    if (!zw.empty()) {
-      std::sort(zw.begin(), zw.end());
-      zw.erase(std::unique(zw.begin(), zw.end()), zw.end());
-      // scatter zeros: upload the word list and clear on device
-      uint64_t* d_zw;
-      TRY(wk.get(&d_zw, zw.size()));
-      CK(cudaMemcpyAsync(d_zw, zw.data(), zw.size() * 8, cudaMemcpyHostToDevice, st));
-      k_clear_words<<<(unsigned)((zw.size() + 255) / 256), 256, 0, st>>>(h->d_bits, d_zw, zw.size());
-      count_launch();
-      CK(cudaGetLastError());
-      CK(cudaStreamSynchronize(st));
-    }
-    k_zero_padding<<<Lm, 256, 0, st>>>(h->d_bits, d_off, d_len, Lm, 1);
-    count_launch();
-    CK(cudaGetLastError());
-  }
   k_reset_lookback<<<1, 1024, 0, st>>>(ring, RING_SLOTS, tickets, h->d_abort);
   count_launch();
   CK(cudaGetLastError());

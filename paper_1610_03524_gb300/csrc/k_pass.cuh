@@ -4,23 +4,24 @@
 // atomic ticket, so every wait below is on a tile that is already running).
 // For a tile it computes, in shared memory:
 //   * the tile's bits of levels a..a+t-1, each in the order that level has
-//     inside the tile (t stable 1-bit splits; Section 4.1: the sub-sequences
-//     of the descendants are a stable integer sort on the next tau bits, and
-//     Section 4.3: for the wavelet matrix the key is the reversed digit);
-//   * the tile's element count of every class (node) of every level, from the
-//     zero counts of the split bits (prefix sums, Section 2);
-//   * the last <= 64 bits the tile contributes to each class ("tails").
-// It then runs a decoupled look-back (single-pass chained scan) over the
-// tiles to get, for each class, the count of elements and the last 64 bits
-// of all earlier tiles.  This is the domain decomposition of Section 4.2:
-// K = number of tiles, per-node offsets by prefix sums across the K
-// sub-problems, words copied whole, and the "boundary" words that several
-// sub-problems share merged specially -- here the earlier tiles' tail bits
-// travel with the prefix, so every word inside a node is stored once, whole,
-// by the tile holding its last bit, and only words that straddle a node
-// boundary are merged with atomicOr (into words zeroed by the plan step).
+//     inside the tile.  Levels are taken two at a time: one 4-way stable split
+//     of the tile on (b_j, b_j+1) per pair of levels (Section 4.1: the
+//     descendants' sub-sequences are a stable integer sort on the next tau
+//     bits; Section 4.3: for the wavelet matrix the key is the reversed
+//     digit).  Level j's bits are the ballot words of b_j in the current order;
+//     level j+1's bits (order after the split on b_j alone) are assembled from
+//     warp-wide OR reductions of the b_j+1 bits of each half;
+//   * the element count of every class (node) of every level, from prefix
+//     popcounts of the bit planes inside each class run (prefix sums,
+//     Section 2).
+// A decoupled look-back (single-pass chained scan) over the tiles then gives,
+// for each class, the count of elements in all earlier tiles: the domain
+// decomposition of Section 4.2 with K = number of tiles and per-node offsets
+// by prefix sums across the K sub-problems.  Words copied whole are stored;
+// the "boundary" words that several tiles or nodes share (Section 4.2) are
+// merged with atomicOr into the level buffer, which the build zeroes first.
 // Finally the tile scatters its elements, narrowed to the bits still needed,
-// to T_{a+t}: a stable partition on the t-bit digit (big nodes, Section 3).
+// to T_{a+t}: the stable partition on the t-bit digit (big nodes, Section 3).
 #pragma once
 #include "wt_internal.cuh"
 
@@ -90,54 +91,86 @@ __device__ __forceinline__ uint32_t get32(const uint32_t* pl, int e) {
   return o ? __funnelshift_r(lo, hi, o) : lo;
 }
 
+// OR a segment of bits into a bit plane at bit position pos
+__device__ __forceinline__ void or_bits(uint32_t* pl, int pos, uint32_t seg) {
+  const int w = pos >> 5, o = pos & 31;
+  atomicOr(pl + w, seg << o);
+  if (o && (seg >> (32 - o))) atomicOr(pl + w + 1, seg >> (32 - o));
+}
+
 template <typename E, int T, int NT, bool DIG>
 struct PassSmem {
   static constexpr int TW = T / 32;
   static constexpr size_t off_buf = 0;
   static constexpr size_t off_lbits = off_buf + 2 * (size_t)T * sizeof(E);
-  static constexpr size_t off_lplane = off_lbits + (size_t)TAU_MAX * TW * 4;
-  static constexpr size_t off_zpw = off_lplane + (DIG ? (size_t)(TAU_MAX / 2) * TW * 4 : 0);
-  static constexpr size_t off_ccnt = off_zpw + (size_t)TW * 4;
+  static constexpr size_t off_pb1 = off_lbits + (size_t)TAU_MAX * TW * 4;
+  static constexpr size_t off_ccnt = off_pb1 + (size_t)(TAU_MAX / 2) * TW * 4;
   static constexpr size_t off_cstart = off_ccnt + (size_t)NCLS * 4;
-  static constexpr size_t off_owntail = off_cstart + (size_t)NCLS * 4;  // 8-aligned
-  static constexpr size_t off_extail = off_owntail + (size_t)NTAIL * 8;
-  static constexpr size_t off_excnt = off_extail + (size_t)NTAIL * 8;
-  static constexpr size_t off_clsce = off_excnt + (size_t)NCLS * 8;
+  static constexpr size_t off_excnt = off_cstart + (size_t)NCLS * 4;  // 8-aligned
+  static constexpr size_t off_clscs = off_excnt + (size_t)NCLS * 8;
+  static constexpr size_t off_clsce = off_clscs + (size_t)NTAIL * 8;
   static constexpr size_t bytes = off_clsce + (size_t)NTAIL * 8;
 };
 
+// NT worker threads run the splits; one extra control warp computes the
+// class counts and runs the look-back meanwhile (block = NT + 32 threads).
 template <typename E, int T, int NT, bool DIG>
-__global__ void __launch_bounds__(NT) k_pass(const PassParams P) {
-  constexpr int W = NT / 32, PW = T / W, EPW = PW / 32, TW = T / 32;
+__global__ void __launch_bounds__(NT + 32, 3) k_pass(const PassParams P) {
+  constexpr int W = NT / 32, PW = T / W, EPW = PW / 32, TW = T / 32, NB = NT + 32, CW = W;
   static_assert(EPW >= 1 && EPW <= 32, "iterations per warp must fit a warp");
   static_assert(T % 64 == 0 && NT >= (1 << TAU_MAX), "tile geometry");
   using SM = PassSmem<E, T, NT, DIG>;
   extern __shared__ __align__(16) unsigned char smem[];
   E* const bufA = (E*)(smem + SM::off_buf);
   E* const bufB = bufA + T;
-  uint32_t* const lbits = (uint32_t*)(smem + SM::off_lbits);
-  uint32_t* const lplane = (uint32_t*)(smem + SM::off_lplane);
-  uint32_t* const zpw = (uint32_t*)(smem + SM::off_zpw);
+  uint32_t* const lbits = (uint32_t*)(smem + SM::off_lbits);  // level bits, P_j order
+  uint32_t* const pb1 = (uint32_t*)(smem + SM::off_pb1);      // b_j+1 plane of pair rounds
   uint32_t* const ccnt = (uint32_t*)(smem + SM::off_ccnt);
   uint32_t* const cstart = (uint32_t*)(smem + SM::off_cstart);
-  uint64_t* const own_tail = (uint64_t*)(smem + SM::off_owntail);
-  uint64_t* const ex_tail = (uint64_t*)(smem + SM::off_extail);
   uint64_t* const ex_cnt = (uint64_t*)(smem + SM::off_excnt);
+  uint64_t* const cls_cs = (uint64_t*)(smem + SM::off_clscs);
   uint64_t* const cls_ce = (uint64_t*)(smem + SM::off_clsce);
-  uint64_t* const cls_cs = own_tail;  // reused once the inclusive state is published
-  uint64_t* const sbase = own_tail;   // reused again by the scatter
+  uint64_t* const sbase = cls_cs;  // reused by the scatter
 
   __shared__ uint32_t s_tile;
-  __shared__ int s_stat, s_stop;
+  __shared__ int s_stat;
+  __shared__ int s_w[4][W];
+  __shared__ int s_scan[W + 1];
   __shared__ int wst[1 << TAU_MAX];
+  __shared__ int btab[W][EPW][4];
   __shared__ uint32_t s_dead[(1 << TAU_MAX) / 32];
-  __shared__ int s_warp[W];
+  __shared__ uint32_t s_hist[1 << TAU_MAX];
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int t = P.t;
   const int bpe = DIG ? 2 : 1;
   const int ncl = (2 << t) - 1, ntl = (1 << t) - 1;
   const uint32_t ntiles = P.tiles ? *P.ntiles_dev : P.ntiles;
+  const uint32_t lt = lanemask_lt();
+  const int wbase = warp * PW;
+
+  auto bar_workers = [&]() { asm volatile("bar.sync 1, %0;" ::"n"(NT) : "memory"); };
+  // block-wide exclusive scan of one int per thread
+  auto block_scan = [&](int v, int& total) -> int {
+    int si = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(FULL, si, o);
+      if (lane >= o) si += y;
+    }
+    if (lane == 31) s_scan[warp] = si;
+    __syncthreads();
+    int base = 0, tot = 0;
+#pragma unroll
+    for (int w2 = 0; w2 <= W; w2++) {
+      const int x = s_scan[w2];
+      base += (w2 < warp) ? x : 0;
+      tot += x;
+    }
+    __syncthreads();
+    total = tot;
+    return base + si - v;
+  };
 
   for (;;) {
     if (tid == 0) {
@@ -165,122 +198,369 @@ __global__ void __launch_bounds__(NT) k_pass(const PassParams P) {
       node = 0;
       first = (ti == 0);
     }
+    const bool full = cnt == T;
 
-    // ---- 1. load the tile -------------------------------------------------
+    // ---- 1. load the tile; clear the planes filled by OR ----------------
     if (P.code_map) {
-      for (int i = tid; i < cnt; i += NT)
+      for (int i = tid; i < cnt; i += NB)
         bufA[i] = (E)P.code_map[load_elem(P.in, P.in_w, ts + i)];
-    } else if (P.in_w == 2 && sizeof(E) == 2 && cnt == T && (ts & 7) == 0) {
+    } else if (P.in_w == 2 && sizeof(E) == 2 && full && (ts & 7) == 0) {
       const uint4* src = (const uint4*)((const uint16_t*)P.in + ts);
       uint4* dst = (uint4*)bufA;
-      for (int i = tid; i < T / 8; i += NT) dst[i] = __ldcs(src + i);
+      for (int i = tid; i < T / 8; i += NB) dst[i] = __ldcs(src + i);
+    } else if (P.in_w == 1 && sizeof(E) == 2 && full && (ts & 15) == 0) {
+      const uint4* src = (const uint4*)((const uint8_t*)P.in + ts);
+      for (int i = tid; i < T / 16; i += NB) {
+        const uint4 q = __ldcs(src + i);
+        const uint32_t w4[4] = {q.x, q.y, q.z, q.w};
+        uint4* d = (uint4*)(bufA + 16 * i);
+        uint32_t o[8];
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+          o[2 * k] = __byte_perm(w4[k], 0, 0x4140);
+          o[2 * k + 1] = __byte_perm(w4[k], 0, 0x4342);
+        }
+        d[0] = make_uint4(o[0], o[1], o[2], o[3]);
+        d[1] = make_uint4(o[4], o[5], o[6], o[7]);
+      }
     } else {
-      for (int i = tid; i < cnt; i += NT) bufA[i] = (E)load_elem(P.in, P.in_w, ts + i);
+      for (int i = tid; i < cnt; i += NB) bufA[i] = (E)load_elem(P.in, P.in_w, ts + i);
     }
-    if (tid == 0) {
-      ccnt[0] = (uint32_t)cnt;
-      cstart[0] = 0;
+    if (!DIG)
+      for (int i = tid; i < (t >> 1) * TW; i += NB) lbits[(2 * (i / TW) + 1) * TW + i % TW] = 0;
+    for (int i = tid; i < (1 << TAU_MAX); i += NB) s_hist[i] = 0;
+    __syncthreads();
+
+    // ---- 2. digit histogram -------------------------------------------------
+    {
+      const uint32_t rmask = (1u << t) - 1u;
+      const int rsh = 32 - P.rbits;
+      for (int p = tid; p < cnt; p += NB)
+        atomicAdd(&s_hist[(__brev((uint32_t)bufA[p]) >> rsh) & rmask], 1u);
     }
     __syncthreads();
 
-    // ---- 2. t stable 1-bit splits ----------------------------------------
-    const uint32_t lt = lanemask_lt();
-    for (int j = 0; j < t; j++) {
-      const E* src = (j & 1) ? bufB : bufA;
-      E* dst = (j & 1) ? bufA : bufB;
-      const bool move = (j < t - 1) || (P.out != nullptr);
-      const int sh = P.rbits - 1 - j;
-      const bool two = DIG && (((P.a + j) & 1) == 0) && (P.a + j + 1 < P.L);
-      const int wbase = warp * PW;
-      uint32_t xr[EPW], br[EPW];
-      uint32_t myb = 0, myb2 = 0;
+    int cur = 0;
+    if (warp == CW) {
+      // ---- 3 (control warp). class counts of every level from the digit
+      //      histogram; per-digit decoupled look-back for the counts of all
+      //      earlier tiles; exclusive counts of every level ----------------
+      // level j classes are the digit values mod 2^j; lane l holds the
+      // digits l + 32i: levels >= 5 sum over i, levels < 5 fold lanes
+      uint32_t h[8];
 #pragma unroll
-      for (int e = 0; e < EPW; e++) {
-        const int p = wbase + e * 32 + lane;
-        const bool v = p < cnt;
-        const uint32_t x = v ? (uint32_t)src[p] : 0u;
-        xr[e] = x;
-        const uint32_t b = __ballot_sync(FULL, v && ((x >> sh) & 1u));
-        br[e] = b;
-        if (lane == e) myb = b;
-        if (DIG && two) {
-          const uint32_t b2 = __ballot_sync(FULL, v && ((x >> (sh - 1)) & 1u));
-          if (lane == e) myb2 = b2;
+      for (int i = 0; i < 8; i++) h[i] = s_hist[lane + 32 * i];
+      {
+        for (int j = 8; j >= 5; j--) {
+          if (j > t) continue;
+          const int nsub = 1 << (j - 5);
+          uint32_t carry = 0;
+          for (int sub = 0; sub < nsub; sub++) {
+            uint32_t c = 0;
+#pragma unroll
+            for (int i = 0; i < 8; i++)
+              if ((i & (nsub - 1)) == sub) c += h[i];
+            ccnt[cls_idx(j, lane + 32 * sub)] = c;
+            uint32_t ci = c;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+              const uint32_t y = __shfl_up_sync(FULL, ci, o);
+              if (lane >= o) ci += y;
+            }
+            cstart[cls_idx(j, lane + 32 * sub)] = carry + ci - c;
+            carry += __shfl_sync(FULL, ci, 31);
+          }
         }
-      }
-      if (lane < EPW) {
-        lbits[j * TW + warp * EPW + lane] = myb;
-        if (DIG && two) lplane[(j >> 1) * TW + warp * EPW + lane] = myb2;
-      }
-      const int vstart = wbase + lane * 32;
-      const int vc = min(max(cnt - vstart, 0), 32);
-      const int z = (lane < EPW) ? vc - __popc(myb) : 0;
-      int zi = z;
+        uint32_t c5 = 0;
 #pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const int y = __shfl_up_sync(FULL, zi, o);
-        if (lane >= o) zi += y;
-      }
-      if (lane == 31) s_warp[warp] = zi;
-      __syncthreads();
-      int wz = 0, Zt = 0;
+        for (int i = 0; i < 8; i++) c5 += h[i];
+        for (int j = 5; j >= 0; j--) {
+          if (j < 5) c5 += __shfl_down_sync(FULL, c5, 1 << j);
+          if (j < 5 && j <= t) {
+            const uint32_t v = lane < (1 << j) ? c5 : 0u;
+            uint32_t ci = v;
 #pragma unroll
-      for (int w2 = 0; w2 < W; w2++) {
-        const int v2 = s_warp[w2];
-        wz += (w2 < warp) ? v2 : 0;
-        Zt += v2;
-      }
-      const int zpre = wz + zi - z;
-      if (lane < EPW) zpw[warp * EPW + lane] = zpre;
-      if (move) {
-#pragma unroll
-        for (int e = 0; e < EPW; e++) {
-          const int zb = __shfl_sync(FULL, zpre, e);
-          const int p = wbase + e * 32 + lane;
-          if (p < cnt) {
-            const uint32_t b = br[e];
-            const int r1 = __popc(b & lt);
-            const int pos0 = wbase + e * 32;
-            const int dest = ((b >> lane) & 1u) ? (Zt + (pos0 - zb) + r1) : (zb + (lane - r1));
-            dst[dest] = (E)xr[e];
+            for (int o = 1; o < 32; o <<= 1) {
+              const uint32_t y = __shfl_up_sync(FULL, ci, o);
+              if (lane >= o) ci += y;
+            }
+            if (lane < (1 << j)) {
+              ccnt[cls_idx(j, lane)] = v;
+              cstart[cls_idx(j, lane)] = ci - v;
+            }
           }
         }
       }
-      __syncthreads();
-      // class counts of level j+1: zeros inside each class run of level j
-      const int nk = 1 << j;
-      for (int k = tid; k < nk; k += NT) {
-        const int s = (int)cstart[cls_idx(j, k)], c = (int)ccnt[cls_idx(j, k)];
-        auto zb4 = [&](int p) -> int {
-          if (p >= cnt) return Zt;
-          const int w = p >> 5;
-          return (int)zpw[w] + __popc(~lbits[j * TW + w] & ((1u << (p & 31)) - 1u));
-        };
-        const int zc = zb4(s + c) - zb4(s);
-        ccnt[cls_idx(j + 1, k)] = (uint32_t)zc;
-        ccnt[cls_idx(j + 1, k + nk)] = (uint32_t)(c - zc);
-      }
-      __syncthreads();
-      // class starts of level j+1 (2nk <= NT classes): block exclusive scan
-      {
-        const int m = 2 * nk;
-        const int v = (tid < m) ? (int)ccnt[cls_idx(j + 1, tid)] : 0;
-        int si = v;
+      // one 64-bit word per digit: 2-bit flag (1 aggregate, 2 inclusive)
+      // above a 62-bit count; the ring is zeroed before every pass
+      const int nd = 1 << t;
+      uint64_t* const slot = P.ring + (uint64_t)(ti & P.ring_mask) * SLOT_U64;
+      constexpr uint64_t CMASK = (1ull << 62) - 1;
 #pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-          const int y = __shfl_up_sync(FULL, si, o);
-          if (lane >= o) si += y;
+      for (int i = 0; i < 8; i++) {
+        const int r = lane + 32 * i;
+        if (r < nd) st_relaxed_u64(slot + r, ((first ? 2ull : 1ull) << 62) | h[i]);
+      }
+      uint64_t acc[8];
+#pragma unroll
+      for (int i = 0; i < 8; i++) acc[i] = 0;
+      int status = 0;
+      if (!first) {
+        uint32_t pred[8];
+        uint32_t todo = 0;
+#pragma unroll
+        for (int i = 0; i < 8; i++) {
+          pred[i] = ti - 1;
+          if (lane + 32 * i < nd) todo |= 1u << i;
         }
-        if (lane == 31) s_warp[warp] = si;
-        __syncthreads();
-        int base = 0;
-        for (int w2 = 0; w2 < warp; w2++) base += s_warp[w2];
-        if (tid < m) cstart[cls_idx(j + 1, tid)] = (uint32_t)(base + si - v);
-        __syncthreads();
+        uint64_t spins = 0;
+        while (__any_sync(FULL, todo != 0)) {
+          uint64_t v[8];
+#pragma unroll
+          for (int i = 0; i < 8; i++)
+            v[i] = (todo >> i & 1u)
+                       ? ld_relaxed_u64(P.ring + (uint64_t)(pred[i] & P.ring_mask) * SLOT_U64 + lane + 32 * i)
+                       : 0ull;
+          bool waited = false;
+#pragma unroll
+          for (int i = 0; i < 8; i++) {
+            if (!(todo >> i & 1u)) continue;
+            const uint64_t st = v[i] >> 62;
+            if (st == 0) {
+              waited = true;
+              continue;
+            }
+            acc[i] += v[i] & CMASK;
+            if (st == 2) todo &= ~(1u << i);
+            else pred[i]--;
+          }
+          if (__any_sync(FULL, waited)) {
+            int ab = 0;
+            if (lane == 0) ab = (++spins > P.spin_limit) || ld_volatile_u32(P.abort_flag);
+            if (__shfl_sync(FULL, ab, 0)) {
+              status = -1;
+              break;
+            }
+            if (spins > 8) __nanosleep(64);
+          }
+        }
+        if (status == 0) {
+#pragma unroll
+          for (int i = 0; i < 8; i++) {
+            const int r = lane + 32 * i;
+            if (r < nd) st_relaxed_u64(slot + r, (2ull << 62) | (acc[i] + h[i]));
+          }
+        }
+      }
+      // exclusive counts of every level from the exclusive digit counts
+      for (int j = 8; j >= 5; j--) {
+        if (j > t) continue;
+        const int nsub = 1 << (j - 5);
+        for (int sub = 0; sub < nsub; sub++) {
+          uint64_t c = 0;
+#pragma unroll
+          for (int i = 0; i < 8; i++)
+            if ((i & (nsub - 1)) == sub) c += acc[i];
+          ex_cnt[cls_idx(j, lane + 32 * sub)] = c;
+        }
+      }
+      uint64_t a5 = 0;
+#pragma unroll
+      for (int i = 0; i < 8; i++) a5 += acc[i];
+      for (int j = 5; j >= 0; j--) {
+        if (j < 5) a5 += __shfl_down_sync(FULL, a5, 1 << j);
+        if (j < 5 && j <= t && lane < (1 << j)) ex_cnt[cls_idx(j, lane)] = a5;
+      }
+      if (lane == 0) s_stat = status;
+    } else {
+      // ---- 4 (worker warps). splits, two levels per shared-memory round --
+      int jj = 0;
+      while (jj < t) {
+        const int j = jj;
+        const bool pair = j + 1 < t;
+        const E* src = cur ? bufB : bufA;
+        E* dst = cur ? bufA : bufB;
+        const bool move = (j + (pair ? 2 : 1) < t) || (P.out != nullptr);
+        const int sh0 = P.rbits - 1 - j;
+        uint32_t* const L0 = lbits + j * TW;
+        if (pair) {
+          uint32_t* const B1p = pb1 + (j >> 1) * TW;
+          uint32_t xr[EPW], b0r[EPW], b1r[EPW];
+          uint32_t my0 = 0, my1 = 0;
+#pragma unroll
+          for (int e = 0; e < EPW; e++) {
+            const int p = wbase + e * 32 + lane;
+            const bool v = full || p < cnt;
+            const uint32_t x = v ? (uint32_t)src[p] : 0u;
+            xr[e] = x;
+            const uint32_t B0 = __ballot_sync(FULL, (x >> sh0) & 1u);
+            const uint32_t B1 = __ballot_sync(FULL, (x >> (sh0 - 1)) & 1u);
+            b0r[e] = B0;
+            b1r[e] = B1;
+            if (lane == e) {
+              my0 = B0;
+              my1 = B1;
+            }
+          }
+          // counts of the four (b_j, b_j+1) classes in iteration `lane`
+          const int vc = lane < EPW ? min(max(cnt - (wbase + lane * 32), 0), 32) : 0;
+          const int o0 = __popc(my0), o1 = __popc(my1), o11 = __popc(my0 & my1);
+          const uint32_t p01 = (uint32_t)(vc - o0 - o1 + o11) | ((uint32_t)(o0 - o11) << 16);
+          const uint32_t p23 = (uint32_t)(o1 - o11) | ((uint32_t)o11 << 16);
+          uint32_t i01 = p01, i23 = p23;
+#pragma unroll
+          for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y01 = __shfl_up_sync(FULL, i01, o);
+            const uint32_t y23 = __shfl_up_sync(FULL, i23, o);
+            if (lane >= o) {
+              i01 += y01;
+              i23 += y23;
+            }
+          }
+          const uint32_t e01 = i01 - p01, e23 = i23 - p23;
+          if (lane == 31) {
+            s_w[0][warp] = (int)(i01 & 0xffffu);
+            s_w[1][warp] = (int)(i01 >> 16);
+            s_w[2][warp] = (int)(i23 & 0xffffu);
+            s_w[3][warp] = (int)(i23 >> 16);
+          }
+          if (lane < EPW) {
+            L0[warp * EPW + lane] = my0;
+            B1p[warp * EPW + lane] = my1;
+          }
+          bar_workers();
+          int tot[4], wo[4];
+#pragma unroll
+          for (int c = 0; c < 4; c++) {
+            tot[c] = 0;
+            wo[c] = 0;
+#pragma unroll
+            for (int w2 = 0; w2 < W; w2++) {
+              const int x = s_w[c][w2];
+              tot[c] += x;
+              wo[c] += (w2 < warp) ? x : 0;
+            }
+          }
+          // ones of b_j before iteration `lane` (classes 1 and 3)
+          const int tp1 = wo[1] + (int)(e01 >> 16), tp3 = wo[3] + (int)(e23 >> 16);
+          const int Z0 = tot[0] + tot[2];  // zeros of b_j in the tile
+          if (lane < EPW) {
+            // where iteration `lane`'s elements of each (b_j, b_j+1) class go
+            btab[warp][lane][0] = wo[0] + (int)(e01 & 0xffffu);
+            btab[warp][lane][1] = tot[0] + tp1;
+            btab[warp][lane][2] = tot[0] + tot[1] + wo[2] + (int)(e23 & 0xffffu);
+            btab[warp][lane][3] = tot[0] + tot[1] + tot[2] + tp3;
+          }
+          __syncwarp();
+          if (move || !DIG) {
+            uint32_t s0 = 0, s1 = 0;
+#pragma unroll
+            for (int e = 0; e < EPW; e++) {
+              const int p = wbase + e * 32 + lane;
+              const bool v = full || p < cnt;
+              const uint32_t B0 = b0r[e], B1 = b1r[e];
+              const uint32_t bb0 = (B0 >> lane) & 1u, bb1 = (B1 >> lane) & 1u;
+              if (move) {
+                const int vcnt = full ? 32 : min(max(cnt - (wbase + e * 32), 0), 32);
+                const uint32_t Vm = vcnt >= 32 ? FULL : ((1u << vcnt) - 1u);
+                const uint32_t peers = (bb0 ? B0 : ~B0) & (bb1 ? B1 : ~B1) & Vm;
+                const int r = __popc(peers & lt);
+                if (v) dst[btab[warp][e][bb0 | (bb1 << 1)] + r] = (E)xr[e];
+              }
+              if (!DIG) {
+                // level j+1 in the order after the split on b_j alone: the
+                // b_j+1 bits of this iteration's zeros and ones of b_j
+                const int ro = __popc(B0 & lt);
+                const uint32_t seg0 =
+                    __reduce_or_sync(FULL, (v && !bb0 && bb1) ? (1u << (lane - ro)) : 0u);
+                const uint32_t seg1 = __reduce_or_sync(FULL, (bb0 && bb1) ? (1u << ro) : 0u);
+                if (lane == e) {
+                  s0 = seg0;
+                  s1 = seg1;
+                }
+              }
+            }
+            if (!DIG && lane < EPW) {
+              // placed by the lane that owns the iteration
+              const int ob = tp1 + tp3;
+              const int zb = (wbase + lane * 32) - ob;
+              if (s0) or_bits(lbits + (j + 1) * TW, zb, s0);
+              if (s1) or_bits(lbits + (j + 1) * TW, Z0 + ob, s1);
+            }
+          }
+          bar_workers();
+        } else {
+          // a single level (the last one of an odd t)
+          uint32_t xr[EPW], br[EPW];
+          uint32_t my0 = 0;
+#pragma unroll
+          for (int e = 0; e < EPW; e++) {
+            const int p = wbase + e * 32 + lane;
+            const bool v = full || p < cnt;
+            const uint32_t x = v ? (uint32_t)src[p] : 0u;
+            xr[e] = x;
+            const uint32_t B0 = __ballot_sync(FULL, (x >> sh0) & 1u);
+            br[e] = B0;
+            if (lane == e) my0 = B0;
+          }
+          const int o0 = __popc(my0);
+          int oi = o0;
+#pragma unroll
+          for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(FULL, oi, o);
+            if (lane >= o) oi += y;
+          }
+          if (lane == 31) s_w[0][warp] = oi;
+          if (lane < EPW) L0[warp * EPW + lane] = my0;
+          bar_workers();
+          int wo = 0, T0 = 0;
+#pragma unroll
+          for (int w2 = 0; w2 < W; w2++) {
+            const int x = s_w[0][w2];
+            wo += (w2 < warp) ? x : 0;
+            T0 += x;
+          }
+          const int ope = wo + oi - o0;  // ones before iteration `lane`
+          const int Z0 = cnt - T0;
+          if (move) {
+#pragma unroll
+            for (int e = 0; e < EPW; e++) {
+              const int ob = __shfl_sync(FULL, ope, e);
+              const int p = wbase + e * 32 + lane;
+              if (full || p < cnt) {
+                const uint32_t B0 = br[e];
+                const int r1 = __popc(B0 & lt);
+                const int pos0 = wbase + e * 32;
+                const int dest = ((B0 >> lane) & 1u) ? (Z0 + ob + r1) : (pos0 - ob + (lane - r1));
+                dst[dest] = (E)xr[e];
+              }
+            }
+          }
+          bar_workers();
+        }
+        if (move) cur ^= 1;
+        jj += pair ? 2 : 1;
       }
     }
+    __syncthreads();
+    if (s_stat < 0) {
+      if (tid == 0) {
+        atomicOr(P.err, ERR_TIMEOUT);
+        atomicExch(P.abort_flag, 1u);
+      }
+      return;
+    }
+    // the final element order is the same for every worker warp
+    {
+      int moves = 0;
+      for (int j = 0; j < t; j += 2) {
+        const bool pair = j + 1 < t;
+        if ((j + (pair ? 2 : 1) < t) || (P.out != nullptr)) moves++;
+      }
+      cur = moves & 1;
+    }
 
-    // ---- 3. own tails of every emitted level ------------------------------
+    // ---- 5. level bitmaps: whole words stored, shared words ORed ----------
     auto emitted = [&](int j) -> bool { return !DIG || (((P.a + j) & 1) == 0); };
     // 64 local bits of level j starting at local bit position bp
     auto get64 = [&](int j, int bp) -> uint64_t {
@@ -292,218 +572,64 @@ __global__ void __launch_bounds__(NT) k_pass(const PassParams P) {
       const int e = bp >> 1;
       const uint32_t b0 = get32<TW>(lbits + j * TW, e);
       if (P.a + j + 1 < P.L) {
-        const uint32_t b1 = get32<TW>(lplane + (j >> 1) * TW, e);
+        const uint32_t b1 = get32<TW>(pb1 + (j >> 1) * TW, e);
         return (spread32(b0) << 1) | spread32(b1);
       }
       return spread32(b0);
     };
-    for (int i = tid; i < ntl; i += NT) {
-      int j = 31 - __clz(i + 1);
-      const int k = i + 1 - (1 << j);
-      uint64_t tl = 0;
-      if (emitted(j)) {
-        const int c = (int)ccnt[i] * bpe;
-        if (c > 0) {
-          const int end = ((int)cstart[i] + (int)ccnt[i]) * bpe;
-          tl = get64(j, end - 64);
-          if (c < 64) tl &= ~0ull << (64 - c);
-        }
-      }
-      (void)k;
-      own_tail[i] = tl;
-    }
-    __syncthreads();
-
-    // ---- 4. publish the aggregate, look back, publish the inclusive state --
-    uint64_t* const slot = P.ring + (uint64_t)(ti & P.ring_mask) * SLOT_U64;
-    uint64_t* const agg = slot + 8;
-    uint64_t* const inc = agg + SLOT_STATE;
-    const uint64_t myseq = P.seq_base + ti;
-    {
-      uint64_t* dstate = first ? inc : agg;
-      for (int i = tid; i < ncl; i += NT) dstate[i] = ccnt[i];
-      for (int i = tid; i < ntl; i += NT) dstate[NCLS + i] = own_tail[i];
-      for (int i = tid; i < ncl; i += NT) ex_cnt[i] = 0;
-      for (int i = tid; i < ntl; i += NT) ex_tail[i] = 0;
-      __threadfence();
-      __syncthreads();
-      if (tid == 0) st_release_u64(slot, (myseq << 2) | (first ? 2u : 1u));
-    }
-    if (!first) {
-      // Windowed look-back: warp 0 polls the flags of the 32 nearest
-      // predecessors at once; the block then folds the whole window (up to the
-      // nearest inclusive state) into the exclusive state in one sweep.
-      uint32_t base = ti;
-      for (;;) {
-        if (warp == 0) {
-          const int64_t p = (int64_t)base - 1 - lane;
-          const bool exists = p >= 0;
-          const uint64_t* f = P.ring + (uint64_t)((uint32_t)p & P.ring_mask) * SLOT_U64;
-          const uint64_t want = P.seq_base + (uint64_t)p;
-          const uint32_t exist_m = __ballot_sync(FULL, exists);
-          uint64_t spins = 0;
-          int nwin = -1, stop = 0;
-          for (;;) {
-            int st = 0;
-            if (exists) {
-              const uint64_t v = ld_acquire_u64(f);
-              if ((v >> 2) == want) st = (int)(v & 3u);
-            }
-            const uint32_t ready = __ballot_sync(FULL, st != 0);
-            const uint32_t incl = __ballot_sync(FULL, st == 2);
-            uint32_t need = exist_m;
-            if (incl) {
-              const int fl = __ffs(incl) - 1;
-              need = fl == 31 ? FULL : ((2u << fl) - 1u);
-            }
-            if ((ready & need) == need) {
-              nwin = __popc(need);
-              stop = incl != 0;
-              break;
-            }
-            int ab = 0;
-            if (lane == 0) ab = (++spins > P.spin_limit) || ld_volatile_u32(P.abort_flag);
-            if (__shfl_sync(FULL, ab, 0)) break;
-            if (spins > 8) __nanosleep(64);
-          }
-          if (lane == 0) {
-            s_stat = nwin;
-            s_stop = stop;
-          }
-        }
-        __syncthreads();
-        const int nwin = s_stat, stop = s_stop;
-        if (nwin < 0) {
-          if (tid == 0) {
-            atomicOr(P.err, ERR_TIMEOUT);
-            atomicExch(P.abort_flag, 1u);
-          }
-          return;
-        }
-        for (int i = tid; i < ncl; i += NT) {
-          uint64_t c = ex_cnt[i];
-          uint64_t tl = i < ntl ? ex_tail[i] : 0;
-          for (int l = 0; l < nwin; l++) {
-            const uint64_t* ps = P.ring + (uint64_t)((base - 1 - l) & P.ring_mask) * SLOT_U64 + 8 +
-                                 ((stop && l == nwin - 1) ? SLOT_STATE : 0);
-            if (i < ntl) tl = tail_combine(__ldcg(ps + NCLS + i), tl, c * bpe);
-            c += __ldcg(ps + i);
-          }
-          ex_cnt[i] = c;
-          if (i < ntl) ex_tail[i] = tl;
-        }
-        __syncthreads();
-        if (stop) break;
-        base -= 32;
-      }
-      for (int i = tid; i < ncl; i += NT) {
-        if (i < ntl) inc[NCLS + i] = tail_combine(ex_tail[i], own_tail[i], (uint64_t)ccnt[i] * bpe);
-        inc[i] = ex_cnt[i] + ccnt[i];
-      }
-      __threadfence();
-      __syncthreads();
-      if (tid == 0) st_release_u64(slot, (myseq << 2) | 2u);
-    }
-
-    // ---- 5. level bitmaps: each word stored once by the tile holding its
-    //         last bit of the class; words shared by two classes are ORed ---
-    // class ranges of every emitted (level, class), loaded once
-    for (int i = tid; i < ntl; i += NT) {
-      const int j = 31 - __clz(i + 1);
+    // words of every (level, class) of this tile, one flattened loop
+    int nw = 0;
+    if (tid < ntl) {
+      const int j = 31 - __clz(tid + 1);
       uint64_t cs = 0, ce = 0;
       bool dead = true;
-      if (emitted(j) && ccnt[i]) class_range(P, j, (uint32_t)(i + 1 - (1 << j)), node, cs, ce, dead);
-      cls_cs[i] = dead ? ~0ull : cs;
-      cls_ce[i] = ce;
+      if (emitted(j) && ccnt[tid]) class_range(P, j, (uint32_t)(tid + 1 - (1 << j)), node, cs, ce, dead);
+      cls_cs[tid] = dead ? ~0ull : cs;
+      cls_ce[tid] = ce;
+      if (!dead) {
+        const uint64_t G0 = (cs + ex_cnt[tid]) * bpe;
+        const uint64_t G1 = G0 + (uint64_t)ccnt[tid] * bpe;
+        nw = (int)(((G1 - 1) >> 6) - (G0 >> 6) + 1);
+      }
     }
+    int wtot;
+    const int wex = block_scan(nw, wtot);
+    if (tid < ntl) wst[tid] = wex;
     __syncthreads();
-    for (int j = 0; j < t; j++) {
-      if (!emitted(j)) continue;
+    for (int x = tid; x < wtot; x += NB) {
+      int lo = 0, hi = ntl - 1;
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (wst[mid] <= x) lo = mid;
+        else hi = mid - 1;
+      }
+      const int ci = lo;
+      const int j = 31 - __clz(ci + 1);
       const int lo_ = DIG ? ((P.a + j) >> 1) : (P.a + j);
       const uint64_t nlb = P.lvl_len[lo_] * (uint64_t)bpe;
       uint64_t* const lb = P.bits + P.lvl_off[lo_];
-      const int nk = 1 << j;
-      // words owned by this tile in class k: [first_w, last_w]
-      auto owned_range = [&](int k, uint64_t& fw, uint64_t& lw) -> bool {
-        const int ci = cls_idx(j, k);
-        const uint64_t cs = cls_cs[ci];
-        if (cs == ~0ull) return false;
-        const uint64_t G0 = (cs + ex_cnt[ci]) * bpe, G1 = G0 + (uint64_t)ccnt[ci] * bpe;
-        const uint64_t CE = cls_ce[ci] * bpe;
-        const uint64_t w0 = G0 >> 6, w1 = (G1 - 1) >> 6;
-        const bool own0 = (w0 * 64 + 63 < G1) || (CE == G1);
-        const bool own1 = (w1 * 64 + 63 == G1 - 1) || (CE == G1);
-        fw = own0 ? w0 : w0 + 1;
-        lw = (w1 == w0) ? (own0 ? w0 : w0) : (own1 ? w1 : w1 - 1);
-        if (w1 == w0 && !own0) return false;
-        return lw + 1 > fw;
-      };
-      int nw = 0;
-      if (tid < nk) {
-        uint64_t fw, lw;
-        if (owned_range(tid, fw, lw)) nw = (int)(lw - fw + 1);
-      }
-      // exclusive scan of the word counts over the classes
-      int si = nw;
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const int y = __shfl_up_sync(FULL, si, o);
-        if (lane >= o) si += y;
-      }
-      if (lane == 31) s_warp[warp] = si;
-      __syncthreads();
-      int wbase = 0, wtot = 0;
-#pragma unroll
-      for (int w2 = 0; w2 < W; w2++) {
-        const int v2 = s_warp[w2];
-        wbase += (w2 < warp) ? v2 : 0;
-        wtot += v2;
-      }
-      if (tid < nk) wst[tid] = wbase + si - nw;
-      __syncthreads();
-      for (int x = tid; x < wtot; x += NT) {
-        // class of word x: last k with wst[k] <= x
-        int lo = 0, hi = nk - 1;
-        while (lo < hi) {
-          const int mid = (lo + hi + 1) >> 1;
-          if (wst[mid] <= x) lo = mid;
-          else hi = mid - 1;
-        }
-        const int k = lo;
-        const int ci = cls_idx(j, k);
-        uint64_t fw, lw;
-        owned_range(k, fw, lw);
-        const uint64_t w = fw + (uint64_t)(x - wst[k]);
-        const uint64_t cs = cls_cs[ci];
-        const uint64_t G0 = (cs + ex_cnt[ci]) * bpe, G1 = G0 + (uint64_t)ccnt[ci] * bpe;
-        const uint64_t CS = cs * bpe, CE = cls_ce[ci] * bpe;
-        const int LS = (int)cstart[ci] * bpe;
-        const uint64_t wb = w << 6;
-        const uint64_t lo2 = wb > G0 ? wb : G0;
-        const uint64_t hi2 = (wb + 64 < G1) ? wb + 64 : G1;
-        uint64_t v = get64(j, LS + (int)(lo2 - G0));
-        const int nb = (int)(hi2 - lo2);
-        if (nb < 64) v &= (1ull << nb) - 1ull;
-        v <<= (int)(lo2 - wb);
-        if (lo2 == G0) {
-          const uint64_t cl = wb > CS ? wb : CS;
-          const int nc = (int)(G0 - cl);
-          if (nc > 0) v |= (ex_tail[ci] >> (64 - nc)) << (int)(G0 - (uint64_t)nc - wb);
-        }
-        const bool mixed = (wb < CS) || (CE < wb + 64 && CE < nlb);
-        if (mixed) atomicOr((unsigned long long*)(lb + w), (unsigned long long)v);
-        else lb[w] = v;
-      }
-      __syncthreads();
+      const uint64_t G0 = (cls_cs[ci] + ex_cnt[ci]) * bpe;
+      const uint64_t G1 = G0 + (uint64_t)ccnt[ci] * bpe;
+      const uint64_t w = (G0 >> 6) + (uint64_t)(x - wst[ci]);
+      const uint64_t wb = w << 6;
+      const uint64_t lo2 = wb > G0 ? wb : G0;
+      const uint64_t hi2 = (wb + 64 < G1) ? wb + 64 : G1;
+      uint64_t v = get64(j, (int)cstart[ci] * bpe + (int)(lo2 - G0));
+      const int nb = (int)(hi2 - lo2);
+      if (nb < 64) v &= (1ull << nb) - 1ull;
+      v <<= (int)(lo2 - wb);
+      const uint64_t wend = (wb + 64 < nlb) ? wb + 64 : nlb;
+      if (G0 <= wb && G1 >= wend) lb[w] = v;
+      else atomicOr((unsigned long long*)(lb + w), (unsigned long long)v);
     }
+    __syncthreads();
 
     // ---- 6. scatter T_{a+t}, narrowed ------------------------------------
     if (P.out) {
-      const E* fin = (t & 1) ? bufB : bufA;
-      __syncthreads();  // own_tail (aliased by sbase) no longer read
+      const E* fin = cur ? bufB : bufA;
       if (tid < 8) s_dead[tid] = 0;
       __syncthreads();
-      for (int r = tid; r < (1 << t); r += NT) {
+      for (int r = tid; r < (1 << t); r += NB) {
         uint64_t cs, ce;
         bool dead;
         class_range(P, t, (uint32_t)r, node, cs, ce, dead);
@@ -517,7 +643,7 @@ __global__ void __launch_bounds__(NT) k_pass(const PassParams P) {
       const uint32_t mask = nb >= 32 ? 0xffffffffu : ((1u << nb) - 1u);
       const uint32_t rmask = (1u << t) - 1u;
       const int rsh = 32 - P.rbits;
-      for (int p = tid; p < cnt; p += NT) {
+      for (int p = tid; p < cnt; p += NB) {
         const uint32_t x = fin[p];
         const uint32_t r = (__brev(x) >> rsh) & rmask;
         if (!((s_dead[r >> 5] >> (r & 31)) & 1u)) store_elem(P.out, P.out_w, sbase[r] + p, x & mask);

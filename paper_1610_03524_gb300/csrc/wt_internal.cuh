@@ -27,10 +27,9 @@ struct TileDesc {
   uint32_t pad;
 };
 
-// Look-back ring slot: flag word followed by the aggregate and the
-// inclusive state (class counts tree, then tails).
-constexpr int SLOT_STATE = NCLS + NTAIL;       // u64 per state
-constexpr int SLOT_U64 = 8 + 2 * SLOT_STATE;   // flag padded to 64 bytes
+// Look-back ring slot: one word per digit value (flag in the top 2 bits,
+// count below), zeroed before every pass.
+constexpr int SLOT_U64 = 1 << TAU_MAX;
 
 struct PassParams {
   // input sequence T_a (elements hold the rbits = L - a low bits still needed)
@@ -84,6 +83,16 @@ __device__ __forceinline__ void st_release_u64(uint64_t* p, uint64_t v) {
   asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 
+__device__ __forceinline__ uint64_t ld_relaxed_u64(const uint64_t* p) {
+  uint64_t v;
+  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ void st_relaxed_u64(uint64_t* p, uint64_t v) {
+  asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
 __device__ __forceinline__ uint32_t ld_volatile_u32(const uint32_t* p) {
   return *(const volatile uint32_t*)p;
 }
@@ -94,13 +103,5 @@ __device__ __forceinline__ uint32_t lanemask_lt() {
   return m;
 }
 
-// Combine the last-64-bit tails of two adjacent bit streams A (earlier) and B:
-// a tail keeps the stream's last bits at the top (bit 63 = last bit) and
-// zeros below them.  nbB = length of B in bits.
-__device__ __forceinline__ uint64_t tail_combine(uint64_t A, uint64_t B, uint64_t nbB) {
-  if (nbB >= 64) return B;
-  if (nbB == 0) return A;
-  return (A >> nbB) | B;
-}
 
 }  // namespace wtk
