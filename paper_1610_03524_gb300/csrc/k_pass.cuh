@@ -385,7 +385,7 @@ __global__ void __launch_bounds__(NT + 32, 3) k_pass(const PassParams P) {
         uint32_t* const L0 = lbits + j * TW;
         if (pair) {
           uint32_t* const B1p = pb1 + (j >> 1) * TW;
-          uint32_t xr[EPW], b0r[EPW], b1r[EPW];
+          uint32_t xr[EPW];
           uint32_t my0 = 0, my1 = 0;
 #pragma unroll
           for (int e = 0; e < EPW; e++) {
@@ -395,8 +395,6 @@ __global__ void __launch_bounds__(NT + 32, 3) k_pass(const PassParams P) {
             xr[e] = x;
             const uint32_t B0 = __ballot_sync(FULL, (x >> sh0) & 1u);
             const uint32_t B1 = __ballot_sync(FULL, (x >> (sh0 - 1)) & 1u);
-            b0r[e] = B0;
-            b1r[e] = B1;
             if (lane == e) {
               my0 = B0;
               my1 = B1;
@@ -458,7 +456,8 @@ __global__ void __launch_bounds__(NT + 32, 3) k_pass(const PassParams P) {
             for (int e = 0; e < EPW; e++) {
               const int p = wbase + e * 32 + lane;
               const bool v = full || p < cnt;
-              const uint32_t B0 = b0r[e], B1 = b1r[e];
+              // this iteration's ballot words, kept in the level planes
+              const uint32_t B0 = L0[warp * EPW + e], B1 = B1p[warp * EPW + e];
               const uint32_t bb0 = (B0 >> lane) & 1u, bb1 = (B1 >> lane) & 1u;
               if (move) {
                 const int vcnt = full ? 32 : min(max(cnt - (wbase + e * 32), 0), 32);
