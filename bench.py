@@ -51,6 +51,17 @@ def parse():
     ap.add_argument("--cpu-log2n", type=int, default=24, help="oracle sample length 2^k")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle baseline leg")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--workload", choices=["wm", "batch", "serve", "genome", "huff"],
+                    default="wm",
+                    help="wm: the headline wavelet-matrix build (default); batch: 4096 "
+                         "wavelet matrices, batched vs plain launches; serve: Poisson "
+                         "builds + query batches through the serving loop; genome: "
+                         "binary and 4-ary trees of a 2^32-symbol DNA-like text; huff: "
+                         "Huffman-shaped and balanced trees over a 2^20 alphabet")
+    ap.add_argument("--lam", type=float, default=20.0, help="serve: builds per second")
+    ap.add_argument("--qlam", type=float, default=50.0,
+                    help="serve: query batches (2^16 queries) per second")
+    ap.add_argument("--duration", type=float, default=10.0, help="serve: seconds of arrivals")
     return ap.parse_args()
 
 
@@ -65,7 +76,7 @@ def workload_config(n_log2):
     return {"workload": f"wavelet matrix build n=2^{n_log2} uint16 sigma=2^16 (16 levels) "
                         "Zipf(1.1) + rank directories + select samples",
             "n": 1 << n_log2, "sigma": SIGMA, "levels": 16, "width_bytes": 2, "tau": 8,
-            "tile_symbols": 8192, "l2": "inputs (2 GiB) larger than L2; no flush needed",
+            "tile_symbols": 4096, "l2": "inputs (2 GiB) larger than L2; no flush needed",
             "seed": SEED}
 
 
@@ -360,8 +371,264 @@ def run_native(args):
     return 0
 
 
+# --------------------------------------------------------------------------
+# the other workloads (one JSON line each; not the headline)
+# --------------------------------------------------------------------------
+def _line(args, metric, value, unit, ms, cfg, **kw):
+    d = {"metric": metric, "value": value, "unit": unit, "n_gpus": 1, "steps": args.steps,
+         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+         "vs_baseline": None, "dtype": kw.pop("dtype", "u16"), "data": "synthetic",
+         "config": cfg}
+    d.update(kw)
+    print(json.dumps(d), flush=True)
+
+
+def _batch_workload(m=4096):
+    """The batched configuration: lengths log-uniform in [2^10, 2^24] (total
+    capped at 2^31), sigma from {4, 256, 4096, 65536}, uniform or Zipf(1.1),
+    uint16; one pinned host array with 16-byte aligned sequence starts."""
+    import numpy as np
+    import torch
+    from concurrent.futures import ThreadPoolExecutor
+    import synth
+    ln, sig, zf, sd, total = synth.batch_plan(synth.SEED_BASE + 5, m, 10, 24, 1 << 31)
+    offs = np.zeros(m + 1, np.int64)
+    for i in range(m):
+        offs[i + 1] = offs[i] + (int(ln[i]) + 7) // 8 * 8
+    pin = torch.empty(int(offs[-1]), dtype=torch.int16).pin_memory()
+    base = pin.data_ptr()
+
+    def gen(i):
+        n, s = int(ln[i]), int(sig[i])
+        if zf[i]:
+            synth.zipf(int(sd[i]), n, s, 1.1, 2, addr=base + 2 * int(offs[i]))
+        else:
+            synth.uniform(int(sd[i]), n, s, 2, addr=base + 2 * int(offs[i]))
+
+    with ThreadPoolExecutor(8) as ex:
+        list(ex.map(gen, range(m)))
+    return pin, offs, [int(x) for x in ln], [int(x) for x in sig], zf, int(total)
+
+
+def run_batch(args, wt):
+    import numpy as np
+    import torch
+    pin, offs, ln, sig, zf, total = _batch_workload()
+    m = len(ln)
+    d = pin.to("cuda")
+    seqs = [d[int(offs[i]):int(offs[i]) + ln[i]] for i in range(m)]
+    torch.cuda.synchronize()
+
+    def timed(fn, reps):
+        out = []
+        for _ in range(reps):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            hs = fn()
+            torch.cuda.synchronize()
+            out.append(time.perf_counter() - t0)
+            for h in hs:
+                h.sync()
+                h.free()
+        return out
+
+    batched = lambda: wt.wm_batch_build(seqs, sig)
+    plain = lambda: [wt.wm_build(seqs[i], sig[i]) for i in range(m)]
+    timed(batched, args.warmup)
+    sampler = ClockSampler(0)
+    sampler.start()
+    wt.prof_enable(True)
+    tb = timed(batched, args.steps)
+    launches, _, _ = wt.prof_read()
+    wt.prof_enable(False)
+    clocks = sampler.stop()
+    timed(plain, 1)
+    wt.prof_enable(True)
+    tp = timed(plain, max(1, min(args.steps, 3)))
+    plain_launches, _, _ = wt.prof_read()
+    wt.prof_enable(False)
+    hs = wt.wm_batch_build(seqs, sig)
+    sl = sum(h.symbol_levels() for h in hs)
+    for h in hs:
+        h.free()
+    mb, mp = statistics.median(tb), statistics.median(tp)
+    # end to end: pinned host -> device copy of every sequence, batched build,
+    # one handle's zero counts read back
+    e2e = None
+    if not args.no_e2e:
+        lib = wt.load_library()
+        view = wt.ExportView()
+        dbuf = torch.empty_like(d)
+        k = max(1, min(args.steps, 3))
+        te = []
+        for _ in range(k):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            dbuf.copy_(pin, non_blocking=True)
+            hs = wt.wm_batch_build([dbuf[int(offs[i]):int(offs[i]) + ln[i]] for i in range(m)], sig)
+            # waits for the batch and copies sequence 0's per-level zero counts
+            wt._check(lib.wt_export(hs[0].raw, ctypes.byref(view)), "wt_export")
+            te.append(time.perf_counter() - t0)
+            for h in hs:
+                h.free()
+        e2e = {"value": sl / statistics.median(te) / 1e9, "unit": UNIT,
+               "h2d_bytes_per_step": 2 * int(offs[-1]), "d2h_bytes_per_step": 8 * view.levels,
+               "steps": k}
+    cfg = {"workload": "4096 wavelet matrices with directories, lengths log-uniform in "
+                       "[2^10, 2^24] (total 2^31), sigma from {4,256,4096,65536}, uniform or "
+                       "Zipf(1.1), uint16: one batched build vs 4096 plain builds",
+           "sequences": m, "symbols": total, "symbol_levels": sl,
+           "l2": "inputs (4 GiB) larger than L2; no flush needed"}
+    _line(args, "Gsymbol-levels/s batched build (wall clock, inputs resident)", sl / mb / 1e9,
+          UNIT, 1e3 * mb, cfg, plain={"value": sl / mp / 1e9, "ms_per_step": 1e3 * mp,
+                                      "gpu_launches": plain_launches // len(tp)},
+          batched_over_plain=mp / mb, gpu_launches=launches // len(tb), clocks=clocks, e2e=e2e,
+          min_ms=1e3 * min(tb), max_ms=1e3 * max(tb))
+
+
+def run_serve(args, wt):
+    import numpy as np
+    pin, offs, ln, sig, zf, total = _batch_workload()
+    host = pin.numpy().view(np.uint16)
+    rng = np.random.Generator(np.random.PCG64(synth_seed(5) ^ 0x5e7e))
+    srv = wt.Server(budget_bytes=64 << 30)
+    # arrivals: builds (Poisson, lam/s, sequences in plan order) and query
+    # batches (Poisson, qlam/s, 2^16 uniform (structure, op, argument) over the
+    # structures already submitted)
+    D = args.duration
+    tb_arr = np.cumsum(rng.exponential(1.0 / args.lam, size=int(args.lam * D * 2) + 10))
+    tq_arr = np.cumsum(rng.exponential(1.0 / args.qlam, size=int(args.qlam * D * 2) + 10))
+    events = sorted([(t, 0) for t in tb_arr if t < D] + [(t, 1) for t in tq_arr if t < D])
+    Q = 1 << 16
+    builds, queries, sub = [], [], []
+    nb = 0
+    t0 = time.perf_counter()
+    for t, kind in events:
+        while time.perf_counter() - t0 < t:
+            time.sleep(0.0005)
+        if kind == 0 and nb < len(ln):
+            i = nb
+            nb += 1
+            sid = srv.submit_build(host[int(offs[i]):int(offs[i]) + ln[i]], sig[i])
+            builds.append(sid)
+            sub.append((sid, ln[i], sig[i]))
+        elif kind == 1 and sub:
+            k = rng.integers(0, len(sub), size=Q)
+            ns = np.array([x[1] for x in sub], np.uint64)[k]
+            ss = np.array([x[2] for x in sub], np.uint32)[k]
+            sid = np.array([x[0] for x in sub], np.uint64)[k]
+            op = rng.integers(0, 3, size=Q).astype(np.uint8)
+            c = (rng.random(Q) * ss).astype(np.uint32)
+            x = (rng.random(Q) * ns).astype(np.uint64)
+            x[op == 2] += 1  # select takes k >= 1
+            queries.append(srv.submit_queries(sid, op, c, x))
+    lat_b, lat_q, done_q = [], [], []
+    for r in queries:
+        st, a, b, _ = srv.poll(r, 0)
+        lat_q.append((b - a) * 1e-6)
+        done_q.append(b)
+    for r in builds:
+        st, a, b, _ = srv.poll(r)
+        lat_b.append((b - a) * 1e-6)
+    wall = time.perf_counter() - t0
+    stats = srv.stats()
+    srv.close()
+    pct = lambda v, p: float(np.percentile(v, p)) if v else None
+    qps = len(queries) * Q / wall
+    cfg = {"workload": f"serving loop: wavelet-matrix builds of the batched configuration's "
+                       f"sequences arriving Poisson at {args.lam}/s, query batches of 2^16 "
+                       f"uniform (structure, op, argument) at {args.qlam}/s, {D} s of arrivals, "
+                       f"64 GB admission budget",
+           "builds": len(builds), "query_batches": len(queries), "queries_per_batch": Q}
+    _line(args, "queries/s through the serving loop (arrival -> answers on host)", qps,
+          "queries/s", 1e3 * wall, cfg,
+          latency_ms={"query_p50": pct(lat_q, 50), "query_p99": pct(lat_q, 99),
+                      "build_p50": pct(lat_b, 50), "build_p99": pct(lat_b, 99)},
+          server=stats)
+
+
+def synth_seed(k):
+    import synth
+    return synth.SEED_BASE + k
+
+
+def run_tree(args, wt):
+    """genome: binary WT and 4-ary WT of n = 2^32 uint8 over {A,C,G,T} plus a
+    sentinel (sigma 5); huff: Huffman-shaped and balanced WT of n = 2^28 uint32
+    Zipf(1.0) over 2^20 symbols."""
+    import numpy as np
+    import torch
+    import synth
+    if args.workload == "genome":
+        n = 1 << 32
+        pin = torch.empty(n, dtype=torch.uint8).pin_memory()
+        synth.genome(synth_seed(3), n, addr=pin.data_ptr())
+        sigma, builds = 5, [("wt", wt.wt_build), ("multiary", wt.multiary_build)]
+        desc = "n=2^32 uint8 DNA-like text (order-3 chain, bursts, sentinel), sigma=5"
+    else:
+        n = 1 << 28
+        pin = torch.empty(n, dtype=torch.int32).pin_memory()
+        synth.zipf(synth_seed(4), n, 1 << 20, 1.0, 4, addr=pin.data_ptr())
+        sigma, builds = 1 << 20, [("huffman", wt.huff_wt_build), ("wt", wt.wt_build)]
+        desc = "n=2^28 uint32 Zipf(1.0) over 2^20 symbols"
+    d = pin.to("cuda")
+    torch.cuda.synchronize()
+    res = {}
+    for name, fn in builds:
+        for _ in range(args.warmup):
+            h = fn(d, sigma)
+            h.sync()
+            h.free()
+        wt.prof_enable(True)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        hs = [fn(d, sigma) for _ in range(args.steps)]
+        e1.record()
+        torch.cuda.synchronize()
+        la, pl, pms = wt.prof_read()
+        wt.prof_enable(False)
+        ms = e0.elapsed_time(e1) / args.steps
+        sl = hs[0].symbol_levels()
+        for h in hs:
+            h.sync()
+            h.free()
+        res[name] = {"ms_per_build": ms, "symbol_levels": sl, "gsl_per_s": sl / ms / 1e6,
+                     "pass_ms": pms / args.steps, "gpu_launches": la // args.steps}
+    first = builds[0][0]
+    cfg = {"workload": f"{' and '.join(b[0] for b in builds)} wavelet trees with directories, "
+                       f"{desc}", "n": n, "sigma": sigma}
+    _line(args, f"Gsymbol-levels/s ({first} build)", res[first]["gsl_per_s"], UNIT,
+          res[first]["ms_per_build"], cfg, dtype="u8" if args.workload == "genome" else "u32",
+          builds=res, gpu_launches=res[first]["gpu_launches"])
+
+
+def run_other(args):
+    ws, rank, local = dist_env()
+    if args.impl == "reference":
+        if rank == 0:
+            print(json.dumps({"impl": "reference", "unavailable":
+                              "the oracle arm is timed on the headline workload only"}))
+        return 0
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1610_03524_gb300 as wt
+    torch.cuda.set_device(local)
+    if args.workload == "batch":
+        run_batch(args, wt)
+    elif args.workload == "serve":
+        run_serve(args, wt)
+    else:
+        run_tree(args, wt)
+    return 0
+
+
 def main():
     args = parse()
+    if args.workload != "wm":
+        return run_other(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_native(args)

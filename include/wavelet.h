@@ -156,6 +156,104 @@ wt_status rs_build(const uint64_t* d_bits, uint64_t nbits, const wt_build_opts* 
 wt_status rs_dir_build_static(const uint64_t* d_bits, uint64_t nbits, uint64_t* d_dir,
                               uint64_t* d_samp0, uint64_t* d_samp1, wt_stream stream);
 
+/* One sequence of a batched build. */
+typedef struct {
+  const void* d_seq;     /* device, read-only, borrowed for the call */
+  uint64_t n;
+  uint32_t sigma;
+  uint32_t width_bytes;  /* 1, 2 or 4 */
+} wt_batch_item;
+
+/* Wavelet matrices of m sequences, with directories, built by one set of
+ * launches (Section 4.2's domain decomposition applied across sequences:
+ * the tiles of all sequences form one work list of a persistent kernel per
+ * pass; class counts are chained only between tiles of one sequence).
+ * outs[i] receives the handle of items[i], exactly the structure wm_build
+ * returns for it; the m handles share one device allocation, released when
+ * the last of them is freed.  opts->tau == 0 takes each sequence's levels
+ * per pass from the autotuner's table (8 when not tuned).  A symbol >= sigma
+ * is reported on that sequence's handle only; a device wait that ran out is
+ * reported on every handle of the batch.  On error every outs[i] is NULL. */
+wt_status wm_batch_build(const wt_batch_item* items, uint32_t m, const wt_build_opts* opts,
+                         wt_stream stream, wt_handle* outs);
+
+/* Autotuner for the levels per pass tau (Section 4.2: fewer, wider passes
+ * against more work per pass).  Times wavelet-matrix builds of d_seq
+ * (without directories; one untimed and the best of two timed builds) for
+ * tau = 1 .. min(8, L), writes the fastest to *best_tau and the times to
+ * ms_out[tau-1] (ms_out may be NULL; 0 where not tried), and records it for
+ * every later wm_build / wm_batch_build with opts->tau == 0 of a sequence
+ * with the same L and ceil(log2 n).  Synchronises the stream. */
+wt_status wm_autotune(const void* d_seq, uint64_t n, uint32_t sigma, uint32_t width_bytes,
+                      wt_stream stream, uint32_t* best_tau, float* ms_out);
+/* Forgets every recorded tau. */
+void wm_autotune_clear(void);
+
+/* Queries over several structures in one launch: query i applies d_op[i]
+ * (0 access, 1 rank, 2 select) with d_c[i] and d_x[i] (i or k) to
+ * hs[d_sid[i]].  d_sid[i] >= nh or d_op[i] > 2 yields UINT64_MAX in that
+ * slot; otherwise each slot is what wt_access / wt_rank / wt_select return
+ * for it.  d_* are device arrays of q entries owned by the caller. */
+wt_status wt_query_multi(const wt_handle* hs, uint32_t nh, const uint32_t* d_sid,
+                         const uint8_t* d_op, const uint32_t* d_c, const uint64_t* d_x,
+                         uint64_t q, uint64_t* d_out, wt_stream stream);
+
+/* Serving loop (no counterpart in the paper): builds and query batches
+ * submitted from any thread are served continuously by two worker threads
+ * of the library on their own streams.  The build worker admits pending
+ * builds in arrival order while the device bytes they need fit in
+ * budget_bytes (structures kept plus the running builds' inputs and
+ * workspace), and builds every admitted sequence with one wm_batch_build.
+ * The query worker gathers every pending query request whose structures are
+ * built into one wt_query_multi launch.  A build's request id is also the id
+ * of its structure; query requests name structures by those ids.
+ * Latency of a request = from its submission to its results in host
+ * memory. */
+typedef struct wt_server_s* wt_server;
+typedef struct {
+  uint64_t budget_bytes;       /* > 0 */
+  uint32_t max_batch_builds;   /* sequences per batched build (0 = 4096) */
+  uint32_t max_batch_queries;  /* queries per launch, whole requests (0 = 2^22) */
+} wt_server_opts;
+typedef struct {
+  wt_status status;
+  uint32_t kind;               /* 1 build, 2 queries */
+  uint64_t submit_ns, done_ns; /* steady-clock nanoseconds */
+} wt_request_info;
+typedef struct {
+  uint64_t used_bytes, budget_bytes, build_batches, query_launches;
+  uint64_t pending_builds, pending_queries, structures;
+} wt_server_stats_t;
+
+wt_status wt_server_create(const wt_server_opts* opts, wt_server* out);
+/* Wavelet matrix of the host sequence h_seq (copied before returning).
+ * *req = request id = structure id.  A build whose own need exceeds the
+ * budget ends with WT_ERR_NO_MEMORY; others wait for memory. */
+wt_status wt_server_submit_build(wt_server s, const void* h_seq, uint64_t n, uint32_t sigma,
+                                 uint32_t width_bytes, uint64_t* req);
+/* q queries on host arrays (copied before returning): structure id, op
+ * (0 access, 1 rank, 2 select), c, i or k.  A query naming an unknown,
+ * failed or released structure yields UINT64_MAX; one naming a structure
+ * still being built waits for it. */
+wt_status wt_server_submit_queries(wt_server s, uint64_t q, const uint64_t* h_sid,
+                                   const uint8_t* h_op, const uint32_t* h_c, const uint64_t* h_x,
+                                   uint64_t* req);
+/* State of a request.  wait != 0 blocks until it has finished; wait == 0
+ * returns WT_ERR_TIMEOUT while it runs.  For a finished query request,
+ * h_out (q u64, may be NULL) receives the answers and the request is
+ * forgotten.  info (may be NULL) receives status and times. */
+wt_status wt_server_poll(wt_server s, uint64_t req, int wait, uint64_t* h_out,
+                         wt_request_info* info);
+/* The handle of a built structure (owned by the server; valid until the
+ * structure is released). */
+wt_status wt_server_handle(wt_server s, uint64_t sid, wt_handle* out);
+/* Frees a built (or failed) structure once no query launch uses it. */
+wt_status wt_server_release(wt_server s, uint64_t sid);
+wt_status wt_server_stats(wt_server s, wt_server_stats_t* out);
+/* Stops the workers (requests not finished end with WT_ERR_INVALID_ARG) and
+ * frees every structure. */
+wt_status wt_server_destroy(wt_server s);
+
 /* Batched queries (definitions of Section 2).  q queries; d_i / d_c / d_k /
  * d_out are device arrays of q entries owned by the caller. */
 wt_status wt_access(wt_handle h, const uint64_t* d_i, uint64_t q, uint64_t* d_out,

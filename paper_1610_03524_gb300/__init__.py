@@ -27,7 +27,11 @@ FLAG_NO_DIRECTORY = 1
 ABI_SYMBOLS = ("wt_build", "wm_build", "huff_wt_build", "multiary_build", "rs_build",
                "wt_access", "wt_rank", "wt_select", "wt_sync", "wt_export", "wt_free",
                "wt_symbol_levels", "wt_status_str", "wt_memcpy_d2h", "wt_huffman_lengths",
-               "wt_canonical_codes", "wt_prof_enable", "wt_prof_read", "rs_dir_build_static")
+               "wt_canonical_codes", "wt_prof_enable", "wt_prof_read", "rs_dir_build_static",
+               "wm_batch_build", "wm_autotune", "wm_autotune_clear", "wt_query_multi",
+               "wt_server_create", "wt_server_submit_build", "wt_server_submit_queries",
+               "wt_server_poll", "wt_server_handle", "wt_server_release", "wt_server_stats",
+               "wt_server_destroy")
 
 
 class WaveletError(RuntimeError):
@@ -54,6 +58,27 @@ class ExportView(ctypes.Structure):
                 ("zeros", ctypes.POINTER(ctypes.c_uint64)),
                 ("code_len", ctypes.POINTER(ctypes.c_uint8)),
                 ("code", ctypes.POINTER(ctypes.c_uint32))]
+
+
+class BatchItem(ctypes.Structure):
+    _fields_ = [("d_seq", ctypes.c_void_p), ("n", ctypes.c_uint64), ("sigma", ctypes.c_uint32),
+                ("width_bytes", ctypes.c_uint32)]
+
+
+class ServerOpts(ctypes.Structure):
+    _fields_ = [("budget_bytes", ctypes.c_uint64), ("max_batch_builds", ctypes.c_uint32),
+                ("max_batch_queries", ctypes.c_uint32)]
+
+
+class RequestInfo(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("kind", ctypes.c_uint32),
+                ("submit_ns", ctypes.c_uint64), ("done_ns", ctypes.c_uint64)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_uint64) for k in
+                ("used_bytes", "budget_bytes", "build_batches", "query_launches",
+                 "pending_builds", "pending_queries", "structures")]
 
 
 _lib = None
@@ -104,6 +129,30 @@ def load_library(path: str = LIB_PATH):
     lib.wt_canonical_codes.argtypes = [vp, u32, vp]
     lib.rs_dir_build_static.restype = c.c_int
     lib.rs_dir_build_static.argtypes = [vp, u64, vp, vp, vp, vp]
+    lib.wm_batch_build.restype = c.c_int
+    lib.wm_batch_build.argtypes = [c.POINTER(BatchItem), u32, c.POINTER(BuildOpts), vp, hp]
+    lib.wm_autotune.restype = c.c_int
+    lib.wm_autotune.argtypes = [vp, u64, u32, u32, vp, c.POINTER(u32), c.POINTER(c.c_float)]
+    lib.wm_autotune_clear.restype = None
+    lib.wm_autotune_clear.argtypes = []
+    lib.wt_query_multi.restype = c.c_int
+    lib.wt_query_multi.argtypes = [hp, u32, vp, vp, vp, vp, u64, vp, vp]
+    lib.wt_server_create.restype = c.c_int
+    lib.wt_server_create.argtypes = [c.POINTER(ServerOpts), hp]
+    lib.wt_server_submit_build.restype = c.c_int
+    lib.wt_server_submit_build.argtypes = [vp, vp, u64, u32, u32, c.POINTER(u64)]
+    lib.wt_server_submit_queries.restype = c.c_int
+    lib.wt_server_submit_queries.argtypes = [vp, u64, vp, vp, vp, vp, c.POINTER(u64)]
+    lib.wt_server_poll.restype = c.c_int
+    lib.wt_server_poll.argtypes = [vp, u64, c.c_int, vp, c.POINTER(RequestInfo)]
+    lib.wt_server_handle.restype = c.c_int
+    lib.wt_server_handle.argtypes = [vp, u64, hp]
+    lib.wt_server_release.restype = c.c_int
+    lib.wt_server_release.argtypes = [vp, u64]
+    lib.wt_server_stats.restype = c.c_int
+    lib.wt_server_stats.argtypes = [vp, c.POINTER(ServerStats)]
+    lib.wt_server_destroy.restype = c.c_int
+    lib.wt_server_destroy.argtypes = [vp]
     lib.wt_prof_enable.restype = None
     lib.wt_prof_enable.argtypes = [c.c_int]
     lib.wt_prof_read.restype = c.c_int
@@ -358,3 +407,116 @@ def canonical_codes(lengths: np.ndarray) -> np.ndarray:
     code = np.zeros(ln.size, dtype=np.uint32)
     load_library().wt_canonical_codes(ln.ctypes.data, ln.size, code.ctypes.data)
     return code
+
+
+def wm_batch_build(seqs, sigmas, ns=None, tau: int = 0, flags: int = 0, stream=None):
+    """Wavelet matrices of several device tensors with one batched build.
+
+    Returns one Handle per sequence (they share one device allocation)."""
+    m = len(seqs)
+    items = (BatchItem * max(m, 1))()
+    for i, (sq, sg) in enumerate(zip(seqs, sigmas)):
+        items[i].d_seq = _ptr(sq) if sq is not None else 0
+        items[i].n = sq.numel() if ns is None else int(ns[i])
+        items[i].sigma = int(sg)
+        items[i].width_bytes = _width(sq) if sq is not None else 2
+    outs = (ctypes.c_void_p * max(m, 1))()
+    o = _opts(tau, 0, flags)
+    _check(load_library().wm_batch_build(items, m, ctypes.byref(o), _stream_ptr(stream), outs),
+           "wm_batch_build")
+    return [Handle(ctypes.c_void_p(outs[i])) for i in range(m)]
+
+
+def wm_autotune(seq, sigma: int, n: int | None = None, stream=None):
+    """Time tau = 1..min(8, L) on this sequence; returns (best tau, ms per tau)
+    and records the choice for later builds with tau = 0."""
+    n = seq.numel() if n is None else n
+    best = ctypes.c_uint32()
+    ms = (ctypes.c_float * 8)()
+    _check(load_library().wm_autotune(_ptr(seq), n, sigma, _width(seq), _stream_ptr(stream),
+                                       ctypes.byref(best), ms), "wm_autotune")
+    return int(best.value), [float(v) for v in ms]
+
+
+def wm_autotune_clear():
+    load_library().wm_autotune_clear()
+
+
+def query_multi(handles, sid, op, c, x, out, q=None, stream=None):
+    """One launch of queries over several structures (device tensors:
+    sid u32, op u8, c u32, x u64, out u64)."""
+    q = x.numel() if q is None else q
+    hs = (ctypes.c_void_p * max(len(handles), 1))()
+    for i, h in enumerate(handles):
+        hs[i] = h._live().value
+    _check(load_library().wt_query_multi(hs, len(handles), _ptr(sid), _ptr(op), _ptr(c), _ptr(x),
+                                          q, _ptr(out), _stream_ptr(stream)), "wt_query_multi")
+    return out
+
+
+class Server:
+    """Serving loop of the library (wt_server_*): builds of host sequences and
+    query batches over built structures, continuously batched on the GPU."""
+
+    def __init__(self, budget_bytes: int, max_batch_builds: int = 0, max_batch_queries: int = 0):
+        o = ServerOpts()
+        o.budget_bytes, o.max_batch_builds, o.max_batch_queries = (budget_bytes, max_batch_builds,
+                                                                   max_batch_queries)
+        self._s = ctypes.c_void_p()
+        _check(load_library().wt_server_create(ctypes.byref(o), ctypes.byref(self._s)),
+               "wt_server_create")
+
+    def submit_build(self, seq: np.ndarray, sigma: int) -> int:
+        a = np.ascontiguousarray(seq)
+        r = ctypes.c_uint64()
+        _check(load_library().wt_server_submit_build(self._s, a.ctypes.data, a.size, sigma,
+                                                      a.dtype.itemsize, ctypes.byref(r)),
+               "wt_server_submit_build")
+        return int(r.value)
+
+    def submit_queries(self, sid, op, c, x) -> int:
+        sid = np.ascontiguousarray(sid, dtype=np.uint64)
+        op = np.ascontiguousarray(op, dtype=np.uint8)
+        c = np.ascontiguousarray(c, dtype=np.uint32)
+        x = np.ascontiguousarray(x, dtype=np.uint64)
+        r = ctypes.c_uint64()
+        _check(load_library().wt_server_submit_queries(self._s, sid.size, sid.ctypes.data,
+                                                        op.ctypes.data, c.ctypes.data,
+                                                        x.ctypes.data, ctypes.byref(r)),
+               "wt_server_submit_queries")
+        return int(r.value)
+
+    def poll(self, req: int, q: int = 0, wait: bool = True):
+        """(status, submit_ns, done_ns, answers or None); status None while running."""
+        out = np.zeros(q, dtype=np.uint64) if q else None
+        info = RequestInfo()
+        st = load_library().wt_server_poll(self._s, req, 1 if wait else 0,
+                                           out.ctypes.data if q else None, ctypes.byref(info))
+        if st == 5 and not wait:
+            return None, info.submit_ns, 0, None
+        _check(st, "wt_server_poll")
+        return info.status, info.submit_ns, info.done_ns, out
+
+    def handle(self, sid: int):
+        h = ctypes.c_void_p()
+        _check(load_library().wt_server_handle(self._s, sid, ctypes.byref(h)), "wt_server_handle")
+        return h
+
+    def release(self, sid: int):
+        _check(load_library().wt_server_release(self._s, sid), "wt_server_release")
+
+    def stats(self) -> dict:
+        st = ServerStats()
+        _check(load_library().wt_server_stats(self._s, ctypes.byref(st)), "wt_server_stats")
+        return {k: int(getattr(st, k)) for k, _ in ServerStats._fields_}
+
+    def close(self):
+        if self._s:
+            load_library().wt_server_destroy(self._s)
+            self._s = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -29,6 +29,14 @@ wt_status check_opts(const wt_build_opts* o) {
 
 void free_arrays(wt_struct* h) {
   cudaStream_t st = h->stream;
+  if (h->arena) {
+    if (h->arena->refs.fetch_sub(1) == 1) {
+      dfree(h->arena->base, st);
+      delete h->arena;
+    }
+    h->arena = nullptr;
+    return;
+  }
   dfree(h->d_bits, st);
   dfree(h->d_dir, st);
   dfree(h->d_samp, st);
@@ -90,6 +98,13 @@ wt_status sync_handle(wt_struct* h) {
   if (err & ERR_SYMBOL) return h->deferred = WT_ERR_SYMBOL_GE_SIGMA;
   if (err & ERR_TIMEOUT) return h->deferred = WT_ERR_TIMEOUT;
   if (err) return h->deferred = WT_ERR_CUDA;
+  if (h->arena) {
+    // a wait that ran out anywhere in the batch stopped every sequence
+    uint32_t ab = 0;
+    e = cudaMemcpy(&ab, h->d_abort, 4, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return h->deferred = WT_ERR_CUDA;
+    if (ab) return h->deferred = WT_ERR_TIMEOUT;
+  }
   if (!h->zeros_valid) {
     h->zeros.assign(h->levels, 0);
     if (h->levels && h->bpe == 1) {

@@ -1,0 +1,564 @@
+// batch.cu -- many wavelet matrices built by one set of launches, and the
+// autotuner that picks the levels per pass.
+//
+// Section 4.2 splits one sequence into K sub-sequences and combines the
+// per-node counts of the pieces by prefix sums.  A batch applies the same
+// decomposition across sequences: the tiles of every sequence form one work
+// list, each tile carries its sequence's parameters, and the per-tile class
+// counts are chained only between tiles of the same sequence.  So a batch of
+// m sequences costs one histogram launch, one planning launch, one partition
+// launch per pass index (two if some sequences need 32-bit working
+// elements), and one set of directory launches over all levels of all
+// sequences, instead of m times that.  Every device array of the batch sits
+// in one allocation (the arena) shared by the m handles.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <vector>
+
+#include "wt_host.h"
+#include "wt_internal.cuh"
+
+namespace wtk {
+
+wt_status launch_pass_batch(const PassParams& P, bool wide, const wt_build_opts* o,
+                            cudaStream_t st);
+wt_status launch_hist_batch(const HistSeg* d_segs, uint32_t nsegs, uint64_t nchunks,
+                            uint64_t* hist, cudaStream_t st);
+wt_status launch_plan_batch(const PlanSeg* d_ps, uint32_t m, cudaStream_t st);
+wt_status dir_build_levels(const uint64_t* bits, const LevelMeta* d_meta, uint32_t nlev,
+                           const std::vector<uint64_t>& sb_first, uint64_t* dir, uint64_t* samp,
+                           uint64_t* zeros, int write_zeros, cudaStream_t st);
+
+#define CK(x)                                                   \
+  do {                                                          \
+    cudaError_t e_ = (x);                                       \
+    if (e_ != cudaSuccess) {                                    \
+      fprintf(stderr, "wavelet: %s -> %s\n", #x, cudaGetErrorString(e_)); \
+      return e_ == cudaErrorMemoryAllocation ? WT_ERR_NO_MEMORY : WT_ERR_CUDA; \
+    }                                                           \
+  } while (0)
+
+#define TRY(x)                     \
+  do {                             \
+    wt_status s_ = (x);            \
+    if (s_ != WT_OK) return s_;    \
+  } while (0)
+
+// ---------------------------------------------------------------------------
+// autotuner table: (L, ceil(log2 n)) -> levels per pass
+// ---------------------------------------------------------------------------
+namespace {
+std::mutex g_tune_mu;
+uint8_t g_tune[33][65];  // 0 = not tuned
+
+int log2_ceil(uint64_t n) {
+  int k = 0;
+  while (k < 64 && ((uint64_t)1 << k) < n) k++;
+  return k;
+}
+
+uint32_t levels_of_b(uint32_t sigma) {
+  uint32_t L = 0;
+  while (L < 32 && ((uint64_t)1 << L) < (uint64_t)sigma) L++;
+  return L == 0 ? 1 : L;
+}
+
+uint64_t level_words_b(uint64_t nbits) { return ((nbits + 2047) / 2048) * 32; }
+int width_for_bits_b(int b) { return b <= 8 ? 1 : (b <= 16 ? 2 : 4); }
+uint64_t up(uint64_t x, uint64_t a) { return (x + a - 1) / a * a; }
+}  // namespace
+
+int tuned_tau(uint32_t L, uint64_t n) {
+  std::lock_guard<std::mutex> g(g_tune_mu);
+  const int k = log2_ceil(n);
+  const int v = (L <= 32 && k <= 64) ? g_tune[L][k] : 0;
+  return v ? v : TAU_MAX;
+}
+
+static void record_tau(uint32_t L, uint64_t n, int tau) {
+  std::lock_guard<std::mutex> g(g_tune_mu);
+  const int k = log2_ceil(n);
+  if (L <= 32 && k <= 64) g_tune[L][k] = (uint8_t)tau;
+}
+
+// ---------------------------------------------------------------------------
+// batch layout
+// ---------------------------------------------------------------------------
+namespace {
+
+struct Pass1 {
+  int a, t, rbits, in_w, out_w;
+  bool wide;
+};
+
+struct SeqPlan {
+  uint64_t n;
+  uint32_t sigma;
+  int w, L, tau, G;
+  std::vector<Pass1> ps;
+  uint64_t W, nsb, cap;      // words per level, superblocks per level, samples per value
+  // arena offsets (u64 units inside each region)
+  uint64_t bits_base, dir_base, samp_base, zeros_base, meta_base;
+  // workspace offsets
+  uint64_t hist_off, cls_off, lvl_base, seq_off;  // seq_off: bytes in each ping-pong buffer
+  uint64_t seq_bytes;
+};
+
+void plan_seq(SeqPlan& p, const wt_build_opts* o) {
+  p.L = (int)levels_of_b(p.sigma);
+  p.tau = (o && o->tau) ? (int)std::min<uint32_t>(o->tau, TAU_MAX) : tuned_tau(p.L, p.n);
+  if (p.tau < 1) p.tau = 1;
+  p.ps.clear();
+  for (int a = 0; a < p.L; a += p.tau) {
+    Pass1 q;
+    q.a = a;
+    q.t = std::min(p.tau, p.L - a);
+    q.rbits = p.L - a;
+    q.in_w = a == 0 ? p.w : width_for_bits_b(p.L - a);
+    q.out_w = (a + q.t < p.L) ? width_for_bits_b(p.L - a - q.t) : 0;
+    q.wide = q.rbits > 16;
+    p.ps.push_back(q);
+  }
+  p.G = (int)p.ps.size();
+  p.W = level_words_b(p.n);
+  p.nsb = (p.n + 2047) / 2048;
+  p.cap = p.n / 4096 + 1;
+  int ow = 0;
+  for (const Pass1& q : p.ps) ow = std::max(ow, q.out_w);
+  p.seq_bytes = up(p.n * (uint64_t)ow, 256);
+}
+
+// bytes of the arena regions of one sequence
+uint64_t bits_u64(const SeqPlan& p) { return (uint64_t)p.L * p.W; }
+uint64_t dir_u64(const SeqPlan& p) { return up((uint64_t)p.L * 2 * (p.nsb + 1), 32); }
+uint64_t samp_u64(const SeqPlan& p) { return up((uint64_t)p.L * 2 * p.cap, 32); }
+
+}  // namespace
+
+uint64_t wm_resident_bytes(uint64_t n, uint32_t sigma) {
+  SeqPlan p{};
+  p.n = n;
+  p.sigma = sigma;
+  p.w = 2;
+  plan_seq(p, nullptr);
+  return 8 * (bits_u64(p) + dir_u64(p) + samp_u64(p) + (uint64_t)p.L) +
+         (uint64_t)p.L * sizeof(LevelMeta) + 8;
+}
+
+// Builds m wavelet matrices with directories; outs[i] receives handle i.
+wt_status batch_build_wm(const wt_batch_item* items, uint32_t m, const wt_build_opts* o,
+                         cudaStream_t st, wt_struct** hs) {
+  std::vector<SeqPlan> sp(m);
+  uint64_t nbits = 0, ndir = 0, nsamp = 0, nzeros = 0, nmeta = 0;
+  uint64_t nhist = 0, ncls = 0, nlvl = 0, nseq = 0;
+  uint64_t nchunks = 0, nlev_tot = 0;
+  int Gmax = 0;
+  for (uint32_t i = 0; i < m; i++) {
+    SeqPlan& p = sp[i];
+    p.n = items[i].n;
+    p.sigma = items[i].sigma;
+    p.w = (int)items[i].width_bytes;
+    plan_seq(p, o);
+    p.bits_base = nbits;
+    p.dir_base = ndir;
+    p.samp_base = nsamp;
+    p.zeros_base = nzeros;
+    p.meta_base = nmeta;
+    nbits += bits_u64(p);
+    ndir += dir_u64(p);
+    nsamp += samp_u64(p);
+    nzeros += p.L;
+    nmeta += p.L;
+    p.hist_off = nhist;
+    p.cls_off = ncls;
+    for (const Pass1& q : p.ps) {
+      nhist += 1u << q.t;
+      ncls += (2u << q.t) + q.t + 1;
+    }
+    p.lvl_base = nlvl;
+    nlvl += 2 * (uint64_t)p.L + 1;  // L+1 word offsets, then L lengths
+    p.seq_off = nseq;
+    nseq += p.G > 1 ? p.seq_bytes : 0;
+    if (p.n) nchunks += (p.n + HIST_CH - 1) / HIST_CH;
+    nlev_tot += p.L;
+    Gmax = std::max(Gmax, p.n ? p.G : 0);
+  }
+  // ---- arena: bits | dir | samp | zeros | meta | err[m] + abort ----------
+  const uint64_t off_dir = 8 * nbits;
+  const uint64_t off_samp = off_dir + 8 * ndir;
+  const uint64_t off_zeros = off_samp + 8 * nsamp;
+  const uint64_t off_meta = up(off_zeros + 8 * nzeros, 256);
+  const uint64_t off_err = up(off_meta + sizeof(LevelMeta) * nmeta, 256);
+  const uint64_t arena_bytes = off_err + up(4 * ((uint64_t)m + 1), 256);
+  Arena* ar = new Arena();
+  ar->bytes = arena_bytes;
+  {
+    cudaError_t e = dmalloc(&ar->base, arena_bytes, st);
+    if (e != cudaSuccess) {
+      delete ar;
+      return WT_ERR_NO_MEMORY;
+    }
+  }
+  uint8_t* A = (uint8_t*)ar->base;
+  uint64_t* a_bits = (uint64_t*)A;
+  uint64_t* a_dir = (uint64_t*)(A + off_dir);
+  uint64_t* a_samp = (uint64_t*)(A + off_samp);
+  uint64_t* a_zeros = (uint64_t*)(A + off_zeros);
+  LevelMeta* a_meta = (LevelMeta*)(A + off_meta);
+  uint32_t* a_err = (uint32_t*)(A + off_err);
+  uint32_t* a_abort = a_err + m;
+  // handles own the arena from here on (a failure below frees it through them)
+  for (uint32_t i = 0; i < m; i++) {
+    wt_struct* h = hs[i];
+    const SeqPlan& p = sp[i];
+    h->arena = ar;
+    ar->refs++;
+    h->kind = WT_KIND_WM;
+    h->n = p.n;
+    h->sigma = p.sigma;
+    h->L = h->levels = (uint32_t)p.L;
+    h->bpe = 1;
+    h->stream = st;
+    h->d_bits = a_bits + p.bits_base;
+    h->d_bits_ro = h->d_bits;
+    h->d_dir = a_dir + p.dir_base;
+    h->d_samp = a_samp + p.samp_base;
+    h->d_zeros = a_zeros + p.zeros_base;
+    h->d_meta = a_meta + p.meta_base;
+    h->d_err = a_err + i;
+    h->d_abort = a_abort;
+    h->level_len.assign(p.L, p.n);
+    h->level_off.assign(p.L + 1, 0);
+    h->dir_off.assign(p.L + 1, 0);
+    h->samp_off.assign(2 * p.L + 1, 0);
+    h->meta.assign(p.L, LevelMeta{});
+    for (int l = 0; l < p.L; l++) {
+      h->level_off[l + 1] = (uint64_t)(l + 1) * p.W;
+      h->dir_off[l + 1] = (uint64_t)(l + 1) * 2 * (p.nsb + 1);
+      h->samp_off[2 * l + 1] = (uint64_t)(2 * l + 1) * p.cap;
+      h->samp_off[2 * l + 2] = (uint64_t)(2 * l + 2) * p.cap;
+      LevelMeta& mt = h->meta[l];
+      mt.bit_off = (uint64_t)l * p.W;
+      mt.dir_off = h->dir_off[l];
+      mt.s0_off = h->samp_off[2 * l];
+      mt.s1_off = h->samp_off[2 * l + 1];
+      mt.n = p.n;
+      mt.nsb = p.nsb;
+    }
+  }
+  // ---- workspace ----------------------------------------------------------
+  uint32_t nh = 0;
+  for (uint32_t i = 0; i < m; i++) nh += sp[i].n ? 1 : 0;
+  uint64_t nsegs_tot = 0;
+  for (int g = 0; g < Gmax; g++)
+    for (uint32_t i = 0; i < m; i++)
+      if (sp[i].n && g < sp[i].G) nsegs_tot++;
+  const uint64_t w_hist = 0;
+  const uint64_t w_cls = up(w_hist + 8 * nhist, 256);
+  const uint64_t w_lvl = up(w_cls + 8 * ncls, 256);
+  const uint64_t w_gmeta = up(w_lvl + 8 * nlvl, 256);
+  const uint64_t w_hseg = up(w_gmeta + sizeof(LevelMeta) * nlev_tot, 256);
+  const uint64_t w_pseg = up(w_hseg + sizeof(HistSeg) * std::max<uint32_t>(nh, 1), 256);
+  const uint64_t w_sseg = up(w_pseg + sizeof(PlanSeg) * std::max<uint32_t>(m, 1), 256);
+  const uint64_t w_tab_end = up(w_sseg + sizeof(SegDesc) * std::max<uint64_t>(nsegs_tot, 1), 256);
+  const uint64_t w_ring = w_tab_end;
+  const uint64_t w_tick = up(w_ring + 8ull * RING_SLOTS * SLOT_U64, 256);
+  const uint64_t w_seq0 = up(w_tick + 4 * 64, 256);
+  const uint64_t w_seq1 = up(w_seq0 + nseq, 256);
+  const uint64_t ws_bytes = up(w_seq1 + nseq, 256);
+  void* wsv = nullptr;
+  CK(dmalloc(&wsv, ws_bytes, st));
+  uint8_t* Wd = (uint8_t*)wsv;
+  uint64_t* d_hist = (uint64_t*)(Wd + w_hist);
+  uint64_t* d_cls = (uint64_t*)(Wd + w_cls);
+  uint64_t* d_lvl = (uint64_t*)(Wd + w_lvl);
+  LevelMeta* d_gmeta = (LevelMeta*)(Wd + w_gmeta);
+  HistSeg* d_hseg = (HistSeg*)(Wd + w_hseg);
+  PlanSeg* d_pseg = (PlanSeg*)(Wd + w_pseg);
+  SegDesc* d_sseg = (SegDesc*)(Wd + w_sseg);
+  uint64_t* d_ring = (uint64_t*)(Wd + w_ring);
+  uint32_t* d_tick = (uint32_t*)(Wd + w_tick);
+  uint8_t* d_seq[2] = {Wd + w_seq0, Wd + w_seq1};
+
+  // host image of the tables [w_lvl, w_tab_end)
+  std::vector<uint8_t> img(w_tab_end - w_lvl, 0);
+  auto at = [&](uint64_t off) { return img.data() + (off - w_lvl); };
+  uint64_t* h_lvl = (uint64_t*)at(w_lvl);
+  LevelMeta* h_gmeta = (LevelMeta*)at(w_gmeta);
+  HistSeg* h_hseg = (HistSeg*)at(w_hseg);
+  PlanSeg* h_pseg = (PlanSeg*)at(w_pseg);
+  SegDesc* h_sseg = (SegDesc*)at(w_sseg);
+  std::vector<uint64_t> sb_first(nlev_tot + 1, 0);
+  std::vector<LevelMeta> h_meta_all(nmeta);
+  {
+    uint64_t lev = 0, chunk = 0;
+    uint32_t hi = 0;
+    for (uint32_t i = 0; i < m; i++) {
+      const SeqPlan& p = sp[i];
+      uint64_t* lo = h_lvl + p.lvl_base;
+      uint64_t* ll = lo + p.L + 1;
+      for (int l = 0; l <= p.L; l++) lo[l] = (uint64_t)l * p.W;
+      for (int l = 0; l < p.L; l++) ll[l] = p.n;
+      for (int l = 0; l < p.L; l++, lev++) {
+        LevelMeta mt = hs[i]->meta[l];
+        h_meta_all[p.meta_base + l] = mt;
+        mt.bit_off += p.bits_base;
+        mt.dir_off += p.dir_base;
+        mt.s0_off += p.samp_base;
+        mt.s1_off += p.samp_base;
+        h_gmeta[lev] = mt;
+        sb_first[lev + 1] = sb_first[lev] + p.nsb;
+      }
+      if (p.n) {
+        HistSeg& d = h_hseg[hi++];
+        d.seq = items[i].d_seq;
+        d.n = p.n;
+        d.chunk0 = chunk;
+        d.hist_off = p.hist_off;
+        d.err = a_err + i;
+        d.sigma = p.sigma;
+        d.w = p.w;
+        d.L = p.L;
+        d.tau = p.tau;
+        chunk += (p.n + HIST_CH - 1) / HIST_CH;
+      }
+      PlanSeg& q = h_pseg[i];
+      q.hist = d_hist + p.hist_off;
+      q.cls = d_cls + p.cls_off;
+      q.zeros = a_zeros + p.zeros_base;
+      q.L = p.L;
+      q.tau = p.tau;
+      q.G = p.n ? p.G : 0;
+    }
+  }
+  // per-launch segment lists: pass g, narrow (E = u16) then wide (E = u32)
+  struct Launch {
+    uint64_t first;
+    uint32_t nsegs, ntiles;
+    bool wide;
+  };
+  std::vector<Launch> launches;
+  {
+    uint64_t k = 0;
+    for (int g = 0; g < Gmax; g++) {
+      for (int wide = 0; wide < 2; wide++) {
+        Launch L0{k, 0, 0, wide != 0};
+        uint32_t tiles = 0;
+        for (uint32_t i = 0; i < m; i++) {
+          const SeqPlan& p = sp[i];
+          if (!p.n || g >= p.G || p.ps[g].wide != (wide != 0)) continue;
+          const Pass1& q = p.ps[g];
+          uint64_t coff = p.cls_off;
+          for (int g2 = 0; g2 < g; g2++) coff += (2u << p.ps[g2].t) + p.ps[g2].t + 1;
+          SegDesc& d = h_sseg[k++];
+          d.in = g == 0 ? items[i].d_seq : (const void*)(d_seq[(g - 1) & 1] + p.seq_off);
+          d.out = (g + 1 < p.G) ? (void*)(d_seq[g & 1] + p.seq_off) : nullptr;
+          d.bits = a_bits + p.bits_base;
+          d.lvl_off = d_lvl + p.lvl_base;
+          d.lvl_len = d_lvl + p.lvl_base + p.L + 1;
+          d.wm_cls = d_cls + coff;
+          d.err = a_err + i;
+          d.n = p.n;
+          d.tile0 = tiles;
+          d.in_w = q.in_w;
+          d.out_w = q.out_w;
+          d.L = p.L;
+          d.a = q.a;
+          d.t = q.t;
+          d.rbits = q.rbits;
+          tiles += (uint32_t)((p.n + PASS_T - 1) / PASS_T);
+          L0.nsegs++;
+        }
+        L0.ntiles = tiles;
+        if (L0.nsegs) launches.push_back(L0);
+      }
+    }
+  }
+  // ---- uploads and launches -------------------------------------------------
+  if (nbits) CK(cudaMemsetAsync(a_bits, 0, 8 * nbits, st));
+  CK(cudaMemsetAsync(a_err, 0, 4 * ((uint64_t)m + 1), st));
+  if (nzeros) CK(cudaMemsetAsync(a_zeros, 0, 8 * nzeros, st));  // empty sequences plan nothing
+  if (nhist) CK(cudaMemsetAsync(d_hist, 0, 8 * nhist, st));
+  CK(cudaMemsetAsync(d_tick, 0, 4 * 64, st));
+  if (nmeta)
+    CK(cudaMemcpyAsync(a_meta, h_meta_all.data(), sizeof(LevelMeta) * nmeta,
+                       cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(Wd + w_lvl, img.data(), img.size(), cudaMemcpyHostToDevice, st));
+  wt_status s = launch_hist_batch(d_hseg, nh, nchunks, d_hist, st);
+  if (s == WT_OK) s = launch_plan_batch(d_pseg, m, st);
+  for (size_t li = 0; li < launches.size() && s == WT_OK; li++) {
+    const Launch& L0 = launches[li];
+    PassParams P;
+    memset(&P, 0, sizeof(P));
+    P.shape = SHAPE_WM;
+    P.ring = d_ring;
+    P.ring_mask = RING_SLOTS - 1;
+    P.ticket = d_tick + li;
+    P.err = a_err;  // replaced per tile by the sequence's own word
+    P.abort_flag = a_abort;
+    P.spin_limit = SPIN_LIMIT;
+    P.ntiles = L0.ntiles;
+    P.segs = d_sseg + L0.first;
+    P.nsegs = L0.nsegs;
+    s = launch_pass_batch(P, L0.wide, o, st);
+  }
+  if (s == WT_OK && !(o && (o->flags & WT_FLAG_NO_DIRECTORY)))
+    s = dir_build_levels(a_bits, d_gmeta, (uint32_t)nlev_tot, sb_first, a_dir, a_samp, nullptr,
+                         0, st);
+  dfree(wsv, st);
+  if (s != WT_OK) return s;
+  CK(cudaGetLastError());
+  return WT_OK;
+}
+
+void batch_status(wt_handle* hs, uint32_t m, wt_status* st) {
+  // the batch's error words are consecutive in its arena, followed by the
+  // shared abort word
+  std::vector<uint32_t> err((size_t)m + 1, 0);
+  const bool ok = m && cudaMemcpy(err.data(), hs[0]->d_err, 4 * ((size_t)m + 1),
+                                  cudaMemcpyDeviceToHost) == cudaSuccess;
+  for (uint32_t i = 0; i < m; i++) {
+    wt_status s = WT_OK;
+    if (!ok) s = WT_ERR_CUDA;
+    else if (err[i] & ERR_SYMBOL) s = WT_ERR_SYMBOL_GE_SIGMA;
+    else if ((err[i] & ERR_TIMEOUT) || err[m]) s = WT_ERR_TIMEOUT;
+    else if (err[i]) s = WT_ERR_CUDA;
+    if (s != WT_OK) hs[i]->deferred = s;
+    st[i] = s;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// autotuner
+// ---------------------------------------------------------------------------
+wt_status build_wm(const void* d_seq, uint64_t n, uint32_t sigma, int w, const wt_build_opts* o,
+                   wt_struct* h);
+
+}  // namespace wtk
+
+using namespace wtk;
+
+namespace {
+void free_handle_partial(wt_struct* h) {
+  // handles of a failed batch: release the arena reference, nothing else
+  if (h->arena && h->arena->refs.fetch_sub(1) == 1) {
+    dfree(h->arena->base, h->stream);
+    delete h->arena;
+  }
+  h->arena = nullptr;
+  delete h;
+}
+}  // namespace
+
+extern "C" wt_status wm_batch_build(const wt_batch_item* items, uint32_t m,
+                                    const wt_build_opts* opts, wt_stream stream, wt_handle* outs) {
+  if (!outs || (m && !items)) return WT_ERR_INVALID_ARG;
+  for (uint32_t i = 0; i < m; i++) outs[i] = nullptr;
+  if (opts) {
+    if (opts->tau > 8) return WT_ERR_INVALID_ARG;
+    if (opts->select_sample != 0 && opts->select_sample != 4096) return WT_ERR_UNSUPPORTED;
+    if (opts->tile_symbols != 0 && opts->tile_symbols != (uint32_t)PASS_T) return WT_ERR_UNSUPPORTED;
+    if (opts->k_chunks != 0) return WT_ERR_UNSUPPORTED;
+  }
+  for (uint32_t i = 0; i < m; i++) {
+    const wt_batch_item& it = items[i];
+    if ((!it.d_seq && it.n) || it.sigma == 0) return WT_ERR_INVALID_ARG;
+    if (it.width_bytes != 1 && it.width_bytes != 2 && it.width_bytes != 4)
+      return WT_ERR_INVALID_ARG;
+    if (it.n >= ((uint64_t)1 << 40)) return WT_ERR_UNSUPPORTED;
+  }
+  if (m == 0) return WT_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  std::vector<wt_struct*> hs(m, nullptr);
+  int dev = 0;
+  cudaGetDevice(&dev);
+  for (uint32_t i = 0; i < m; i++) {
+    hs[i] = new (std::nothrow) wt_struct();
+    if (!hs[i]) {
+      for (uint32_t j = 0; j < i; j++) delete hs[j];
+      return WT_ERR_NO_MEMORY;
+    }
+    hs[i]->device = dev;
+    hs[i]->stream = st;
+  }
+  wt_status s = batch_build_wm(items, m, opts, st, hs.data());
+  if (s == WT_OK && cudaGetLastError() != cudaSuccess) s = WT_ERR_CUDA;
+  if (s != WT_OK) {
+    cudaStreamSynchronize(st);
+    for (uint32_t i = 0; i < m; i++) free_handle_partial(hs[i]);
+    cudaStreamSynchronize(st);
+    return s;
+  }
+  for (uint32_t i = 0; i < m; i++) outs[i] = hs[i];
+  return WT_OK;
+}
+
+extern "C" wt_status wm_autotune(const void* d_seq, uint64_t n, uint32_t sigma,
+                                 uint32_t width_bytes, wt_stream stream, uint32_t* best_tau,
+                                 float* ms_out) {
+  if ((!d_seq && n) || sigma == 0 || !best_tau) return WT_ERR_INVALID_ARG;
+  if (width_bytes != 1 && width_bytes != 2 && width_bytes != 4) return WT_ERR_INVALID_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  const uint32_t L = levels_of_b(sigma);
+  const uint32_t tmax = std::min<uint32_t>(L, TAU_MAX);
+  if (ms_out)
+    for (int i = 0; i < TAU_MAX; i++) ms_out[i] = 0.f;
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  float best = 0.f;
+  uint32_t bt = tmax;
+  wt_status s = WT_OK;
+  for (uint32_t tau = 1; tau <= tmax && s == WT_OK; tau++) {
+    // one untimed build, then the best of two timed ones
+    float t_best = 0.f;
+    for (int r = 0; r < 3 && s == WT_OK; r++) {
+      wt_build_opts o{};
+      o.tau = tau;
+      o.flags = WT_FLAG_NO_DIRECTORY;
+      wt_handle h = nullptr;
+      cudaEventRecord(e0, st);
+      s = wm_build(d_seq, n, sigma, width_bytes, &o, stream, &h);
+      cudaEventRecord(e1, st);
+      if (s != WT_OK) break;
+      s = wt_sync(h);
+      wt_free(h);
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (r > 0 && (t_best == 0.f || ms < t_best)) t_best = ms;
+    }
+    if (s != WT_OK) break;
+    if (ms_out) ms_out[tau - 1] = t_best;
+    if (best == 0.f || t_best < best) {
+      best = t_best;
+      bt = tau;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (s != WT_OK) return s;
+  *best_tau = bt;
+  record_tau(L, n, (int)bt);
+  return WT_OK;
+}
+
+extern "C" void wm_autotune_clear(void) {
+  std::lock_guard<std::mutex> g(g_tune_mu);
+  memset(g_tune, 0, sizeof(g_tune));
+}
+
+extern "C" wt_status wt_query_multi(const wt_handle* hs, uint32_t nh, const uint32_t* d_sid,
+                                    const uint8_t* d_op, const uint32_t* d_c,
+                                    const uint64_t* d_x, uint64_t q, uint64_t* d_out,
+                                    wt_stream stream) {
+  if ((nh && !hs) || (q && (!d_sid || !d_op || !d_c || !d_x || !d_out))) return WT_ERR_INVALID_ARG;
+  for (uint32_t i = 0; i < nh; i++) {
+    if (!hs[i]) return WT_ERR_INVALID_ARG;
+    if (hs[i]->deferred != WT_OK) return hs[i]->deferred;
+  }
+  return launch_query_multi(hs, nh, d_sid, d_op, d_c, d_x, q, d_out, (cudaStream_t)stream);
+}

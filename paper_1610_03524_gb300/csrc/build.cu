@@ -25,8 +25,6 @@
 namespace wtk {
 
 static std::atomic<uint64_t> g_seq{1};
-constexpr uint32_t RING_SLOTS = 4096;
-constexpr uint64_t SPIN_LIMIT = 1ull << 24;
 
 #define CK(x)                                                   \
   do {                                                          \
@@ -158,11 +156,15 @@ __global__ void k_hist_full(const void* seq, uint64_t n, uint32_t sigma, uint64_
                         bad |= !ok;
                         if (use_smem) {
                           if (ok) atomicAdd(&shh[x], 1u);
-                        } else if (ok) {
-                          atomicAdd((unsigned long long*)&hist[x], 1ull);
+                        } else {
+                          // lanes holding the same symbol add once (skewed
+                          // alphabets put many lanes on the frequent ones)
+                          const uint32_t act = __activemask();
+                          const uint32_t peers = __match_any_sync(act, x);
+                          if (ok && lane == __ffs(peers) - 1)
+                            atomicAdd((unsigned long long*)&hist[x], (unsigned long long)__popc(peers));
                         }
                       });
-  (void)lane;
   if (bad) atomicOr(err, ERR_SYMBOL);
   if (use_smem) {
     __syncthreads();
@@ -303,14 +305,12 @@ static std::vector<PassGeom> make_passes(int L, int tau, int first_w) {
   return ps;
 }
 
-// Wavelet-matrix plan, one block: class starts of every level of every pass
-// (classes of level a+j are the values of the low j bits of the reversed
-// digit), zero counts, zeroing of node-boundary words and of the padding,
-// reset of the look-back ring and tickets.
-__global__ void k_plan_wm(const uint64_t* hist, uint64_t n, int L, int tau, int G,
-                          uint64_t* cls, uint64_t* zeros, uint64_t* bits, uint64_t W,
-                          uint64_t* ring, uint32_t ring_slots, uint32_t* tickets,
-                          uint32_t* abort_flag) {
+// Class starts of every level of every pass of one wavelet matrix, by one
+// block (classes of level a+j are the values of the low j bits of the
+// reversed digit: prefix sums over the digit histogram folded mod 2^j), and
+// the zero count of every level (the class-0 size after its split).
+__device__ void plan_wm_classes(const uint64_t* hist, int L, int tau, int G, uint64_t* cls,
+                                uint64_t* zeros) {
   __shared__ uint64_t cnt[512];
   __shared__ uint64_t st[512];
   int hoff = 0, coff = 0;
@@ -341,6 +341,15 @@ __global__ void k_plan_wm(const uint64_t* hist, uint64_t n, int L, int tau, int 
     hoff += 1 << t;
     coff += (2 << t) + t + 1;
   }
+}
+
+// Wavelet-matrix plan, one block: class starts and zero counts; reset of the
+// look-back ring and tickets.
+__global__ void k_plan_wm(const uint64_t* hist, uint64_t n, int L, int tau, int G,
+                          uint64_t* cls, uint64_t* zeros, uint64_t* bits, uint64_t W,
+                          uint64_t* ring, uint32_t ring_slots, uint32_t* tickets,
+                          uint32_t* abort_flag) {
+  plan_wm_classes(hist, L, tau, G, cls, zeros);
   for (uint32_t i = threadIdx.x; i < ring_slots; i += blockDim.x) ring[(uint64_t)i * SLOT_U64] = 0;
   for (int g = threadIdx.x; g < 32; g += blockDim.x) tickets[g] = 0;
   if (threadIdx.x == 0) *abort_flag = 0;
@@ -425,13 +434,13 @@ __global__ void k_tiles_write(const uint64_t* bnd, uint64_t stride, uint64_t nn,
 // ---------------------------------------------------------------------------
 // 3. pass launch
 // ---------------------------------------------------------------------------
-constexpr int PT = 4096, PNT = 256;
+constexpr int PT = PASS_T, PNT = 256;
 
-template <typename E, bool DIG>
+template <typename E, bool DIG, bool BATCH = false>
 static wt_status launch_pass_t(const PassParams& P, uint64_t max_tiles, const wt_build_opts* o,
                                cudaStream_t st) {
   using SM = PassSmem<E, PT, PNT, DIG>;
-  auto kern = k_pass<E, PT, PNT, DIG>;
+  auto kern = k_pass<E, PT, PNT, DIG, BATCH>;
   static bool attr = false;
   static int occ = 0;
   if (!attr) {
@@ -474,8 +483,16 @@ static wt_status launch_pass(const PassParams& P, bool wide, bool dig, uint64_t 
               : launch_pass_t<uint16_t, false>(P, max_tiles, o, st);
 }
 
-static int pick_tau(const wt_build_opts* o, int L, bool even) {
-  int tau = (o && o->tau) ? (int)o->tau : 8;
+// Batched wavelet matrices: one launch over the tiles of every sequence in
+// P.segs (P.ntiles tiles in total).
+wt_status launch_pass_batch(const PassParams& P, bool wide, const wt_build_opts* o,
+                            cudaStream_t st) {
+  return wide ? launch_pass_t<uint32_t, false, true>(P, P.ntiles, o, st)
+              : launch_pass_t<uint16_t, false, true>(P, P.ntiles, o, st);
+}
+
+static int pick_tau(const wt_build_opts* o, int L, bool even, uint64_t n = 0) {
+  int tau = (o && o->tau) ? (int)o->tau : (even ? 8 : tuned_tau((uint32_t)L, n));
   if (tau < 1) tau = 1;
   if (tau > TAU_MAX) tau = TAU_MAX;
   if (even && (tau & 1)) tau = tau > 1 ? tau - 1 : 2;
@@ -557,7 +574,7 @@ wt_status build_wm(const void* d_seq, uint64_t n, uint32_t sigma, int w, const w
   TRY(alloc_outputs(h, W * L));
   Work wk{st, {}};
   if (n == 0) return build_directories(h);
-  const int tau = pick_tau(o, L, false);
+  const int tau = pick_tau(o, L, false, n);
   std::vector<PassGeom> ps = make_passes(L, tau, w);
   const int G = (int)ps.size();
   uint32_t T = PT;
@@ -773,11 +790,18 @@ wt_status build_huff(const void* d_seq, uint64_t n, uint32_t sigma, int w, const
   h->max_code_len = maxlen;
   const int Lm = (int)maxlen;
   h->L = h->levels = (uint32_t)Lm;
-  // symbols in canonical order (= order of the left-aligned codewords)
+  // symbols in canonical order (= order of the left-aligned codewords):
+  // by (length, symbol), a counting sort on the length
   std::vector<uint32_t> order;
-  for (uint32_t ln = 1; ln <= 32; ln++)
+  uint64_t lcount[34] = {0};
+  {
+    for (uint32_t s = 0; s < sigma; s++) lcount[h->code_len[s]]++;
+    uint64_t lpos[34] = {0};
+    for (int ln = 2; ln <= 33; ln++) lpos[ln] = lpos[ln - 1] + (ln - 1 >= 1 ? lcount[ln - 1] : 0);
+    order.resize(lpos[33]);
     for (uint32_t s = 0; s < sigma; s++)
-      if (h->code_len[s] == ln) order.push_back(s);
+      if (h->code_len[s]) order[lpos[h->code_len[s]]++] = s;
+  }
   // level sizes, internal nodes of every level and their start positions
   h->level_len.assign(Lm, 0);
   std::vector<uint64_t> node, node_lvl(3 * (size_t)std::max(Lm, 1), 0);
@@ -822,18 +846,15 @@ wt_status build_huff(const void* d_seq, uint64_t n, uint32_t sigma, int w, const
   std::vector<uint32_t> left(sigma);
   for (uint32_t s = 0; s < sigma; s++)
     left[s] = h->code_len[s] ? (uint32_t)((uint64_t)h->code[s] << (Lm - h->code_len[s])) : 0;
+  // per length: first canonical code, its index in `order`, symbol count
   std::vector<uint64_t> lentab(3 * 34, 0);
   {
     uint64_t idx = 0;
     for (uint32_t ln = 1; ln <= 32; ln++) {
       lentab[34 + ln] = idx;
-      bool f = true;
-      for (uint32_t s : order)
-        if (h->code_len[s] == ln) {
-          if (f) { lentab[ln] = h->code[s]; f = false; }
-          lentab[68 + ln]++;
-        }
-      idx += lentab[68 + ln];
+      lentab[68 + ln] = lcount[ln];
+      if (lcount[ln]) lentab[ln] = h->code[order[idx]];
+      idx += lcount[ln];
     }
   }
   CK(dmalloc((void**)&h->d_code, (size_t)sigma * 4, st));
@@ -930,6 +951,100 @@ wt_status build_huff(const void* d_seq, uint64_t n, uint32_t sigma, int w, const
   return build_directories(h);
 }
 
+
+}  // namespace wtk
+
+namespace wtk {
+
+// ---------------------------------------------------------------------------
+// batched wavelet matrices: histograms and plans of many sequences per launch
+// ---------------------------------------------------------------------------
+template <int WB>
+__device__ __forceinline__ void hist_chunk(const HistSeg& d, uint64_t i0, uint64_t i1,
+                                           uint32_t* sh, const int* off, const int* tt,
+                                           const int* shf, int G, bool& bad) {
+  using T = typename std::conditional<WB == 1, uint8_t,
+                                      typename std::conditional<WB == 2, uint16_t, uint32_t>::type>::type;
+  const T* s = (const T*)d.seq;
+  for (uint64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+    const uint32_t x = (uint32_t)__ldcs(s + i);
+    bad |= x >= d.sigma;
+    for (int g = 0; g < G; g++) {
+      const uint32_t dg = (x >> shf[g]) & ((1u << tt[g]) - 1u);
+      atomicAdd(&sh[off[g] + rev_bits(dg, tt[g])], 1u);
+    }
+  }
+}
+
+// Reversed-digit histograms of every pass of every sequence (the per-sequence
+// counterpart of k_hist_digits), with the symbol check.  The launch walks
+// chunks of HIST_CH symbols; segs are sorted by chunk0.
+__global__ void k_hist_batch(const HistSeg* segs, uint32_t nsegs, uint64_t nchunks,
+                             uint64_t* hist) {
+  __shared__ uint32_t sh[1024];
+  __shared__ int off[33], tt[32], shf[32];
+  __shared__ HistSeg d;
+  __shared__ int sG;
+  for (uint64_t c = blockIdx.x; c < nchunks; c += gridDim.x) {
+    if (threadIdx.x == 0) {
+      uint32_t lo = 0, hi = nsegs - 1;
+      while (lo < hi) {
+        const uint32_t mid = (lo + hi + 1) >> 1;
+        if (segs[mid].chunk0 <= c) lo = mid;
+        else hi = mid - 1;
+      }
+      d = segs[lo];
+      int o = 0, G = 0;
+      for (int a = 0; a < d.L && G < 32; a += d.tau, G++) {
+        tt[G] = min(d.tau, d.L - a);
+        shf[G] = d.L - a - tt[G];
+        off[G] = o;
+        o += 1 << tt[G];
+      }
+      off[G] = o;
+      sG = G;
+    }
+    __syncthreads();
+    const int G = sG, nb = off[G];
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) sh[i] = 0;
+    __syncthreads();
+    const uint64_t i0 = (c - d.chunk0) * HIST_CH;
+    const uint64_t i1 = min(i0 + HIST_CH, d.n);
+    bool bad = false;
+    if (d.w == 1) hist_chunk<1>(d, i0, i1, sh, off, tt, shf, G, bad);
+    else if (d.w == 2) hist_chunk<2>(d, i0, i1, sh, off, tt, shf, G, bad);
+    else hist_chunk<4>(d, i0, i1, sh, off, tt, shf, G, bad);
+    if (bad) atomicOr(d.err, ERR_SYMBOL);
+    __syncthreads();
+    for (int i = threadIdx.x; i < nb; i += blockDim.x)
+      if (sh[i]) atomicAdd((unsigned long long*)&hist[d.hist_off + i], (unsigned long long)sh[i]);
+    __syncthreads();
+  }
+}
+
+// One block per sequence: class starts and zero counts (plan_wm_classes).
+__global__ void k_plan_batch(const PlanSeg* ps) {
+  const PlanSeg p = ps[blockIdx.x];
+  plan_wm_classes(p.hist, p.L, p.tau, p.G, p.cls, p.zeros);
+}
+
+wt_status launch_hist_batch(const HistSeg* d_segs, uint32_t nsegs, uint64_t nchunks,
+                            uint64_t* hist, cudaStream_t st) {
+  if (!nchunks) return WT_OK;
+  const uint32_t blocks = (uint32_t)std::min<uint64_t>((uint64_t)num_sms() * 4, nchunks);
+  k_hist_batch<<<blocks, 512, 0, st>>>(d_segs, nsegs, nchunks, hist);
+  count_launch();
+  CK(cudaGetLastError());
+  return WT_OK;
+}
+
+wt_status launch_plan_batch(const PlanSeg* d_ps, uint32_t m, cudaStream_t st) {
+  if (!m) return WT_OK;
+  k_plan_batch<<<m, 256, 0, st>>>(d_ps);
+  count_launch();
+  CK(cudaGetLastError());
+  return WT_OK;
+}
 
 }  // namespace wtk
 

@@ -36,10 +36,16 @@ wt_status scan_excl_u64_pub(const uint64_t* in, uint64_t* out, uint64_t n, uint6
                             cudaStream_t st);
 uint64_t scan_scratch_pub(uint64_t n);
 
+// the level holding superblock g: last l with first[l] <= g (levels with no
+// superblock share their first with the next level and are skipped)
 __device__ __forceinline__ int find_level(const uint64_t* first, int nlev, uint64_t g) {
-  int l = 0;
-  while (l + 1 < nlev && first[l + 1] <= g) l++;
-  return l;
+  int lo = 0, hi = nlev - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (first[mid] <= g) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
 }
 
 // r-th (0-based) set bit of v
@@ -225,6 +231,48 @@ wt_status upload_meta(wt_struct* h) {
   return WT_OK;
 }
 
+// Binary directories and select samples of nlev levels described by d_meta
+// (offsets relative to bits / dir / samp); sb_first: first superblock of each
+// level in one numbering, nlev + 1 entries.  write_zeros: also store each
+// level's zero count in zeros[l].
+wt_status dir_build_levels(const uint64_t* bits, const LevelMeta* d_meta, uint32_t nlev,
+                           const std::vector<uint64_t>& sb_first, uint64_t* dir, uint64_t* samp,
+                           uint64_t* zeros, int write_zeros, cudaStream_t st) {
+  if (nlev == 0) return WT_OK;
+  const uint64_t total_sb = sb_first[nlev];
+  uint64_t *d_first, *sbz, *sbx, *scr;
+  CK(dmalloc((void**)&d_first, (nlev + 1) * 8, st));
+  CK(dmalloc((void**)&sbz, std::max<uint64_t>(total_sb, 1) * 8, st));
+  CK(dmalloc((void**)&sbx, (total_sb + 1) * 8, st));
+  CK(dmalloc((void**)&scr, scan_scratch_pub(total_sb) * 8, st));
+  CK(cudaMemcpyAsync(d_first, sb_first.data(), (nlev + 1) * 8, cudaMemcpyHostToDevice, st));
+  const unsigned cgrid = (unsigned)std::min<uint64_t>((total_sb * 32 + 255) / 256 + 1,
+                                                       (uint64_t)num_sms() * 16);
+  const unsigned fgrid = (unsigned)((total_sb + nlev + 255) / 256);
+  if (total_sb) {
+    k_dir_count<<<cgrid, 256, 0, st>>>(bits, d_meta, (int)nlev, d_first, total_sb, dir, sbz);
+    count_launch();
+  }
+  wt_status s = scan_excl_u64_pub(sbz, sbx, total_sb, scr, st);
+  if (s == WT_OK) {
+    k_dir_finish<<<fgrid, 256, 0, st>>>(d_meta, (int)nlev, d_first, total_sb, sbx, dir, zeros,
+                                        write_zeros);
+    count_launch();
+    if (total_sb) {
+      k_select_samples<<<(unsigned)((total_sb + 255) / 256), 256, 0, st>>>(
+          bits, d_meta, (int)nlev, d_first, total_sb, dir, samp);
+      count_launch();
+    }
+  }
+  cudaError_t e = cudaGetLastError();
+  dfree(d_first, st);
+  dfree(sbz, st);
+  dfree(sbx, st);
+  dfree(scr, st);
+  if (s != WT_OK) return s;
+  return e == cudaSuccess ? WT_OK : WT_ERR_CUDA;
+}
+
 wt_status build_directories(wt_struct* h) {
   cudaStream_t st = h->stream;
   const uint32_t nlev = h->levels;
@@ -255,46 +303,29 @@ wt_status build_directories(wt_struct* h) {
   wt_status s = upload_meta(h);
   if (s != WT_OK) return s;
   if (nlev == 0) return WT_OK;
+  if (!dig)
+    return dir_build_levels(h->d_bits_ro, h->d_meta, nlev, sb_first, h->d_dir, h->d_samp,
+                            h->d_zeros, h->kind == WT_KIND_RS ? 1 : 0, st);
   uint64_t *d_first, *sbz, *sbx, *scr;
-  const int nval = dig ? 4 : 1;
   CK(dmalloc((void**)&d_first, (nlev + 1) * 8, st));
-  CK(dmalloc((void**)&sbz, std::max<uint64_t>(total_sb, 1) * 8 * nval, st));
-  CK(dmalloc((void**)&sbx, (total_sb + 1) * 8 * nval, st));
+  CK(dmalloc((void**)&sbz, std::max<uint64_t>(total_sb, 1) * 8 * 4, st));
+  CK(dmalloc((void**)&sbx, (total_sb + 1) * 8 * 4, st));
   CK(dmalloc((void**)&scr, scan_scratch_pub(total_sb) * 8, st));
   CK(cudaMemcpyAsync(d_first, sb_first.data(), (nlev + 1) * 8, cudaMemcpyHostToDevice, st));
   const unsigned cgrid = (unsigned)std::min<uint64_t>((total_sb * 32 + 255) / 256 + 1,
                                                        (uint64_t)num_sms() * 16);
   const unsigned fgrid = (unsigned)((total_sb + nlev + 255) / 256);
-  if (!dig) {
-    if (total_sb) {
-      k_dir_count<<<cgrid, 256, 0, st>>>(h->d_bits_ro, h->d_meta, nlev, d_first, total_sb,
-                                         h->d_dir, sbz);
-      count_launch();
-    }
-    s = scan_excl_u64_pub(sbz, sbx, total_sb, scr, st);
-    if (s == WT_OK) {
-      k_dir_finish<<<fgrid, 256, 0, st>>>(h->d_meta, nlev, d_first, total_sb, sbx, h->d_dir,
-                                          h->d_zeros, h->kind == WT_KIND_RS ? 1 : 0);
-      count_launch();
-      if (total_sb) {
-        k_select_samples<<<(unsigned)((total_sb + 255) / 256), 256, 0, st>>>(
-            h->d_bits_ro, h->d_meta, nlev, d_first, total_sb, h->d_dir, h->d_samp);
-        count_launch();
-      }
-    }
-  } else {
-    if (total_sb) {
-      k_mdir_count<<<cgrid, 256, 0, st>>>(h->d_bits_ro, h->d_meta, nlev, d_first, total_sb,
-                                          h->d_dir, sbz);
-      count_launch();
-    }
-    for (int d = 0; d < 4 && s == WT_OK; d++)
-      s = scan_excl_u64_pub(sbz + (uint64_t)d * total_sb, sbx + (uint64_t)d * (total_sb + 1),
-                            total_sb, scr, st);
-    if (s == WT_OK) {
-      k_mdir_finish<<<fgrid, 256, 0, st>>>(h->d_meta, nlev, d_first, total_sb, sbx, h->d_dir);
-      count_launch();
-    }
+  if (total_sb) {
+    k_mdir_count<<<cgrid, 256, 0, st>>>(h->d_bits_ro, h->d_meta, nlev, d_first, total_sb,
+                                        h->d_dir, sbz);
+    count_launch();
+  }
+  for (int d = 0; d < 4 && s == WT_OK; d++)
+    s = scan_excl_u64_pub(sbz + (uint64_t)d * total_sb, sbx + (uint64_t)d * (total_sb + 1),
+                          total_sb, scr, st);
+  if (s == WT_OK) {
+    k_mdir_finish<<<fgrid, 256, 0, st>>>(h->d_meta, nlev, d_first, total_sb, sbx, h->d_dir);
+    count_launch();
   }
   cudaError_t e = cudaGetLastError();
   dfree(d_first, st);
@@ -715,10 +746,7 @@ __global__ void k_query(QStruct S, int op, const uint32_t* c, const uint64_t* x,
   out[i] = r;
 }
 
-wt_status launch_query(wt_struct* h, int op, const uint32_t* c, const uint64_t* x, uint64_t q,
-                       uint64_t* out, cudaStream_t st) {
-  if (q == 0) return WT_OK;
-  QStruct S;
+static void fill_qstruct(const wt_struct* h, QStruct& S) {
   S.kind = h->kind;
   S.n = h->n;
   S.sigma = h->sigma;
@@ -737,9 +765,60 @@ wt_status launch_query(wt_struct* h, int op, const uint32_t* c, const uint64_t* 
   S.hq.len_count = h->d_len_tab ? h->d_len_tab + 68 : nullptr;
   S.hq.node = h->d_node;
   S.hq.node_lvl = h->d_node_lvl;
+}
+
+wt_status launch_query(wt_struct* h, int op, const uint32_t* c, const uint64_t* x, uint64_t q,
+                       uint64_t* out, cudaStream_t st) {
+  if (q == 0) return WT_OK;
+  QStruct S;
+  fill_qstruct(h, S);
   k_query<<<(unsigned)((q + 127) / 128), 128, 0, st>>>(S, op, c, x, q, out);
   count_launch();
   CK(cudaGetLastError());
+  return WT_OK;
+}
+
+// Queries over several structures in one launch: query i applies op[i] to
+// structure sid[i] of the table.
+__global__ void k_query_multi(const QStruct* tab, uint32_t ns, const uint32_t* sid,
+                              const uint8_t* op, const uint32_t* c, const uint64_t* x, uint64_t q,
+                              uint64_t* out) {
+  const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= q) return;
+  const uint32_t s = sid[i];
+  const int o = op[i];
+  if (s >= ns || o > 2) {
+    out[i] = NONE;
+    return;
+  }
+  const QStruct& S = tab[s];
+  const uint32_t ci = c[i];
+  const uint64_t xi = x[i];
+  uint64_t r;
+  switch (S.kind) {
+    case WT_KIND_WM: r = q_wm(S, o, ci, xi); break;
+    case WT_KIND_WT: r = q_wt(S, o, ci, xi); break;
+    case WT_KIND_HUFF: r = q_huff(S, o, ci, xi); break;
+    case WT_KIND_MULTI: r = q_multi(S, o, ci, xi); break;
+    default: r = q_rs(S, o, ci, xi); break;
+  }
+  out[i] = r;
+}
+
+wt_status launch_query_multi(wt_struct* const* hs, uint32_t nh, const uint32_t* sid,
+                             const uint8_t* op, const uint32_t* c, const uint64_t* x, uint64_t q,
+                             uint64_t* out, cudaStream_t st) {
+  if (q == 0) return WT_OK;
+  std::vector<QStruct> tab(std::max<uint32_t>(nh, 1));
+  for (uint32_t i = 0; i < nh; i++) fill_qstruct(hs[i], tab[i]);
+  QStruct* d_tab = nullptr;
+  CK(dmalloc((void**)&d_tab, tab.size() * sizeof(QStruct), st));
+  CK(cudaMemcpyAsync(d_tab, tab.data(), tab.size() * sizeof(QStruct), cudaMemcpyHostToDevice, st));
+  k_query_multi<<<(unsigned)((q + 127) / 128), 128, 0, st>>>(d_tab, nh, sid, op, c, x, q, out);
+  count_launch();
+  cudaError_t e = cudaGetLastError();
+  dfree(d_tab, st);
+  CK(e);
   return WT_OK;
 }
 

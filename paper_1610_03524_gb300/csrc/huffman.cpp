@@ -13,19 +13,11 @@
 #include <stdint.h>
 
 #include <algorithm>
-#include <functional>
-#include <queue>
 #include <vector>
 
 namespace wtk {
 
 namespace {
-
-struct HNode {
-  uint64_t w;
-  uint64_t id;
-  bool operator>(const HNode& o) const { return w != o.w ? w > o.w : id > o.id; }
-};
 
 void limited_lengths(const std::vector<uint64_t>& w, const std::vector<uint32_t>& sym,
                      uint32_t cap, uint8_t* len) {
@@ -77,18 +69,47 @@ uint32_t huffman_lengths(const uint64_t* hist, uint32_t sigma, uint32_t cap, uin
     len[present[0]] = 1;
     return 1;
   }
-  std::priority_queue<HNode, std::vector<HNode>, std::greater<HNode>> pq;
-  for (uint32_t s : present) pq.push({hist[s], s});
-  std::vector<uint64_t> parent((size_t)sigma + present.size(), 0);
+  // Two-queue form of the (weight, id) min-heap merge: leaves sorted by
+  // (weight, symbol) in one queue, internal nodes in creation order in a
+  // second one (their weights never decrease, and every internal id exceeds
+  // every leaf id, so both queues stay sorted by (weight, id) and the smaller
+  // head is exactly the heap's minimum).
+  const size_t m = present.size();
+  std::vector<uint32_t> leaf = present, tmp(m);
+  {
+    // stable LSD radix sort of the symbols by weight (8 bits per round)
+    uint64_t wmax = 0;
+    for (uint32_t x : present) wmax = std::max(wmax, hist[x]);
+    for (int sh = 0; sh < 64 && (wmax >> sh); sh += 8) {
+      size_t cnt[257] = {0};
+      for (uint32_t x : leaf) cnt[((hist[x] >> sh) & 255) + 1]++;
+      for (int b = 0; b < 256; b++) cnt[b + 1] += cnt[b];
+      for (uint32_t x : leaf) tmp[cnt[(hist[x] >> sh) & 255]++] = x;
+      leaf.swap(tmp);
+    }
+  }
+  std::vector<uint64_t> parent((size_t)sigma + m, 0);
+  std::vector<uint64_t> iw(m);  // weights of internal node sigma + k
+  size_t li = 0, qi = 0, nint = 0;
+  auto take = [&](uint64_t& w, uint64_t& id) {
+    const bool use_leaf =
+        li < m && (qi >= nint || hist[leaf[li]] <= iw[qi]);  // equal weight: leaf id is smaller
+    if (use_leaf) {
+      w = hist[leaf[li]];
+      id = leaf[li++];
+    } else {
+      w = iw[qi];
+      id = sigma + qi++;
+    }
+  };
   uint64_t next = sigma;
-  while (pq.size() > 1) {
-    const HNode a = pq.top();
-    pq.pop();
-    const HNode b = pq.top();
-    pq.pop();
-    parent[a.id] = next;
-    parent[b.id] = next;
-    pq.push({a.w + b.w, next});
+  for (size_t k = 0; k + 1 < m; k++) {
+    uint64_t wa, ida, wb, idb;
+    take(wa, ida);
+    take(wb, idb);
+    parent[ida] = next;
+    parent[idb] = next;
+    iw[nint++] = wa + wb;
     next++;
   }
   // depths: internal nodes are created after their children, so walking ids
@@ -116,13 +137,17 @@ uint32_t huffman_lengths(const uint64_t* hist, uint32_t sigma, uint32_t cap, uin
 }
 
 void canonical_codes(const uint8_t* len, uint32_t sigma, uint32_t* code) {
-  std::vector<uint32_t> order;
+  // symbols ordered by (length, symbol): a counting sort on the length
+  size_t cnt[256] = {0};
   for (uint32_t s = 0; s < sigma; s++) {
     code[s] = 0;
-    if (len[s]) order.push_back(s);
+    if (len[s]) cnt[len[s]]++;
   }
-  std::stable_sort(order.begin(), order.end(),
-                   [&](uint32_t a, uint32_t b) { return len[a] < len[b]; });
+  size_t pos[257] = {0};  // pos[l]: symbols shorter than l (l >= 1)
+  for (int l = 2; l <= 256; l++) pos[l] = pos[l - 1] + cnt[l - 1];
+  std::vector<uint32_t> order(pos[256]);
+  for (uint32_t s = 0; s < sigma; s++)
+    if (len[s]) order[pos[len[s]]++] = s;
   uint64_t c = 0;
   for (size_t i = 0; i < order.size(); i++) {
     if (i) c = (c + 1) << (len[order[i]] - len[order[i - 1]]);

@@ -114,8 +114,13 @@ struct PassSmem {
 
 // NT worker threads run the splits; one extra control warp computes the
 // class counts and runs the look-back meanwhile (block = NT + 32 threads).
-template <typename E, int T, int NT, bool DIG>
-__global__ void __launch_bounds__(NT + 32, 3) k_pass(const PassParams P) {
+// BATCH: the launch covers the tiles of several sequences (wavelet matrices
+// of a batched build); each tile reads its sequence's part of the parameters
+// from P0.segs into shared memory.  Otherwise every field comes from P0.
+template <typename E, int T, int NT, bool DIG, bool BATCH>
+__global__ void __launch_bounds__(NT + 32, 3) k_pass(const __grid_constant__ PassParams P0) {
+  __shared__ PassParams s_P;
+  const PassParams& P = BATCH ? s_P : P0;
   constexpr int W = NT / 32, PW = T / W, EPW = PW / 32, TW = T / 32, NB = NT + 32, CW = W;
   static_assert(EPW >= 1 && EPW <= 32, "iterations per warp must fit a warp");
   static_assert(T % 64 == 0 && NT >= (1 << TAU_MAX), "tile geometry");
@@ -142,10 +147,9 @@ __global__ void __launch_bounds__(NT + 32, 3) k_pass(const PassParams P) {
   __shared__ uint32_t s_hist[1 << TAU_MAX];
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int t = P.t;
   const int bpe = DIG ? 2 : 1;
-  const int ncl = (2 << t) - 1, ntl = (1 << t) - 1;
-  const uint32_t ntiles = P.tiles ? *P.ntiles_dev : P.ntiles;
+  const uint32_t ntiles = P0.tiles ? *P0.ntiles_dev : P0.ntiles;
+  if (BATCH && tid == 0) s_P = P0;
   const uint32_t lt = lanemask_lt();
   const int wbase = warp * PW;
 
@@ -174,13 +178,40 @@ __global__ void __launch_bounds__(NT + 32, 3) k_pass(const PassParams P) {
 
   for (;;) {
     if (tid == 0) {
-      uint32_t ti = atomicAdd(P.ticket, 1u);
-      if (ld_volatile_u32(P.abort_flag)) ti = 0xffffffffu;
+      uint32_t ti = atomicAdd(P0.ticket, 1u);
+      if (ld_volatile_u32(P0.abort_flag)) ti = 0xffffffffu;
       s_tile = ti;
+      if (BATCH && ti < ntiles) {
+        // the sequence of this tile: last segment with tile0 <= ti
+        uint32_t lo = 0, hi = P0.nsegs - 1;
+        while (lo < hi) {
+          const uint32_t mid = (lo + hi + 1) >> 1;
+          if (P0.segs[mid].tile0 <= ti) lo = mid;
+          else hi = mid - 1;
+        }
+        const SegDesc& d = P0.segs[lo];
+        s_P.in = d.in;
+        s_P.in_w = d.in_w;
+        s_P.out = d.out;
+        s_P.out_w = d.out_w;
+        s_P.L = d.L;
+        s_P.a = d.a;
+        s_P.t = d.t;
+        s_P.rbits = d.rbits;
+        s_P.bits = d.bits;
+        s_P.lvl_off = d.lvl_off;
+        s_P.lvl_len = d.lvl_len;
+        s_P.wm_cls = d.wm_cls;
+        s_P.err = d.err;
+        s_P.n_in = d.n;
+        s_P.tile0 = d.tile0;
+      }
     }
     __syncthreads();
     const uint32_t ti = s_tile;
     if (ti >= ntiles) break;
+    const int t = P.t;
+    const int ntl = (1 << t) - 1;
     uint64_t ts;
     int cnt;
     uint32_t node;
@@ -192,11 +223,11 @@ __global__ void __launch_bounds__(NT + 32, 3) k_pass(const PassParams P) {
       node = d.node;
       first = d.first != 0;
     } else {
-      ts = (uint64_t)ti * T;
+      ts = (uint64_t)(ti - P.tile0) * T;
       const uint64_t rem = P.n_in - ts;
       cnt = (int)(rem < (uint64_t)T ? rem : (uint64_t)T);
       node = 0;
-      first = (ti == 0);
+      first = (ti == P.tile0);
     }
     const bool full = cnt == T;
 
@@ -294,7 +325,7 @@ __global__ void __launch_bounds__(NT + 32, 3) k_pass(const PassParams P) {
       // one 64-bit word per digit: 2-bit flag (1 aggregate, 2 inclusive)
       // above a 62-bit count; the ring is zeroed before every pass
       const int nd = 1 << t;
-      uint64_t* const slot = P.ring + (uint64_t)(ti & P.ring_mask) * SLOT_U64;
+      uint64_t* const slot = P0.ring + (uint64_t)(ti & P0.ring_mask) * SLOT_U64;
       constexpr uint64_t CMASK = (1ull << 62) - 1;
 #pragma unroll
       for (int i = 0; i < 8; i++) {
@@ -319,7 +350,7 @@ __global__ void __launch_bounds__(NT + 32, 3) k_pass(const PassParams P) {
 #pragma unroll
           for (int i = 0; i < 8; i++)
             v[i] = (todo >> i & 1u)
-                       ? ld_relaxed_u64(P.ring + (uint64_t)(pred[i] & P.ring_mask) * SLOT_U64 + lane + 32 * i)
+                       ? ld_relaxed_u64(P0.ring + (uint64_t)(pred[i] & P0.ring_mask) * SLOT_U64 + lane + 32 * i)
                        : 0ull;
           bool waited = false;
 #pragma unroll
@@ -336,7 +367,7 @@ __global__ void __launch_bounds__(NT + 32, 3) k_pass(const PassParams P) {
           }
           if (__any_sync(FULL, waited)) {
             int ab = 0;
-            if (lane == 0) ab = (++spins > P.spin_limit) || ld_volatile_u32(P.abort_flag);
+            if (lane == 0) ab = (++spins > P0.spin_limit) || ld_volatile_u32(P0.abort_flag);
             if (__shfl_sync(FULL, ab, 0)) {
               status = -1;
               break;
@@ -545,7 +576,7 @@ __global__ void __launch_bounds__(NT + 32, 3) k_pass(const PassParams P) {
     if (s_stat < 0) {
       if (tid == 0) {
         atomicOr(P.err, ERR_TIMEOUT);
-        atomicExch(P.abort_flag, 1u);
+        atomicExch(P0.abort_flag, 1u);
       }
       return;
     }

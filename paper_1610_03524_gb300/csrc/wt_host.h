@@ -4,11 +4,20 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
 #include <vector>
 
 #include "../../include/wavelet.h"
 
 namespace wtk {
+
+// One device allocation shared by the handles of a batched build; freed when
+// the last of them is freed.
+struct Arena {
+  void* base = nullptr;
+  std::atomic<int> refs{0};
+  uint64_t bytes = 0;
+};
 
 // Per-level metadata used by the query kernels (device copy in the handle).
 struct LevelMeta {
@@ -68,6 +77,9 @@ struct wt_struct {
   uint32_t max_code_len = 0;
   bool zeros_valid = false;
   wt_status deferred = WT_OK;
+  // batched builds: the shared allocation holding every device array above
+  // (d_abort is then shared by the whole batch)
+  wtk::Arena* arena = nullptr;
 };
 
 namespace wtk {
@@ -89,7 +101,7 @@ uint32_t num_sms();
 // timing of the partition-pass launches, for the benchmark's roofline.
 struct Prof {
   bool on = false;
-  uint64_t launches = 0;
+  std::atomic<uint64_t> launches{0};
   uint64_t pass_launches = 0;
   std::vector<cudaEvent_t> ev;  // pairs: before, after each pass launch
 };
@@ -109,4 +121,14 @@ wt_status launch_query(wt_struct* h, int op, const uint32_t* c, const uint64_t* 
                        uint64_t* out, cudaStream_t st);
 uint32_t huffman_lengths(const uint64_t* hist, uint32_t sigma, uint32_t cap, uint8_t* len);
 void canonical_codes(const uint8_t* len, uint32_t sigma, uint32_t* code);
+wt_status launch_query_multi(wt_struct* const* hs, uint32_t nh, const uint32_t* sid,
+                             const uint8_t* op, const uint32_t* c, const uint64_t* x, uint64_t q,
+                             uint64_t* out, cudaStream_t st);
+// levels per pass recorded by the autotuner for (L, ceil(log2 n)); 8 if none
+int tuned_tau(uint32_t L, uint64_t n);
+// bytes a batched wavelet-matrix build keeps for one sequence
+uint64_t wm_resident_bytes(uint64_t n, uint32_t sigma);
+// final status of the m handles of one batched build (after its stream is
+// synchronised), read with one copy of the batch's error words
+void batch_status(wt_handle* hs, uint32_t m, wt_status* st);
 }  // namespace wtk

@@ -27,9 +27,52 @@ struct TileDesc {
   uint32_t pad;
 };
 
+// Symbols per tile of the partition pass, look-back ring geometry, and the
+// bound on every device-side wait (polls before a wait gives up).
+constexpr int PASS_T = 4096;
+constexpr uint32_t RING_SLOTS = 4096;
+constexpr uint64_t SPIN_LIMIT = 1ull << 24;
+
 // Look-back ring slot: one word per digit value (flag in the top 2 bits,
 // count below), zeroed before every pass.
 constexpr int SLOT_U64 = 1 << TAU_MAX;
+
+// Batched builds: the per-sequence part of a pass, one entry per sequence
+// taking part in the launch.  Its tiles are tile0 .. tile0 + ceil(n/T) - 1 of
+// the launch's tile numbering.
+struct SegDesc {
+  const void* in;
+  void* out;
+  uint64_t* bits;
+  const uint64_t* lvl_off;
+  const uint64_t* lvl_len;
+  const uint64_t* wm_cls;
+  uint32_t* err;
+  uint64_t n;
+  uint32_t tile0;
+  int in_w, out_w, L, a, t, rbits;
+};
+
+// Batched histogram: one entry per sequence, sorted by chunk0 (its first
+// chunk of HIST_CH symbols in the launch's chunk numbering).
+constexpr uint64_t HIST_CH = 16384;
+struct HistSeg {
+  const void* seq;
+  uint64_t n;
+  uint64_t chunk0;
+  uint64_t hist_off;   // first histogram entry of the sequence
+  uint32_t* err;
+  uint32_t sigma;
+  int w, L, tau;
+};
+
+// Batched plan: one entry per sequence.
+struct PlanSeg {
+  const uint64_t* hist;
+  uint64_t* cls;
+  uint64_t* zeros;
+  int L, tau, G;
+};
 
 struct PassParams {
   // input sequence T_a (elements hold the rbits = L - a low bits still needed)
@@ -59,6 +102,10 @@ struct PassParams {
   const uint32_t* ntiles_dev;
   uint32_t ntiles;
   uint64_t n_in;
+  uint32_t tile0;           // first tile of the sequence (0 unless batched)
+  // batched builds: per-sequence parts, sorted by tile0
+  const SegDesc* segs;
+  uint32_t nsegs;
   // decoupled look-back
   uint64_t* ring;
   uint32_t ring_mask;

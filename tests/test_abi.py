@@ -77,3 +77,15 @@ def test_no_cpu_fallback(lib, monkeypatch):
     monkeypatch.setattr(lib, "_lib", None)
     with pytest.raises(ImportError):
         lib.load_library(os.path.join(ROOT, "no_such_libwavelet.so"))
+
+
+@pytest.mark.parametrize("seed,sigma,hi", [(7, 1000, 3), (8, 4096, 1), (9, 300, 40), (10, 70000, 5)])
+def test_library_huffman_ties_match_oracle(lib, seed, sigma, hi):
+    """Many equal weights (and zero counts): the library's merge order must
+    break every tie as the (weight, id) heap of the definition does."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    hist = rng.integers(0, hi + 1, size=sigma).astype(np.uint64)
+    la, ma = lib.huffman_lengths(hist, 32)
+    lo, mo = oracle.huffman_lengths(hist, 32)
+    assert ma == mo and np.array_equal(la, lo)
+    assert np.array_equal(lib.canonical_codes(la), oracle.canonical_codes(lo))
