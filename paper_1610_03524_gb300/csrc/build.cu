@@ -150,6 +150,24 @@ __global__ void k_hist_full(const void* seq, uint64_t n, uint32_t sigma, uint64_
   }
   bool bad = false;
   const int lane = threadIdx.x & 31;
+  if (sigma <= 8) {
+    // tiny alphabets (DNA-like text): counters in registers, no atomics per symbol
+    uint32_t cnt[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    for_each_symbol<WB>(seq, n, (uint64_t)blockIdx.x * blockDim.x + threadIdx.x,
+                        (uint64_t)gridDim.x * blockDim.x, [&](uint32_t x) {
+                          bad |= x >= sigma;
+#pragma unroll
+                          for (int k = 0; k < 8; k++) cnt[k] += (x == (uint32_t)k) ? 1u : 0u;
+                        });
+    if (bad) atomicOr(err, ERR_SYMBOL);
+#pragma unroll
+    for (int k = 0; k < 8; k++) {
+      const uint32_t c = __reduce_add_sync(FULL, cnt[k]);
+      if (lane == 0 && c && (uint32_t)k < sigma)
+        atomicAdd((unsigned long long*)&hist[k], (unsigned long long)c);
+    }
+    return;
+  }
   for_each_symbol<WB>(seq, n, (uint64_t)blockIdx.x * blockDim.x + threadIdx.x,
                       (uint64_t)gridDim.x * blockDim.x, [&](uint32_t x) {
                         const bool ok = x < sigma;
@@ -412,23 +430,31 @@ __global__ void k_tiles_count(const uint64_t* bnd, uint64_t stride, uint64_t nn,
   tcnt[p] = (sz + T - 1) / T;
 }
 
+// One thread per tile: tile i belongs to the node p with toff[p] <= i <
+// toff[p+1] (nodes without tiles share their toff with the next node, so the
+// last p with toff[p] <= i is the right one).
 __global__ void k_tiles_write(const uint64_t* bnd, uint64_t stride, uint64_t nn, uint32_t T,
                               uint64_t node_base, const uint64_t* toff, TileDesc* tiles,
-                              uint32_t* ntiles) {
-  const uint64_t p = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (p == 0) *ntiles = (uint32_t)toff[nn];
-  if (p >= nn) return;
-  const uint64_t s = bnd[p * stride], e = bnd[(p + 1) * stride];
-  uint64_t o = toff[p];
-  for (uint64_t x = s; x < e; x += T, o++) {
-    TileDesc d;
-    d.start = x;
-    d.count = (uint32_t)std::min<uint64_t>(T, e - x);
-    d.node = (uint32_t)(node_base + p);
-    d.first = (x == s);
-    d.pad = 0;
-    tiles[o] = d;
+                              uint32_t* ntiles, uint64_t max_tiles) {
+  const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const uint64_t total = toff[nn];
+  if (i == 0) *ntiles = (uint32_t)total;
+  if (i >= total || i >= max_tiles) return;
+  uint64_t lo = 0, hi = nn - 1;
+  while (lo < hi) {
+    const uint64_t mid = (lo + hi + 1) >> 1;
+    if (toff[mid] <= i) lo = mid;
+    else hi = mid - 1;
   }
+  const uint64_t p = lo, k = i - toff[p];
+  const uint64_t s = bnd[p * stride] + k * T, e = bnd[(p + 1) * stride];
+  TileDesc d;
+  d.start = s;
+  d.count = (uint32_t)std::min<uint64_t>(T, e - s);
+  d.node = (uint32_t)(node_base + p);
+  d.first = (k == 0);
+  d.pad = 0;
+  tiles[i] = d;
 }
 
 // ---------------------------------------------------------------------------
@@ -708,9 +734,12 @@ wt_status build_wt(const void* d_seq, uint64_t n, uint32_t sigma, int w, const w
     k_tiles_count<<<(unsigned)((nn + 255) / 256), 256, 0, st>>>(C, stride, nn, T, tcnt);
     count_launch();
     TRY(scan_excl_u64(tcnt, toff, nn, scr, st));
-    k_tiles_write<<<(unsigned)((nn + 255) / 256), 256, 0, st>>>(C, stride, nn, T, 0, toff, tiles,
-                                                               d_ntiles);
-  count_launch();
+    {
+      const uint64_t mt = (n + T - 1) / T + nn;
+      k_tiles_write<<<(unsigned)((mt + 255) / 256), 256, 0, st>>>(C, stride, nn, T, 0, toff, tiles,
+                                                                 d_ntiles, mt);
+      count_launch();
+    }
     CK(cudaGetLastError());
     PassParams P = base_params(h, wk, ring, tickets + g, d_off, d_len);
     P.in = in;
@@ -802,46 +831,53 @@ wt_status build_huff(const void* d_seq, uint64_t n, uint32_t sigma, int w, const
     for (uint32_t s = 0; s < sigma; s++)
       if (h->code_len[s]) order[lpos[h->code_len[s]]++] = s;
   }
-  // level sizes, internal nodes of every level and their start positions
+  // level sizes, internal nodes of every level and their start positions,
+  // and zero counts.  `order` is sorted by length, so the elements still on
+  // level l (length > l) are a suffix of it; their l-bit prefixes (top bits
+  // of the left-aligned codewords) never decrease along it.
+  const size_t np = order.size();
+  std::vector<uint64_t> lc(np), cnt(np);
+  for (size_t i = 0; i < np; i++) {
+    const uint32_t sy = order[i];
+    lc[i] = (uint64_t)h->code[sy] << (Lm - h->code_len[sy]);
+    cnt[i] = hh[sy];
+  }
   h->level_len.assign(Lm, 0);
   std::vector<uint64_t> node, node_lvl(3 * (size_t)std::max(Lm, 1), 0);
+  std::vector<uint64_t> zc(std::max(Lm, 1), 0);
+  node.reserve(np + Lm);
+  size_t first_gt = 0;  // first index of `order` with length > l
   for (int l = 0; l < Lm; l++) {
+    while (first_gt < np && h->code_len[order[first_gt]] <= (uint32_t)l) first_gt++;
     node_lvl[3 * l] = node.size();
-    uint64_t pos = 0;
-    bool any = false;
-    uint64_t firstq = 0, lastq = 0;
-    for (uint32_t s : order) {
-      if (h->code_len[s] <= (uint32_t)l) continue;
-      const uint64_t q = l == 0 ? 0 : ((uint64_t)h->code[s] >> (h->code_len[s] - l));
-      if (!any) {
-        firstq = lastq = q;
-        node.push_back(pos);
-        any = true;
-      }
+    uint64_t pos = 0, z = 0, firstq = 0, lastq = 0;
+    const int sh = Lm - l, bsh = Lm - 1 - l;
+    if (first_gt < np) {
+      firstq = lastq = l == 0 ? 0 : lc[first_gt] >> sh;
+      node.push_back(0);
+    }
+    for (size_t i = first_gt; i < np; i++) {
+      const uint64_t q = l == 0 ? 0 : lc[i] >> sh;
       while (lastq < q) {  // consecutive prefixes (empty ones for incomplete codes)
         lastq++;
         node.push_back(pos);
       }
-      pos += hh[s];
+      pos += cnt[i];
+      z += ((lc[i] >> bsh) & 1u) ? 0 : cnt[i];
     }
     node.push_back(pos);  // sentinel = level length
     h->level_len[l] = pos;
+    zc[l] = z;
     node_lvl[3 * l + 1] = firstq;
-    node_lvl[3 * l + 2] = any ? lastq - firstq + 1 : 0;
+    node_lvl[3 * l + 2] = first_gt < np ? lastq - firstq + 1 : 0;
   }
   h->level_off.assign(Lm + 1, 0);
   for (int l = 0; l < Lm; l++) h->level_off[l + 1] = h->level_off[l] + level_words(h->level_len[l]);
   TRY(alloc_outputs(h, std::max<uint64_t>(h->level_off.back(), 1)));
-  // zero counts per level (host): elements whose code bit l is 0
-  {
-    std::vector<uint64_t> z(std::max(Lm, 1), 0);
-    for (uint32_t s = 0; s < sigma; s++)
-      for (uint32_t l = 0; l < h->code_len[s]; l++)
-        if (!((h->code[s] >> (h->code_len[s] - 1 - l)) & 1u)) z[l] += hh[s];
-    h->zeros.assign(z.begin(), z.begin() + Lm);
-    if (Lm) CK(cudaMemcpyAsync(h->d_zeros, h->zeros.data(), Lm * 8, cudaMemcpyHostToDevice, st));
-    h->zeros_valid = true;
-  }
+  // zero counts per level: elements whose code bit l is 0
+  h->zeros.assign(zc.begin(), zc.begin() + Lm);
+  if (Lm) CK(cudaMemcpyAsync(h->d_zeros, h->zeros.data(), Lm * 8, cudaMemcpyHostToDevice, st));
+  h->zeros_valid = true;
   // device tables
   std::vector<uint32_t> left(sigma);
   for (uint32_t s = 0; s < sigma; s++)
@@ -919,9 +955,10 @@ wt_status build_huff(const void* d_seq, uint64_t n, uint32_t sigma, int w, const
       k_tiles_count<<<(unsigned)((nn + 255) / 256), 256, 0, st>>>(bnd, 1, nn, T, tcnt);
       count_launch();
       TRY(scan_excl_u64(tcnt, toff, nn, scr, st));
-      k_tiles_write<<<(unsigned)((nn + 255) / 256), 256, 0, st>>>(bnd, 1, nn, T, node_lvl[3 * pg.a + 1],
-                                                                 toff, tiles, d_ntiles);
-  count_launch();
+      const uint64_t mtw = (h->level_len[pg.a] + T - 1) / T + nn;
+      k_tiles_write<<<(unsigned)((mtw + 255) / 256), 256, 0, st>>>(
+          bnd, 1, nn, T, node_lvl[3 * pg.a + 1], toff, tiles, d_ntiles, mtw);
+      count_launch();
     } else {
       CK(cudaMemsetAsync(d_ntiles, 0, 4, st));
     }

@@ -75,17 +75,31 @@ uint32_t huffman_lengths(const uint64_t* hist, uint32_t sigma, uint32_t cap, uin
   // every leaf id, so both queues stay sorted by (weight, id) and the smaller
   // head is exactly the heap's minimum).
   const size_t m = present.size();
-  std::vector<uint32_t> leaf = present, tmp(m);
+  std::vector<uint32_t> leaf(m);
   {
-    // stable LSD radix sort of the symbols by weight (8 bits per round)
+    // leaves sorted by (weight, symbol): LSD radix sort of the packed keys
+    // weight * 2^24 + symbol (11-bit digits), or a comparison sort when the
+    // weights do not fit 40 bits
     uint64_t wmax = 0;
     for (uint32_t x : present) wmax = std::max(wmax, hist[x]);
-    for (int sh = 0; sh < 64 && (wmax >> sh); sh += 8) {
-      size_t cnt[257] = {0};
-      for (uint32_t x : leaf) cnt[((hist[x] >> sh) & 255) + 1]++;
-      for (int b = 0; b < 256; b++) cnt[b + 1] += cnt[b];
-      for (uint32_t x : leaf) tmp[cnt[(hist[x] >> sh) & 255]++] = x;
-      leaf.swap(tmp);
+    if (wmax < (1ull << 40)) {
+      std::vector<uint64_t> key(m), tmp(m);
+      for (size_t i = 0; i < m; i++) key[i] = (hist[present[i]] << 24) | present[i];
+      int bits = 24;
+      while (bits < 64 && (wmax >> (bits - 24))) bits++;
+      for (int sh = 0; sh < bits; sh += 11) {
+        std::vector<size_t> cnt(2049, 0);
+        for (uint64_t k : key) cnt[((k >> sh) & 2047) + 1]++;
+        for (int b = 0; b < 2048; b++) cnt[b + 1] += cnt[b];
+        for (uint64_t k : key) tmp[cnt[(k >> sh) & 2047]++] = k;
+        key.swap(tmp);
+      }
+      for (size_t i = 0; i < m; i++) leaf[i] = (uint32_t)(key[i] & 0xffffffu);
+    } else {
+      leaf = present;
+      std::sort(leaf.begin(), leaf.end(), [&](uint32_t a, uint32_t b) {
+        return hist[a] != hist[b] ? hist[a] < hist[b] : a < b;
+      });
     }
   }
   std::vector<uint64_t> parent((size_t)sigma + m, 0);

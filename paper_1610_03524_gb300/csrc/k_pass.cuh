@@ -4,16 +4,13 @@
 // atomic ticket, so every wait below is on a tile that is already running).
 // For a tile it computes, in shared memory:
 //   * the tile's bits of levels a..a+t-1, each in the order that level has
-//     inside the tile.  Levels are taken two at a time: one 4-way stable split
-//     of the tile on (b_j, b_j+1) per pair of levels (Section 4.1: the
+//     inside the tile, by t stable 1-bit splits of the tile (Section 4.1: the
 //     descendants' sub-sequences are a stable integer sort on the next tau
 //     bits; Section 4.3: for the wavelet matrix the key is the reversed
-//     digit).  Level j's bits are the ballot words of b_j in the current order;
-//     level j+1's bits (order after the split on b_j alone) are assembled from
-//     warp-wide OR reductions of the b_j+1 bits of each half;
-//   * the element count of every class (node) of every level, from prefix
-//     popcounts of the bit planes inside each class run (prefix sums,
-//     Section 2).
+//     digit, i.e. the splits run from the level-a bit up).  Level j's bits
+//     are the ballot words of b_j in the order after j splits;
+//   * the element count of every class (node) of every level, from the
+//     tile's digit histogram (prefix sums, Section 2).
 // A decoupled look-back (single-pass chained scan) over the tiles then gives,
 // for each class, the count of elements in all earlier tiles: the domain
 // decomposition of Section 4.2 with K = number of tiles and per-node offsets
@@ -23,6 +20,8 @@
 // Finally the tile scatters its elements, narrowed to the bits still needed,
 // to T_{a+t}: the stable partition on the t-bit digit (big nodes, Section 3).
 #pragma once
+#include <type_traits>
+
 #include "wt_internal.cuh"
 
 namespace wtk {
@@ -139,10 +138,9 @@ __global__ void __launch_bounds__(NT + 32, 3) k_pass(const __grid_constant__ Pas
 
   __shared__ uint32_t s_tile;
   __shared__ int s_stat;
-  __shared__ int s_w[4][W];
+  __shared__ int s_ones[W];
   __shared__ int s_scan[W + 1];
   __shared__ int wst[1 << TAU_MAX];
-  __shared__ int btab[W][EPW][4];
   __shared__ uint32_t s_dead[(1 << TAU_MAX) / 32];
   __shared__ uint32_t s_hist[1 << TAU_MAX];
 
@@ -257,8 +255,6 @@ __global__ void __launch_bounds__(NT + 32, 3) k_pass(const __grid_constant__ Pas
     } else {
       for (int i = tid; i < cnt; i += NB) bufA[i] = (E)load_elem(P.in, P.in_w, ts + i);
     }
-    if (!DIG)
-      for (int i = tid; i < (t >> 1) * TW; i += NB) lbits[(2 * (i / TW) + 1) * TW + i % TW] = 0;
     for (int i = tid; i < (1 << TAU_MAX); i += NB) s_hist[i] = 0;
     __syncthreads();
 
@@ -271,7 +267,7 @@ __global__ void __launch_bounds__(NT + 32, 3) k_pass(const __grid_constant__ Pas
     }
     __syncthreads();
 
-    int cur = 0;
+    int cur;
     if (warp == CW) {
       // ---- 3 (control warp). class counts of every level from the digit
       //      histogram; per-digit decoupled look-back for the counts of all
@@ -404,173 +400,65 @@ __global__ void __launch_bounds__(NT + 32, 3) k_pass(const __grid_constant__ Pas
       }
       if (lane == 0) s_stat = status;
     } else {
-      // ---- 4 (worker warps). splits, two levels per shared-memory round --
-      int jj = 0;
-      while (jj < t) {
-        const int j = jj;
-        const bool pair = j + 1 < t;
-        const E* src = cur ? bufB : bufA;
-        E* dst = cur ? bufA : bufB;
-        const bool move = (j + (pair ? 2 : 1) < t) || (P.out != nullptr);
-        const int sh0 = P.rbits - 1 - j;
-        uint32_t* const L0 = lbits + j * TW;
-        if (pair) {
-          uint32_t* const B1p = pb1 + (j >> 1) * TW;
+      // ---- 4 (worker warps). t stable 1-bit splits in shared memory -------
+      // Warp w holds rows 16w..16w+15 of the tile (row = 32 consecutive
+      // positions, one per lane).  Each level: one ballot per row gives the
+      // level's bits in the current order (stored as they are) and, because
+      // every lane sees every ballot of its warp, the ones before each row
+      // are a running sum in uniform registers.  After one exchange of the
+      // warps' one counts, an element at position p with k ones before it
+      // goes to Z + k if its bit is 1 and to p - k otherwise.
+      auto splits = [&](auto full_c) {
+        constexpr bool F = decltype(full_c)::value;
+        const int nmove = P.out != nullptr ? t : t - 1;
+        for (int j = 0; j < t; j++) {
+          const E* src = (j & 1) ? bufB : bufA;
+          E* dst = (j & 1) ? bufA : bufB;
+          const uint32_t m = 1u << (P.rbits - 1 - j);
+          const bool two = DIG && (((P.a + j) & 1) == 0) && (P.a + j + 1 < P.L);
+          uint32_t* const Lj = lbits + j * TW + warp * EPW;
           uint32_t xr[EPW];
-          uint32_t my0 = 0, my1 = 0;
+          int ones = 0;
 #pragma unroll
           for (int e = 0; e < EPW; e++) {
             const int p = wbase + e * 32 + lane;
-            const bool v = full || p < cnt;
-            const uint32_t x = v ? (uint32_t)src[p] : 0u;
+            const uint32_t x = (F || p < cnt) ? (uint32_t)src[p] : 0u;
             xr[e] = x;
-            const uint32_t B0 = __ballot_sync(FULL, (x >> sh0) & 1u);
-            const uint32_t B1 = __ballot_sync(FULL, (x >> (sh0 - 1)) & 1u);
-            if (lane == e) {
-              my0 = B0;
-              my1 = B1;
+            const uint32_t B = __ballot_sync(FULL, x & m);
+            if (lane == 0) Lj[e] = B;
+            ones += __popc(B);
+            if (DIG && two) {
+              const uint32_t B2 = __ballot_sync(FULL, x & (m >> 1));
+              if (lane == 0) pb1[(j >> 1) * TW + warp * EPW + e] = B2;
             }
           }
-          // counts of the four (b_j, b_j+1) classes in iteration `lane`
-          const int vc = lane < EPW ? min(max(cnt - (wbase + lane * 32), 0), 32) : 0;
-          const int o0 = __popc(my0), o1 = __popc(my1), o11 = __popc(my0 & my1);
-          const uint32_t p01 = (uint32_t)(vc - o0 - o1 + o11) | ((uint32_t)(o0 - o11) << 16);
-          const uint32_t p23 = (uint32_t)(o1 - o11) | ((uint32_t)o11 << 16);
-          uint32_t i01 = p01, i23 = p23;
-#pragma unroll
-          for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t y01 = __shfl_up_sync(FULL, i01, o);
-            const uint32_t y23 = __shfl_up_sync(FULL, i23, o);
-            if (lane >= o) {
-              i01 += y01;
-              i23 += y23;
-            }
-          }
-          const uint32_t e01 = i01 - p01, e23 = i23 - p23;
-          if (lane == 31) {
-            s_w[0][warp] = (int)(i01 & 0xffffu);
-            s_w[1][warp] = (int)(i01 >> 16);
-            s_w[2][warp] = (int)(i23 & 0xffffu);
-            s_w[3][warp] = (int)(i23 >> 16);
-          }
-          if (lane < EPW) {
-            L0[warp * EPW + lane] = my0;
-            B1p[warp * EPW + lane] = my1;
-          }
-          bar_workers();
-          int tot[4], wo[4];
-#pragma unroll
-          for (int c = 0; c < 4; c++) {
-            tot[c] = 0;
-            wo[c] = 0;
+          if (j < nmove) {
+            if (lane == 0) s_ones[warp] = ones;
+            bar_workers();
+            int ob = 0, T1 = 0;
 #pragma unroll
             for (int w2 = 0; w2 < W; w2++) {
-              const int x = s_w[c][w2];
-              tot[c] += x;
-              wo[c] += (w2 < warp) ? x : 0;
+              const int v = s_ones[w2];
+              ob += (w2 < warp) ? v : 0;
+              T1 += v;
             }
-          }
-          // ones of b_j before iteration `lane` (classes 1 and 3)
-          const int tp1 = wo[1] + (int)(e01 >> 16), tp3 = wo[3] + (int)(e23 >> 16);
-          const int Z0 = tot[0] + tot[2];  // zeros of b_j in the tile
-          if (lane < EPW) {
-            // where iteration `lane`'s elements of each (b_j, b_j+1) class go
-            btab[warp][lane][0] = wo[0] + (int)(e01 & 0xffffu);
-            btab[warp][lane][1] = tot[0] + tp1;
-            btab[warp][lane][2] = tot[0] + tot[1] + wo[2] + (int)(e23 & 0xffffu);
-            btab[warp][lane][3] = tot[0] + tot[1] + tot[2] + tp3;
-          }
-          __syncwarp();
-          if (move || !DIG) {
-            uint32_t s0 = 0, s1 = 0;
+            const int zb = cnt - T1 + ob;      // destination of this warp's first one
+            const int pl = wbase + lane - ob;  // position minus ones before the warp
+            int u = 0;                         // ones in earlier rows of this warp
 #pragma unroll
             for (int e = 0; e < EPW; e++) {
-              const int p = wbase + e * 32 + lane;
-              const bool v = full || p < cnt;
-              // this iteration's ballot words, kept in the level planes
-              const uint32_t B0 = L0[warp * EPW + e], B1 = B1p[warp * EPW + e];
-              const uint32_t bb0 = (B0 >> lane) & 1u, bb1 = (B1 >> lane) & 1u;
-              if (move) {
-                const int vcnt = full ? 32 : min(max(cnt - (wbase + e * 32), 0), 32);
-                const uint32_t Vm = vcnt >= 32 ? FULL : ((1u << vcnt) - 1u);
-                const uint32_t peers = (bb0 ? B0 : ~B0) & (bb1 ? B1 : ~B1) & Vm;
-                const int r = __popc(peers & lt);
-                if (v) dst[btab[warp][e][bb0 | (bb1 << 1)] + r] = (E)xr[e];
-              }
-              if (!DIG) {
-                // level j+1 in the order after the split on b_j alone: the
-                // b_j+1 bits of this iteration's zeros and ones of b_j
-                const int ro = __popc(B0 & lt);
-                const uint32_t seg0 =
-                    __reduce_or_sync(FULL, (v && !bb0 && bb1) ? (1u << (lane - ro)) : 0u);
-                const uint32_t seg1 = __reduce_or_sync(FULL, (bb0 && bb1) ? (1u << ro) : 0u);
-                if (lane == e) {
-                  s0 = seg0;
-                  s1 = seg1;
-                }
-              }
+              const uint32_t B = Lj[e];
+              const int q = u + __popc(B & lt);
+              const int dest = (xr[e] & m) ? zb + q : pl + 32 * e - q;
+              if (F || wbase + e * 32 + lane < cnt) dst[dest] = (E)xr[e];
+              u += __popc(B);
             }
-            if (!DIG && lane < EPW) {
-              // placed by the lane that owns the iteration
-              const int ob = tp1 + tp3;
-              const int zb = (wbase + lane * 32) - ob;
-              if (s0) or_bits(lbits + (j + 1) * TW, zb, s0);
-              if (s1) or_bits(lbits + (j + 1) * TW, Z0 + ob, s1);
-            }
+            bar_workers();
           }
-          bar_workers();
-        } else {
-          // a single level (the last one of an odd t)
-          uint32_t xr[EPW], br[EPW];
-          uint32_t my0 = 0;
-#pragma unroll
-          for (int e = 0; e < EPW; e++) {
-            const int p = wbase + e * 32 + lane;
-            const bool v = full || p < cnt;
-            const uint32_t x = v ? (uint32_t)src[p] : 0u;
-            xr[e] = x;
-            const uint32_t B0 = __ballot_sync(FULL, (x >> sh0) & 1u);
-            br[e] = B0;
-            if (lane == e) my0 = B0;
-          }
-          const int o0 = __popc(my0);
-          int oi = o0;
-#pragma unroll
-          for (int o = 1; o < 32; o <<= 1) {
-            const int y = __shfl_up_sync(FULL, oi, o);
-            if (lane >= o) oi += y;
-          }
-          if (lane == 31) s_w[0][warp] = oi;
-          if (lane < EPW) L0[warp * EPW + lane] = my0;
-          bar_workers();
-          int wo = 0, T0 = 0;
-#pragma unroll
-          for (int w2 = 0; w2 < W; w2++) {
-            const int x = s_w[0][w2];
-            wo += (w2 < warp) ? x : 0;
-            T0 += x;
-          }
-          const int ope = wo + oi - o0;  // ones before iteration `lane`
-          const int Z0 = cnt - T0;
-          if (move) {
-#pragma unroll
-            for (int e = 0; e < EPW; e++) {
-              const int ob = __shfl_sync(FULL, ope, e);
-              const int p = wbase + e * 32 + lane;
-              if (full || p < cnt) {
-                const uint32_t B0 = br[e];
-                const int r1 = __popc(B0 & lt);
-                const int pos0 = wbase + e * 32;
-                const int dest = ((B0 >> lane) & 1u) ? (Z0 + ob + r1) : (pos0 - ob + (lane - r1));
-                dst[dest] = (E)xr[e];
-              }
-            }
-          }
-          bar_workers();
         }
-        if (move) cur ^= 1;
-        jj += pair ? 2 : 1;
-      }
+      };
+      if (full) splits(std::true_type{});
+      else splits(std::false_type{});
     }
     __syncthreads();
     if (s_stat < 0) {
@@ -580,15 +468,8 @@ __global__ void __launch_bounds__(NT + 32, 3) k_pass(const __grid_constant__ Pas
       }
       return;
     }
-    // the final element order is the same for every worker warp
-    {
-      int moves = 0;
-      for (int j = 0; j < t; j += 2) {
-        const bool pair = j + 1 < t;
-        if ((j + (pair ? 2 : 1) < t) || (P.out != nullptr)) moves++;
-      }
-      cur = moves & 1;
-    }
+    // the final element order is in bufB after an odd number of moves
+    cur = (P.out != nullptr ? t : t - 1) & 1;
 
     // ---- 5. level bitmaps: whole words stored, shared words ORed ----------
     auto emitted = [&](int j) -> bool { return !DIG || (((P.a + j) & 1) == 0); };
