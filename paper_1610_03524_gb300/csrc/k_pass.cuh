@@ -116,8 +116,18 @@ struct PassSmem {
 // BATCH: the launch covers the tiles of several sequences (wavelet matrices
 // of a batched build); each tile reads its sequence's part of the parameters
 // from P0.segs into shared memory.  Otherwise every field comes from P0.
+// resident CTAs per SM the register budget is sized for, and whether a
+// split keeps its 16 elements in registers between its two phases (else it
+// reads them from shared memory again)
+#ifndef WT_PASS_MIN_CTAS
+#define WT_PASS_MIN_CTAS 5
+#endif
+#ifndef WT_PASS_KEEP_X
+#define WT_PASS_KEEP_X 1
+#endif
+
 template <typename E, int T, int NT, bool DIG, bool BATCH>
-__global__ void __launch_bounds__(NT + 32, 3) k_pass(const __grid_constant__ PassParams P0) {
+__global__ void __launch_bounds__(NT + 32, WT_PASS_MIN_CTAS) k_pass(const __grid_constant__ PassParams P0) {
   __shared__ PassParams s_P;
   const PassParams& P = BATCH ? s_P : P0;
   constexpr int W = NT / 32, PW = T / W, EPW = PW / 32, TW = T / 32, NB = NT + 32, CW = W;
@@ -272,131 +282,99 @@ __global__ void __launch_bounds__(NT + 32, 3) k_pass(const __grid_constant__ Pas
       // ---- 3 (control warp). class counts of every level from the digit
       //      histogram; per-digit decoupled look-back for the counts of all
       //      earlier tiles; exclusive counts of every level ----------------
-      // level j classes are the digit values mod 2^j; lane l holds the
-      // digits l + 32i: levels >= 5 sum over i, levels < 5 fold lanes
-      uint32_t h[8];
+      // level j classes are the digit values mod 2^j: level t holds the
+      // digit counts, level j-1 class k sums classes k and k + 2^(j-1)
+      const int nd = 1 << t;
+      for (int k = lane; k < nd; k += 32) ccnt[cls_idx(t, k)] = s_hist[k];
+      __syncwarp();
+      for (int j = t - 1; j >= 0; j--) {
+        for (int k = lane; k < (1 << j); k += 32)
+          ccnt[cls_idx(j, k)] = ccnt[cls_idx(j + 1, k)] + ccnt[cls_idx(j + 1, k + (1 << j))];
+        __syncwarp();
+      }
+      // tile-local class starts: exclusive scan of each level's counts
+      for (int j = 0; j <= t; j++) {
+        uint32_t carry = 0;
+        for (int k0 = 0; k0 < (1 << j); k0 += 32) {
+          const int k = k0 + lane;
+          const uint32_t c = k < (1 << j) ? ccnt[cls_idx(j, k)] : 0u;
+          uint32_t ci = c;
 #pragma unroll
-      for (int i = 0; i < 8; i++) h[i] = s_hist[lane + 32 * i];
-      {
-        for (int j = 8; j >= 5; j--) {
-          if (j > t) continue;
-          const int nsub = 1 << (j - 5);
-          uint32_t carry = 0;
-          for (int sub = 0; sub < nsub; sub++) {
-            uint32_t c = 0;
-#pragma unroll
-            for (int i = 0; i < 8; i++)
-              if ((i & (nsub - 1)) == sub) c += h[i];
-            ccnt[cls_idx(j, lane + 32 * sub)] = c;
-            uint32_t ci = c;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-              const uint32_t y = __shfl_up_sync(FULL, ci, o);
-              if (lane >= o) ci += y;
-            }
-            cstart[cls_idx(j, lane + 32 * sub)] = carry + ci - c;
-            carry += __shfl_sync(FULL, ci, 31);
+          for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(FULL, ci, o);
+            if (lane >= o) ci += y;
           }
-        }
-        uint32_t c5 = 0;
-#pragma unroll
-        for (int i = 0; i < 8; i++) c5 += h[i];
-        for (int j = 5; j >= 0; j--) {
-          if (j < 5) c5 += __shfl_down_sync(FULL, c5, 1 << j);
-          if (j < 5 && j <= t) {
-            const uint32_t v = lane < (1 << j) ? c5 : 0u;
-            uint32_t ci = v;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-              const uint32_t y = __shfl_up_sync(FULL, ci, o);
-              if (lane >= o) ci += y;
-            }
-            if (lane < (1 << j)) {
-              ccnt[cls_idx(j, lane)] = v;
-              cstart[cls_idx(j, lane)] = ci - v;
-            }
-          }
+          if (k < (1 << j)) cstart[cls_idx(j, k)] = carry + ci - c;
+          carry += __shfl_sync(FULL, ci, 31);
         }
       }
       // one 64-bit word per digit: 2-bit flag (1 aggregate, 2 inclusive)
       // above a 62-bit count; the ring is zeroed before every pass
-      const int nd = 1 << t;
       uint64_t* const slot = P0.ring + (uint64_t)(ti & P0.ring_mask) * SLOT_U64;
       constexpr uint64_t CMASK = (1ull << 62) - 1;
-#pragma unroll
-      for (int i = 0; i < 8; i++) {
-        const int r = lane + 32 * i;
-        if (r < nd) st_relaxed_u64(slot + r, ((first ? 2ull : 1ull) << 62) | h[i]);
-      }
-      uint64_t acc[8];
-#pragma unroll
-      for (int i = 0; i < 8; i++) acc[i] = 0;
+      for (int r = lane; r < nd; r += 32)
+        st_relaxed_u64(slot + r, ((first ? 2ull : 1ull) << 62) | s_hist[r]);
       int status = 0;
-      if (!first) {
-        uint32_t pred[8];
-        uint32_t todo = 0;
+      uint64_t* const exd = ex_cnt + cls_idx(t, 0);  // exclusive digit counts
+      // two rounds of four digits per lane keep the look-back state small
+      for (int g = 0; g < 2; g++) {
+        uint64_t acc[4] = {0, 0, 0, 0};
+        if (!first && status == 0) {
+          uint32_t pred[4];
+          uint32_t todo = 0;
 #pragma unroll
-        for (int i = 0; i < 8; i++) {
-          pred[i] = ti - 1;
-          if (lane + 32 * i < nd) todo |= 1u << i;
-        }
-        uint64_t spins = 0;
-        while (__any_sync(FULL, todo != 0)) {
-          uint64_t v[8];
-#pragma unroll
-          for (int i = 0; i < 8; i++)
-            v[i] = (todo >> i & 1u)
-                       ? ld_relaxed_u64(P0.ring + (uint64_t)(pred[i] & P0.ring_mask) * SLOT_U64 + lane + 32 * i)
-                       : 0ull;
-          bool waited = false;
-#pragma unroll
-          for (int i = 0; i < 8; i++) {
-            if (!(todo >> i & 1u)) continue;
-            const uint64_t st = v[i] >> 62;
-            if (st == 0) {
-              waited = true;
-              continue;
-            }
-            acc[i] += v[i] & CMASK;
-            if (st == 2) todo &= ~(1u << i);
-            else pred[i]--;
+          for (int i = 0; i < 4; i++) {
+            pred[i] = ti - 1;
+            if (lane + 32 * (4 * g + i) < nd) todo |= 1u << i;
           }
-          if (__any_sync(FULL, waited)) {
-            int ab = 0;
-            if (lane == 0) ab = (++spins > P0.spin_limit) || ld_volatile_u32(P0.abort_flag);
-            if (__shfl_sync(FULL, ab, 0)) {
-              status = -1;
-              break;
+          uint64_t spins = 0;
+          while (__any_sync(FULL, todo != 0)) {
+            uint64_t v[4];
+#pragma unroll
+            for (int i = 0; i < 4; i++)
+              v[i] = (todo >> i & 1u)
+                         ? ld_relaxed_u64(P0.ring + (uint64_t)(pred[i] & P0.ring_mask) * SLOT_U64 +
+                                          lane + 32 * (4 * g + i))
+                         : 0ull;
+            bool waited = false;
+#pragma unroll
+            for (int i = 0; i < 4; i++) {
+              if (!(todo >> i & 1u)) continue;
+              const uint64_t st = v[i] >> 62;
+              if (st == 0) {
+                waited = true;
+                continue;
+              }
+              acc[i] += v[i] & CMASK;
+              if (st == 2) todo &= ~(1u << i);
+              else pred[i]--;
             }
-            if (spins > 8) __nanosleep(64);
+            if (__any_sync(FULL, waited)) {
+              int ab = 0;
+              if (lane == 0) ab = (++spins > P0.spin_limit) || ld_volatile_u32(P0.abort_flag);
+              if (__shfl_sync(FULL, ab, 0)) {
+                status = -1;
+                break;
+              }
+              if (spins > 8) __nanosleep(64);
+            }
           }
         }
-        if (status == 0) {
 #pragma unroll
-          for (int i = 0; i < 8; i++) {
-            const int r = lane + 32 * i;
-            if (r < nd) st_relaxed_u64(slot + r, (2ull << 62) | (acc[i] + h[i]));
+        for (int i = 0; i < 4; i++) {
+          const int r = lane + 32 * (4 * g + i);
+          if (r < nd) {
+            exd[r] = acc[i];
+            if (!first && status == 0) st_relaxed_u64(slot + r, (2ull << 62) | (acc[i] + s_hist[r]));
           }
         }
       }
+      __syncwarp();
       // exclusive counts of every level from the exclusive digit counts
-      for (int j = 8; j >= 5; j--) {
-        if (j > t) continue;
-        const int nsub = 1 << (j - 5);
-        for (int sub = 0; sub < nsub; sub++) {
-          uint64_t c = 0;
-#pragma unroll
-          for (int i = 0; i < 8; i++)
-            if ((i & (nsub - 1)) == sub) c += acc[i];
-          ex_cnt[cls_idx(j, lane + 32 * sub)] = c;
-        }
-      }
-      uint64_t a5 = 0;
-#pragma unroll
-      for (int i = 0; i < 8; i++) a5 += acc[i];
-      for (int j = 5; j >= 0; j--) {
-        if (j < 5) a5 += __shfl_down_sync(FULL, a5, 1 << j);
-        if (j < 5 && j <= t && lane < (1 << j)) ex_cnt[cls_idx(j, lane)] = a5;
+      for (int j = t - 1; j >= 0; j--) {
+        for (int k = lane; k < (1 << j); k += 32)
+          ex_cnt[cls_idx(j, k)] = ex_cnt[cls_idx(j + 1, k)] + ex_cnt[cls_idx(j + 1, k + (1 << j))];
+        __syncwarp();
       }
       if (lane == 0) s_stat = status;
     } else {
@@ -417,13 +395,17 @@ __global__ void __launch_bounds__(NT + 32, 3) k_pass(const __grid_constant__ Pas
           const uint32_t m = 1u << (P.rbits - 1 - j);
           const bool two = DIG && (((P.a + j) & 1) == 0) && (P.a + j + 1 < P.L);
           uint32_t* const Lj = lbits + j * TW + warp * EPW;
+#if WT_PASS_KEEP_X
           uint32_t xr[EPW];
+#endif
           int ones = 0;
 #pragma unroll
           for (int e = 0; e < EPW; e++) {
             const int p = wbase + e * 32 + lane;
             const uint32_t x = (F || p < cnt) ? (uint32_t)src[p] : 0u;
+#if WT_PASS_KEEP_X
             xr[e] = x;
+#endif
             const uint32_t B = __ballot_sync(FULL, x & m);
             if (lane == 0) Lj[e] = B;
             ones += __popc(B);
@@ -449,8 +431,13 @@ __global__ void __launch_bounds__(NT + 32, 3) k_pass(const __grid_constant__ Pas
             for (int e = 0; e < EPW; e++) {
               const uint32_t B = Lj[e];
               const int q = u + __popc(B & lt);
-              const int dest = (xr[e] & m) ? zb + q : pl + 32 * e - q;
-              if (F || wbase + e * 32 + lane < cnt) dst[dest] = (E)xr[e];
+#if WT_PASS_KEEP_X
+              const uint32_t x = xr[e];
+#else
+              const uint32_t x = (F || wbase + e * 32 + lane < cnt) ? (uint32_t)src[wbase + e * 32 + lane] : 0u;
+#endif
+              const int dest = (x & m) ? zb + q : pl + 32 * e - q;
+              if (F || wbase + e * 32 + lane < cnt) dst[dest] = (E)x;
               u += __popc(B);
             }
             bar_workers();
