@@ -17,6 +17,7 @@
 #include <atomic>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <vector>
 
 #include "k_pass.cuh"
@@ -35,7 +36,27 @@ static std::atomic<uint64_t> g_seq{1};
     }                                                           \
   } while (0)
 
+// Device memory comes from the device's stream-ordered pool.  The pool keeps
+// up to POOL_KEEP bytes of freed memory reserved instead of returning it to
+// the driver at every synchronisation, so repeated builds do not map and
+// unmap their multi-GB buffers each time.
+constexpr uint64_t POOL_KEEP = 32ull << 30;
+
 cudaError_t dmalloc(void** p, size_t bytes, cudaStream_t s) {
+  static std::mutex mu;
+  static bool done[64] = {false};
+  int dev = 0;
+  if (cudaGetDevice(&dev) == cudaSuccess && dev >= 0 && dev < 64) {
+    std::lock_guard<std::mutex> g(mu);
+    if (!done[dev]) {
+      cudaMemPool_t pool;
+      if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+        uint64_t keep = POOL_KEEP;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+      }
+      done[dev] = true;
+    }
+  }
   if (bytes == 0) bytes = 16;
   return cudaMallocAsync(p, bytes, s);
 }
@@ -99,44 +120,71 @@ __device__ __forceinline__ void for_each_symbol(const void* seq, uint64_t n, uin
   for (uint64_t i = nvec * PER + gtid; i < n; i += gstride) f((uint32_t)s[i]);
 }
 
-// Per-pass reversed-digit histograms (wavelet matrix).  Pass g covers levels
-// a = g*tau .. a+t-1; its digit is the t bits below level a read with the
-// level-a bit as the least significant one (Section 4.3: sort on the
-// reverse of the tau bits).
-template <int WB>
-__global__ void k_hist_digits(const void* seq, uint64_t n, uint32_t sigma, int L, int tau,
-                              int G, uint64_t* hist, uint32_t* err) {
+// Per-pass digit histograms (wavelet matrix).  Pass g covers levels
+// a = g*tau .. a+t-1; its digit is the t bits below level a.  The counts are
+// kept by digit value d; the plan reads them by the reversed digit (Section
+// 4.3: the sort key of a pass is the reverse of its tau bits).
+struct HistGeom {
+  int shf[32];
+  uint32_t mask[32];
+  int off[33];
+  int G;
+};
+
+__host__ HistGeom hist_geom(int L, int tau) {
+  HistGeom g;
+  memset(&g, 0, sizeof(g));
+  int o = 0;
+  for (int a = 0; a < L && g.G < 32; a += tau, g.G++) {
+    const int t = std::min(tau, L - a);
+    g.shf[g.G] = L - a - t;
+    g.mask[g.G] = (1u << t) - 1u;
+    g.off[g.G] = o;
+    o += 1 << t;
+  }
+  g.off[g.G] = o;
+  return g;
+}
+
+// NG > 0: the pass count is a compile-time constant and the geometry stays in
+// registers; NG == 0: any pass count, geometry read from shared memory.
+template <int WB, int NG>
+__global__ void k_hist_digits(const void* seq, uint64_t n, uint32_t sigma,
+                              const __grid_constant__ HistGeom geo, uint64_t* hist, uint32_t* err) {
   // at most 1024 bins in total: G passes of 2^t bins, G*2^tau <= 1024 for tau <= 8
   __shared__ uint32_t sh[1024];
-  __shared__ int off[33], tt[32], shf[32];
-  if (threadIdx.x == 0) {
-    int o = 0;
-    for (int g = 0; g < G; g++) {
-      const int a = g * tau;
-      tt[g] = min(tau, L - a);
-      shf[g] = L - a - tt[g];
-      off[g] = o;
-      o += 1 << tt[g];
-    }
-    off[G] = o;
-  }
-  __syncthreads();
-  const int o = off[G];
-  for (int i = threadIdx.x; i < o; i += blockDim.x) sh[i] = 0;
+  const int tot = geo.off[geo.G];
+  for (int i = threadIdx.x; i < tot; i += blockDim.x) sh[i] = 0;
   __syncthreads();
   bool bad = false;
   for_each_symbol<WB>(seq, n, (uint64_t)blockIdx.x * blockDim.x + threadIdx.x,
                       (uint64_t)gridDim.x * blockDim.x, [&](uint32_t x) {
                         bad |= x >= sigma;
-                        for (int g = 0; g < G; g++) {
-                          const uint32_t d = (x >> shf[g]) & ((1u << tt[g]) - 1u);
-                          atomicAdd(&sh[off[g] + rev_bits(d, tt[g])], 1u);
+                        if (NG > 0) {
+#pragma unroll
+                          for (int g = 0; g < NG; g++)
+                            atomicAdd(&sh[geo.off[g] + ((x >> geo.shf[g]) & geo.mask[g])], 1u);
+                        } else {
+                          for (int g = 0; g < geo.G; g++)
+                            atomicAdd(&sh[geo.off[g] + ((x >> geo.shf[g]) & geo.mask[g])], 1u);
                         }
                       });
   if (bad) atomicOr(err, ERR_SYMBOL);
   __syncthreads();
-  for (int i = threadIdx.x; i < o; i += blockDim.x)
+  for (int i = threadIdx.x; i < tot; i += blockDim.x)
     if (sh[i]) atomicAdd((unsigned long long*)&hist[i], (unsigned long long)sh[i]);
+}
+
+template <int WB>
+static void launch_hist_digits_w(const void* seq, uint64_t n, uint32_t sigma, const HistGeom& geo,
+                                 uint64_t* hist, uint32_t* err, uint32_t blocks, cudaStream_t st) {
+  switch (geo.G) {
+    case 1: k_hist_digits<WB, 1><<<blocks, 512, 0, st>>>(seq, n, sigma, geo, hist, err); break;
+    case 2: k_hist_digits<WB, 2><<<blocks, 512, 0, st>>>(seq, n, sigma, geo, hist, err); break;
+    case 3: k_hist_digits<WB, 3><<<blocks, 512, 0, st>>>(seq, n, sigma, geo, hist, err); break;
+    case 4: k_hist_digits<WB, 4><<<blocks, 512, 0, st>>>(seq, n, sigma, geo, hist, err); break;
+    default: k_hist_digits<WB, 0><<<blocks, 512, 0, st>>>(seq, n, sigma, geo, hist, err); break;
+  }
 }
 
 // Full symbol histogram (balanced / Huffman / 4-ary trees).
@@ -308,6 +356,13 @@ struct PassGeom {
   bool wide;  // 32-bit working elements
 };
 
+// bytes per element of the widest intermediate sequence
+static int max_out_w(const std::vector<PassGeom>& ps) {
+  int w = 1;
+  for (const PassGeom& p : ps) w = std::max(w, p.out_w);
+  return w;
+}
+
 static std::vector<PassGeom> make_passes(int L, int tau, int first_w) {
   std::vector<PassGeom> ps;
   for (int a = 0; a < L; a += tau) {
@@ -325,7 +380,8 @@ static std::vector<PassGeom> make_passes(int L, int tau, int first_w) {
 
 // Class starts of every level of every pass of one wavelet matrix, by one
 // block (classes of level a+j are the values of the low j bits of the
-// reversed digit: prefix sums over the digit histogram folded mod 2^j), and
+// reversed digit r: prefix sums over the histogram, read at digit rev(r),
+// folded mod 2^j), and
 // the zero count of every level (the class-0 size after its split).
 __device__ void plan_wm_classes(const uint64_t* hist, int L, int tau, int G, uint64_t* cls,
                                 uint64_t* zeros) {
@@ -338,7 +394,7 @@ __device__ void plan_wm_classes(const uint64_t* hist, int L, int tau, int G, uin
       const int nk = 1 << j;
       for (int k = threadIdx.x; k < nk; k += blockDim.x) {
         uint64_t s = 0;
-        for (int r = k; r < (1 << t); r += nk) s += hist[hoff + r];
+        for (int r = k; r < (1 << t); r += nk) s += hist[hoff + rev_bits((uint32_t)r, t)];
         cnt[k] = s;
       }
       __syncthreads();
@@ -622,9 +678,10 @@ wt_status build_wm(const void* d_seq, uint64_t n, uint32_t sigma, int w, const w
   CK(cudaMemsetAsync(hist, 0, nh * 8, st));
   {
     const uint32_t blocks = std::min<uint64_t>(num_sms() * 4, (n + 8191) / 8192 + 1);
-    if (w == 1) k_hist_digits<1><<<blocks, 512, 0, st>>>(d_seq, n, sigma, L, tau, G, hist, h->d_err);
-    else if (w == 2) k_hist_digits<2><<<blocks, 512, 0, st>>>(d_seq, n, sigma, L, tau, G, hist, h->d_err);
-    else k_hist_digits<4><<<blocks, 512, 0, st>>>(d_seq, n, sigma, L, tau, G, hist, h->d_err);
+    const HistGeom geo = hist_geom(L, tau);
+    if (w == 1) launch_hist_digits_w<1>(d_seq, n, sigma, geo, hist, h->d_err, blocks, st);
+    else if (w == 2) launch_hist_digits_w<2>(d_seq, n, sigma, geo, hist, h->d_err, blocks, st);
+    else launch_hist_digits_w<4>(d_seq, n, sigma, geo, hist, h->d_err, blocks, st);
     count_launch();
     CK(cudaGetLastError());
   }
@@ -637,7 +694,7 @@ wt_status build_wm(const void* d_seq, uint64_t n, uint32_t sigma, int w, const w
   for (int g = 0; g + 1 < G; g++) {
     if (!seqbuf[g & 1]) {
       uint8_t* b;
-      TRY(wk.get(&b, (size_t)n * 4));
+      TRY(wk.get(&b, (size_t)n * max_out_w(ps)));
       seqbuf[g & 1] = b;
     }
   }
@@ -722,7 +779,7 @@ wt_status build_wt(const void* d_seq, uint64_t n, uint32_t sigma, int w, const w
   for (int g = 0; g + 1 < G; g++) {
     if (!seqbuf[g & 1]) {
       uint8_t* b;
-      TRY(wk.get(&b, (size_t)n * 4));
+      TRY(wk.get(&b, (size_t)n * max_out_w(ps)));
       seqbuf[g & 1] = b;
     }
   }
@@ -942,7 +999,7 @@ wt_status build_huff(const void* d_seq, uint64_t n, uint32_t sigma, int w, const
   for (int g = 0; g + 1 < G; g++) {
     if (!seqbuf[g & 1]) {
       uint8_t* b;
-      TRY(wk.get(&b, (size_t)n * 4));
+      TRY(wk.get(&b, (size_t)n * max_out_w(ps)));
       seqbuf[g & 1] = b;
     }
   }
@@ -1008,12 +1065,12 @@ __device__ __forceinline__ void hist_chunk(const HistSeg& d, uint64_t i0, uint64
     bad |= x >= d.sigma;
     for (int g = 0; g < G; g++) {
       const uint32_t dg = (x >> shf[g]) & ((1u << tt[g]) - 1u);
-      atomicAdd(&sh[off[g] + rev_bits(dg, tt[g])], 1u);
+      atomicAdd(&sh[off[g] + dg], 1u);
     }
   }
 }
 
-// Reversed-digit histograms of every pass of every sequence (the per-sequence
+// Digit histograms of every pass of every sequence (the per-sequence
 // counterpart of k_hist_digits), with the symbol check.  The launch walks
 // chunks of HIST_CH symbols; segs are sorted by chunk0.
 __global__ void k_hist_batch(const HistSeg* segs, uint32_t nsegs, uint64_t nchunks,

@@ -59,21 +59,42 @@ __device__ __forceinline__ uint32_t sel64(uint64_t v, uint32_t r) {
 // ---------------------------------------------------------------------------
 // binary directories
 // ---------------------------------------------------------------------------
-__global__ void k_dir_count(const uint64_t* bits, const LevelMeta* meta, int nlev,
-                            const uint64_t* sb_first, uint64_t total_sb, uint64_t* dir,
-                            uint64_t* sbz) {
-  const int lane = threadIdx.x & 31;
-  const uint64_t gw = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
-  for (uint64_t g = gw; g < total_sb; g += nw) {
-    const int l = find_level(sb_first, nlev, g);
-    const LevelMeta m = meta[l];
-    const uint64_t s = g - sb_first[l];
+// One block covers DIR_SB_PER_BLOCK superblocks of one level (blk_first[l]:
+// first block of level l), so the level is found once per block; each warp
+// counts DIR_SB_PER_WARP superblocks with their words loaded together.
+constexpr int DIR_SB_PER_WARP = 4;
+constexpr int DIR_SB_PER_BLOCK = 8 * DIR_SB_PER_WARP;  // 256 threads
+
+__global__ void __launch_bounds__(256) k_dir_count(const uint64_t* bits, const LevelMeta* meta,
+                                                   int nlev, const uint64_t* sb_first,
+                                                   const uint64_t* blk_first, uint64_t* dir,
+                                                   uint64_t* sbz) {
+  __shared__ LevelMeta m;
+  __shared__ uint64_t s_sb0, s_g0;
+  if (threadIdx.x == 0) {
+    const int l = find_level(blk_first, nlev, blockIdx.x);
+    m = meta[l];
+    s_sb0 = (blockIdx.x - blk_first[l]) * DIR_SB_PER_BLOCK;
+    s_g0 = sb_first[l];
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const uint64_t s0 = s_sb0 + (uint64_t)warp * DIR_SB_PER_WARP;
+  uint64_t w[DIR_SB_PER_WARP];
+  int valid[DIR_SB_PER_WARP];
+#pragma unroll
+  for (int u = 0; u < DIR_SB_PER_WARP; u++) {
+    const uint64_t s = s0 + u;
     const int64_t rem = (int64_t)m.n - (int64_t)(2048 * s + 64 * (uint64_t)lane);
-    const int valid = rem <= 0 ? 0 : (rem >= 64 ? 64 : (int)rem);
+    valid[u] = (s >= m.nsb || rem <= 0) ? 0 : (rem >= 64 ? 64 : (int)rem);
     // words past the last valid bit are not read (a caller bitvector may end there)
-    const uint64_t w = valid ? __ldcs(bits + m.bit_off + 32 * s + lane) : 0ull;
-    const int z = valid - __popcll(w);
+    w[u] = valid[u] ? __ldcs(bits + m.bit_off + 32 * s + lane) : 0ull;
+  }
+#pragma unroll
+  for (int u = 0; u < DIR_SB_PER_WARP; u++) {
+    const uint64_t s = s0 + u;
+    if (s >= m.nsb) break;
+    const int z = valid[u] - __popcll(w[u]);
     int zi = z;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -84,7 +105,7 @@ __global__ void k_dir_count(const uint64_t* bits, const LevelMeta* meta, int nle
     const uint64_t r2 = (uint64_t)__shfl_sync(FULL, zi, 15);
     const uint64_t r3 = (uint64_t)__shfl_sync(FULL, zi, 23);
     if (lane == 0) dir[m.dir_off + 2 * s + 1] = (r1 << 16) | (r2 << 32) | (r3 << 48);
-    if (lane == 31) sbz[g] = (uint64_t)zi;
+    if (lane == 31) sbz[s_g0 + s] = (uint64_t)zi;
   }
 }
 
@@ -240,17 +261,25 @@ wt_status dir_build_levels(const uint64_t* bits, const LevelMeta* d_meta, uint32
                            uint64_t* zeros, int write_zeros, cudaStream_t st) {
   if (nlev == 0) return WT_OK;
   const uint64_t total_sb = sb_first[nlev];
+  // blocks of the counting kernel: DIR_SB_PER_BLOCK superblocks of one level each
+  std::vector<uint64_t> firsts(2 * ((size_t)nlev + 1), 0);
+  std::copy(sb_first.begin(), sb_first.end(), firsts.begin());
+  uint64_t* blk_first = firsts.data() + nlev + 1;
+  for (uint32_t l = 0; l < nlev; l++) {
+    const uint64_t nsb = sb_first[l + 1] - sb_first[l];
+    blk_first[l + 1] = blk_first[l] + (nsb + DIR_SB_PER_BLOCK - 1) / DIR_SB_PER_BLOCK;
+  }
+  const uint64_t nblk = blk_first[nlev];
   uint64_t *d_first, *sbz, *sbx, *scr;
-  CK(dmalloc((void**)&d_first, (nlev + 1) * 8, st));
+  CK(dmalloc((void**)&d_first, 2 * ((size_t)nlev + 1) * 8, st));
   CK(dmalloc((void**)&sbz, std::max<uint64_t>(total_sb, 1) * 8, st));
   CK(dmalloc((void**)&sbx, (total_sb + 1) * 8, st));
   CK(dmalloc((void**)&scr, scan_scratch_pub(total_sb) * 8, st));
-  CK(cudaMemcpyAsync(d_first, sb_first.data(), (nlev + 1) * 8, cudaMemcpyHostToDevice, st));
-  const unsigned cgrid = (unsigned)std::min<uint64_t>((total_sb * 32 + 255) / 256 + 1,
-                                                       (uint64_t)num_sms() * 16);
+  CK(cudaMemcpyAsync(d_first, firsts.data(), firsts.size() * 8, cudaMemcpyHostToDevice, st));
   const unsigned fgrid = (unsigned)((total_sb + nlev + 255) / 256);
   if (total_sb) {
-    k_dir_count<<<cgrid, 256, 0, st>>>(bits, d_meta, (int)nlev, d_first, total_sb, dir, sbz);
+    k_dir_count<<<(unsigned)nblk, 256, 0, st>>>(bits, d_meta, (int)nlev, d_first, d_first + nlev + 1,
+                                               dir, sbz);
     count_launch();
   }
   wt_status s = scan_excl_u64_pub(sbz, sbx, total_sb, scr, st);
@@ -312,8 +341,8 @@ wt_status build_directories(wt_struct* h) {
   CK(dmalloc((void**)&sbx, (total_sb + 1) * 8 * 4, st));
   CK(dmalloc((void**)&scr, scan_scratch_pub(total_sb) * 8, st));
   CK(cudaMemcpyAsync(d_first, sb_first.data(), (nlev + 1) * 8, cudaMemcpyHostToDevice, st));
-  const unsigned cgrid = (unsigned)std::min<uint64_t>((total_sb * 32 + 255) / 256 + 1,
-                                                       (uint64_t)num_sms() * 16);
+  // one warp per superblock: enough loads in flight to stream the bitmaps
+  const unsigned cgrid = (unsigned)std::min<uint64_t>((total_sb * 32 + 255) / 256 + 1, 1u << 24);
   const unsigned fgrid = (unsigned)((total_sb + nlev + 255) / 256);
   if (total_sb) {
     k_mdir_count<<<cgrid, 256, 0, st>>>(h->d_bits_ro, h->d_meta, nlev, d_first, total_sb,

@@ -149,6 +149,7 @@ __global__ void __launch_bounds__(NT + 32, WT_PASS_MIN_CTAS) k_pass(const __grid
   __shared__ uint32_t s_tile;
   __shared__ int s_stat;
   __shared__ int s_ones[W];
+  __shared__ uint2 rowq[W * EPW];
   __shared__ int s_scan[W + 1];
   __shared__ int wst[1 << TAU_MAX];
   __shared__ uint32_t s_dead[(1 << TAU_MAX) / 32];
@@ -395,6 +396,7 @@ __global__ void __launch_bounds__(NT + 32, WT_PASS_MIN_CTAS) k_pass(const __grid
           const uint32_t m = 1u << (P.rbits - 1 - j);
           const bool two = DIG && (((P.a + j) & 1) == 0) && (P.a + j + 1 < P.L);
           uint32_t* const Lj = lbits + j * TW + warp * EPW;
+          uint2* const Rw = rowq + warp * EPW;  // (ballot, ones before the row)
 #if WT_PASS_KEEP_X
           uint32_t xr[EPW];
 #endif
@@ -407,7 +409,10 @@ __global__ void __launch_bounds__(NT + 32, WT_PASS_MIN_CTAS) k_pass(const __grid
             xr[e] = x;
 #endif
             const uint32_t B = __ballot_sync(FULL, x & m);
-            if (lane == 0) Lj[e] = B;
+            if (lane == 0) {
+              Lj[e] = B;
+              Rw[e] = make_uint2(B, (uint32_t)ones);
+            }
             ones += __popc(B);
             if (DIG && two) {
               const uint32_t B2 = __ballot_sync(FULL, x & (m >> 1));
@@ -417,20 +422,15 @@ __global__ void __launch_bounds__(NT + 32, WT_PASS_MIN_CTAS) k_pass(const __grid
           if (j < nmove) {
             if (lane == 0) s_ones[warp] = ones;
             bar_workers();
-            int ob = 0, T1 = 0;
-#pragma unroll
-            for (int w2 = 0; w2 < W; w2++) {
-              const int v = s_ones[w2];
-              ob += (w2 < warp) ? v : 0;
-              T1 += v;
-            }
+            const int v = lane < W ? s_ones[lane] : 0;
+            const int T1 = __reduce_add_sync(FULL, v);
+            const int ob = __reduce_add_sync(FULL, lane < warp ? v : 0);
             const int zb = cnt - T1 + ob;      // destination of this warp's first one
             const int pl = wbase + lane - ob;  // position minus ones before the warp
-            int u = 0;                         // ones in earlier rows of this warp
 #pragma unroll
             for (int e = 0; e < EPW; e++) {
-              const uint32_t B = Lj[e];
-              const int q = u + __popc(B & lt);
+              const uint2 R = Rw[e];
+              const int q = (int)R.y + __popc(R.x & lt);
 #if WT_PASS_KEEP_X
               const uint32_t x = xr[e];
 #else
@@ -438,7 +438,6 @@ __global__ void __launch_bounds__(NT + 32, WT_PASS_MIN_CTAS) k_pass(const __grid
 #endif
               const int dest = (x & m) ? zb + q : pl + 32 * e - q;
               if (F || wbase + e * 32 + lane < cnt) dst[dest] = (E)x;
-              u += __popc(B);
             }
             bar_workers();
           }
