@@ -153,6 +153,8 @@ __global__ void __launch_bounds__(NT + 32, WT_PASS_MIN_CTAS) k_pass(const __grid
   __shared__ int s_scan[W + 1];
   __shared__ int wst[1 << TAU_MAX];
   __shared__ uint32_t s_dead[(1 << TAU_MAX) / 32];
+  __shared__ uint64_t s_lvl_bits[TAU_MAX];
+  __shared__ uint64_t* s_lvl_ptr[TAU_MAX];
   __shared__ uint32_t s_hist[1 << TAU_MAX];
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -475,37 +477,48 @@ __global__ void __launch_bounds__(NT + 32, WT_PASS_MIN_CTAS) k_pass(const __grid
       return spread32(b0);
     };
     // words of every (level, class) of this tile, one flattened loop
+    uint64_t* const cls_g0 = cls_cs;  // first global bit of each class run
     int nw = 0;
     if (tid < ntl) {
       const int j = 31 - __clz(tid + 1);
       uint64_t cs = 0, ce = 0;
       bool dead = true;
       if (emitted(j) && ccnt[tid]) class_range(P, j, (uint32_t)(tid + 1 - (1 << j)), node, cs, ce, dead);
-      cls_cs[tid] = dead ? ~0ull : cs;
-      cls_ce[tid] = ce;
       if (!dead) {
         const uint64_t G0 = (cs + ex_cnt[tid]) * bpe;
         const uint64_t G1 = G0 + (uint64_t)ccnt[tid] * bpe;
         nw = (int)(((G1 - 1) >> 6) - (G0 >> 6) + 1);
+        cls_g0[tid] = G0;
       }
+    } else if (tid >= NT && tid - NT < t) {
+      // the control warp: output level of each level of the pass
+      const int j = tid - NT;
+      const int lo_ = DIG ? ((P.a + j) >> 1) : (P.a + j);
+      s_lvl_bits[j] = P.lvl_len[lo_] * (uint64_t)bpe;
+      s_lvl_ptr[j] = P.bits + P.lvl_off[lo_];
     }
     int wtot;
     const int wex = block_scan(nw, wtot);
     if (tid < ntl) wst[tid] = wex;
     __syncthreads();
+    // first word of each level (classes of level j are 2^j-1 .. 2^(j+1)-2)
+    int lvw[TAU_MAX];
+#pragma unroll
+    for (int j = 1; j < TAU_MAX; j++) lvw[j] = j < t ? wst[(1 << j) - 1] : 0x7fffffff;
     for (int x = tid; x < wtot; x += NB) {
-      int lo = 0, hi = ntl - 1;
+      int j = 0;
+#pragma unroll
+      for (int j2 = 1; j2 < TAU_MAX; j2++) j += lvw[j2] <= x ? 1 : 0;
+      int lo = (1 << j) - 1, hi = (2 << j) - 2;
       while (lo < hi) {
         const int mid = (lo + hi + 1) >> 1;
         if (wst[mid] <= x) lo = mid;
         else hi = mid - 1;
       }
       const int ci = lo;
-      const int j = 31 - __clz(ci + 1);
-      const int lo_ = DIG ? ((P.a + j) >> 1) : (P.a + j);
-      const uint64_t nlb = P.lvl_len[lo_] * (uint64_t)bpe;
-      uint64_t* const lb = P.bits + P.lvl_off[lo_];
-      const uint64_t G0 = (cls_cs[ci] + ex_cnt[ci]) * bpe;
+      const uint64_t nlb = s_lvl_bits[j];
+      uint64_t* const lb = s_lvl_ptr[j];
+      const uint64_t G0 = cls_g0[ci];
       const uint64_t G1 = G0 + (uint64_t)ccnt[ci] * bpe;
       const uint64_t w = (G0 >> 6) + (uint64_t)(x - wst[ci]);
       const uint64_t wb = w << 6;
@@ -540,10 +553,26 @@ __global__ void __launch_bounds__(NT + 32, WT_PASS_MIN_CTAS) k_pass(const __grid
       const uint32_t mask = nb >= 32 ? 0xffffffffu : ((1u << nb) - 1u);
       const uint32_t rmask = (1u << t) - 1u;
       const int rsh = 32 - P.rbits;
-      for (int p = tid; p < cnt; p += NB) {
-        const uint32_t x = fin[p];
-        const uint32_t r = (__brev(x) >> rsh) & rmask;
-        if (!((s_dead[r >> 5] >> (r & 31)) & 1u)) store_elem(P.out, P.out_w, sbase[r] + p, x & mask);
+      // only Huffman trees have dead classes (elements leaving the tree)
+      auto scatter = [&](auto out_t, auto huff_c) {
+        using O = decltype(out_t);
+        constexpr bool HF = decltype(huff_c)::value;
+        O* const out = (O*)P.out;
+        for (int p = tid; p < cnt; p += NB) {
+          const uint32_t x = fin[p];
+          const uint32_t r = (__brev(x) >> rsh) & rmask;
+          if (HF && ((s_dead[r >> 5] >> (r & 31)) & 1u)) continue;
+          out[sbase[r] + p] = (O)(x & mask);
+        }
+      };
+      if (P.shape == SHAPE_HUFF) {
+        if (P.out_w == 1) scatter(uint8_t{}, std::true_type{});
+        else if (P.out_w == 2) scatter(uint16_t{}, std::true_type{});
+        else scatter(uint32_t{}, std::true_type{});
+      } else {
+        if (P.out_w == 1) scatter(uint8_t{}, std::false_type{});
+        else if (P.out_w == 2) scatter(uint16_t{}, std::false_type{});
+        else scatter(uint32_t{}, std::false_type{});
       }
     }
     __syncthreads();
