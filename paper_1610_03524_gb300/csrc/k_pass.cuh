@@ -90,11 +90,13 @@ __device__ __forceinline__ uint32_t get32(const uint32_t* pl, int e) {
   return o ? __funnelshift_r(lo, hi, o) : lo;
 }
 
-// OR a segment of bits into a bit plane at bit position pos
-__device__ __forceinline__ void or_bits(uint32_t* pl, int pos, uint32_t seg) {
-  const int w = pos >> 5, o = pos & 31;
-  atomicOr(pl + w, seg << o);
-  if (o && (seg >> (32 - o))) atomicOr(pl + w + 1, seg >> (32 - o));
+// the same over the ballot halves of a level's row words
+template <int TW>
+__device__ __forceinline__ uint32_t get32q(const uint2* pl, int e) {
+  const int w = e >> 5, o = e & 31;
+  const uint32_t lo = (w >= 0 && w < TW) ? pl[w].x : 0u;
+  const uint32_t hi = (w + 1 >= 0 && w + 1 < TW) ? pl[w + 1].x : 0u;
+  return o ? __funnelshift_r(lo, hi, o) : lo;
 }
 
 template <typename E, int T, int NT, bool DIG>
@@ -102,7 +104,7 @@ struct PassSmem {
   static constexpr int TW = T / 32;
   static constexpr size_t off_buf = 0;
   static constexpr size_t off_lbits = off_buf + 2 * (size_t)T * sizeof(E);
-  static constexpr size_t off_pb1 = off_lbits + (size_t)TAU_MAX * TW * 4;
+  static constexpr size_t off_pb1 = off_lbits + (size_t)TAU_MAX * TW * 8;
   static constexpr size_t off_ccnt = off_pb1 + (size_t)(TAU_MAX / 2) * TW * 4;
   static constexpr size_t off_cstart = off_ccnt + (size_t)NCLS * 4;
   static constexpr size_t off_excnt = off_cstart + (size_t)NCLS * 4;  // 8-aligned
@@ -137,7 +139,9 @@ __global__ void __launch_bounds__(NT + 32, WT_PASS_MIN_CTAS) k_pass(const __grid
   extern __shared__ __align__(16) unsigned char smem[];
   E* const bufA = (E*)(smem + SM::off_buf);
   E* const bufB = bufA + T;
-  uint32_t* const lbits = (uint32_t*)(smem + SM::off_lbits);  // level bits, P_j order
+  // per level and row: (ballot of the level's bit = the level's bits in its
+  // order, ones before the row inside its warp)
+  uint2* const rowq = (uint2*)(smem + SM::off_lbits);
   uint32_t* const pb1 = (uint32_t*)(smem + SM::off_pb1);      // b_j+1 plane of pair rounds
   uint32_t* const ccnt = (uint32_t*)(smem + SM::off_ccnt);
   uint32_t* const cstart = (uint32_t*)(smem + SM::off_cstart);
@@ -149,7 +153,6 @@ __global__ void __launch_bounds__(NT + 32, WT_PASS_MIN_CTAS) k_pass(const __grid
   __shared__ uint32_t s_tile;
   __shared__ int s_stat;
   __shared__ int s_ones[W];
-  __shared__ uint2 rowq[W * EPW];
   __shared__ int s_scan[W + 1];
   __shared__ int wst[1 << TAU_MAX];
   __shared__ uint32_t s_dead[(1 << TAU_MAX) / 32];
@@ -397,8 +400,7 @@ __global__ void __launch_bounds__(NT + 32, WT_PASS_MIN_CTAS) k_pass(const __grid
           E* dst = (j & 1) ? bufA : bufB;
           const uint32_t m = 1u << (P.rbits - 1 - j);
           const bool two = DIG && (((P.a + j) & 1) == 0) && (P.a + j + 1 < P.L);
-          uint32_t* const Lj = lbits + j * TW + warp * EPW;
-          uint2* const Rw = rowq + warp * EPW;  // (ballot, ones before the row)
+          uint2* const Rw = rowq + j * TW + warp * EPW;
 #if WT_PASS_KEEP_X
           uint32_t xr[EPW];
 #endif
@@ -411,10 +413,7 @@ __global__ void __launch_bounds__(NT + 32, WT_PASS_MIN_CTAS) k_pass(const __grid
             xr[e] = x;
 #endif
             const uint32_t B = __ballot_sync(FULL, x & m);
-            if (lane == 0) {
-              Lj[e] = B;
-              Rw[e] = make_uint2(B, (uint32_t)ones);
-            }
+            if (lane == 0) Rw[e] = make_uint2(B, (uint32_t)ones);
             ones += __popc(B);
             if (DIG && two) {
               const uint32_t B2 = __ballot_sync(FULL, x & (m >> 1));
@@ -464,12 +463,12 @@ __global__ void __launch_bounds__(NT + 32, WT_PASS_MIN_CTAS) k_pass(const __grid
     // 64 local bits of level j starting at local bit position bp
     auto get64 = [&](int j, int bp) -> uint64_t {
       if (!DIG) {
-        const uint32_t lo = get32<TW>(lbits + j * TW, bp);
-        const uint32_t hi = get32<TW>(lbits + j * TW, bp + 32);
+        const uint32_t lo = get32q<TW>(rowq + j * TW, bp);
+        const uint32_t hi = get32q<TW>(rowq + j * TW, bp + 32);
         return ((uint64_t)hi << 32) | lo;
       }
       const int e = bp >> 1;
-      const uint32_t b0 = get32<TW>(lbits + j * TW, e);
+      const uint32_t b0 = get32q<TW>(rowq + j * TW, e);
       if (P.a + j + 1 < P.L) {
         const uint32_t b1 = get32<TW>(pb1 + (j >> 1) * TW, e);
         return (spread32(b0) << 1) | spread32(b1);

@@ -29,7 +29,10 @@ struct TileDesc {
 
 // Symbols per tile of the partition pass, look-back ring geometry, and the
 // bound on every device-side wait (polls before a wait gives up).
-constexpr int PASS_T = 4096;
+#ifndef WT_PASS_T
+#define WT_PASS_T 4096
+#endif
+constexpr int PASS_T = WT_PASS_T;
 constexpr uint32_t RING_SLOTS = 4096;
 constexpr uint64_t SPIN_LIMIT = 1ull << 24;
 
