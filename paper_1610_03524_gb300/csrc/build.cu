@@ -516,7 +516,10 @@ __global__ void k_tiles_write(const uint64_t* bnd, uint64_t stride, uint64_t nn,
 // ---------------------------------------------------------------------------
 // 3. pass launch
 // ---------------------------------------------------------------------------
-constexpr int PT = PASS_T, PNT = 256;
+#ifndef WT_PASS_NT
+#define WT_PASS_NT 256
+#endif
+constexpr int PT = PASS_T, PNT = WT_PASS_NT;
 
 template <typename E, bool DIG, bool BATCH = false>
 static wt_status launch_pass_t(const PassParams& P, uint64_t max_tiles, const wt_build_opts* o,

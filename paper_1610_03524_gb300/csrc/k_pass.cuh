@@ -102,22 +102,16 @@ __device__ __forceinline__ uint32_t get32q(const uint2* pl, int e) {
 template <typename E, int T, int NT, bool DIG>
 struct PassSmem {
   static constexpr int TW = T / 32;
-  static constexpr size_t off_buf = 0;
-  static constexpr size_t off_lbits = off_buf + 2 * (size_t)T * sizeof(E);
-  static constexpr size_t off_pb1 = off_lbits + (size_t)TAU_MAX * TW * 8;
-  static constexpr size_t off_ccnt = off_pb1 + (size_t)(TAU_MAX / 2) * TW * 4;
+  static constexpr size_t off_buf = 0;                                        // 2 x T elements
+  static constexpr size_t off_lbits = off_buf + 2 * (size_t)T * sizeof(E);   // row words per level
+  static constexpr size_t off_pb1 = off_lbits + (size_t)TAU_MAX * TW * 8;    // second digit bits
+  static constexpr size_t off_ccnt = off_pb1 + (DIG ? (size_t)(TAU_MAX / 2) * TW * 4 : 0);
   static constexpr size_t off_cstart = off_ccnt + (size_t)NCLS * 4;
   static constexpr size_t off_excnt = off_cstart + (size_t)NCLS * 4;  // 8-aligned
   static constexpr size_t off_clscs = off_excnt + (size_t)NCLS * 8;
-  static constexpr size_t off_clsce = off_clscs + (size_t)NTAIL * 8;
-  static constexpr size_t bytes = off_clsce + (size_t)NTAIL * 8;
+  static constexpr size_t bytes = off_clscs + (size_t)(1 << TAU_MAX) * 8;
 };
 
-// NT worker threads run the splits; one extra control warp computes the
-// class counts and runs the look-back meanwhile (block = NT + 32 threads).
-// BATCH: the launch covers the tiles of several sequences (wavelet matrices
-// of a batched build); each tile reads its sequence's part of the parameters
-// from P0.segs into shared memory.  Otherwise every field comes from P0.
 // resident CTAs per SM the register budget is sized for, and whether a
 // split keeps its 16 elements in registers between its two phases (else it
 // reads them from shared memory again)
@@ -147,7 +141,6 @@ __global__ void __launch_bounds__(NT + 32, WT_PASS_MIN_CTAS) k_pass(const __grid
   uint32_t* const cstart = (uint32_t*)(smem + SM::off_cstart);
   uint64_t* const ex_cnt = (uint64_t*)(smem + SM::off_excnt);
   uint64_t* const cls_cs = (uint64_t*)(smem + SM::off_clscs);
-  uint64_t* const cls_ce = (uint64_t*)(smem + SM::off_clsce);
   uint64_t* const sbase = cls_cs;  // reused by the scatter
 
   __shared__ uint32_t s_tile;

@@ -8,7 +8,6 @@ namespace wtk {
 
 constexpr int TAU_MAX = 8;                  // levels per partition pass (upper bound)
 constexpr int NCLS = 1 << (TAU_MAX + 1);    // class-tree slots: level j class k at 2^j-1+k
-constexpr int NTAIL = 1 << TAU_MAX;         // tail slots: levels 0..t-1
 constexpr uint32_t FULL = 0xffffffffu;
 
 // device error word bits
