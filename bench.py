@@ -474,6 +474,9 @@ def run_batch(args, wt):
         e2e = {"value": sl / statistics.median(te) / 1e9, "unit": UNIT,
                "h2d_bytes_per_step": 2 * int(offs[-1]), "d2h_bytes_per_step": 8 * view.levels,
                "steps": k}
+    cpu = None
+    if not args.no_cpu:
+        cpu = _cpu_batch(pin, offs, ln, sig)
     cfg = {"workload": "4096 wavelet matrices with directories, lengths log-uniform in "
                        "[2^10, 2^24] (total 2^31), sigma from {4,256,4096,65536}, uniform or "
                        "Zipf(1.1), uint16: one batched build vs 4096 plain builds",
@@ -483,7 +486,32 @@ def run_batch(args, wt):
           UNIT, 1e3 * mb, cfg, plain={"value": sl / mp / 1e9, "ms_per_step": 1e3 * mp,
                                       "gpu_launches": plain_launches // len(tp)},
           batched_over_plain=mp / mb, gpu_launches=launches // len(tb), clocks=clocks, e2e=e2e,
-          min_ms=1e3 * min(tb), max_ms=1e3 * max(tb))
+          cpu_baseline=cpu, min_ms=1e3 * min(tb), max_ms=1e3 * max(tb))
+
+
+def _cpu_batch(pin, offs, ln, sig, target=1 << 24):
+    """The oracle on the batch's first sequences (about 2^24 symbols): WM
+    levels, rank directory and select samples of every level."""
+    import numpy as np
+    import oracle
+    host = pin.numpy().view(np.uint16)
+    tot = sl = 0
+    t0 = time.perf_counter()
+    i = 0
+    while i < len(ln) and tot < target:
+        S = host[int(offs[i]):int(offs[i]) + ln[i]]
+        bits, _ = oracle.wm_build(S, sig[i])
+        for l in range(bits.shape[0]):
+            oracle.rank_dir(bits[l], S.size)
+            oracle.select_samples(bits[l], S.size, 0)
+            oracle.select_samples(bits[l], S.size, 1)
+        tot += S.size
+        sl += S.size * bits.shape[0]
+        i += 1
+    dt = time.perf_counter() - t0
+    return {"value": sl / dt / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"the first {i} sequences of the batch ({tot} symbols), single-threaded C "
+                      f"oracle: WM levels + rank directory + select samples; {dt:.2f} s"}
 
 
 def run_serve(args, wt):
@@ -500,28 +528,38 @@ def run_serve(args, wt):
     tq_arr = np.cumsum(rng.exponential(1.0 / args.qlam, size=int(args.qlam * D * 2) + 10))
     events = sorted([(t, 0) for t in tb_arr if t < D] + [(t, 1) for t in tq_arr if t < D])
     Q = 1 << 16
-    builds, queries, sub = [], [], []
-    nb = 0
-    t0 = time.perf_counter()
+    # every query batch is drawn before the clock starts: uniform over the
+    # builds submitted before it (by submission index), op, and argument
+    pre = []
+    nsub = 0
     for t, kind in events:
-        while time.perf_counter() - t0 < t:
-            time.sleep(0.0005)
-        if kind == 0 and nb < len(ln):
-            i = nb
-            nb += 1
-            sid = srv.submit_build(host[int(offs[i]):int(offs[i]) + ln[i]], sig[i])
-            builds.append(sid)
-            sub.append((sid, ln[i], sig[i]))
-        elif kind == 1 and sub:
-            k = rng.integers(0, len(sub), size=Q)
-            ns = np.array([x[1] for x in sub], np.uint64)[k]
-            ss = np.array([x[2] for x in sub], np.uint32)[k]
-            sid = np.array([x[0] for x in sub], np.uint64)[k]
+        if kind == 0 and nsub < len(ln):
+            nsub += 1
+            pre.append(None)
+        elif kind == 1 and nsub:
+            k = rng.integers(0, nsub, size=Q)
+            ns = np.array(ln[:nsub], np.uint64)[k]
+            ss = np.array(sig[:nsub], np.uint32)[k]
             op = rng.integers(0, 3, size=Q).astype(np.uint8)
             c = (rng.random(Q) * ss).astype(np.uint32)
             x = (rng.random(Q) * ns).astype(np.uint64)
             x[op == 2] += 1  # select takes k >= 1
-            queries.append(srv.submit_queries(sid, op, c, x))
+            pre.append((k, op, c, x))
+        else:
+            pre.append(False)
+    builds, queries = [], []
+    nb = 0
+    t0 = time.perf_counter()
+    for (t, kind), item in zip(events, pre):
+        while time.perf_counter() - t0 < t:
+            time.sleep(0.0002)
+        if item is None:
+            i = nb
+            nb += 1
+            builds.append(srv.submit_build(host[int(offs[i]):int(offs[i]) + ln[i]], sig[i]))
+        elif item:
+            k, op, c, x = item
+            queries.append(srv.submit_queries(np.array(builds, np.uint64)[k], op, c, x))
     lat_b, lat_q, done_q = [], [], []
     for r in queries:
         st, a, b, _ = srv.poll(r, 0)
@@ -540,8 +578,28 @@ def run_serve(args, wt):
                        f"uniform (structure, op, argument) at {args.qlam}/s, {D} s of arrivals, "
                        f"64 GB admission budget",
            "builds": len(builds), "query_batches": len(queries), "queries_per_batch": Q}
+    cpu = None
+    if not args.no_cpu:
+        # the oracle answering queries of the same mix on one sequence of the
+        # median length (each answer by definition over the sequence)
+        import oracle
+        i = int(np.argsort(np.array(ln))[len(ln) // 2])
+        S = host[int(offs[i]):int(offs[i]) + ln[i]]
+        qn = 256
+        op = rng.integers(0, 3, size=qn).astype(np.uint8)
+        c = (rng.random(qn) * sig[i]).astype(np.uint32)
+        x = (rng.random(qn) * ln[i]).astype(np.uint64)
+        x[op == 2] += 1
+        t0c = time.perf_counter()
+        oracle.access(S, x[op == 0])
+        oracle.rank(S, sig[i], c[op == 1], x[op == 1])
+        oracle.select(S, sig[i], c[op == 2], x[op == 2])
+        dtc = time.perf_counter() - t0c
+        cpu = {"value": qn / dtc, "unit": "queries/s", "cores": 1, "kind": "oracle",
+               "sample": f"{qn} queries of the same mix on one sequence of {ln[i]} symbols "
+                         f"(the median length), single-threaded C oracle; {dtc:.3f} s"}
     _line(args, "queries/s through the serving loop (arrival -> answers on host)", qps,
-          "queries/s", 1e3 * wall, cfg,
+          "queries/s", 1e3 * wall, cfg, cpu_baseline=cpu,
           latency_ms={"query_p50": pct(lat_q, 50), "query_p99": pct(lat_q, 99),
                       "build_p50": pct(lat_b, 50), "build_p99": pct(lat_b, 99)},
           server=stats)
@@ -596,12 +654,48 @@ def run_tree(args, wt):
             h.free()
         res[name] = {"ms_per_build": ms, "symbol_levels": sl, "gsl_per_s": sl / ms / 1e6,
                      "pass_ms": pms / args.steps, "gpu_launches": la // args.steps}
+    cpu = None
+    if not args.no_cpu:
+        cpu = _cpu_tree(args.workload, pin.numpy(), sigma)
     first = builds[0][0]
     cfg = {"workload": f"{' and '.join(b[0] for b in builds)} wavelet trees with directories, "
                        f"{desc}", "n": n, "sigma": sigma}
     _line(args, f"Gsymbol-levels/s ({first} build)", res[first]["gsl_per_s"], UNIT,
           res[first]["ms_per_build"], cfg, dtype="u8" if args.workload == "genome" else "u32",
-          builds=res, gpu_launches=res[first]["gpu_launches"])
+          builds=res, gpu_launches=res[first]["gpu_launches"], cpu_baseline=cpu)
+
+
+def _cpu_tree(workload, host, sigma):
+    """The oracle on a prefix of the same input: the first build of the line
+    (balanced WT for the genome, Huffman-shaped WT for the 2^20 alphabet)
+    with the directories of every level."""
+    import numpy as np
+    import oracle
+    n = 1 << 24 if workload == "genome" else 1 << 22
+    S = np.ascontiguousarray(host[:n])
+    t0 = time.perf_counter()
+    if workload == "genome":
+        bits = oracle.wt_build(S, sigma)
+        for l in range(bits.shape[0]):
+            oracle.rank_dir(bits[l], n)
+            oracle.select_samples(bits[l], n, 0)
+            oracle.select_samples(bits[l], n, 1)
+        sl = n * bits.shape[0]
+        what = "balanced WT levels + rank directory + select samples"
+    else:
+        hist = np.bincount(S.astype(np.int64), minlength=sigma).astype(np.uint64)
+        ln, _ = oracle.huffman_lengths(hist, 32)
+        cd = oracle.canonical_codes(ln)
+        bits, woff, nl = oracle.huff_wt_build(S, ln, cd)
+        for l in range(nl.size):
+            lv = bits[int(woff[l]):int(woff[l + 1])]
+            oracle.rank_dir(lv, int(nl[l]))
+        sl = int(nl.sum())
+        what = "Huffman code + Huffman-shaped WT levels + rank directory"
+    dt = time.perf_counter() - t0
+    return {"value": sl / dt / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"first 2^{n.bit_length() - 1} symbols of the input, single-threaded C oracle: "
+                      f"{what}; {dt:.2f} s"}
 
 
 def run_other(args):

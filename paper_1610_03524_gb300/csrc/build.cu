@@ -18,6 +18,7 @@
 #include <cstdio>
 #include <cstring>
 #include <mutex>
+#include <thread>
 #include <vector>
 
 #include "k_pass.cuh"
@@ -903,13 +904,16 @@ wt_status build_huff(const void* d_seq, uint64_t n, uint32_t sigma, int w, const
     cnt[i] = hh[sy];
   }
   h->level_len.assign(Lm, 0);
-  std::vector<uint64_t> node, node_lvl(3 * (size_t)std::max(Lm, 1), 0);
+  std::vector<uint64_t> node_lvl(3 * (size_t)std::max(Lm, 1), 0);
   std::vector<uint64_t> zc(std::max(Lm, 1), 0);
-  node.reserve(np + Lm);
-  size_t first_gt = 0;  // first index of `order` with length > l
-  for (int l = 0; l < Lm; l++) {
-    while (first_gt < np && h->code_len[order[first_gt]] <= (uint32_t)l) first_gt++;
-    node_lvl[3 * l] = node.size();
+  // levels are independent: each host thread takes every nth level
+  std::vector<std::vector<uint64_t>> lnode(std::max(Lm, 1));
+  std::vector<uint64_t> firstq_l(std::max(Lm, 1), 0), nnode_l(std::max(Lm, 1), 0);
+  auto level_nodes = [&](int l) {
+    // first index of `order` with length > l
+    uint64_t first_gt = 0;
+    for (int ln = 1; ln <= l && ln <= 33; ln++) first_gt += lcount[ln];
+    std::vector<uint64_t>& node = lnode[l];
     uint64_t pos = 0, z = 0, firstq = 0, lastq = 0;
     const int sh = Lm - l, bsh = Lm - 1 - l;
     if (first_gt < np) {
@@ -928,8 +932,30 @@ wt_status build_huff(const void* d_seq, uint64_t n, uint32_t sigma, int w, const
     node.push_back(pos);  // sentinel = level length
     h->level_len[l] = pos;
     zc[l] = z;
-    node_lvl[3 * l + 1] = firstq;
-    node_lvl[3 * l + 2] = first_gt < np ? lastq - firstq + 1 : 0;
+    firstq_l[l] = firstq;
+    nnode_l[l] = first_gt < np ? lastq - firstq + 1 : 0;
+  };
+  {
+    const int nth = std::max(1, std::min<int>(Lm, (int)std::thread::hardware_concurrency()));
+    std::vector<std::thread> th;
+    for (int k = 1; k < nth; k++)
+      th.emplace_back([&, k] {
+        for (int l = k; l < Lm; l += nth) level_nodes(l);
+      });
+    for (int l = 0; l < Lm; l += nth) level_nodes(l);
+    for (auto& x : th) x.join();
+  }
+  std::vector<uint64_t> node;
+  {
+    size_t tot = 0;
+    for (int l = 0; l < Lm; l++) tot += lnode[l].size();
+    node.reserve(tot);
+    for (int l = 0; l < Lm; l++) {
+      node_lvl[3 * l] = node.size();
+      node_lvl[3 * l + 1] = firstq_l[l];
+      node_lvl[3 * l + 2] = nnode_l[l];
+      node.insert(node.end(), lnode[l].begin(), lnode[l].end());
+    }
   }
   h->level_off.assign(Lm + 1, 0);
   for (int l = 0; l < Lm; l++) h->level_off[l + 1] = h->level_off[l] + level_words(h->level_len[l]);

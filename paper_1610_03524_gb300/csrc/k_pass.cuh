@@ -242,11 +242,12 @@ __global__ void __launch_bounds__(NT + 32, WT_PASS_MIN_CTAS) k_pass(const __grid
     if (P.code_map) {
       for (int i = tid; i < cnt; i += NB)
         bufA[i] = (E)P.code_map[load_elem(P.in, P.in_w, ts + i)];
-    } else if (P.in_w == 2 && sizeof(E) == 2 && full && (ts & 7) == 0) {
+    } else if (P.in_w == 2 && sizeof(E) == 2 && full &&
+               (((uintptr_t)P.in + 2 * ts) & 15) == 0) {
       const uint4* src = (const uint4*)((const uint16_t*)P.in + ts);
       uint4* dst = (uint4*)bufA;
       for (int i = tid; i < T / 8; i += NB) dst[i] = __ldcs(src + i);
-    } else if (P.in_w == 1 && sizeof(E) == 2 && full && (ts & 15) == 0) {
+    } else if (P.in_w == 1 && sizeof(E) == 2 && full && (((uintptr_t)P.in + ts) & 15) == 0) {
       const uint4* src = (const uint4*)((const uint8_t*)P.in + ts);
       for (int i = tid; i < T / 16; i += NB) {
         const uint4 q = __ldcs(src + i);

@@ -255,3 +255,24 @@ def test_huffman_tau_levels(wt, tau, seed, n, sigma):
         assert bad.size == 0, (f"level {l} of {mx}: {bad.size} words differ, first {bad[0]} "
                                f"of {a.size}, got {int(a[bad[0]]):016x} exp {int(b[bad[0]]):016x}")
     h.free()
+
+
+@pytest.mark.parametrize("width,off", [(1, 5), (2, 3), (4, 1)])
+def test_unaligned_input_pointer(wt, width, off):
+    """A sequence that starts at an address not 16-byte aligned (a slice of a
+    larger buffer) takes the scalar load paths and builds the same bits."""
+    sigma = {1: 200, 2: 40000, 4: 70000}[width]
+    S = synth.uniform(300 + width, 20000 + off, sigma, width)
+    d = to_dev(S)[off:]
+    Sv = S[off:]
+    for fn in (wt.wm_build, wt.wt_build):
+        h = fn(d, sigma)
+        ex = h.export()
+        ob = oracle.wm_build(Sv, sigma)[0] if fn is wt.wm_build else oracle.wt_build(Sv, sigma)
+        assert np.array_equal(ex.bits.reshape(ob.shape), ob)
+        h.free()
+    hs = wt.wm_batch_build([d, to_dev(S)[1:]], [sigma, sigma])
+    ob, _ = oracle.wm_build(Sv, sigma)
+    assert np.array_equal(hs[0].export().bits.reshape(ob.shape), ob)
+    ob, _ = oracle.wm_build(S[1:], sigma)
+    assert np.array_equal(hs[1].export().bits.reshape(ob.shape), ob)
