@@ -157,6 +157,7 @@ __global__ void __launch_bounds__(NT + 32, WT_PASS_MIN_CTAS) k_pass(const __grid
   const int bpe = DIG ? 2 : 1;
   const uint32_t ntiles = P0.tiles ? *P0.ntiles_dev : P0.ntiles;
   if (BATCH && tid == 0) s_P = P0;
+  for (int i = tid; i < (1 << TAU_MAX); i += NB) s_hist[i] = 0;
   const uint32_t lt = lanemask_lt();
   const int wbase = warp * PW;
 
@@ -238,42 +239,56 @@ __global__ void __launch_bounds__(NT + 32, WT_PASS_MIN_CTAS) k_pass(const __grid
     }
     const bool full = cnt == T;
 
-    // ---- 1. load the tile; clear the planes filled by OR ----------------
-    if (P.code_map) {
-      for (int i = tid; i < cnt; i += NB)
-        bufA[i] = (E)P.code_map[load_elem(P.in, P.in_w, ts + i)];
-    } else if (P.in_w == 2 && sizeof(E) == 2 && full &&
-               (((uintptr_t)P.in + 2 * ts) & 15) == 0) {
-      const uint4* src = (const uint4*)((const uint16_t*)P.in + ts);
-      uint4* dst = (uint4*)bufA;
-      for (int i = tid; i < T / 8; i += NB) dst[i] = __ldcs(src + i);
-    } else if (P.in_w == 1 && sizeof(E) == 2 && full && (((uintptr_t)P.in + ts) & 15) == 0) {
-      const uint4* src = (const uint4*)((const uint8_t*)P.in + ts);
-      for (int i = tid; i < T / 16; i += NB) {
-        const uint4 q = __ldcs(src + i);
-        const uint32_t w4[4] = {q.x, q.y, q.z, q.w};
-        uint4* d = (uint4*)(bufA + 16 * i);
-        uint32_t o[8];
-#pragma unroll
-        for (int k = 0; k < 4; k++) {
-          o[2 * k] = __byte_perm(w4[k], 0, 0x4140);
-          o[2 * k + 1] = __byte_perm(w4[k], 0, 0x4342);
-        }
-        d[0] = make_uint4(o[0], o[1], o[2], o[3]);
-        d[1] = make_uint4(o[4], o[5], o[6], o[7]);
-      }
-    } else {
-      for (int i = tid; i < cnt; i += NB) bufA[i] = (E)load_elem(P.in, P.in_w, ts + i);
-    }
-    for (int i = tid; i < (1 << TAU_MAX); i += NB) s_hist[i] = 0;
-    __syncthreads();
-
-    // ---- 2. digit histogram -------------------------------------------------
+    // ---- 1. load the tile and count its digits (the counters were cleared
+    //      during the previous tile) -------------------------------------
     {
       const uint32_t rmask = (1u << t) - 1u;
       const int rsh = 32 - P.rbits;
-      for (int p = tid; p < cnt; p += NB)
-        atomicAdd(&s_hist[(__brev((uint32_t)bufA[p]) >> rsh) & rmask], 1u);
+      auto count = [&](uint32_t x) { atomicAdd(&s_hist[(__brev(x) >> rsh) & rmask], 1u); };
+      if (P.code_map) {
+        for (int i = tid; i < cnt; i += NB) {
+          const uint32_t x = P.code_map[load_elem(P.in, P.in_w, ts + i)];
+          bufA[i] = (E)x;
+          count(x);
+        }
+      } else if (P.in_w == 2 && sizeof(E) == 2 && full &&
+                 (((uintptr_t)P.in + 2 * ts) & 15) == 0) {
+        const uint4* src = (const uint4*)((const uint16_t*)P.in + ts);
+        uint4* dst = (uint4*)bufA;
+        for (int i = tid; i < T / 8; i += NB) {
+          const uint4 q = __ldcs(src + i);
+          dst[i] = q;
+          const uint32_t w4[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+          for (int k = 0; k < 4; k++) {
+            count(w4[k] & 0xffffu);
+            count(w4[k] >> 16);
+          }
+        }
+      } else if (P.in_w == 1 && sizeof(E) == 2 && full && (((uintptr_t)P.in + ts) & 15) == 0) {
+        const uint4* src = (const uint4*)((const uint8_t*)P.in + ts);
+        for (int i = tid; i < T / 16; i += NB) {
+          const uint4 q = __ldcs(src + i);
+          const uint32_t w4[4] = {q.x, q.y, q.z, q.w};
+          uint4* d = (uint4*)(bufA + 16 * i);
+          uint32_t o[8];
+#pragma unroll
+          for (int k = 0; k < 4; k++) {
+            o[2 * k] = __byte_perm(w4[k], 0, 0x4140);
+            o[2 * k + 1] = __byte_perm(w4[k], 0, 0x4342);
+#pragma unroll
+            for (int b = 0; b < 4; b++) count((w4[k] >> (8 * b)) & 0xffu);
+          }
+          d[0] = make_uint4(o[0], o[1], o[2], o[3]);
+          d[1] = make_uint4(o[4], o[5], o[6], o[7]);
+        }
+      } else {
+        for (int i = tid; i < cnt; i += NB) {
+          const uint32_t x = load_elem(P.in, P.in_w, ts + i);
+          bufA[i] = (E)x;
+          count(x);
+        }
+      }
     }
     __syncthreads();
 
@@ -451,6 +466,10 @@ __global__ void __launch_bounds__(NT + 32, WT_PASS_MIN_CTAS) k_pass(const __grid
     }
     // the final element order is in bufB after an odd number of moves
     cur = (P.out != nullptr ? t : t - 1) & 1;
+
+    // the digit counters are read for the last time by the control warp
+    // before the splits end: clear them for the next tile
+    for (int i = tid; i < (1 << TAU_MAX); i += NB) s_hist[i] = 0;
 
     // ---- 5. level bitmaps: whole words stored, shared words ORed ----------
     auto emitted = [&](int j) -> bool { return !DIG || (((P.a + j) & 1) == 0); };
