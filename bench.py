@@ -375,7 +375,8 @@ def run_native(args):
 # the other workloads (one JSON line each; not the headline)
 # --------------------------------------------------------------------------
 def _line(args, metric, value, unit, ms, cfg, **kw):
-    d = {"metric": metric, "value": value, "unit": unit, "n_gpus": 1, "steps": args.steps,
+    d = {"metric": metric, "value": value, "unit": unit, "n_gpus": kw.pop("n_gpus", 1),
+         "steps": args.steps,
          "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
          "vs_baseline": None, "dtype": kw.pop("dtype", "u16"), "data": "synthetic",
          "config": cfg}
@@ -383,15 +384,23 @@ def _line(args, metric, value, unit, ms, cfg, **kw):
     print(json.dumps(d), flush=True)
 
 
-def _batch_workload(m=4096):
+def _batch_workload(m=4096, world=1, rank=0):
     """The batched configuration: lengths log-uniform in [2^10, 2^24] (total
     capped at 2^31), sigma from {4, 256, 4096, 65536}, uniform or Zipf(1.1),
-    uint16; one pinned host array with 16-byte aligned sequence starts."""
+    uint16; one pinned host array with 16-byte aligned sequence starts.  With
+    several ranks, this rank's share of the sequences (independent problems,
+    longest-first balanced)."""
     import numpy as np
     import torch
     from concurrent.futures import ThreadPoolExecutor
     import synth
+    from paper_1610_03524_gb300 import dist as wdist
     ln, sig, zf, sd, total = synth.batch_plan(synth.SEED_BASE + 5, m, 10, 24, 1 << 31)
+    if world > 1:
+        mine = wdist.shard(ln, world, rank)
+        ln, sig, zf, sd = ln[mine], sig[mine], zf[mine], sd[mine]
+        m = len(mine)
+        total = int(ln.sum())
     offs = np.zeros(m + 1, np.int64)
     for i in range(m):
         offs[i + 1] = offs[i] + (int(ln[i]) + 7) // 8 * 8
@@ -413,7 +422,10 @@ def _batch_workload(m=4096):
 def run_batch(args, wt):
     import numpy as np
     import torch
-    pin, offs, ln, sig, zf, total = _batch_workload()
+    import torch.distributed as tdist
+    from paper_1610_03524_gb300 import dist as wdist
+    ws, rank, _ = dist_env()
+    pin, offs, ln, sig, zf, total = _batch_workload(world=ws, rank=rank)
     m = len(ln)
     d = pin.to("cuda")
     seqs = [d[int(offs[i]):int(offs[i]) + ln[i]] for i in range(m)]
@@ -422,11 +434,15 @@ def run_batch(args, wt):
     def timed(fn, reps):
         out = []
         for _ in range(reps):
+            if ws > 1:
+                tdist.barrier()
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             hs = fn()
             torch.cuda.synchronize()
-            out.append(time.perf_counter() - t0)
+            if ws > 1:
+                tdist.barrier()
+            out.append(wdist.max_over_ranks(time.perf_counter() - t0))
             for h in hs:
                 h.sync()
                 h.free()
@@ -448,7 +464,8 @@ def run_batch(args, wt):
     plain_launches, _, _ = wt.prof_read()
     wt.prof_enable(False)
     hs = wt.wm_batch_build(seqs, sig)
-    sl = sum(h.symbol_levels() for h in hs)
+    sl = int(wdist.sum_over_ranks(sum(h.symbol_levels() for h in hs)))
+    total = int(wdist.sum_over_ranks(total))
     for h in hs:
         h.free()
     mb, mp = statistics.median(tb), statistics.median(tp)
@@ -462,28 +479,34 @@ def run_batch(args, wt):
         k = max(1, min(args.steps, 3))
         te = []
         for _ in range(k):
+            if ws > 1:
+                tdist.barrier()
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             dbuf.copy_(pin, non_blocking=True)
             hs = wt.wm_batch_build([dbuf[int(offs[i]):int(offs[i]) + ln[i]] for i in range(m)], sig)
             # waits for the batch and copies sequence 0's per-level zero counts
             wt._check(lib.wt_export(hs[0].raw, ctypes.byref(view)), "wt_export")
-            te.append(time.perf_counter() - t0)
+            te.append(wdist.max_over_ranks(time.perf_counter() - t0))
             for h in hs:
                 h.free()
         e2e = {"value": sl / statistics.median(te) / 1e9, "unit": UNIT,
-               "h2d_bytes_per_step": 2 * int(offs[-1]), "d2h_bytes_per_step": 8 * view.levels,
+               "h2d_bytes_per_step": int(wdist.sum_over_ranks(2 * int(offs[-1]))),
+               "d2h_bytes_per_step": int(wdist.sum_over_ranks(8 * view.levels)),
                "steps": k}
     cpu = None
-    if not args.no_cpu:
+    if not args.no_cpu and ws == 1:
         cpu = _cpu_batch(pin, offs, ln, sig)
+    if rank != 0:
+        return
     cfg = {"workload": "4096 wavelet matrices with directories, lengths log-uniform in "
                        "[2^10, 2^24] (total 2^31), sigma from {4,256,4096,65536}, uniform or "
                        "Zipf(1.1), uint16: one batched build vs 4096 plain builds",
            "sequences": m, "symbols": total, "symbol_levels": sl,
            "l2": "inputs (4 GiB) larger than L2; no flush needed"}
+    cfg["parallelism"] = f"sequences sharded over {ws} rank(s), no data-path collective"
     _line(args, "Gsymbol-levels/s batched build (wall clock, inputs resident)", sl / mb / 1e9,
-          UNIT, 1e3 * mb, cfg, plain={"value": sl / mp / 1e9, "ms_per_step": 1e3 * mp,
+          UNIT, 1e3 * mb, cfg, n_gpus=ws, plain={"value": sl / mp / 1e9, "ms_per_step": 1e3 * mp,
                                       "gpu_launches": plain_launches // len(tp)},
           batched_over_plain=mp / mb, gpu_launches=launches // len(tb), clocks=clocks, e2e=e2e,
           cpu_baseline=cpu, min_ms=1e3 * min(tb), max_ms=1e3 * max(tb))
@@ -710,6 +733,17 @@ def run_other(args):
     __graft_entry__.build()
     import paper_1610_03524_gb300 as wt
     torch.cuda.set_device(local)
+    if args.workload == "batch":
+        if ws > 1:
+            import torch.distributed as tdist
+            tdist.init_process_group("nccl")
+        run_batch(args, wt)
+        if ws > 1:
+            tdist.barrier()
+            tdist.destroy_process_group()
+        return 0
+    if rank != 0:
+        return 0  # the other workloads run on one GPU
     if args.workload == "batch":
         run_batch(args, wt)
     elif args.workload == "serve":
