@@ -54,6 +54,31 @@ void orc_rank_dir(const uint64_t* bits, uint64_t nbits, uint64_t* rec);
 uint64_t orc_select_samples(const uint64_t* bits, uint64_t nbits, uint32_t b,
                             uint64_t* samp);
 
+/* Constant-time select directory after Clark (§5.1 select: positions of
+ * every k-th occurrence define ranges; long ranges store all answers,
+ * short ones are sampled again into sub-ranges, long sub-ranges store all
+ * answers, short ones are searched within a bounded span).  Fixed here for
+ * 64-bit words: ranges of 4096 occurrences (the select samples), 16
+ * sub-ranges of 256 occurrences per range; a range of at least huge_min
+ * bits stores the absolute positions of its 4096 occurrences; a sub-range of
+ * at least sparse_min bits stores the offsets (from its range's start) of
+ * its 256 occurrences.  For occurrences of bit value b:
+ *   desc[k]   range k: huge: 2^63 | 4096 * (huge ranges before k);
+ *             else (sparse sub-ranges in earlier non-huge ranges) |
+ *             (16-bit mask of its sparse sub-ranges) << 40
+ *   sub[16k+i] offset of occurrence 4096k+256i from the range's start
+ *             (0xffffffff past the last occurrence; 0 in huge ranges)
+ *   sparse[256s+j] offset from its range's start of occurrence j of the
+ *             s-th sparse sub-range (0xffffffff past the last occurrence)
+ *   huge[4096h+j]  position of occurrence j of the h-th huge range
+ *             (UINT64_MAX past the last occurrence)
+ * huge_min <= 2^32 keeps every stored offset within 32 bits.  Call with
+ * NULL arrays to get the three counts first.  Returns 0, or -1 when out of
+ * memory. */
+int orc_clark_build(const uint64_t* bits, uint64_t nbits, uint32_t b, uint64_t huge_min,
+                    uint64_t sparse_min, uint64_t* nranges, uint64_t* nhuge, uint64_t* nsparse,
+                    uint64_t* desc, uint32_t* sub, uint32_t* sparse, uint64_t* huge);
+
 /* Huffman code lengths (§4.3 arbitrary-shaped trees; Huffman shape).
  * Heap keyed (weight, id), leaf id = symbol, internal id = sigma + creation
  * index; symbols with count 0 get length 0; a single present symbol gets

@@ -142,6 +142,74 @@ uint64_t orc_select_samples(const uint64_t* bits, uint64_t nbits, uint32_t b,
 }
 
 /* ---------------------------------------------------------------------- */
+/* Clark-style select directory (§5.1 select), as defined in oracle.h.      */
+/* ---------------------------------------------------------------------- */
+int orc_clark_build(const uint64_t* bits, uint64_t nbits, uint32_t b, uint64_t huge_min,
+                    uint64_t sparse_min, uint64_t* nranges, uint64_t* nhuge, uint64_t* nsparse,
+                    uint64_t* desc, uint32_t* sub, uint32_t* sparse, uint64_t* huge) {
+  /* pass 1: the positions of occurrences 0, 256, 512, ... */
+  uint64_t cnt = 0;
+  for (uint64_t p = 0; p < nbits; p++)
+    if ((uint32_t)getbit(bits, p) == b) cnt++;
+  uint64_t M = (cnt + 255) / 256, R = (cnt + 4095) / 4096;
+  uint64_t* p256 = (uint64_t*)malloc((M + 1) * sizeof(uint64_t));
+  if (!p256) return -1;
+  uint64_t c = 0;
+  for (uint64_t p = 0; p < nbits; p++) {
+    if ((uint32_t)getbit(bits, p) == b) {
+      if (c % 256 == 0) p256[c / 256] = p;
+      c++;
+    }
+  }
+  /* ranges: range k starts at occurrence 4096k and ends where range k+1
+     starts (the last one at the end of the bitvector) */
+  uint64_t nh = 0, ns = 0;
+  for (uint64_t k = 0; k < R; k++) {
+    uint64_t S1 = p256[16 * k];
+    uint64_t e = (k + 1 < R) ? p256[16 * (k + 1)] : nbits;
+    int is_huge = (e - S1) >= huge_min;
+    uint32_t mask = 0;
+    for (uint64_t i = 0; i < 16; i++) {
+      uint64_t m = 16 * k + i;
+      if (sub) sub[m] = is_huge ? 0u : (m < M ? (uint32_t)(p256[m] - S1) : 0xffffffffu);
+      if (is_huge || m >= M) continue;
+      uint64_t end = (i + 1 < 16 && m + 1 < M) ? p256[m + 1] : e;
+      if (end - p256[m] >= sparse_min) mask |= 1u << i;
+    }
+    if (desc) {
+      if (is_huge) desc[k] = ((uint64_t)1 << 63) | (4096 * nh);
+      else desc[k] = ns | ((uint64_t)mask << 40);
+    }
+    /* pass 2 for this range: every occurrence it stores explicitly */
+    if (is_huge) {
+      if (huge) {
+        uint64_t j = 0;
+        for (uint64_t p = S1; p < e && j < 4096; p++)
+          if ((uint32_t)getbit(bits, p) == b) huge[4096 * nh + j++] = p;
+        for (; j < 4096; j++) huge[4096 * nh + j] = NONE;
+      }
+      nh++;
+    } else {
+      for (uint64_t i = 0; i < 16; i++) {
+        if (!((mask >> i) & 1u)) continue;
+        if (sparse) {
+          uint64_t m = 16 * k + i, j = 0;
+          for (uint64_t p = p256[m]; p < nbits && j < 256; p++)
+            if ((uint32_t)getbit(bits, p) == b) sparse[256 * ns + j++] = (uint32_t)(p - S1);
+          for (; j < 256; j++) sparse[256 * ns + j] = 0xffffffffu;
+        }
+        ns++;
+      }
+    }
+  }
+  free(p256);
+  if (nranges) *nranges = R;
+  if (nhuge) *nhuge = nh;
+  if (nsparse) *nsparse = ns;
+  return 0;
+}
+
+/* ---------------------------------------------------------------------- */
 /* Huffman code lengths (§4.3: the tree shape is given by codewords; the    */
 /* Huffman shape is the example the paper names).                          */
 /* ---------------------------------------------------------------------- */

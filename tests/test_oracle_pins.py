@@ -361,3 +361,71 @@ def test_queries_definition():
         occ = [j for j in range(n) if Sl[j] == c] if c < sigma else []
         exp = occ[k - 1] if (c < sigma and 1 <= k <= len(occ)) else 2 ** 64 - 1
         assert int(sl[t]) == exp
+
+
+# ---------------------------------------------------------------------------
+# constant-time select directory (§5.1 select after Clark): answers read
+# from the oracle's arrays by the definition in oracle.h equal the brute-force
+# position of every occurrence; small thresholds make all three kinds of
+# range and sub-range appear
+# ---------------------------------------------------------------------------
+def _clark_answer(desc, sub, sparse, huge, samp, bits, nbits, b, j):
+    k = j >> 12
+    d = int(desc[k])
+    if d >> 63:
+        return int(huge[(d & ((1 << 63) - 1)) + (j & 4095)])
+    i = (j >> 8) & 15
+    mask = (d >> 40) & 0xFFFF
+    S1 = int(samp[k])
+    if (mask >> i) & 1:
+        s = (d & ((1 << 40) - 1)) + bin(mask & ((1 << i) - 1)).count("1")
+        return S1 + int(sparse[256 * s + (j & 255)])
+    p = S1 + int(sub[16 * k + i])
+    need = j & 255  # occurrences to skip after the sub-range's first one
+    while True:
+        if ((int(bits[p >> 6]) >> (p & 63)) & 1) == b:
+            if need == 0:
+                return p
+            need -= 1
+        p += 1
+
+
+@pytest.mark.parametrize("seed,nbits,density,huge_min,sparse_min", [
+    (1, 30000, 0.5, 1 << 32, 1 << 16),
+    (2, 200000, 0.02, 1 << 14, 1 << 11),
+    (3, 200000, 0.002, 1 << 14, 1 << 11),
+    (4, 120000, 0.98, 1 << 13, 1 << 10),
+    (5, 65536, 0.0001, 1 << 12, 1 << 9),
+    (6, 5000, 0.3, 1 << 32, 1 << 16),
+])
+def test_clark_select_answers_every_occurrence(seed, nbits, density, huge_min, sparse_min):
+    rng = np.random.default_rng(seed)
+    # runs of dense and sparse stretches, so ranges of every kind appear
+    raw = rng.random(nbits)
+    dens = np.where((np.arange(nbits) // 7000) % 3 == 0, density, min(0.5, density * 50))
+    x = (raw < dens).astype(np.uint8)
+    words = np.zeros(oracle.level_words(nbits), dtype=np.uint64)
+    packed = np.packbits(x, bitorder="little")
+    words.view(np.uint8)[:packed.size] = packed
+    kinds = set()
+    for b in (0, 1):
+        pos = np.nonzero(x == b)[0]
+        desc, sub, sparse, huge = oracle.clark(words, nbits, b, huge_min, sparse_min)
+        samp = oracle.select_samples(words, nbits, b)
+        assert desc.size == (pos.size + 4095) // 4096 == samp.size
+        for k in range(desc.size):
+            d = int(desc[k])
+            kinds.add("huge" if d >> 63 else ("sparse" if (d >> 40) & 0xFFFF else "dense"))
+            if not d >> 63:
+                assert sub[16 * k] == 0
+        # every occurrence on small inputs; every 4096-th, every sub-range
+        # start and a seeded sample on the larger ones
+        js = np.arange(pos.size)
+        if pos.size > 20000:
+            js = np.unique(np.concatenate([js[::256], js[255::256], js[-300:],
+                                           rng.integers(0, pos.size, 6000)]))
+        for j in js:
+            j = int(j)
+            assert _clark_answer(desc, sub, sparse, huge, samp, words, nbits, b, j) == pos[j], (b, j)
+    if seed in (2, 3, 5):
+        assert "huge" in kinds or "sparse" in kinds
