@@ -67,6 +67,8 @@ typedef struct {
 } wt_build_opts;
 
 #define WT_FLAG_NO_DIRECTORY 1u  /* skip rank/select directories (timing of the bitmap build) */
+#define WT_FLAG_SELECT_O1 2u     /* also build the constant-time select directory of every
+                                    binary level (wt/wm/Huffman/rs builds; not 4-ary, not batched) */
 
 enum { WT_KIND_WT = 0, WT_KIND_WM = 1, WT_KIND_HUFF = 2, WT_KIND_MULTI = 3, WT_KIND_RS = 4 };
 
@@ -268,6 +270,30 @@ wt_status wt_sync(wt_handle h);
 
 /* Fills *out with views of the handle's arrays (synchronises the stream). */
 wt_status wt_export(wt_handle h, wt_export_view* out);
+
+/* The constant-time select directory of one binary level and bit value
+ * (after Clark, Section 5.1 select), built with WT_FLAG_SELECT_O1.  Ranges
+ * of 4096 occurrences start at the select samples; a range of at least 2^32
+ * bits keeps the positions of its occurrences ("huge"); the others keep the
+ * offsets of occurrences 256i (i < 16) from the range's start ("sub"), and a
+ * sub-range of at least 2^16 bits keeps the offsets of its 256 occurrences
+ * ("sparse").  Shorter sub-ranges are searched in the rank directory within
+ * their fewer than 2^16 bits, so a select visits a bounded number of words.
+ *   desc[k]: huge: 2^63 | first index of the range in huge;
+ *            else: index (in sub-ranges of 256) of its first sparse sub-range
+ *            | (16-bit mask of its sparse sub-ranges) << 40
+ *   sub[16k+i], sparse[256s+j]: u32 offsets (0xffffffff past the last
+ *   occurrence; sub is 0 in huge ranges); huge[4096h+j]: u64 positions
+ *   (UINT64_MAX past the last occurrence).
+ * Device pointers, owned by the handle.  Synchronises the stream. */
+typedef struct {
+  uint64_t nranges, nhuge, nsparse;
+  const uint64_t* desc;    /* nranges */
+  const uint32_t* sub;     /* 16 * nranges */
+  const uint32_t* sparse;  /* 256 * nsparse */
+  const uint64_t* huge;    /* 4096 * nhuge */
+} wt_select_view;
+wt_status wt_export_select(wt_handle h, uint32_t level, uint32_t bit, wt_select_view* out);
 
 /* Frees the handle and every array it owns (after its stream's work). */
 wt_status wt_free(wt_handle h);

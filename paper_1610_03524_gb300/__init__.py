@@ -22,6 +22,7 @@ STATUS = {0: "ok", 1: "invalid argument", 2: "symbol >= sigma", 3: "out of devic
           4: "CUDA error", 5: "bounded device wait ran out", 6: "unsupported"}
 KIND_WT, KIND_WM, KIND_HUFF, KIND_MULTI, KIND_RS = range(5)
 FLAG_NO_DIRECTORY = 1
+FLAG_SELECT_O1 = 2
 
 #: every entry point declared in include/wavelet.h
 ABI_SYMBOLS = ("wt_build", "wm_build", "huff_wt_build", "multiary_build", "rs_build",
@@ -31,7 +32,7 @@ ABI_SYMBOLS = ("wt_build", "wm_build", "huff_wt_build", "multiary_build", "rs_bu
                "wm_batch_build", "wm_autotune", "wm_autotune_clear", "wt_query_multi",
                "wt_server_create", "wt_server_submit_build", "wt_server_submit_queries",
                "wt_server_poll", "wt_server_handle", "wt_server_release", "wt_server_stats",
-               "wt_server_destroy")
+               "wt_server_destroy", "wt_export_select")
 
 
 class WaveletError(RuntimeError):
@@ -58,6 +59,12 @@ class ExportView(ctypes.Structure):
                 ("zeros", ctypes.POINTER(ctypes.c_uint64)),
                 ("code_len", ctypes.POINTER(ctypes.c_uint8)),
                 ("code", ctypes.POINTER(ctypes.c_uint32))]
+
+
+class SelectView(ctypes.Structure):
+    _fields_ = [("nranges", ctypes.c_uint64), ("nhuge", ctypes.c_uint64),
+                ("nsparse", ctypes.c_uint64), ("desc", ctypes.c_void_p), ("sub", ctypes.c_void_p),
+                ("sparse", ctypes.c_void_p), ("huge", ctypes.c_void_p)]
 
 
 class BatchItem(ctypes.Structure):
@@ -129,6 +136,8 @@ def load_library(path: str = LIB_PATH):
     lib.wt_canonical_codes.argtypes = [vp, u32, vp]
     lib.rs_dir_build_static.restype = c.c_int
     lib.rs_dir_build_static.argtypes = [vp, u64, vp, vp, vp, vp]
+    lib.wt_export_select.restype = c.c_int
+    lib.wt_export_select.argtypes = [vp, u32, u32, c.POINTER(SelectView)]
     lib.wm_batch_build.restype = c.c_int
     lib.wm_batch_build.argtypes = [c.POINTER(BatchItem), u32, c.POINTER(BuildOpts), vp, hp]
     lib.wm_autotune.restype = c.c_int
@@ -294,6 +303,19 @@ class Handle:
         return Exported(v.kind, L, v.n, v.sigma, v.bits_per_elem, v.max_code_len, level_len,
                         level_off, dir_off, samp_off, zeros, bits, dirs, samp, code_len, code)
 
+    def export_select(self, level: int, bit: int):
+        """Arrays of the constant-time select directory of one level and bit
+        value (desc, sub, sparse, huge), copied to the host."""
+        v = SelectView()
+        _check(load_library().wt_export_select(self._live(), level, bit, ctypes.byref(v)),
+               "wt_export_select")
+        R, H, S = int(v.nranges), int(v.nhuge), int(v.nsparse)
+        desc = d2h(v.desc, 8 * R)
+        sub = d2h(v.sub, 4 * 16 * R, np.uint32)
+        sparse = d2h(v.sparse, 4 * 256 * S, np.uint32)
+        huge = d2h(v.huge, 8 * 4096 * H)
+        return desc, sub, sparse, huge
+
     def free(self):
         if self._h:
             _check(load_library().wt_free(self._h), "wt_free")
@@ -364,9 +386,9 @@ def multiary_build(seq, sigma: int, degree: int = 4, n: int | None = None, tau: 
     return Handle(h)
 
 
-def rs_build(bits, nbits: int, stream=None) -> Handle:
+def rs_build(bits, nbits: int, flags: int = 0, stream=None) -> Handle:
     """Rank/select directory over a device bitvector (kept referenced by the handle)."""
-    o = _opts()
+    o = _opts(flags=flags)
     h = ctypes.c_void_p()
     _check(load_library().rs_build(_ptr(bits), nbits, ctypes.byref(o), _stream_ptr(stream),
                                     ctypes.byref(h)), "rs_build")

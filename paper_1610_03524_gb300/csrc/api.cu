@@ -50,6 +50,9 @@ void free_arrays(wt_struct* h) {
   dfree(h->d_len_tab, st);
   dfree(h->d_node, st);
   dfree(h->d_node_lvl, st);
+  dfree(h->d_ck64, st);
+  dfree(h->d_ck32, st);
+  dfree(h->d_cmeta, st);
 }
 
 wt_status new_handle(wt_stream stream, uint64_t n, uint32_t sigma, wt_struct** out) {
@@ -133,6 +136,11 @@ wt_status seq_build(int kind, const void* d_seq, uint64_t n, uint32_t sigma, uin
   wt_struct* h = nullptr;
   s = new_handle(stream, n, sigma, &h);
   if (s != WT_OK) return s;
+  h->flags = opts ? opts->flags : 0u;
+  if ((h->flags & WT_FLAG_SELECT_O1) && kind == WT_KIND_MULTI) {
+    finish(h, WT_ERR_UNSUPPORTED, out);
+    return WT_ERR_UNSUPPORTED;
+  }
   switch (kind) {
     case WT_KIND_WM: s = build_wm(d_seq, n, sigma, (int)width, opts, h); break;
     case WT_KIND_WT: s = build_wt(d_seq, n, sigma, (int)width, opts, h, false); break;
@@ -179,6 +187,7 @@ wt_status rs_build(const uint64_t* d_bits, uint64_t nbits, const wt_build_opts* 
   wt_struct* h = nullptr;
   s = new_handle(stream, nbits, 2, &h);
   if (s != WT_OK) return s;
+  h->flags = opts ? opts->flags : 0u;
   h->kind = WT_KIND_RS;
   h->levels = h->L = 1;
   h->bpe = 1;
@@ -249,6 +258,24 @@ wt_status wt_free(wt_handle h) {
   cudaError_t e = cudaStreamSynchronize(h->stream);
   delete h;
   return e == cudaSuccess ? WT_OK : WT_ERR_CUDA;
+}
+
+wt_status wt_export_select(wt_handle h, uint32_t level, uint32_t bit, wt_select_view* out) {
+  if (!h || !out || bit > 1) return WT_ERR_INVALID_ARG;
+  wt_status s = sync_handle(h);
+  if (s != WT_OK) return s;
+  if (!(h->flags & WT_FLAG_SELECT_O1) || h->bpe != 1 || level >= h->cmeta.size())
+    return WT_ERR_INVALID_ARG;
+  const ClarkMeta& m = h->cmeta[level];
+  memset(out, 0, sizeof(*out));
+  out->nranges = m.nr[bit];
+  out->nhuge = m.nh[bit];
+  out->nsparse = m.ns[bit];
+  out->desc = h->d_ck64 + m.desc[bit];
+  out->huge = h->d_ck64 + m.huge[bit];
+  out->sub = h->d_ck32 + m.sub[bit];
+  out->sparse = h->d_ck32 + m.sparse[bit];
+  return WT_OK;
 }
 
 uint64_t wt_symbol_levels(wt_handle h) {

@@ -463,6 +463,7 @@ extern "C" wt_status wm_batch_build(const wt_batch_item* items, uint32_t m,
     if (opts->select_sample != 0 && opts->select_sample != 4096) return WT_ERR_UNSUPPORTED;
     if (opts->tile_symbols != 0 && opts->tile_symbols != (uint32_t)PASS_T) return WT_ERR_UNSUPPORTED;
     if (opts->k_chunks != 0) return WT_ERR_UNSUPPORTED;
+    if (opts->flags & WT_FLAG_SELECT_O1) return WT_ERR_UNSUPPORTED;
   }
   for (uint32_t i = 0; i < m; i++) {
     const wt_batch_item& it = items[i];

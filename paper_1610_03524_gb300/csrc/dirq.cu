@@ -302,6 +302,264 @@ wt_status dir_build_levels(const uint64_t* bits, const LevelMeta* d_meta, uint32
   return e == cudaSuccess ? WT_OK : WT_ERR_CUDA;
 }
 
+// ---------------------------------------------------------------------------
+// constant-time select directory (after Clark, Section 5.1 select)
+// ---------------------------------------------------------------------------
+constexpr uint64_t CK_HUGE_MIN = 1ull << 32;    // range length that keeps all positions
+constexpr uint64_t CK_SPARSE_MIN = 1ull << 16;  // sub-range length that keeps all offsets
+
+// occurrences of bit value b before superblock s of a level
+__device__ __forceinline__ uint64_t occ_before(const uint64_t* ldir, int b, uint64_t s) {
+  const uint64_t z = ldir[2 * s];
+  return b ? 2048 * s - z : z;
+}
+
+// position of occurrence q of bit value b, known to lie in superblocks
+// [lo, hi] of the level (q >= occurrences before lo)
+__device__ uint64_t dir_select(const uint64_t* lbits, const uint64_t* ldir, int b, uint64_t q,
+                               uint64_t lo, uint64_t hi) {
+  while (lo < hi) {
+    const uint64_t mid = (lo + hi + 1) >> 1;
+    if (occ_before(ldir, b, mid) <= q) lo = mid;
+    else hi = mid - 1;
+  }
+  return 2048 * lo + find_in_sb(lbits, ldir, lo, b, (uint32_t)(q - occ_before(ldir, b, lo)));
+}
+
+// one (level, bit value) of the directory build
+struct CkSeg {
+  uint64_t g0;        // its first range in the global numbering
+  uint64_t cnt;       // occurrences
+  uint64_t bit_off, dir_off, samp_off, n, nsb;
+  int b;
+};
+
+__device__ __forceinline__ uint32_t ck_seg_of(const CkSeg* segs, uint32_t nseg, uint64_t g) {
+  uint32_t lo = 0, hi = nseg - 1;
+  while (lo < hi) {
+    const uint32_t mid = (lo + hi + 1) >> 1;
+    if (segs[mid].g0 <= g) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+// per range: kind, sub-sample offsets, mask of long sub-ranges
+__global__ void k_ck_ranges(const uint64_t* bits, const uint64_t* dir, const uint64_t* samp,
+                            const CkSeg* segs, uint32_t nseg, uint64_t G, uint32_t* sub,
+                            uint64_t* mask_or_huge, uint64_t* nh, uint64_t* ns) {
+  const uint64_t g = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= G) return;
+  const CkSeg sg = segs[ck_seg_of(segs, nseg, g)];
+  const uint64_t k = g - sg.g0, R = (sg.cnt + 4095) / 4096;
+  const uint64_t* lbits = bits + sg.bit_off;
+  const uint64_t* ldir = dir + sg.dir_off;
+  const uint64_t* ls = samp + sg.samp_off;
+  const uint64_t S1 = ls[k];
+  const uint64_t e = (k + 1 < R) ? ls[k + 1] : sg.n;
+  const uint64_t M = (sg.cnt + 255) / 256;
+  const bool huge = e - S1 >= CK_HUGE_MIN;
+  uint32_t mask = 0;
+  uint64_t prev = S1;  // start of sub-range i
+  const uint64_t lo_sb = S1 >> 11, hi_sb = (e - 1) >> 11;
+  for (int i = 0; i < 16; i++) {
+    const uint64_t m = 16 * k + i;
+    uint64_t start = 0;
+    if (!huge && m < M) start = i == 0 ? S1 : dir_select(lbits, ldir, sg.b, 256 * m, lo_sb, hi_sb);
+    sub[16 * g + i] = huge ? 0u : (m < M ? (uint32_t)(start - S1) : 0xffffffffu);
+    if (!huge && i > 0 && m - 1 < M && m < M && start - prev >= CK_SPARSE_MIN) mask |= 1u << (i - 1);
+    if (!huge && m < M) prev = start;
+    if (!huge && m < M && (i == 15 || m + 1 >= M) && e - start >= CK_SPARSE_MIN) mask |= 1u << i;
+  }
+  mask_or_huge[g] = huge ? (1ull << 63) : (uint64_t)mask;
+  nh[g] = huge ? 1 : 0;
+  ns[g] = huge ? 0 : (uint64_t)__popc(mask);
+}
+
+// descriptors, numbered inside their (level, bit value)
+__global__ void k_ck_desc(const CkSeg* segs, uint32_t nseg, uint64_t G, const uint64_t* kind,
+                          const uint64_t* gh, const uint64_t* gs, uint64_t* desc) {
+  const uint64_t g = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= G) return;
+  const CkSeg sg = segs[ck_seg_of(segs, nseg, g)];
+  const uint64_t kd = kind[g];
+  if (kd >> 63) desc[g] = (1ull << 63) | (4096 * (gh[g] - gh[sg.g0]));
+  else desc[g] = (gs[g] - gs[sg.g0]) | (kd << 40);
+}
+
+// explicit answers: one block per range that keeps any
+__global__ void k_ck_fill(const uint64_t* bits, const uint64_t* dir, const uint64_t* samp,
+                          const CkSeg* segs, uint32_t nseg, uint64_t G, const uint64_t* kind,
+                          const uint64_t* gh, const uint64_t* gs, const uint32_t* sub,
+                          uint64_t* huge_all, uint32_t* sparse_all) {
+  for (uint64_t g = blockIdx.x; g < G; g += gridDim.x) {
+    const uint64_t kd = kind[g];
+    if (kd == 0) continue;
+    const CkSeg sg = segs[ck_seg_of(segs, nseg, g)];
+    const uint64_t k = g - sg.g0, R = (sg.cnt + 4095) / 4096;
+    const uint64_t* lbits = bits + sg.bit_off;
+    const uint64_t* ldir = dir + sg.dir_off;
+    const uint64_t S1 = samp[sg.samp_off + k];
+    const uint64_t e = (k + 1 < R) ? samp[sg.samp_off + k + 1] : sg.n;
+    const uint64_t lo_sb = S1 >> 11, hi_sb = (e - 1) >> 11;
+    if (kd >> 63) {
+      for (uint32_t j = threadIdx.x; j < 4096; j += blockDim.x) {
+        const uint64_t q = 4096 * k + j;
+        huge_all[4096 * gh[g] + j] = q < sg.cnt ? dir_select(lbits, ldir, sg.b, q, lo_sb, hi_sb) : ~0ull;
+      }
+    } else {
+      uint32_t mask = (uint32_t)kd;
+      uint64_t s = gs[g];
+      while (mask) {
+        const int i = __ffs(mask) - 1;
+        mask &= mask - 1;
+        for (uint32_t j = threadIdx.x; j < 256; j += blockDim.x) {
+          const uint64_t q = 4096 * k + 256 * i + j;
+          sparse_all[256 * s + j] =
+              q < sg.cnt ? (uint32_t)(dir_select(lbits, ldir, sg.b, q, lo_sb, hi_sb) - S1) : 0xffffffffu;
+        }
+        s++;
+      }
+    }
+  }
+}
+
+__global__ void k_gather_u64(const uint64_t* src, const uint64_t* idx, uint64_t n, uint64_t* out) {
+  const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = src[idx[i]];
+}
+
+static wt_status build_clark(wt_struct* h) {
+  cudaStream_t st = h->stream;
+  const uint32_t nlev = h->levels;
+  // occurrence counts per level need the zero counts on the host
+  std::vector<uint64_t> zeros(nlev, 0);
+  if (nlev) {
+    CK(cudaMemcpyAsync(zeros.data(), h->d_zeros, nlev * 8, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+  }
+  std::vector<CkSeg> segs;
+  h->cmeta.assign(nlev, ClarkMeta{});
+  uint64_t G = 0;
+  for (uint32_t l = 0; l < nlev; l++) {
+    const LevelMeta& m = h->meta[l];
+    for (int b = 0; b < 2; b++) {
+      CkSeg sg;
+      sg.g0 = G;
+      sg.cnt = b ? m.n - zeros[l] : zeros[l];
+      sg.bit_off = m.bit_off;
+      sg.dir_off = m.dir_off;
+      sg.samp_off = b ? m.s1_off : m.s0_off;
+      sg.n = m.n;
+      sg.nsb = m.nsb;
+      sg.b = b;
+      const uint64_t R = (sg.cnt + 4095) / 4096;
+      h->cmeta[l].nr[b] = R;
+      h->cmeta[l].desc[b] = G;
+      h->cmeta[l].sub[b] = 16 * G;
+      if (R) segs.push_back(sg);
+      G += R;
+    }
+  }
+  const uint32_t nseg = (uint32_t)segs.size();
+  uint64_t *d_kind, *d_nh, *d_ns, *d_gh, *d_gs, *scr;
+  CkSeg* d_segs;
+  uint32_t* d_sub;
+  CK(dmalloc((void**)&d_sub, std::max<uint64_t>(16 * G, 1) * 4, st));
+  CK(dmalloc((void**)&d_kind, std::max<uint64_t>(G, 1) * 8, st));
+  CK(dmalloc((void**)&d_nh, std::max<uint64_t>(G, 1) * 8, st));
+  CK(dmalloc((void**)&d_ns, std::max<uint64_t>(G, 1) * 8, st));
+  CK(dmalloc((void**)&d_gh, (G + 1) * 8, st));
+  CK(dmalloc((void**)&d_gs, (G + 1) * 8, st));
+  CK(dmalloc((void**)&scr, scan_scratch_pub(G) * 8, st));
+  CK(dmalloc((void**)&d_segs, std::max<uint32_t>(nseg, 1) * sizeof(CkSeg), st));
+  if (nseg)
+    CK(cudaMemcpyAsync(d_segs, segs.data(), nseg * sizeof(CkSeg), cudaMemcpyHostToDevice, st));
+  const unsigned gg = (unsigned)((G + 255) / 256);
+  if (G) {
+    k_ck_ranges<<<gg, 256, 0, st>>>(h->d_bits_ro, h->d_dir, h->d_samp, d_segs, nseg, G, d_sub,
+                                    d_kind, d_nh, d_ns);
+    count_launch();
+  }
+  wt_status s = scan_excl_u64_pub(d_nh, d_gh, G, scr, st);
+  if (s == WT_OK) s = scan_excl_u64_pub(d_ns, d_gs, G, scr, st);
+  uint64_t tot[2] = {0, 0};
+  if (s == WT_OK) {
+    CK(cudaMemcpyAsync(&tot[0], d_gh + G, 8, cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(&tot[1], d_gs + G, 8, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+  }
+  const uint64_t H = tot[0], S = tot[1];
+  if (s == WT_OK) {
+    CK(dmalloc((void**)&h->d_ck64, std::max<uint64_t>(G + 4096 * H, 1) * 8, st));
+    CK(dmalloc((void**)&h->d_ck32, std::max<uint64_t>(16 * G + 256 * S, 1) * 4, st));
+    if (G) {
+      CK(cudaMemcpyAsync(h->d_ck32, d_sub, 16 * G * 4, cudaMemcpyDeviceToDevice, st));
+      k_ck_desc<<<gg, 256, 0, st>>>(d_segs, nseg, G, d_kind, d_gh, d_gs, h->d_ck64);
+      count_launch();
+      const unsigned fg = (unsigned)std::min<uint64_t>(G, (uint64_t)num_sms() * 16);
+      k_ck_fill<<<fg, 256, 0, st>>>(h->d_bits_ro, h->d_dir, h->d_samp, d_segs, nseg, G, d_kind,
+                                    d_gh, d_gs, d_sub, h->d_ck64 + G, h->d_ck32 + 16 * G);
+      count_launch();
+    }
+    // per (level, bit value): the scans at its first and one-past-last range
+    std::vector<uint64_t> idx(4 * (size_t)nlev, 0), got(4 * (size_t)nlev, 0);
+    for (uint32_t l = 0; l < nlev; l++)
+      for (int b = 0; b < 2; b++) {
+        idx[4 * l + 2 * b] = h->cmeta[l].desc[b];
+        idx[4 * l + 2 * b + 1] = h->cmeta[l].desc[b] + h->cmeta[l].nr[b];
+      }
+    std::vector<uint64_t> gh_first(2 * nlev), gh_end(2 * nlev), gs_first(2 * nlev), gs_end(2 * nlev);
+    if (nlev) {
+      uint64_t *d_idx, *d_got;
+      CK(dmalloc((void**)&d_idx, idx.size() * 8, st));
+      CK(dmalloc((void**)&d_got, 2 * idx.size() * 8, st));
+      CK(cudaMemcpyAsync(d_idx, idx.data(), idx.size() * 8, cudaMemcpyHostToDevice, st));
+      k_gather_u64<<<(unsigned)((idx.size() + 255) / 256), 256, 0, st>>>(d_gh, d_idx, idx.size(), d_got);
+      count_launch();
+      k_gather_u64<<<(unsigned)((idx.size() + 255) / 256), 256, 0, st>>>(d_gs, d_idx, idx.size(),
+                                                                         d_got + idx.size());
+      count_launch();
+      std::vector<uint64_t> both(2 * idx.size());
+      CK(cudaMemcpyAsync(both.data(), d_got, both.size() * 8, cudaMemcpyDeviceToHost, st));
+      CK(cudaStreamSynchronize(st));
+      dfree(d_idx, st);
+      dfree(d_got, st);
+      for (uint32_t l = 0; l < nlev; l++)
+        for (int b = 0; b < 2; b++) {
+          gh_first[2 * l + b] = both[4 * l + 2 * b];
+          gh_end[2 * l + b] = both[4 * l + 2 * b + 1];
+          gs_first[2 * l + b] = both[idx.size() + 4 * l + 2 * b];
+          gs_end[2 * l + b] = both[idx.size() + 4 * l + 2 * b + 1];
+        }
+    }
+    for (uint32_t l = 0; l < nlev; l++)
+      for (int b = 0; b < 2; b++) {
+        ClarkMeta& cm = h->cmeta[l];
+        cm.nh[b] = gh_end[2 * l + b] - gh_first[2 * l + b];
+        cm.ns[b] = gs_end[2 * l + b] - gs_first[2 * l + b];
+        cm.huge[b] = G + 4096 * gh_first[2 * l + b];
+        cm.sparse[b] = 16 * G + 256 * gs_first[2 * l + b];
+      }
+    CK(dmalloc((void**)&h->d_cmeta, std::max<uint32_t>(nlev, 1) * sizeof(ClarkMeta), st));
+    if (nlev)
+      CK(cudaMemcpyAsync(h->d_cmeta, h->cmeta.data(), nlev * sizeof(ClarkMeta),
+                         cudaMemcpyHostToDevice, st));
+    CK(cudaStreamSynchronize(st));  // host vectors above are pageable and local
+  }
+  cudaError_t e = cudaGetLastError();
+  dfree(d_sub, st);
+  dfree(d_kind, st);
+  dfree(d_nh, st);
+  dfree(d_ns, st);
+  dfree(d_gh, st);
+  dfree(d_gs, st);
+  dfree(scr, st);
+  dfree(d_segs, st);
+  if (s != WT_OK) return s;
+  return e == cudaSuccess ? WT_OK : WT_ERR_CUDA;
+}
+
 wt_status build_directories(wt_struct* h) {
   cudaStream_t st = h->stream;
   const uint32_t nlev = h->levels;
@@ -332,9 +590,12 @@ wt_status build_directories(wt_struct* h) {
   wt_status s = upload_meta(h);
   if (s != WT_OK) return s;
   if (nlev == 0) return WT_OK;
-  if (!dig)
-    return dir_build_levels(h->d_bits_ro, h->d_meta, nlev, sb_first, h->d_dir, h->d_samp,
-                            h->d_zeros, h->kind == WT_KIND_RS ? 1 : 0, st);
+  if (!dig) {
+    s = dir_build_levels(h->d_bits_ro, h->d_meta, nlev, sb_first, h->d_dir, h->d_samp,
+                         h->d_zeros, h->kind == WT_KIND_RS ? 1 : 0, st);
+    if (s == WT_OK && (h->flags & WT_FLAG_SELECT_O1)) s = build_clark(h);
+    return s;
+  }
   uint64_t *d_first, *sbz, *sbx, *scr;
   CK(dmalloc((void**)&d_first, (nlev + 1) * 8, st));
   CK(dmalloc((void**)&sbz, std::max<uint64_t>(total_sb, 1) * 8 * 4, st));
@@ -381,6 +642,9 @@ struct QStruct {
   const LevelMeta* meta;
   const uint64_t* zeros;
   HuffQuery hq;
+  const ClarkMeta* cmeta;  // constant-time select directory, or null
+  const uint64_t* ck64;
+  const uint32_t* ck32;
 };
 
 struct BinLevel {
@@ -389,6 +653,9 @@ struct BinLevel {
   const uint64_t* s0;
   const uint64_t* s1;
   uint64_t n, nsb, zeros;
+  const ClarkMeta* cm;
+  const uint64_t* ck64;
+  const uint32_t* ck32;
 };
 
 __device__ __forceinline__ BinLevel bin_level(const QStruct& S, int l) {
@@ -401,6 +668,9 @@ __device__ __forceinline__ BinLevel bin_level(const QStruct& S, int l) {
   v.n = m.n;
   v.nsb = m.nsb;
   v.zeros = S.zeros[l];
+  v.cm = S.cmeta ? S.cmeta + l : nullptr;
+  v.ck64 = S.ck64;
+  v.ck32 = S.ck32;
   return v;
 }
 
@@ -424,6 +694,25 @@ __device__ __forceinline__ uint64_t rank1(const BinLevel& v, uint64_t x) { retur
 // position of the k-th (0-based) bit equal to bv; k < count
 __device__ uint64_t select_b(const BinLevel& v, int bv, uint64_t k) {
   const uint64_t* samp = bv ? v.s1 : v.s0;
+  if (v.cm) {
+    // constant-time directory: the range's descriptor gives the stored
+    // answer, or a sub-range shorter than 2^16 bits to search
+    const uint64_t kk = k >> 12;
+    const uint64_t d = v.ck64[v.cm->desc[bv] + kk];
+    if (d >> 63) return v.ck64[v.cm->huge[bv] + (d & ((1ull << 63) - 1)) + (k & 4095)];
+    const uint32_t mask = (uint32_t)((d >> 40) & 0xffffu);
+    const int i = (int)((k >> 8) & 15);
+    const uint64_t S1 = samp[kk];
+    if ((mask >> i) & 1u) {
+      const uint64_t sidx = (d & ((1ull << 40) - 1)) + (uint64_t)__popc(mask & ((1u << i) - 1u));
+      return S1 + v.ck32[v.cm->sparse[bv] + 256 * sidx + (k & 255)];
+    }
+    const uint64_t p0 = S1 + v.ck32[v.cm->sub[bv] + 16 * kk + i];
+    if ((k & 255) == 0) return p0;
+    uint64_t hi = (p0 + CK_SPARSE_MIN - 1) >> 11;
+    if (hi >= v.nsb) hi = v.nsb - 1;
+    return dir_select(v.bits, v.dir, bv, k, p0 >> 11, hi);
+  }
   const uint64_t cnt = bv ? v.n - v.zeros : v.zeros;
   const uint64_t ns = (cnt + 4095) / 4096;
   const uint64_t idx = k >> 12;
@@ -794,6 +1083,9 @@ static void fill_qstruct(const wt_struct* h, QStruct& S) {
   S.hq.len_count = h->d_len_tab ? h->d_len_tab + 68 : nullptr;
   S.hq.node = h->d_node;
   S.hq.node_lvl = h->d_node_lvl;
+  S.cmeta = h->d_cmeta;
+  S.ck64 = h->d_ck64;
+  S.ck32 = h->d_ck32;
 }
 
 wt_status launch_query(wt_struct* h, int op, const uint32_t* c, const uint64_t* x, uint64_t q,

@@ -29,6 +29,15 @@ struct LevelMeta {
   uint64_t nsb;       // superblocks
 };
 
+// Constant-time select directory of one level (offsets, in elements, into
+// the handle's two arrays: ck64 = descriptors | long-range positions,
+// ck32 = sub-sample offsets | long-sub-range offsets), per bit value.
+struct ClarkMeta {
+  uint64_t nr[2], nh[2], ns[2];
+  uint64_t desc[2], huge[2];    // in ck64
+  uint64_t sub[2], sparse[2];   // in ck32
+};
+
 // Huffman query tables (device): symbols in canonical order, per length the
 // first code and the offset into that order; per level the internal nodes.
 struct HuffQuery {
@@ -77,6 +86,12 @@ struct wt_struct {
   uint32_t max_code_len = 0;
   bool zeros_valid = false;
   wt_status deferred = WT_OK;
+  // constant-time select directory (WT_FLAG_SELECT_O1)
+  uint32_t flags = 0;
+  uint64_t* d_ck64 = nullptr;
+  uint32_t* d_ck32 = nullptr;
+  wtk::ClarkMeta* d_cmeta = nullptr;
+  std::vector<wtk::ClarkMeta> cmeta;
   // batched builds: the shared allocation holding every device array above
   // (d_abort is then shared by the whole batch)
   wtk::Arena* arena = nullptr;
