@@ -51,13 +51,15 @@ def parse():
     ap.add_argument("--cpu-log2n", type=int, default=24, help="oracle sample length 2^k")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle baseline leg")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--workload", choices=["wm", "batch", "serve", "genome", "huff"],
+    ap.add_argument("--workload", choices=["wm", "batch", "serve", "genome", "huff", "select"],
                     default="wm",
                     help="wm: the headline wavelet-matrix build (default); batch: 4096 "
                          "wavelet matrices, batched vs plain launches; serve: Poisson "
                          "builds + query batches through the serving loop; genome: "
                          "binary and 4-ary trees of a 2^32-symbol DNA-like text; huff: "
-                         "Huffman-shaped and balanced trees over a 2^20 alphabet")
+                         "Huffman-shaped and balanced trees over a 2^20 alphabet; select: "
+                         "select queries with the sampled and the constant-time select "
+                         "directories")
     ap.add_argument("--lam", type=float, default=20.0, help="serve: builds per second")
     ap.add_argument("--qlam", type=float, default=50.0,
                     help="serve: query batches (2^16 queries) per second")
@@ -628,6 +630,102 @@ def run_serve(args, wt):
           server=stats)
 
 
+def run_select(args, wt):
+    """Select queries through the sampled select directory and through the
+    constant-time one (FLAG_SELECT_O1), on the headline wavelet matrix
+    (n = 2^30, sigma = 2^16) and on a 2^32-bit bitvector whose ones
+    alternate between dense stretches and stretches with one 1 in 300 bits
+    (long sampled searches); plus what the constant-time directory adds to
+    the build."""
+    import numpy as np
+    import torch
+    import synth
+    res = {}
+    Q = 1 << 22
+    rng = np.random.Generator(np.random.PCG64(synth_seed(2) ^ 0x5e1))
+
+    def timed(fn, reps=5):
+        ts = []
+        for _ in range(reps):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            fn()
+            e1.record()
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return statistics.median(ts[1:])
+
+    # wavelet matrix of the headline workload
+    n = 1 << 30
+    pin = torch.empty(n, dtype=torch.int16).pin_memory()
+    synth.zipf(SEED, n, SIGMA, ZIPF_S, 2, addr=pin.data_ptr())
+    d = pin.to("cuda")
+    S = pin.numpy().view(np.uint16)
+    hist = np.bincount(S, minlength=SIGMA)
+    present = np.nonzero(hist)[0]
+    c = present[rng.integers(0, present.size, Q)].astype(np.uint32)
+    k = (rng.random(Q) * hist[c]).astype(np.uint64) + 1
+    dc, dk = torch.from_numpy(c.view(np.int32)).cuda(), torch.from_numpy(k.view(np.int64)).cuda()
+    out = torch.empty(Q, dtype=torch.int64, device="cuda")
+    for name, fl in (("sampled", 0), ("o1", wt.FLAG_SELECT_O1)):
+        bms = timed(lambda: wt.wm_build(d, SIGMA, flags=fl).free(), 3)
+        h = wt.wm_build(d, SIGMA, flags=fl)
+        h.sync()
+        qms = timed(lambda: h.select(dc, dk, out))
+        res[f"wm_{name}"] = {"build_ms": bms, "select_ms": qms, "queries_per_s": Q / qms * 1e3}
+        h.free()
+    del d
+    # bitvector with long sparse stretches
+    nb = 1 << 32
+    words = np.zeros(nb // 64, dtype=np.uint64)
+    st = np.arange(nb // (1 << 24))
+    dense = st % 2 == 0
+    # dense stretches: random words; sparse stretches: one 1 every 300 bits
+    wpr = (1 << 24) // 64
+    rw = synth.words(synth_seed(2) ^ 0xb17, int(dense.sum()) * wpr)
+    for i, s0 in enumerate(np.nonzero(dense)[0]):
+        words[s0 * wpr:(s0 + 1) * wpr] = rw[i * wpr:(i + 1) * wpr]
+    for s0 in np.nonzero(~dense)[0]:
+        ones = np.arange(s0 << 24, (s0 + 1) << 24, 300, dtype=np.uint64)
+        np.bitwise_or.at(words, (ones >> np.uint64(6)).astype(np.int64),
+                         np.left_shift(np.uint64(1), ones & np.uint64(63)))
+    dw = torch.from_numpy(words.view(np.int64)).cuda()
+    for name, fl in (("sampled", 0), ("o1", wt.FLAG_SELECT_O1)):
+        bms = timed(lambda: wt.rs_build(dw, nb, flags=fl).free(), 3)
+        h = wt.rs_build(dw, nb, flags=fl)
+        ex_ones = nb - int(h.export().zeros[0])
+        k1 = (rng.random(Q) * ex_ones).astype(np.uint64) + 1
+        dk1 = torch.from_numpy(k1.view(np.int64)).cuda()
+        dc1 = torch.ones(Q, dtype=torch.int32, device="cuda")
+        qms = timed(lambda: h.select(dc1, dk1, out))
+        res[f"bitvector_{name}"] = {"build_ms": bms, "select_ms": qms,
+                                    "queries_per_s": Q / qms * 1e3}
+        h.free()
+    cpu = None
+    if not args.no_cpu:
+        import oracle
+        Sm = np.ascontiguousarray(S[: 1 << 22])
+        hm = np.bincount(Sm, minlength=SIGMA)
+        pm = np.nonzero(hm)[0]
+        cq = pm[rng.integers(0, pm.size, 256)].astype(np.uint32)
+        kq = (rng.random(256) * hm[cq]).astype(np.uint64) + 1
+        t0 = time.perf_counter()
+        oracle.select(Sm, SIGMA, cq, kq)
+        dt = time.perf_counter() - t0
+        cpu = {"value": 256 / dt, "unit": "queries/s", "cores": 1, "kind": "oracle",
+               "sample": f"256 selects on the first 2^22 symbols, single-threaded C oracle "
+                         f"(scan by definition); {dt:.3f} s"}
+    cfg = {"workload": f"2^22 select queries (c, k uniform over present symbols and their "
+                       f"counts) on the wavelet matrix of n=2^30 uint16 Zipf(1.1), sigma 2^16; "
+                       f"and 2^22 select-1 queries on a 2^32-bit bitvector of dense and 1-in-300 "
+                       f"stretches; sampled vs constant-time select directory",
+           "queries": Q}
+    _line(args, "select queries/s, constant-time directory (wavelet matrix n=2^30)",
+          res["wm_o1"]["queries_per_s"], "queries/s", res["wm_o1"]["select_ms"], cfg, dtype="u16",
+          results=res, cpu_baseline=cpu)
+
+
 def synth_seed(k):
     import synth
     return synth.SEED_BASE + k
@@ -748,6 +846,8 @@ def run_other(args):
         run_batch(args, wt)
     elif args.workload == "serve":
         run_serve(args, wt)
+    elif args.workload == "select":
+        run_select(args, wt)
     else:
         run_tree(args, wt)
     return 0

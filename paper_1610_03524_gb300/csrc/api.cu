@@ -131,6 +131,7 @@ wt_status seq_build(int kind, const void* d_seq, uint64_t n, uint32_t sigma, uin
   wt_status s = check_opts(opts);
   if (s != WT_OK) return s;
   if (kind == WT_KIND_MULTI && degree != 4) return WT_ERR_UNSUPPORTED;
+  if (n >= ((uint64_t)1 << 40)) return WT_ERR_UNSUPPORTED;  // look-back counts are 40 bits
   if ((kind == WT_KIND_WT || kind == WT_KIND_MULTI || kind == WT_KIND_HUFF) && sigma > (1u << 24))
     return WT_ERR_UNSUPPORTED;
   wt_struct* h = nullptr;

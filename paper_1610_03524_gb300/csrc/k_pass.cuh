@@ -323,12 +323,20 @@ __global__ void __launch_bounds__(NT + 32, WT_PASS_MIN_CTAS) k_pass(const __grid
           carry += __shfl_sync(FULL, ci, 31);
         }
       }
-      // one 64-bit word per digit: 2-bit flag (1 aggregate, 2 inclusive)
-      // above a 62-bit count; the ring is zeroed before every pass
+      // one 64-bit word per digit: a 2-bit flag (1 aggregate, 2 inclusive),
+      // the 22-bit generation of the tile on the ring (tile / ring slots:
+      // which reuse of the slot it is) and a 40-bit count.  The ring is
+      // zeroed before every pass; a word whose generation is not the one of
+      // the tile looked for belongs to an earlier or later tile that shares
+      // the slot, and counts as not yet published.
       uint64_t* const slot = P0.ring + (uint64_t)(ti & P0.ring_mask) * SLOT_U64;
-      constexpr uint64_t CMASK = (1ull << 62) - 1;
+      constexpr uint64_t CMASK = (1ull << 40) - 1, GMASK = ((1ull << 22) - 1) << 40;
+      auto gen_of = [&](uint32_t x) -> uint64_t {
+        return ((uint64_t)(x / (P0.ring_mask + 1u)) << 40) & GMASK;
+      };
+      const uint64_t mygen = gen_of(ti);
       for (int r = lane; r < nd; r += 32)
-        st_relaxed_u64(slot + r, ((first ? 2ull : 1ull) << 62) | s_hist[r]);
+        st_relaxed_u64(slot + r, ((first ? 2ull : 1ull) << 62) | mygen | s_hist[r]);
       int status = 0;
       uint64_t* const exd = ex_cnt + cls_idx(t, 0);  // exclusive digit counts
       // two rounds of four digits per lane keep the look-back state small
@@ -356,7 +364,7 @@ __global__ void __launch_bounds__(NT + 32, WT_PASS_MIN_CTAS) k_pass(const __grid
             for (int i = 0; i < 4; i++) {
               if (!(todo >> i & 1u)) continue;
               const uint64_t st = v[i] >> 62;
-              if (st == 0) {
+              if (st == 0 || (v[i] & GMASK) != gen_of(pred[i])) {
                 waited = true;
                 continue;
               }
@@ -380,7 +388,8 @@ __global__ void __launch_bounds__(NT + 32, WT_PASS_MIN_CTAS) k_pass(const __grid
           const int r = lane + 32 * (4 * g + i);
           if (r < nd) {
             exd[r] = acc[i];
-            if (!first && status == 0) st_relaxed_u64(slot + r, (2ull << 62) | (acc[i] + s_hist[r]));
+            if (!first && status == 0)
+              st_relaxed_u64(slot + r, (2ull << 62) | mygen | (acc[i] + s_hist[r]));
           }
         }
       }
