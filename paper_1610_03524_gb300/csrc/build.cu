@@ -510,7 +510,7 @@ __global__ void k_tiles_write(const uint64_t* bnd, uint64_t stride, uint64_t nn,
   d.count = (uint32_t)std::min<uint64_t>(T, e - s);
   d.node = (uint32_t)(node_base + p);
   d.first = (k == 0);
-  d.pad = 0;
+  d.seg0 = (uint32_t)toff[p];
   tiles[i] = d;
 }
 
@@ -521,6 +521,97 @@ __global__ void k_tiles_write(const uint64_t* bnd, uint64_t stride, uint64_t nn,
 #define WT_PASS_NT 256
 #endif
 constexpr int PT = PASS_T, PNT = WT_PASS_NT;
+
+// Digit counts of every tile of a pass (the K sub-problems' per-class counts
+// of Section 4.2): one block per tile, the same tiles and digits as k_pass.
+template <typename E, bool BATCH>
+__global__ void __launch_bounds__(256) k_tile_counts(const __grid_constant__ PassParams P0,
+                                                     uint32_t* tcnt) {
+  __shared__ uint32_t h[TC_STRIDE];
+  __shared__ PassParams s_P;
+  const PassParams& P = BATCH ? s_P : P0;
+  const uint32_t ntiles = P0.tiles ? *P0.ntiles_dev : P0.ntiles;
+  const int tid = threadIdx.x;
+  if (BATCH && tid == 0) s_P = P0;
+  for (uint32_t ti = blockIdx.x; ti < ntiles; ti += gridDim.x) {
+    if (BATCH && tid == 0) fill_seg(s_P, P0, ti);
+    h[tid] = 0;
+    __syncthreads();
+    uint64_t ts;
+    int cnt;
+    if (P.tiles) {
+      const TileDesc d = P.tiles[ti];
+      ts = d.start;
+      cnt = (int)d.count;
+    } else {
+      ts = (uint64_t)(ti - P.tile0) * PASS_T;
+      const uint64_t rem = P.n_in - ts;
+      cnt = (int)(rem < (uint64_t)PASS_T ? rem : (uint64_t)PASS_T);
+    }
+    const uint32_t rmask = (1u << P.t) - 1u;
+    const int rsh = 32 - P.rbits;
+    auto count = [&](uint32_t x) { atomicAdd(&h[(__brev(x) >> rsh) & rmask], 1u); };
+    const uintptr_t a = (uintptr_t)P.in + ts * (uint64_t)P.in_w;
+    if (P.code_map) {
+      for (int i = tid; i < cnt; i += 256) count(P.code_map[load_elem(P.in, P.in_w, ts + i)]);
+    } else if (P.in_w == 2 && cnt == PASS_T && (a & 15) == 0) {
+      const uint4* src = (const uint4*)a;
+      for (int i = tid; i < PASS_T / 8; i += 256) {
+        const uint4 q = __ldcs(src + i);
+        const uint32_t w4[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+          count(w4[k] & 0xffffu);
+          count(w4[k] >> 16);
+        }
+      }
+    } else if (P.in_w == 1 && cnt == PASS_T && (a & 15) == 0) {
+      const uint4* src = (const uint4*)a;
+      for (int i = tid; i < PASS_T / 16; i += 256) {
+        const uint4 q = __ldcs(src + i);
+        const uint32_t w4[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+        for (int k = 0; k < 4; k++)
+#pragma unroll
+          for (int b = 0; b < 4; b++) count((w4[k] >> (8 * b)) & 0xffu);
+      }
+    } else {
+      for (int i = tid; i < cnt; i += 256) count(load_elem(P.in, P.in_w, ts + i));
+    }
+    __syncthreads();
+    tcnt[(uint64_t)ti * TC_STRIDE + tid] = h[tid];
+    __syncthreads();
+  }
+}
+
+// Prefix sums of the tiles' counts, per digit value: exclusive inside each
+// chunk of TCHUNK tiles (in place, u32), and the chunks' totals.
+__global__ void __launch_bounds__(256) k_tile_scan_chunk(uint32_t* tcnt, const uint32_t* ntiles_dev,
+                                                         uint32_t ntiles_host, uint64_t* tchunk) {
+  const uint32_t nt = ntiles_dev ? *ntiles_dev : ntiles_host;
+  const uint32_t c = blockIdx.x, r = threadIdx.x;
+  const uint64_t t0 = (uint64_t)c * TCHUNK;
+  const uint64_t t1 = t0 + TCHUNK < nt ? t0 + TCHUNK : nt;
+  uint32_t run = 0;
+#pragma unroll 8
+  for (uint64_t ti = t0; ti < t1; ti++) {
+    const uint32_t v = tcnt[ti * TC_STRIDE + r];
+    tcnt[ti * TC_STRIDE + r] = run;
+    run += v;
+  }
+  tchunk[(uint64_t)c * TC_STRIDE + r] = run;
+}
+
+// ... and the exclusive prefix of the chunks' totals (u64)
+__global__ void __launch_bounds__(256) k_tile_scan_top(uint64_t* tchunk, uint32_t nchunk) {
+  const uint32_t r = threadIdx.x;
+  uint64_t run = 0;
+  for (uint32_t c = 0; c < nchunk; c++) {
+    const uint64_t v = tchunk[(uint64_t)c * TC_STRIDE + r];
+    tchunk[(uint64_t)c * TC_STRIDE + r] = run;
+    run += v;
+  }
+}
 
 template <typename E, bool DIG, bool BATCH = false>
 static wt_status launch_pass_t(const PassParams& P, uint64_t max_tiles, const wt_build_opts* o,
@@ -539,9 +630,23 @@ static wt_status launch_pass_t(const PassParams& P, uint64_t max_tiles, const wt
   if (o && o->ctas_per_sm) per_sm = std::min<int>(occ, (int)o->ctas_per_sm);
   uint64_t grid = (uint64_t)num_sms() * per_sm;
   if (grid > max_tiles) grid = std::max<uint64_t>(max_tiles, 1);
-  if (grid >= RING_SLOTS / 4) grid = RING_SLOTS / 4 - 1;
-  // per-digit look-back words carry no pass tag: clear them for this pass
-  CK(cudaMemsetAsync(P.ring, 0, (size_t)RING_SLOTS * SLOT_U64 * 8, st));
+  // every tile's digit counts and their prefix sums across the tiles
+  const uint64_t mt = std::max<uint64_t>(max_tiles, 1);
+  const uint32_t nchunk = (uint32_t)((mt + TCHUNK - 1) / TCHUNK);
+  uint32_t* tcnt = nullptr;
+  uint64_t* tchunk = nullptr;
+  CK(dmalloc((void**)&tcnt, mt * TC_STRIDE * 4, st));
+  CK(dmalloc((void**)&tchunk, (uint64_t)nchunk * TC_STRIDE * 8, st));
+  k_tile_counts<E, BATCH><<<(unsigned)std::min<uint64_t>(mt, (uint64_t)num_sms() * 16), 256, 0, st>>>(
+      P, tcnt);
+  count_launch();
+  k_tile_scan_chunk<<<nchunk, 256, 0, st>>>(tcnt, P.tiles ? P.ntiles_dev : nullptr, P.ntiles, tchunk);
+  count_launch();
+  k_tile_scan_top<<<1, 256, 0, st>>>(tchunk, nchunk);
+  count_launch();
+  PassParams Q = P;
+  Q.tcnt = tcnt;
+  Q.tchunk = tchunk;
   Prof& pf = prof();
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (pf.on) {
@@ -549,9 +654,11 @@ static wt_status launch_pass_t(const PassParams& P, uint64_t max_tiles, const wt
     cudaEventCreate(&e1);
     cudaEventRecord(e0, st);
   }
-  kern<<<(unsigned)grid, PNT + 32, SM::bytes, st>>>(P);
+  kern<<<(unsigned)grid, PNT + 32, SM::bytes, st>>>(Q);
   CK(cudaGetLastError());
   count_launch();
+  dfree(tcnt, st);
+  dfree(tchunk, st);
   if (pf.on) {
     cudaEventRecord(e1, st);
     pf.ev.push_back(e0);

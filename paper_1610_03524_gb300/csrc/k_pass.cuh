@@ -11,10 +11,10 @@
 //     are the ballot words of b_j in the order after j splits;
 //   * the element count of every class (node) of every level, from the
 //     tile's digit histogram (prefix sums, Section 2).
-// A decoupled look-back (single-pass chained scan) over the tiles then gives,
-// for each class, the count of elements in all earlier tiles: the domain
-// decomposition of Section 4.2 with K = number of tiles and per-node offsets
-// by prefix sums across the K sub-problems.  Words copied whole are stored;
+// The count of every class in the earlier tiles of the tile's sequence or
+// node comes from prefix sums, taken before the pass, of every tile's digit
+// counts: the domain decomposition of Section 4.2 with K = number of tiles
+// and per-node offsets by prefix sums across the K sub-problems.  Words copied whole are stored;
 // the "boundary" words that several tiles or nodes share (Section 4.2) are
 // merged with atomicOr into the level buffer, which the build zeroes first.
 // Finally the tile scatters its elements, narrowed to the bits still needed,
@@ -38,6 +38,33 @@ __device__ __forceinline__ void store_elem(void* p, int w, uint64_t i, uint32_t 
   if (w == 1) ((uint8_t*)p)[i] = (uint8_t)v;
   else if (w == 2) ((uint16_t*)p)[i] = (uint16_t)v;
   else ((uint32_t*)p)[i] = v;
+}
+
+// Batched builds: the part of the parameters that belongs to tile ti's
+// sequence (the last segment with tile0 <= ti) into D.
+__device__ __forceinline__ void fill_seg(PassParams& D, const PassParams& P0, uint32_t ti) {
+  uint32_t lo = 0, hi = P0.nsegs - 1;
+  while (lo < hi) {
+    const uint32_t mid = (lo + hi + 1) >> 1;
+    if (P0.segs[mid].tile0 <= ti) lo = mid;
+    else hi = mid - 1;
+  }
+  const SegDesc& d = P0.segs[lo];
+  D.in = d.in;
+  D.in_w = d.in_w;
+  D.out = d.out;
+  D.out_w = d.out_w;
+  D.L = d.L;
+  D.a = d.a;
+  D.t = d.t;
+  D.rbits = d.rbits;
+  D.bits = d.bits;
+  D.lvl_off = d.lvl_off;
+  D.lvl_len = d.lvl_len;
+  D.wm_cls = d.wm_cls;
+  D.err = d.err;
+  D.n_in = d.n;
+  D.tile0 = d.tile0;
 }
 
 // Global class range [cs, ce) of level a+j, class k (k = the tile-local key
@@ -189,31 +216,7 @@ __global__ void __launch_bounds__(NT + 32, WT_PASS_MIN_CTAS) k_pass(const __grid
       uint32_t ti = atomicAdd(P0.ticket, 1u);
       if (ld_volatile_u32(P0.abort_flag)) ti = 0xffffffffu;
       s_tile = ti;
-      if (BATCH && ti < ntiles) {
-        // the sequence of this tile: last segment with tile0 <= ti
-        uint32_t lo = 0, hi = P0.nsegs - 1;
-        while (lo < hi) {
-          const uint32_t mid = (lo + hi + 1) >> 1;
-          if (P0.segs[mid].tile0 <= ti) lo = mid;
-          else hi = mid - 1;
-        }
-        const SegDesc& d = P0.segs[lo];
-        s_P.in = d.in;
-        s_P.in_w = d.in_w;
-        s_P.out = d.out;
-        s_P.out_w = d.out_w;
-        s_P.L = d.L;
-        s_P.a = d.a;
-        s_P.t = d.t;
-        s_P.rbits = d.rbits;
-        s_P.bits = d.bits;
-        s_P.lvl_off = d.lvl_off;
-        s_P.lvl_len = d.lvl_len;
-        s_P.wm_cls = d.wm_cls;
-        s_P.err = d.err;
-        s_P.n_in = d.n;
-        s_P.tile0 = d.tile0;
-      }
+      if (BATCH && ti < ntiles) fill_seg(s_P, P0, ti);
     }
     __syncthreads();
     const uint32_t ti = s_tile;
@@ -222,20 +225,19 @@ __global__ void __launch_bounds__(NT + 32, WT_PASS_MIN_CTAS) k_pass(const __grid
     const int ntl = (1 << t) - 1;
     uint64_t ts;
     int cnt;
-    uint32_t node;
-    bool first;
+    uint32_t node, seg0;  // seg0: first tile of the tile's sequence or node
     if (P.tiles) {
       const TileDesc d = P.tiles[ti];
       ts = d.start;
       cnt = (int)d.count;
       node = d.node;
-      first = d.first != 0;
+      seg0 = d.seg0;
     } else {
       ts = (uint64_t)(ti - P.tile0) * T;
       const uint64_t rem = P.n_in - ts;
       cnt = (int)(rem < (uint64_t)T ? rem : (uint64_t)T);
       node = 0;
-      first = (ti == P.tile0);
+      seg0 = P.tile0;
     }
     const bool full = cnt == T;
 
@@ -297,9 +299,22 @@ __global__ void __launch_bounds__(NT + 32, WT_PASS_MIN_CTAS) k_pass(const __grid
       // ---- 3 (control warp). class counts of every level from the digit
       //      histogram; per-digit decoupled look-back for the counts of all
       //      earlier tiles; exclusive counts of every level ----------------
+      const int nd = 1 << t;
+      // this tile's count of every digit value in the earlier tiles of its
+      // sequence or node: the prefix sums of the per-tile counts (Section
+      // 4.2, prefix sums across the K sub-problems), taken before the pass
+      int status = 0;
+      uint64_t* const exd = ex_cnt + cls_idx(t, 0);  // exclusive digit counts
+      {
+        const uint64_t* ca = P0.tchunk + (uint64_t)(ti / TCHUNK) * TC_STRIDE;
+        const uint64_t* cb = P0.tchunk + (uint64_t)(seg0 / TCHUNK) * TC_STRIDE;
+        const uint32_t* ta = P0.tcnt + (uint64_t)ti * TC_STRIDE;
+        const uint32_t* tb = P0.tcnt + (uint64_t)seg0 * TC_STRIDE;
+        for (int r = lane; r < nd; r += 32) exd[r] = (ca[r] + ta[r]) - (cb[r] + tb[r]);
+      }
+      // class counts and tile-local class starts
       // level j classes are the digit values mod 2^j: level t holds the
       // digit counts, level j-1 class k sums classes k and k + 2^(j-1)
-      const int nd = 1 << t;
       for (int k = lane; k < nd; k += 32) ccnt[cls_idx(t, k)] = s_hist[k];
       __syncwarp();
       for (int j = t - 1; j >= 0; j--) {
@@ -321,76 +336,6 @@ __global__ void __launch_bounds__(NT + 32, WT_PASS_MIN_CTAS) k_pass(const __grid
           }
           if (k < (1 << j)) cstart[cls_idx(j, k)] = carry + ci - c;
           carry += __shfl_sync(FULL, ci, 31);
-        }
-      }
-      // one 64-bit word per digit: a 2-bit flag (1 aggregate, 2 inclusive),
-      // the 22-bit generation of the tile on the ring (tile / ring slots:
-      // which reuse of the slot it is) and a 40-bit count.  The ring is
-      // zeroed before every pass; a word whose generation is not the one of
-      // the tile looked for belongs to an earlier or later tile that shares
-      // the slot, and counts as not yet published.
-      uint64_t* const slot = P0.ring + (uint64_t)(ti & P0.ring_mask) * SLOT_U64;
-      constexpr uint64_t CMASK = (1ull << 40) - 1, GMASK = ((1ull << 22) - 1) << 40;
-      auto gen_of = [&](uint32_t x) -> uint64_t {
-        return ((uint64_t)(x / (P0.ring_mask + 1u)) << 40) & GMASK;
-      };
-      const uint64_t mygen = gen_of(ti);
-      for (int r = lane; r < nd; r += 32)
-        st_relaxed_u64(slot + r, ((first ? 2ull : 1ull) << 62) | mygen | s_hist[r]);
-      int status = 0;
-      uint64_t* const exd = ex_cnt + cls_idx(t, 0);  // exclusive digit counts
-      // two rounds of four digits per lane keep the look-back state small
-      for (int g = 0; g < 2; g++) {
-        uint64_t acc[4] = {0, 0, 0, 0};
-        if (!first && status == 0) {
-          uint32_t pred[4];
-          uint32_t todo = 0;
-#pragma unroll
-          for (int i = 0; i < 4; i++) {
-            pred[i] = ti - 1;
-            if (lane + 32 * (4 * g + i) < nd) todo |= 1u << i;
-          }
-          uint64_t spins = 0;
-          while (__any_sync(FULL, todo != 0)) {
-            uint64_t v[4];
-#pragma unroll
-            for (int i = 0; i < 4; i++)
-              v[i] = (todo >> i & 1u)
-                         ? ld_relaxed_u64(P0.ring + (uint64_t)(pred[i] & P0.ring_mask) * SLOT_U64 +
-                                          lane + 32 * (4 * g + i))
-                         : 0ull;
-            bool waited = false;
-#pragma unroll
-            for (int i = 0; i < 4; i++) {
-              if (!(todo >> i & 1u)) continue;
-              const uint64_t st = v[i] >> 62;
-              if (st == 0 || (v[i] & GMASK) != gen_of(pred[i])) {
-                waited = true;
-                continue;
-              }
-              acc[i] += v[i] & CMASK;
-              if (st == 2) todo &= ~(1u << i);
-              else pred[i]--;
-            }
-            if (__any_sync(FULL, waited)) {
-              int ab = 0;
-              if (lane == 0) ab = (++spins > P0.spin_limit) || ld_volatile_u32(P0.abort_flag);
-              if (__shfl_sync(FULL, ab, 0)) {
-                status = -1;
-                break;
-              }
-              if (spins > 8) __nanosleep(64);
-            }
-          }
-        }
-#pragma unroll
-        for (int i = 0; i < 4; i++) {
-          const int r = lane + 32 * (4 * g + i);
-          if (r < nd) {
-            exd[r] = acc[i];
-            if (!first && status == 0)
-              st_relaxed_u64(slot + r, (2ull << 62) | mygen | (acc[i] + s_hist[r]));
-          }
         }
       }
       __syncwarp();

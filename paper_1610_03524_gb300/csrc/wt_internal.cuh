@@ -23,8 +23,16 @@ struct TileDesc {
   uint32_t count;
   uint32_t node;
   uint32_t first;
-  uint32_t pad;
+  uint32_t seg0;  // index of the node's first tile
 };
+
+// Per-tile digit counts of a pass (the K sub-problems' per-node counts of
+// Section 4.2) and their prefix sums across tiles: tile ti's counts sit at
+// tcnt[ti * TC_STRIDE + r] (u32, exclusive within its chunk of TCHUNK tiles
+// after the scan) and the chunk's exclusive counts at tchunk[c * TC_STRIDE + r]
+// (u64).
+constexpr int TC_STRIDE = 256;
+constexpr uint32_t TCHUNK = 1024;
 
 // Symbols per tile of the partition pass, look-back ring geometry, and the
 // bound on every device-side wait (polls before a wait gives up).
@@ -108,7 +116,10 @@ struct PassParams {
   // batched builds: per-sequence parts, sorted by tile0
   const SegDesc* segs;
   uint32_t nsegs;
-  // decoupled look-back
+  // prefix sums of the tiles' digit counts (see TileDesc)
+  const uint32_t* tcnt;
+  const uint64_t* tchunk;
+  // decoupled look-back (unused by the two-phase prefix sums)
   uint64_t* ring;
   uint32_t ring_mask;
   uint64_t seq_base;
