@@ -265,8 +265,7 @@ wt_status batch_build_wm(const wt_batch_item* items, uint32_t m, const wt_build_
   const uint64_t w_pseg = up(w_hseg + sizeof(HistSeg) * std::max<uint32_t>(nh, 1), 256);
   const uint64_t w_sseg = up(w_pseg + sizeof(PlanSeg) * std::max<uint32_t>(m, 1), 256);
   const uint64_t w_tab_end = up(w_sseg + sizeof(SegDesc) * std::max<uint64_t>(nsegs_tot, 1), 256);
-  const uint64_t w_ring = w_tab_end;
-  const uint64_t w_tick = up(w_ring + 8ull * RING_SLOTS * SLOT_U64, 256);
+  const uint64_t w_tick = w_tab_end;
   const uint64_t w_seq0 = up(w_tick + 4 * 64, 256);
   const uint64_t w_seq1 = up(w_seq0 + nseq, 256);
   const uint64_t ws_bytes = up(w_seq1 + nseq, 256);
@@ -280,7 +279,6 @@ wt_status batch_build_wm(const wt_batch_item* items, uint32_t m, const wt_build_
   HistSeg* d_hseg = (HistSeg*)(Wd + w_hseg);
   PlanSeg* d_pseg = (PlanSeg*)(Wd + w_pseg);
   SegDesc* d_sseg = (SegDesc*)(Wd + w_sseg);
-  uint64_t* d_ring = (uint64_t*)(Wd + w_ring);
   uint32_t* d_tick = (uint32_t*)(Wd + w_tick);
   uint8_t* d_seq[2] = {Wd + w_seq0, Wd + w_seq1};
 
@@ -395,12 +393,9 @@ wt_status batch_build_wm(const wt_batch_item* items, uint32_t m, const wt_build_
     PassParams P;
     memset(&P, 0, sizeof(P));
     P.shape = SHAPE_WM;
-    P.ring = d_ring;
-    P.ring_mask = RING_SLOTS - 1;
     P.ticket = d_tick + li;
     P.err = a_err;  // replaced per tile by the sequence's own word
     P.abort_flag = a_abort;
-    P.spin_limit = SPIN_LIMIT;
     P.ntiles = L0.ntiles;
     P.segs = d_sseg + L0.first;
     P.nsegs = L0.nsegs;

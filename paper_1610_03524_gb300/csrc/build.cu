@@ -26,7 +26,6 @@
 
 namespace wtk {
 
-static std::atomic<uint64_t> g_seq{1};
 
 #define CK(x)                                                   \
   do {                                                          \
@@ -419,13 +418,10 @@ __device__ void plan_wm_classes(const uint64_t* hist, int L, int tau, int G, uin
 }
 
 // Wavelet-matrix plan, one block: class starts and zero counts; reset of the
-// look-back ring and tickets.
-__global__ void k_plan_wm(const uint64_t* hist, uint64_t n, int L, int tau, int G,
-                          uint64_t* cls, uint64_t* zeros, uint64_t* bits, uint64_t W,
-                          uint64_t* ring, uint32_t ring_slots, uint32_t* tickets,
-                          uint32_t* abort_flag) {
+// tile tickets.
+__global__ void k_plan_wm(const uint64_t* hist, int L, int tau, int G, uint64_t* cls,
+                          uint64_t* zeros, uint32_t* tickets, uint32_t* abort_flag) {
   plan_wm_classes(hist, L, tau, G, cls, zeros);
-  for (uint32_t i = threadIdx.x; i < ring_slots; i += blockDim.x) ring[(uint64_t)i * SLOT_U64] = 0;
   for (int g = threadIdx.x; g < 32; g += blockDim.x) tickets[g] = 0;
   if (threadIdx.x == 0) *abort_flag = 0;
 }
@@ -471,9 +467,7 @@ __global__ void k_zero_padding(uint64_t* bits, const uint64_t* lvl_off, const ui
   for (uint64_t w = used + threadIdx.x; w < W; w += blockDim.x) bits[lvl_off[l] + w] = 0;
 }
 
-__global__ void k_reset_lookback(uint64_t* ring, uint32_t ring_slots, uint32_t* tickets,
-                                 uint32_t* abort_flag) {
-  for (uint32_t i = threadIdx.x; i < ring_slots; i += blockDim.x) ring[(uint64_t)i * SLOT_U64] = 0;
+__global__ void k_reset_tickets(uint32_t* tickets, uint32_t* abort_flag) {
   for (int g = threadIdx.x; g < 32; g += blockDim.x) tickets[g] = 0;
   if (threadIdx.x == 0) *abort_flag = 0;
 }
@@ -735,19 +729,16 @@ static void set_uniform_levels(wt_struct* h, uint64_t elems_per_level) {
     h->level_off[l + 1] = h->level_off[l] + level_words(elems_per_level * h->bpe);
 }
 
-static PassParams base_params(wt_struct* h, Work& wk, uint64_t* ring, uint32_t* tickets,
+static PassParams base_params(wt_struct* h, Work& wk, uint32_t* tickets,
                               const uint64_t* d_lvl_off, const uint64_t* d_lvl_len) {
   PassParams P;
   memset(&P, 0, sizeof(P));
   P.bits = h->d_bits;
   P.lvl_off = d_lvl_off;
   P.lvl_len = d_lvl_len;
-  P.ring = ring;
-  P.ring_mask = RING_SLOTS - 1;
   P.ticket = tickets;
   P.err = h->d_err;
   P.abort_flag = h->d_abort;
-  P.spin_limit = SPIN_LIMIT;
   (void)wk;
   return P;
 }
@@ -771,7 +762,7 @@ wt_status build_wm(const void* d_seq, uint64_t n, uint32_t sigma, int w, const w
   std::vector<PassGeom> ps = make_passes(L, tau, w);
   const int G = (int)ps.size();
   uint32_t T = PT;
-  uint64_t *hist, *cls, *ring, *d_off, *d_len;
+  uint64_t *hist, *cls, *d_off, *d_len;
   uint32_t* tickets;
   int nh = 0, ncls = 0;
   for (auto& p : ps) {
@@ -780,7 +771,6 @@ wt_status build_wm(const void* d_seq, uint64_t n, uint32_t sigma, int w, const w
   }
   TRY(wk.get(&hist, nh));
   TRY(wk.get(&cls, ncls));
-  TRY(wk.get(&ring, (size_t)RING_SLOTS * SLOT_U64));
   TRY(wk.get(&tickets, 32));
   TRY(wk.get(&d_off, L + 1));
   TRY(wk.get(&d_len, L));
@@ -796,8 +786,7 @@ wt_status build_wm(const void* d_seq, uint64_t n, uint32_t sigma, int w, const w
     count_launch();
     CK(cudaGetLastError());
   }
-  k_plan_wm<<<1, 1024, 0, st>>>(hist, n, L, tau, G, cls, h->d_zeros, h->d_bits, W, ring,
-                                RING_SLOTS, tickets, h->d_abort);
+  k_plan_wm<<<1, 1024, 0, st>>>(hist, L, tau, G, cls, h->d_zeros, tickets, h->d_abort);
   count_launch();
   CK(cudaGetLastError());
   // intermediate sequences
@@ -814,7 +803,7 @@ wt_status build_wm(const void* d_seq, uint64_t n, uint32_t sigma, int w, const w
   const uint64_t ntiles = (n + T - 1) / T;
   for (int g = 0; g < G; g++) {
     const PassGeom& pg = ps[g];
-    PassParams P = base_params(h, wk, ring, tickets + g, d_off, d_len);
+    PassParams P = base_params(h, wk, tickets + g, d_off, d_len);
     P.in = in;
     P.in_w = pg.in_w;
     P.out = (g + 1 < G) ? seqbuf[g & 1] : nullptr;
@@ -827,7 +816,6 @@ wt_status build_wm(const void* d_seq, uint64_t n, uint32_t sigma, int w, const w
     P.wm_cls = cls + coff;
     P.ntiles = (uint32_t)ntiles;
     P.n_in = n;
-    P.seq_base = g_seq.fetch_add(ntiles + 1);
     TRY(launch_pass(P, pg.wide, false, ntiles, o, st));
     coff += (2 << pg.t) + pg.t + 1;
     in = P.out;
@@ -857,7 +845,7 @@ wt_status build_wt(const void* d_seq, uint64_t n, uint32_t sigma, int w, const w
   const int G = (int)ps.size();
   const uint32_t T = PT;
   const uint64_t V = (uint64_t)1 << L;
-  uint64_t *hist, *C, *scr, *ring, *d_off, *d_len, *tcnt, *toff;
+  uint64_t *hist, *C, *scr, *d_off, *d_len, *tcnt, *toff;
   uint32_t *tickets, *d_ntiles;
   TileDesc* tiles;
   uint64_t max_nodes = (uint64_t)1 << ps.back().a;
@@ -865,7 +853,6 @@ wt_status build_wt(const void* d_seq, uint64_t n, uint32_t sigma, int w, const w
   TRY(wk.get(&hist, V));
   TRY(wk.get(&C, V + 1));
   TRY(wk.get(&scr, scan_scratch(std::max(V, max_nodes))));
-  TRY(wk.get(&ring, (size_t)RING_SLOTS * SLOT_U64));
   TRY(wk.get(&tickets, 32));
   TRY(wk.get(&d_off, h->levels + 1));
   TRY(wk.get(&d_len, h->levels));
@@ -883,7 +870,7 @@ wt_status build_wt(const void* d_seq, uint64_t n, uint32_t sigma, int w, const w
     count_launch();
     CK(cudaGetLastError());
   }
-  k_reset_lookback<<<1, 1024, 0, st>>>(ring, RING_SLOTS, tickets, h->d_abort);
+  k_reset_tickets<<<1, 32, 0, st>>>(tickets, h->d_abort);
   count_launch();
   CK(cudaGetLastError());
   void* seqbuf[2] = {nullptr, nullptr};
@@ -909,7 +896,7 @@ wt_status build_wt(const void* d_seq, uint64_t n, uint32_t sigma, int w, const w
       count_launch();
     }
     CK(cudaGetLastError());
-    PassParams P = base_params(h, wk, ring, tickets + g, d_off, d_len);
+    PassParams P = base_params(h, wk, tickets + g, d_off, d_len);
     P.in = in;
     P.in_w = pg.in_w;
     P.out = (g + 1 < G) ? seqbuf[g & 1] : nullptr;
@@ -925,7 +912,6 @@ wt_status build_wt(const void* d_seq, uint64_t n, uint32_t sigma, int w, const w
     P.ntiles_dev = d_ntiles;
     P.n_in = n;
     const uint64_t mt = (n + T - 1) / T + nn;
-    P.seq_base = g_seq.fetch_add(mt + 1);
     TRY(launch_pass(P, pg.wide, multiary, mt, o, st));
     in = P.out;
   }
@@ -1111,13 +1097,12 @@ wt_status build_huff(const void* d_seq, uint64_t n, uint32_t sigma, int w, const
   std::vector<PassGeom> ps = make_passes(Lm, tau, 4);
   const int G = (int)ps.size();
   const uint32_t T = PT;
-  uint64_t *ring, *d_off, *d_len, *scr, *tcnt, *toff;
+  uint64_t *d_off, *d_len, *scr, *tcnt, *toff;
   uint32_t *tickets, *d_ntiles;
   TileDesc* tiles;
   uint64_t max_nodes = 1;
   for (int l = 0; l < Lm; l++) max_nodes = std::max<uint64_t>(max_nodes, node_lvl[3 * l + 2]);
   const uint64_t max_tiles = (n + T - 1) / T + max_nodes + 1;
-  TRY(wk.get(&ring, (size_t)RING_SLOTS * SLOT_U64));
   TRY(wk.get(&tickets, 32));
   TRY(wk.get(&d_off, Lm + 1));
   TRY(wk.get(&d_len, Lm));
@@ -1128,7 +1113,7 @@ wt_status build_huff(const void* d_seq, uint64_t n, uint32_t sigma, int w, const
   TRY(wk.get(&d_ntiles, 1));
   CK(cudaMemcpyAsync(d_off, h->level_off.data(), (Lm + 1) * 8, cudaMemcpyHostToDevice, st));
   CK(cudaMemcpyAsync(d_len, h->level_len.data(), Lm * 8, cudaMemcpyHostToDevice, st));
-  k_reset_lookback<<<1, 1024, 0, st>>>(ring, RING_SLOTS, tickets, h->d_abort);
+  k_reset_tickets<<<1, 32, 0, st>>>(tickets, h->d_abort);
   count_launch();
   CK(cudaGetLastError());
   void* seqbuf[2] = {nullptr, nullptr};
@@ -1156,7 +1141,7 @@ wt_status build_huff(const void* d_seq, uint64_t n, uint32_t sigma, int w, const
       CK(cudaMemsetAsync(d_ntiles, 0, 4, st));
     }
     CK(cudaGetLastError());
-    PassParams P = base_params(h, wk, ring, tickets + g, d_off, d_len);
+    PassParams P = base_params(h, wk, tickets + g, d_off, d_len);
     P.in = in;
     P.in_w = g == 0 ? w : pg.in_w;
     P.code_map = g == 0 ? d_left : nullptr;
@@ -1173,7 +1158,6 @@ wt_status build_huff(const void* d_seq, uint64_t n, uint32_t sigma, int w, const
     P.ntiles_dev = d_ntiles;
     P.n_in = h->level_len[pg.a];
     const uint64_t mt = (P.n_in + T - 1) / T + nn;
-    P.seq_base = g_seq.fetch_add(mt + 1);
     TRY(launch_pass(P, pg.wide, false, mt, o, st));
     in = P.out;
   }

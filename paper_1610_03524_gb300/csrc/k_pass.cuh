@@ -171,7 +171,6 @@ __global__ void __launch_bounds__(NT + 32, WT_PASS_MIN_CTAS) k_pass(const __grid
   uint64_t* const sbase = cls_cs;  // reused by the scatter
 
   __shared__ uint32_t s_tile;
-  __shared__ int s_stat;
   __shared__ int s_ones[W];
   __shared__ int s_scan[W + 1];
   __shared__ int wst[1 << TAU_MAX];
@@ -303,7 +302,6 @@ __global__ void __launch_bounds__(NT + 32, WT_PASS_MIN_CTAS) k_pass(const __grid
       // this tile's count of every digit value in the earlier tiles of its
       // sequence or node: the prefix sums of the per-tile counts (Section
       // 4.2, prefix sums across the K sub-problems), taken before the pass
-      int status = 0;
       uint64_t* const exd = ex_cnt + cls_idx(t, 0);  // exclusive digit counts
       {
         const uint64_t* ca = P0.tchunk + (uint64_t)(ti / TCHUNK) * TC_STRIDE;
@@ -345,7 +343,6 @@ __global__ void __launch_bounds__(NT + 32, WT_PASS_MIN_CTAS) k_pass(const __grid
           ex_cnt[cls_idx(j, k)] = ex_cnt[cls_idx(j + 1, k)] + ex_cnt[cls_idx(j + 1, k + (1 << j))];
         __syncwarp();
       }
-      if (lane == 0) s_stat = status;
     } else {
       // ---- 4 (worker warps). t stable 1-bit splits in shared memory -------
       // Warp w holds rows 16w..16w+15 of the tile (row = 32 consecutive
@@ -411,13 +408,6 @@ __global__ void __launch_bounds__(NT + 32, WT_PASS_MIN_CTAS) k_pass(const __grid
       else splits(std::false_type{});
     }
     __syncthreads();
-    if (s_stat < 0) {
-      if (tid == 0) {
-        atomicOr(P.err, ERR_TIMEOUT);
-        atomicExch(P0.abort_flag, 1u);
-      }
-      return;
-    }
     // the final element order is in bufB after an odd number of moves
     cur = (P.out != nullptr ? t : t - 1) & 1;
 

@@ -111,12 +111,13 @@ struct wt_server_s {
 namespace {
 
 // device bytes a build of (n, sigma, width) holds: the structure, plus while
-// it runs the device copy of the sequence and its intermediate sequences
+// it runs the device copy of the sequence, its intermediate sequences and its
+// tiles' digit counts (1 KB per 4096-symbol tile)
 uint64_t build_need(uint64_t n, uint32_t sigma, uint32_t width) {
-  return wtk::wm_resident_bytes(n, sigma) + n * (uint64_t)width + 2 * n * 2 + 4096;
+  return wtk::wm_resident_bytes(n, sigma) + n * (uint64_t)width + 2 * n * 2 + n / 4 + 8192;
 }
 
-// bytes a batched build holds besides its sequences' needs (look-back ring,
+// bytes a batched build holds besides its sequences' needs (tile counts,
 // tables, directory scratch)
 constexpr uint64_t BATCH_OVERHEAD = 16ull << 20;
 

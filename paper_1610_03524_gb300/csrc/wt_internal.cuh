@@ -34,18 +34,11 @@ struct TileDesc {
 constexpr int TC_STRIDE = 256;
 constexpr uint32_t TCHUNK = 1024;
 
-// Symbols per tile of the partition pass, look-back ring geometry, and the
-// bound on every device-side wait (polls before a wait gives up).
+// Symbols per tile of the partition pass.
 #ifndef WT_PASS_T
 #define WT_PASS_T 4096
 #endif
 constexpr int PASS_T = WT_PASS_T;
-constexpr uint32_t RING_SLOTS = 4096;
-constexpr uint64_t SPIN_LIMIT = 1ull << 24;
-
-// Look-back ring slot: one word per digit value (flag in the top 2 bits,
-// count below), zeroed before every pass.
-constexpr int SLOT_U64 = 1 << TAU_MAX;
 
 // Batched builds: the per-sequence part of a pass, one entry per sequence
 // taking part in the launch.  Its tiles are tile0 .. tile0 + ceil(n/T) - 1 of
@@ -119,38 +112,13 @@ struct PassParams {
   // prefix sums of the tiles' digit counts (see TileDesc)
   const uint32_t* tcnt;
   const uint64_t* tchunk;
-  // decoupled look-back (unused by the two-phase prefix sums)
-  uint64_t* ring;
-  uint32_t ring_mask;
-  uint64_t seq_base;
-  uint32_t* ticket;
+  uint32_t* ticket;      // tiles are taken in order from this counter
   uint32_t* err;
   uint32_t* abort_flag;
-  uint64_t spin_limit;
 };
 
 __device__ __forceinline__ uint32_t rev_bits(uint32_t k, int j) {
   return j == 0 ? 0u : (__brev(k) >> (32 - j));
-}
-
-__device__ __forceinline__ uint64_t ld_acquire_u64(const uint64_t* p) {
-  uint64_t v;
-  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
-  return v;
-}
-
-__device__ __forceinline__ void st_release_u64(uint64_t* p, uint64_t v) {
-  asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
-}
-
-__device__ __forceinline__ uint64_t ld_relaxed_u64(const uint64_t* p) {
-  uint64_t v;
-  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
-  return v;
-}
-
-__device__ __forceinline__ void st_relaxed_u64(uint64_t* p, uint64_t v) {
-  asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 
 __device__ __forceinline__ uint32_t ld_volatile_u32(const uint32_t* p) {
