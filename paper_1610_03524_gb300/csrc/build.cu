@@ -175,6 +175,81 @@ __global__ void k_hist_digits(const void* seq, uint64_t n, uint32_t sigma,
     if (sh[i]) atomicAdd((unsigned long long*)&hist[i], (unsigned long long)sh[i]);
 }
 
+// The same histograms, walked tile by tile (tiles of PASS_T symbols, as the
+// first partition pass sees them), also writing each tile's counts of the
+// first pass's reversed digit: the first pass's per-tile counts come with
+// the one read of the sequence.
+template <int WB, int NG>
+__global__ void __launch_bounds__(256) k_hist_digits_tiles(const void* seq, uint64_t n,
+                                                           uint32_t sigma,
+                                                           const __grid_constant__ HistGeom geo,
+                                                           int L, int t0, uint64_t* hist,
+                                                           uint32_t* err, uint32_t* tcnt) {
+  using T = typename std::conditional<WB == 1, uint8_t,
+                                      typename std::conditional<WB == 2, uint16_t, uint32_t>::type>::type;
+  __shared__ uint32_t sh[1024];
+  __shared__ uint32_t th[2][TC_STRIDE];
+  const int tot = geo.off[geo.G];
+  const int tid = threadIdx.x;
+  for (int i = tid; i < tot; i += blockDim.x) sh[i] = 0;
+  th[0][tid] = 0;
+  th[1][tid] = 0;
+  __syncthreads();
+  const uint32_t rmask = (1u << t0) - 1u;
+  const int rsh = 32 - L;
+  const uint64_t ntiles = (n + PASS_T - 1) / PASS_T;
+  const T* s = (const T*)seq;
+  const bool vec = (((uintptr_t)seq) & 15) == 0;
+  bool bad = false;
+  int buf = 0;
+  auto count = [&](uint32_t x) {
+    bad |= x >= sigma;
+    if (NG > 0) {
+#pragma unroll
+      for (int g = 0; g < NG; g++) atomicAdd(&sh[geo.off[g] + ((x >> geo.shf[g]) & geo.mask[g])], 1u);
+    } else {
+      for (int g = 0; g < geo.G; g++)
+        atomicAdd(&sh[geo.off[g] + ((x >> geo.shf[g]) & geo.mask[g])], 1u);
+    }
+    atomicAdd(&th[buf][(__brev(x) >> rsh) & rmask], 1u);
+  };
+  for (uint64_t ti = blockIdx.x; ti < ntiles; ti += gridDim.x) {
+    const uint64_t i0 = ti * PASS_T;
+    const uint64_t i1 = i0 + PASS_T < n ? i0 + PASS_T : n;
+    if (vec && i1 - i0 == PASS_T) {
+      constexpr int PER = 16 / WB;
+      const uint4* v = (const uint4*)(s + i0);
+      for (int k = tid; k < PASS_T / PER; k += blockDim.x) {
+        const uint4 q = __ldcs(v + k);
+        const uint32_t w[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+        for (int m = 0; m < 4; m++) {
+          if (WB == 1) {
+#pragma unroll
+            for (int b = 0; b < 4; b++) count((w[m] >> (8 * b)) & 0xffu);
+          } else if (WB == 2) {
+            count(w[m] & 0xffffu);
+            count(w[m] >> 16);
+          } else {
+            count(w[m]);
+          }
+        }
+      }
+    } else {
+      for (uint64_t i = i0 + tid; i < i1; i += blockDim.x) count((uint32_t)s[i]);
+    }
+    __syncthreads();
+    // the other buffer was written out one tile ago; this one now
+    tcnt[ti * TC_STRIDE + tid] = th[buf][tid];
+    th[buf][tid] = 0;
+    buf ^= 1;
+  }
+  if (bad) atomicOr(err, ERR_SYMBOL);
+  __syncthreads();
+  for (int i = tid; i < tot; i += blockDim.x)
+    if (sh[i]) atomicAdd((unsigned long long*)&hist[i], (unsigned long long)sh[i]);
+}
+
 template <int WB>
 static void launch_hist_digits_w(const void* seq, uint64_t n, uint32_t sigma, const HistGeom& geo,
                                  uint64_t* hist, uint32_t* err, uint32_t blocks, cudaStream_t st) {
@@ -596,20 +671,29 @@ __global__ void __launch_bounds__(256) k_tile_scan_chunk(uint32_t* tcnt, const u
   tchunk[(uint64_t)c * TC_STRIDE + r] = run;
 }
 
-// ... and the exclusive prefix of the chunks' totals (u64)
-__global__ void __launch_bounds__(256) k_tile_scan_top(uint64_t* tchunk, uint32_t nchunk) {
-  const uint32_t r = threadIdx.x;
-  uint64_t run = 0;
-  for (uint32_t c = 0; c < nchunk; c++) {
-    const uint64_t v = tchunk[(uint64_t)c * TC_STRIDE + r];
-    tchunk[(uint64_t)c * TC_STRIDE + r] = run;
-    run += v;
+// ... and the exclusive prefix of the chunks' totals (u64): one warp per
+// digit value, 32 chunks per step
+__global__ void __launch_bounds__(32) k_tile_scan_top(uint64_t* tchunk, uint32_t nchunk) {
+  const uint32_t r = blockIdx.x, lane = threadIdx.x;
+  uint64_t carry = 0;
+  for (uint32_t c0 = 0; c0 < nchunk; c0 += 32) {
+    const uint32_t c = c0 + lane;
+    const uint64_t v = c < nchunk ? tchunk[(uint64_t)c * TC_STRIDE + r] : 0ull;
+    uint64_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint64_t y = __shfl_up_sync(FULL, x, o);
+      if ((int)lane >= o) x += y;
+    }
+    if (c < nchunk) tchunk[(uint64_t)c * TC_STRIDE + r] = carry + x - v;
+    carry += __shfl_sync(FULL, x, 31);
   }
 }
 
+// tcnt_pre: the tiles' digit counts when already taken (else counted here)
 template <typename E, bool DIG, bool BATCH = false>
 static wt_status launch_pass_t(const PassParams& P, uint64_t max_tiles, const wt_build_opts* o,
-                               cudaStream_t st) {
+                               cudaStream_t st, uint32_t* tcnt_pre = nullptr) {
   using SM = PassSmem<E, PT, PNT, DIG>;
   auto kern = k_pass<E, PT, PNT, DIG, BATCH>;
   static bool attr = false;
@@ -627,16 +711,18 @@ static wt_status launch_pass_t(const PassParams& P, uint64_t max_tiles, const wt
   // every tile's digit counts and their prefix sums across the tiles
   const uint64_t mt = std::max<uint64_t>(max_tiles, 1);
   const uint32_t nchunk = (uint32_t)((mt + TCHUNK - 1) / TCHUNK);
-  uint32_t* tcnt = nullptr;
+  uint32_t* tcnt = tcnt_pre;
   uint64_t* tchunk = nullptr;
-  CK(dmalloc((void**)&tcnt, mt * TC_STRIDE * 4, st));
+  if (!tcnt) {
+    CK(dmalloc((void**)&tcnt, mt * TC_STRIDE * 4, st));
+    k_tile_counts<E, BATCH><<<(unsigned)std::min<uint64_t>(mt, (uint64_t)num_sms() * 16), 256, 0,
+                              st>>>(P, tcnt);
+    count_launch();
+  }
   CK(dmalloc((void**)&tchunk, (uint64_t)nchunk * TC_STRIDE * 8, st));
-  k_tile_counts<E, BATCH><<<(unsigned)std::min<uint64_t>(mt, (uint64_t)num_sms() * 16), 256, 0, st>>>(
-      P, tcnt);
-  count_launch();
   k_tile_scan_chunk<<<nchunk, 256, 0, st>>>(tcnt, P.tiles ? P.ntiles_dev : nullptr, P.ntiles, tchunk);
   count_launch();
-  k_tile_scan_top<<<1, 256, 0, st>>>(tchunk, nchunk);
+  k_tile_scan_top<<<TC_STRIDE, 32, 0, st>>>(tchunk, nchunk);
   count_launch();
   PassParams Q = P;
   Q.tcnt = tcnt;
@@ -651,7 +737,7 @@ static wt_status launch_pass_t(const PassParams& P, uint64_t max_tiles, const wt
   kern<<<(unsigned)grid, PNT + 32, SM::bytes, st>>>(Q);
   CK(cudaGetLastError());
   count_launch();
-  dfree(tcnt, st);
+  if (!tcnt_pre) dfree(tcnt, st);
   dfree(tchunk, st);
   if (pf.on) {
     cudaEventRecord(e1, st);
@@ -663,11 +749,12 @@ static wt_status launch_pass_t(const PassParams& P, uint64_t max_tiles, const wt
 }
 
 static wt_status launch_pass(const PassParams& P, bool wide, bool dig, uint64_t max_tiles,
-                             const wt_build_opts* o, cudaStream_t st) {
-  if (dig) return wide ? launch_pass_t<uint32_t, true>(P, max_tiles, o, st)
-                       : launch_pass_t<uint16_t, true>(P, max_tiles, o, st);
-  return wide ? launch_pass_t<uint32_t, false>(P, max_tiles, o, st)
-              : launch_pass_t<uint16_t, false>(P, max_tiles, o, st);
+                             const wt_build_opts* o, cudaStream_t st,
+                             uint32_t* tcnt_pre = nullptr) {
+  if (dig) return wide ? launch_pass_t<uint32_t, true>(P, max_tiles, o, st, tcnt_pre)
+                       : launch_pass_t<uint16_t, true>(P, max_tiles, o, st, tcnt_pre);
+  return wide ? launch_pass_t<uint32_t, false>(P, max_tiles, o, st, tcnt_pre)
+              : launch_pass_t<uint16_t, false>(P, max_tiles, o, st, tcnt_pre);
 }
 
 // Batched wavelet matrices: one launch over the tiles of every sequence in
@@ -777,12 +864,30 @@ wt_status build_wm(const void* d_seq, uint64_t n, uint32_t sigma, int w, const w
   CK(cudaMemcpyAsync(d_off, h->level_off.data(), (L + 1) * 8, cudaMemcpyHostToDevice, st));
   CK(cudaMemcpyAsync(d_len, h->level_len.data(), L * 8, cudaMemcpyHostToDevice, st));
   CK(cudaMemsetAsync(hist, 0, nh * 8, st));
+  // digit histograms of every pass, and the first pass's per-tile counts
+  uint32_t* tcnt0;
+  const uint64_t ntiles0 = (n + PASS_T - 1) / PASS_T;
+  TRY(wk.get(&tcnt0, (size_t)ntiles0 * TC_STRIDE));
   {
-    const uint32_t blocks = std::min<uint64_t>(num_sms() * 4, (n + 8191) / 8192 + 1);
+    const uint32_t blocks = (uint32_t)std::min<uint64_t>((uint64_t)num_sms() * 8, ntiles0);
     const HistGeom geo = hist_geom(L, tau);
-    if (w == 1) launch_hist_digits_w<1>(d_seq, n, sigma, geo, hist, h->d_err, blocks, st);
-    else if (w == 2) launch_hist_digits_w<2>(d_seq, n, sigma, geo, hist, h->d_err, blocks, st);
-    else launch_hist_digits_w<4>(d_seq, n, sigma, geo, hist, h->d_err, blocks, st);
+    const int t0 = ps[0].t;
+#define WT_HT(WB, NG)                                                                       \
+  k_hist_digits_tiles<WB, NG><<<blocks, 256, 0, st>>>(d_seq, n, sigma, geo, L, t0, hist, \
+                                                      h->d_err, tcnt0)
+#define WT_HTW(WB)                                 \
+  switch (geo.G) {                                 \
+    case 1: WT_HT(WB, 1); break;                   \
+    case 2: WT_HT(WB, 2); break;                   \
+    case 3: WT_HT(WB, 3); break;                   \
+    case 4: WT_HT(WB, 4); break;                   \
+    default: WT_HT(WB, 0); break;                  \
+  }
+    if (w == 1) { WT_HTW(1) }
+    else if (w == 2) { WT_HTW(2) }
+    else { WT_HTW(4) }
+#undef WT_HTW
+#undef WT_HT
     count_launch();
     CK(cudaGetLastError());
   }
@@ -816,7 +921,7 @@ wt_status build_wm(const void* d_seq, uint64_t n, uint32_t sigma, int w, const w
     P.wm_cls = cls + coff;
     P.ntiles = (uint32_t)ntiles;
     P.n_in = n;
-    TRY(launch_pass(P, pg.wide, false, ntiles, o, st));
+    TRY(launch_pass(P, pg.wide, false, ntiles, o, st, g == 0 ? tcnt0 : nullptr));
     coff += (2 << pg.t) + pg.t + 1;
     in = P.out;
   }

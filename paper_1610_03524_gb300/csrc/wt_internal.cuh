@@ -32,7 +32,7 @@ struct TileDesc {
 // after the scan) and the chunk's exclusive counts at tchunk[c * TC_STRIDE + r]
 // (u64).
 constexpr int TC_STRIDE = 256;
-constexpr uint32_t TCHUNK = 1024;
+constexpr uint32_t TCHUNK = 256;
 
 // Symbols per tile of the partition pass.
 #ifndef WT_PASS_T
