@@ -671,8 +671,8 @@ __global__ void __launch_bounds__(256) k_tile_scan_chunk(uint32_t* tcnt, const u
   tchunk[(uint64_t)c * TC_STRIDE + r] = run;
 }
 
-// ... and the exclusive prefix of the chunks' totals (u64): one warp per
-// digit value, 32 chunks per step
+// ... and the exclusive prefix of the chunks' totals (u64), with the grand
+// total after the last chunk: one warp per digit value, 32 chunks per step
 __global__ void __launch_bounds__(32) k_tile_scan_top(uint64_t* tchunk, uint32_t nchunk) {
   const uint32_t r = blockIdx.x, lane = threadIdx.x;
   uint64_t carry = 0;
@@ -688,6 +688,7 @@ __global__ void __launch_bounds__(32) k_tile_scan_top(uint64_t* tchunk, uint32_t
     if (c < nchunk) tchunk[(uint64_t)c * TC_STRIDE + r] = carry + x - v;
     carry += __shfl_sync(FULL, x, 31);
   }
+  if (lane == 0) tchunk[(uint64_t)nchunk * TC_STRIDE + r] = carry;
 }
 
 // tcnt_pre: the tiles' digit counts when already taken (else counted here)
@@ -719,7 +720,7 @@ static wt_status launch_pass_t(const PassParams& P, uint64_t max_tiles, const wt
                               st>>>(P, tcnt);
     count_launch();
   }
-  CK(dmalloc((void**)&tchunk, (uint64_t)nchunk * TC_STRIDE * 8, st));
+  CK(dmalloc((void**)&tchunk, ((uint64_t)nchunk + 1) * TC_STRIDE * 8, st));
   k_tile_scan_chunk<<<nchunk, 256, 0, st>>>(tcnt, P.tiles ? P.ntiles_dev : nullptr, P.ntiles, tchunk);
   count_launch();
   k_tile_scan_top<<<TC_STRIDE, 32, 0, st>>>(tchunk, nchunk);

@@ -177,13 +177,12 @@ __global__ void __launch_bounds__(NT + 32, WT_PASS_MIN_CTAS) k_pass(const __grid
   __shared__ uint32_t s_dead[(1 << TAU_MAX) / 32];
   __shared__ uint64_t s_lvl_bits[TAU_MAX];
   __shared__ uint64_t* s_lvl_ptr[TAU_MAX];
-  __shared__ uint32_t s_hist[1 << TAU_MAX];
+  __shared__ int s_bad;
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int bpe = DIG ? 2 : 1;
   const uint32_t ntiles = P0.tiles ? *P0.ntiles_dev : P0.ntiles;
   if (BATCH && tid == 0) s_P = P0;
-  for (int i = tid; i < (1 << TAU_MAX); i += NB) s_hist[i] = 0;
   const uint32_t lt = lanemask_lt();
   const int wbase = warp * PW;
 
@@ -240,32 +239,15 @@ __global__ void __launch_bounds__(NT + 32, WT_PASS_MIN_CTAS) k_pass(const __grid
     }
     const bool full = cnt == T;
 
-    // ---- 1. load the tile and count its digits (the counters were cleared
-    //      during the previous tile) -------------------------------------
+    // ---- 1. load the tile (its digit counts were taken before the pass) --
     {
-      const uint32_t rmask = (1u << t) - 1u;
-      const int rsh = 32 - P.rbits;
-      auto count = [&](uint32_t x) { atomicAdd(&s_hist[(__brev(x) >> rsh) & rmask], 1u); };
       if (P.code_map) {
-        for (int i = tid; i < cnt; i += NB) {
-          const uint32_t x = P.code_map[load_elem(P.in, P.in_w, ts + i)];
-          bufA[i] = (E)x;
-          count(x);
-        }
+        for (int i = tid; i < cnt; i += NB) bufA[i] = (E)P.code_map[load_elem(P.in, P.in_w, ts + i)];
       } else if (P.in_w == 2 && sizeof(E) == 2 && full &&
                  (((uintptr_t)P.in + 2 * ts) & 15) == 0) {
         const uint4* src = (const uint4*)((const uint16_t*)P.in + ts);
         uint4* dst = (uint4*)bufA;
-        for (int i = tid; i < T / 8; i += NB) {
-          const uint4 q = __ldcs(src + i);
-          dst[i] = q;
-          const uint32_t w4[4] = {q.x, q.y, q.z, q.w};
-#pragma unroll
-          for (int k = 0; k < 4; k++) {
-            count(w4[k] & 0xffffu);
-            count(w4[k] >> 16);
-          }
-        }
+        for (int i = tid; i < T / 8; i += NB) dst[i] = __ldcs(src + i);
       } else if (P.in_w == 1 && sizeof(E) == 2 && full && (((uintptr_t)P.in + ts) & 15) == 0) {
         const uint4* src = (const uint4*)((const uint8_t*)P.in + ts);
         for (int i = tid; i < T / 16; i += NB) {
@@ -277,43 +259,56 @@ __global__ void __launch_bounds__(NT + 32, WT_PASS_MIN_CTAS) k_pass(const __grid
           for (int k = 0; k < 4; k++) {
             o[2 * k] = __byte_perm(w4[k], 0, 0x4140);
             o[2 * k + 1] = __byte_perm(w4[k], 0, 0x4342);
-#pragma unroll
-            for (int b = 0; b < 4; b++) count((w4[k] >> (8 * b)) & 0xffu);
           }
           d[0] = make_uint4(o[0], o[1], o[2], o[3]);
           d[1] = make_uint4(o[4], o[5], o[6], o[7]);
         }
       } else {
-        for (int i = tid; i < cnt; i += NB) {
-          const uint32_t x = load_elem(P.in, P.in_w, ts + i);
-          bufA[i] = (E)x;
-          count(x);
-        }
+        for (int i = tid; i < cnt; i += NB) bufA[i] = (E)load_elem(P.in, P.in_w, ts + i);
       }
     }
     __syncthreads();
 
     int cur;
     if (warp == CW) {
-      // ---- 3 (control warp). class counts of every level from the digit
-      //      histogram; per-digit decoupled look-back for the counts of all
-      //      earlier tiles; exclusive counts of every level ----------------
+      // ---- 3 (control warp). class counts of every level from the tile's
+      //      digit counts; counts of all earlier tiles from their prefix
+      //      sums; exclusive counts of every level -------------------------
       const int nd = 1 << t;
       // this tile's count of every digit value in the earlier tiles of its
       // sequence or node: the prefix sums of the per-tile counts (Section
       // 4.2, prefix sums across the K sub-problems), taken before the pass
+      // (the tables are exclusive inside chunks of TCHUNK tiles, with the
+      // chunks' exclusive prefixes and their total after the last chunk: the
+      // tile's own digit counts are the difference to the next tile, or to
+      // the next chunk for the last tile of a chunk)
       uint64_t* const exd = ex_cnt + cls_idx(t, 0);  // exclusive digit counts
       {
-        const uint64_t* ca = P0.tchunk + (uint64_t)(ti / TCHUNK) * TC_STRIDE;
+        const uint32_t ch = ti / TCHUNK;
+        const uint64_t* ca = P0.tchunk + (uint64_t)ch * TC_STRIDE;
         const uint64_t* cb = P0.tchunk + (uint64_t)(seg0 / TCHUNK) * TC_STRIDE;
         const uint32_t* ta = P0.tcnt + (uint64_t)ti * TC_STRIDE;
         const uint32_t* tb = P0.tcnt + (uint64_t)seg0 * TC_STRIDE;
-        for (int r = lane; r < nd; r += 32) exd[r] = (ca[r] + ta[r]) - (cb[r] + tb[r]);
+        const bool last = (ti + 1) % TCHUNK == 0 || ti + 1 >= ntiles;
+        uint32_t sum = 0;
+        for (int r = lane; r < nd; r += 32) {
+          const uint32_t a = ta[r];
+          const uint32_t c = last ? (uint32_t)(ca[TC_STRIDE + r] - ca[r]) - a : ta[TC_STRIDE + r] - a;
+          exd[r] = (ca[r] + a) - (cb[r] + tb[r]);
+          ccnt[cls_idx(t, r)] = c;
+          sum += c;
+        }
+        // a table that disagrees with the tile would misplace its bits: flag
+        // it and leave the tile's outputs alone
+        const bool bad = __reduce_add_sync(FULL, sum) != (uint32_t)cnt;
+        if (lane == 0) {
+          s_bad = bad;
+          if (bad) atomicOr(P.err, ERR_INTERNAL);
+        }
       }
       // class counts and tile-local class starts
       // level j classes are the digit values mod 2^j: level t holds the
       // digit counts, level j-1 class k sums classes k and k + 2^(j-1)
-      for (int k = lane; k < nd; k += 32) ccnt[cls_idx(t, k)] = s_hist[k];
       __syncwarp();
       for (int j = t - 1; j >= 0; j--) {
         for (int k = lane; k < (1 << j); k += 32)
@@ -411,9 +406,7 @@ __global__ void __launch_bounds__(NT + 32, WT_PASS_MIN_CTAS) k_pass(const __grid
     // the final element order is in bufB after an odd number of moves
     cur = (P.out != nullptr ? t : t - 1) & 1;
 
-    // the digit counters are read for the last time by the control warp
-    // before the splits end: clear them for the next tile
-    for (int i = tid; i < (1 << TAU_MAX); i += NB) s_hist[i] = 0;
+    if (s_bad) continue;  // uniform: read after the barrier above
 
     // ---- 5. level bitmaps: whole words stored, shared words ORed ----------
     auto emitted = [&](int j) -> bool { return !DIG || (((P.a + j) & 1) == 0); };
@@ -485,7 +478,8 @@ __global__ void __launch_bounds__(NT + 32, WT_PASS_MIN_CTAS) k_pass(const __grid
       if (nb < 64) v &= (1ull << nb) - 1ull;
       v <<= (int)(lo2 - wb);
       const uint64_t wend = (wb + 64 < nlb) ? wb + 64 : nlb;
-      if (G0 <= wb && G1 >= wend) lb[w] = v;
+      if (wb >= nlb) atomicOr(P.err, ERR_INTERNAL);  // never for consistent tables
+      else if (G0 <= wb && G1 >= wend) lb[w] = v;
       else atomicOr((unsigned long long*)(lb + w), (unsigned long long)v);
     }
     __syncthreads();
@@ -518,7 +512,9 @@ __global__ void __launch_bounds__(NT + 32, WT_PASS_MIN_CTAS) k_pass(const __grid
           const uint32_t x = fin[p];
           const uint32_t r = (__brev(x) >> rsh) & rmask;
           if (HF && ((s_dead[r >> 5] >> (r & 31)) & 1u)) continue;
-          out[sbase[r] + p] = (O)(x & mask);
+          const uint64_t o = sbase[r] + p;
+          if (o < P.n_in) out[o] = (O)(x & mask);
+          else atomicOr(P.err, ERR_INTERNAL);  // never for consistent tables
         }
       };
       if (P.shape == SHAPE_HUFF) {
