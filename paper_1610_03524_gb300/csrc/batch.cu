@@ -338,13 +338,14 @@ wt_status batch_build_wm(const wt_batch_item* items, uint32_t m, const wt_build_
     uint64_t first;
     uint32_t nsegs, ntiles;
     bool wide;
+    int tmax;  // widest digit of its segments
   };
   std::vector<Launch> launches;
   {
     uint64_t k = 0;
     for (int g = 0; g < Gmax; g++) {
       for (int wide = 0; wide < 2; wide++) {
-        Launch L0{k, 0, 0, wide != 0};
+        Launch L0{k, 0, 0, wide != 0, 1};
         uint32_t tiles = 0;
         for (uint32_t i = 0; i < m; i++) {
           const SeqPlan& p = sp[i];
@@ -370,6 +371,7 @@ wt_status batch_build_wm(const wt_batch_item* items, uint32_t m, const wt_build_
           d.rbits = q.rbits;
           tiles += (uint32_t)((p.n + PASS_T - 1) / PASS_T);
           L0.nsegs++;
+          L0.tmax = std::max(L0.tmax, q.t);
         }
         L0.ntiles = tiles;
         if (L0.nsegs) launches.push_back(L0);
@@ -399,6 +401,7 @@ wt_status batch_build_wm(const wt_batch_item* items, uint32_t m, const wt_build_
     P.ntiles = L0.ntiles;
     P.segs = d_sseg + L0.first;
     P.nsegs = L0.nsegs;
+    P.tcs = tc_stride(L0.tmax);
     s = launch_pass_batch(P, L0.wide, o, st);
   }
   if (s == WT_OK && !(o && (o->flags & WT_FLAG_NO_DIRECTORY)))

@@ -184,9 +184,12 @@ __global__ void __launch_bounds__(256) k_hist_digits_tiles(const void* seq, uint
                                                            uint32_t sigma,
                                                            const __grid_constant__ HistGeom geo,
                                                            int L, int t0, uint64_t* hist,
-                                                           uint32_t* err, uint32_t* tcnt) {
+                                                           uint32_t* err, uint32_t* tcnt,
+                                                           uint32_t tcs) {
   using T = typename std::conditional<WB == 1, uint8_t,
                                       typename std::conditional<WB == 2, uint16_t, uint32_t>::type>::type;
+  // the first pass's digits are counted per tile only (its global counts
+  // are the sums of the tile counts); the other passes' in sh
   __shared__ uint32_t sh[1024];
   __shared__ uint32_t th[2][TC_STRIDE];
   const int tot = geo.off[geo.G];
@@ -194,6 +197,7 @@ __global__ void __launch_bounds__(256) k_hist_digits_tiles(const void* seq, uint
   for (int i = tid; i < tot; i += blockDim.x) sh[i] = 0;
   th[0][tid] = 0;
   th[1][tid] = 0;
+  uint32_t own = 0;  // this thread's reversed digit, summed over the block's tiles
   __syncthreads();
   const uint32_t rmask = (1u << t0) - 1u;
   const int rsh = 32 - L;
@@ -206,9 +210,9 @@ __global__ void __launch_bounds__(256) k_hist_digits_tiles(const void* seq, uint
     bad |= x >= sigma;
     if (NG > 0) {
 #pragma unroll
-      for (int g = 0; g < NG; g++) atomicAdd(&sh[geo.off[g] + ((x >> geo.shf[g]) & geo.mask[g])], 1u);
+      for (int g = 1; g < NG; g++) atomicAdd(&sh[geo.off[g] + ((x >> geo.shf[g]) & geo.mask[g])], 1u);
     } else {
-      for (int g = 0; g < geo.G; g++)
+      for (int g = 1; g < geo.G; g++)
         atomicAdd(&sh[geo.off[g] + ((x >> geo.shf[g]) & geo.mask[g])], 1u);
     }
     atomicAdd(&th[buf][(__brev(x) >> rsh) & rmask], 1u);
@@ -240,14 +244,19 @@ __global__ void __launch_bounds__(256) k_hist_digits_tiles(const void* seq, uint
     }
     __syncthreads();
     // the other buffer was written out one tile ago; this one now
-    tcnt[ti * TC_STRIDE + tid] = th[buf][tid];
+    const uint32_t c = th[buf][tid];
+    if (tid < (int)tcs) tcnt[ti * tcs + tid] = c;
+    own += c;
     th[buf][tid] = 0;
     buf ^= 1;
   }
   if (bad) atomicOr(err, ERR_SYMBOL);
+  // first pass: digit value = the reverse of this thread's t0-bit key
+  if (tid <= (int)rmask && own)
+    atomicAdd((unsigned long long*)&hist[__brev((uint32_t)tid) >> (32 - t0)], (unsigned long long)own);
   __syncthreads();
-  for (int i = tid; i < tot; i += blockDim.x)
-    if (sh[i]) atomicAdd((unsigned long long*)&hist[i], (unsigned long long)sh[i]);
+  for (int i = geo.off[1]; i < tot; i += blockDim.x)
+    if (i + tid < tot && sh[i + tid]) atomicAdd((unsigned long long*)&hist[i + tid], (unsigned long long)sh[i + tid]);
 }
 
 template <int WB>
@@ -648,7 +657,7 @@ __global__ void __launch_bounds__(256) k_tile_counts(const __grid_constant__ Pas
       for (int i = tid; i < cnt; i += 256) count(load_elem(P.in, P.in_w, ts + i));
     }
     __syncthreads();
-    tcnt[(uint64_t)ti * TC_STRIDE + tid] = h[tid];
+    if (tid < (int)P0.tcs) tcnt[(uint64_t)ti * P0.tcs + tid] = h[tid];
     __syncthreads();
   }
 }
@@ -658,37 +667,44 @@ __global__ void __launch_bounds__(256) k_tile_counts(const __grid_constant__ Pas
 __global__ void __launch_bounds__(256) k_tile_scan_chunk(uint32_t* tcnt, const uint32_t* ntiles_dev,
                                                          uint32_t ntiles_host, uint64_t* tchunk) {
   const uint32_t nt = ntiles_dev ? *ntiles_dev : ntiles_host;
-  const uint32_t c = blockIdx.x, r = threadIdx.x;
+  const uint32_t c = blockIdx.x, r = threadIdx.x, S = blockDim.x;  // one thread per digit
   const uint64_t t0 = (uint64_t)c * TCHUNK;
   const uint64_t t1 = t0 + TCHUNK < nt ? t0 + TCHUNK : nt;
   uint32_t run = 0;
-#pragma unroll 8
-  for (uint64_t ti = t0; ti < t1; ti++) {
-    const uint32_t v = tcnt[ti * TC_STRIDE + r];
-    tcnt[ti * TC_STRIDE + r] = run;
-    run += v;
+  // sixteen loads in flight before their stores (in place: the stores
+  // would otherwise wait for each load in turn)
+  constexpr int B = 16;
+  for (uint64_t ti = t0; ti < t1; ti += B) {
+    uint32_t v[B];
+#pragma unroll
+    for (int k = 0; k < B; k++) v[k] = ti + k < t1 ? tcnt[(ti + k) * S + r] : 0u;
+#pragma unroll
+    for (int k = 0; k < B; k++) {
+      if (ti + k < t1) tcnt[(ti + k) * S + r] = run;
+      run += v[k];
+    }
   }
-  tchunk[(uint64_t)c * TC_STRIDE + r] = run;
+  tchunk[(uint64_t)c * S + r] = run;
 }
 
 // ... and the exclusive prefix of the chunks' totals (u64), with the grand
 // total after the last chunk: one warp per digit value, 32 chunks per step
 __global__ void __launch_bounds__(32) k_tile_scan_top(uint64_t* tchunk, uint32_t nchunk) {
-  const uint32_t r = blockIdx.x, lane = threadIdx.x;
+  const uint32_t r = blockIdx.x, lane = threadIdx.x, S = gridDim.x;  // one warp per digit
   uint64_t carry = 0;
   for (uint32_t c0 = 0; c0 < nchunk; c0 += 32) {
     const uint32_t c = c0 + lane;
-    const uint64_t v = c < nchunk ? tchunk[(uint64_t)c * TC_STRIDE + r] : 0ull;
+    const uint64_t v = c < nchunk ? tchunk[(uint64_t)c * S + r] : 0ull;
     uint64_t x = v;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
       const uint64_t y = __shfl_up_sync(FULL, x, o);
       if ((int)lane >= o) x += y;
     }
-    if (c < nchunk) tchunk[(uint64_t)c * TC_STRIDE + r] = carry + x - v;
+    if (c < nchunk) tchunk[(uint64_t)c * S + r] = carry + x - v;
     carry += __shfl_sync(FULL, x, 31);
   }
-  if (lane == 0) tchunk[(uint64_t)nchunk * TC_STRIDE + r] = carry;
+  if (lane == 0) tchunk[(uint64_t)nchunk * S + r] = carry;
 }
 
 // tcnt_pre: the tiles' digit counts when already taken (else counted here)
@@ -712,20 +728,22 @@ static wt_status launch_pass_t(const PassParams& P, uint64_t max_tiles, const wt
   // every tile's digit counts and their prefix sums across the tiles
   const uint64_t mt = std::max<uint64_t>(max_tiles, 1);
   const uint32_t nchunk = (uint32_t)((mt + TCHUNK - 1) / TCHUNK);
+  PassParams Q = P;
+  Q.tcs = P.tcs ? P.tcs : tc_stride(P.t);  // batched passes give the widest digit's
   uint32_t* tcnt = tcnt_pre;
   uint64_t* tchunk = nullptr;
   if (!tcnt) {
-    CK(dmalloc((void**)&tcnt, mt * TC_STRIDE * 4, st));
+    CK(dmalloc((void**)&tcnt, mt * Q.tcs * 4, st));
     k_tile_counts<E, BATCH><<<(unsigned)std::min<uint64_t>(mt, (uint64_t)num_sms() * 16), 256, 0,
-                              st>>>(P, tcnt);
+                              st>>>(Q, tcnt);
     count_launch();
   }
-  CK(dmalloc((void**)&tchunk, ((uint64_t)nchunk + 1) * TC_STRIDE * 8, st));
-  k_tile_scan_chunk<<<nchunk, 256, 0, st>>>(tcnt, P.tiles ? P.ntiles_dev : nullptr, P.ntiles, tchunk);
+  CK(dmalloc((void**)&tchunk, ((uint64_t)nchunk + 1) * Q.tcs * 8, st));
+  k_tile_scan_chunk<<<nchunk, Q.tcs, 0, st>>>(tcnt, P.tiles ? P.ntiles_dev : nullptr, P.ntiles,
+                                              tchunk);
   count_launch();
-  k_tile_scan_top<<<TC_STRIDE, 32, 0, st>>>(tchunk, nchunk);
+  k_tile_scan_top<<<Q.tcs, 32, 0, st>>>(tchunk, nchunk);
   count_launch();
-  PassParams Q = P;
   Q.tcnt = tcnt;
   Q.tchunk = tchunk;
   Prof& pf = prof();
@@ -868,14 +886,14 @@ wt_status build_wm(const void* d_seq, uint64_t n, uint32_t sigma, int w, const w
   // digit histograms of every pass, and the first pass's per-tile counts
   uint32_t* tcnt0;
   const uint64_t ntiles0 = (n + PASS_T - 1) / PASS_T;
-  TRY(wk.get(&tcnt0, (size_t)ntiles0 * TC_STRIDE));
+  TRY(wk.get(&tcnt0, (size_t)ntiles0 * tc_stride(ps[0].t)));
   {
     const uint32_t blocks = (uint32_t)std::min<uint64_t>((uint64_t)num_sms() * 8, ntiles0);
     const HistGeom geo = hist_geom(L, tau);
     const int t0 = ps[0].t;
 #define WT_HT(WB, NG)                                                                       \
   k_hist_digits_tiles<WB, NG><<<blocks, 256, 0, st>>>(d_seq, n, sigma, geo, L, t0, hist, \
-                                                      h->d_err, tcnt0)
+                                                      h->d_err, tcnt0, tc_stride(t0))
 #define WT_HTW(WB)                                 \
   switch (geo.G) {                                 \
     case 1: WT_HT(WB, 1); break;                   \

@@ -285,15 +285,16 @@ __global__ void __launch_bounds__(NT + 32, WT_PASS_MIN_CTAS) k_pass(const __grid
       uint64_t* const exd = ex_cnt + cls_idx(t, 0);  // exclusive digit counts
       {
         const uint32_t ch = ti / TCHUNK;
-        const uint64_t* ca = P0.tchunk + (uint64_t)ch * TC_STRIDE;
-        const uint64_t* cb = P0.tchunk + (uint64_t)(seg0 / TCHUNK) * TC_STRIDE;
-        const uint32_t* ta = P0.tcnt + (uint64_t)ti * TC_STRIDE;
-        const uint32_t* tb = P0.tcnt + (uint64_t)seg0 * TC_STRIDE;
+        const uint32_t S = P0.tcs;
+        const uint64_t* ca = P0.tchunk + (uint64_t)ch * S;
+        const uint64_t* cb = P0.tchunk + (uint64_t)(seg0 / TCHUNK) * S;
+        const uint32_t* ta = P0.tcnt + (uint64_t)ti * S;
+        const uint32_t* tb = P0.tcnt + (uint64_t)seg0 * S;
         const bool last = (ti + 1) % TCHUNK == 0 || ti + 1 >= ntiles;
         uint32_t sum = 0;
         for (int r = lane; r < nd; r += 32) {
           const uint32_t a = ta[r];
-          const uint32_t c = last ? (uint32_t)(ca[TC_STRIDE + r] - ca[r]) - a : ta[TC_STRIDE + r] - a;
+          const uint32_t c = last ? (uint32_t)(ca[S + r] - ca[r]) - a : ta[S + r] - a;
           exd[r] = (ca[r] + a) - (cb[r] + tb[r]);
           ccnt[cls_idx(t, r)] = c;
           sum += c;

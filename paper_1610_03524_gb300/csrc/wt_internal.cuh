@@ -28,10 +28,12 @@ struct TileDesc {
 
 // Per-tile digit counts of a pass (the K sub-problems' per-node counts of
 // Section 4.2) and their prefix sums across tiles: tile ti's counts sit at
-// tcnt[ti * TC_STRIDE + r] (u32, exclusive within its chunk of TCHUNK tiles
-// after the scan) and the chunk's exclusive counts at tchunk[c * TC_STRIDE + r]
+// tcnt[ti * tcs + r] (u32, exclusive within its chunk of TCHUNK tiles
+// after the scan) and the chunk's exclusive counts at tchunk[c * tcs + r]
 // (u64).
-constexpr int TC_STRIDE = 256;
+constexpr int TC_STRIDE = 256;  // the largest stride (t = 8)
+// the stride of a pass's tables: its digit values, at least one warp's worth
+__host__ __device__ inline uint32_t tc_stride(int t) { return t >= 5 ? (1u << t) : 32u; }
 constexpr uint32_t TCHUNK = 256;
 
 // Symbols per tile of the partition pass.
@@ -112,6 +114,7 @@ struct PassParams {
   // prefix sums of the tiles' digit counts (see TileDesc)
   const uint32_t* tcnt;
   const uint64_t* tchunk;
+  uint32_t tcs;          // their stride (tc_stride of the largest digit width)
   uint32_t* ticket;      // tiles are taken in order from this counter
   uint32_t* err;
   uint32_t* abort_flag;
