@@ -1111,68 +1111,64 @@ wt_status build_huff(const void* d_seq, uint64_t n, uint32_t sigma, int w, const
   }
   // level sizes, internal nodes of every level and their start positions,
   // and zero counts.  `order` is sorted by length, so the elements still on
-  // level l (length > l) are a suffix of it; their l-bit prefixes (top bits
-  // of the left-aligned codewords) never decrease along it.
+  // level l (length > l) are a suffix of it, starting at first_gt[l]; their
+  // l-bit prefixes (top bits of the left-aligned codewords) never decrease
+  // along it and, the codes being canonical, grow by at most one from one
+  // symbol to the next (the next codeword adds 2^(Lm - len) to the left-
+  // aligned value, len > l).  So symbol i opens a node on level l exactly
+  // when l < len(i) and l exceeds the common prefix of codewords i-1 and i
+  // (every level below len(0) for i = 0), and the node starts at the
+  // elements before i on that level: S[i] - S[first_gt[l]], S = prefix sums
+  // of the symbol counts along `order`.  One sweep over the symbols.
   const size_t np = order.size();
-  std::vector<uint64_t> lc(np), cnt(np);
+  const int Lw = std::max(Lm, 1);
+  std::vector<uint64_t> S(np + 1, 0), lc(np);
+  std::vector<uint8_t> ln(np), lo(np);
   for (size_t i = 0; i < np; i++) {
     const uint32_t sy = order[i];
-    lc[i] = (uint64_t)h->code[sy] << (Lm - h->code_len[sy]);
-    cnt[i] = hh[sy];
+    ln[i] = h->code_len[sy];
+    lc[i] = (uint64_t)h->code[sy] << (Lm - ln[i]);
+    S[i + 1] = S[i] + hh[sy];
+    // first level on which symbol i opens a node
+    lo[i] = i == 0 ? 0 : (uint8_t)(__builtin_clzll((lc[i - 1] ^ lc[i]) << (64 - Lm)) + 1);
+  }
+  std::vector<uint64_t> first_gt(Lw + 1, np);
+  {
+    uint64_t acc = 0;
+    for (int l = 0; l <= Lw; l++) {
+      first_gt[l] = acc;  // symbols with length <= l come first
+      if (l + 1 <= 33) acc += lcount[std::min(l + 1, 33)];
+    }
+    for (int l = 0; l <= Lw; l++) first_gt[l] = std::min<uint64_t>(first_gt[l], np);
   }
   h->level_len.assign(Lm, 0);
-  std::vector<uint64_t> node_lvl(3 * (size_t)std::max(Lm, 1), 0);
-  std::vector<uint64_t> zc(std::max(Lm, 1), 0);
-  // levels are independent: each host thread takes every nth level
-  std::vector<std::vector<uint64_t>> lnode(std::max(Lm, 1));
-  std::vector<uint64_t> firstq_l(std::max(Lm, 1), 0), nnode_l(std::max(Lm, 1), 0);
-  auto level_nodes = [&](int l) {
-    // first index of `order` with length > l
-    uint64_t first_gt = 0;
-    for (int ln = 1; ln <= l && ln <= 33; ln++) first_gt += lcount[ln];
-    std::vector<uint64_t>& node = lnode[l];
-    uint64_t pos = 0, z = 0, firstq = 0, lastq = 0;
-    const int sh = Lm - l, bsh = Lm - 1 - l;
-    if (first_gt < np) {
-      firstq = lastq = l == 0 ? 0 : lc[first_gt] >> sh;
-      node.push_back(0);
-    }
-    for (size_t i = first_gt; i < np; i++) {
-      const uint64_t q = l == 0 ? 0 : lc[i] >> sh;
-      while (lastq < q) {  // consecutive prefixes (empty ones for incomplete codes)
-        lastq++;
-        node.push_back(pos);
-      }
-      pos += cnt[i];
-      z += ((lc[i] >> bsh) & 1u) ? 0 : cnt[i];
-    }
-    node.push_back(pos);  // sentinel = level length
-    h->level_len[l] = pos;
-    zc[l] = z;
-    firstq_l[l] = firstq;
-    nnode_l[l] = first_gt < np ? lastq - firstq + 1 : 0;
-  };
-  {
-    const int nth = std::max(1, std::min<int>(Lm, (int)std::thread::hardware_concurrency()));
-    std::vector<std::thread> th;
-    for (int k = 1; k < nth; k++)
-      th.emplace_back([&, k] {
-        for (int l = k; l < Lm; l += nth) level_nodes(l);
-      });
-    for (int l = 0; l < Lm; l += nth) level_nodes(l);
-    for (auto& x : th) x.join();
-  }
+  std::vector<uint64_t> node_lvl(3 * (size_t)Lw, 0);
+  std::vector<uint64_t> zc(Lw, 0), nn(Lw, 0);
+  for (size_t i = 0; i < np; i++)
+    for (int l = lo[i]; l < ln[i]; l++) nn[l]++;
   std::vector<uint64_t> node;
   {
-    size_t tot = 0;
-    for (int l = 0; l < Lm; l++) tot += lnode[l].size();
-    node.reserve(tot);
+    uint64_t tot = 0;
     for (int l = 0; l < Lm; l++) {
-      node_lvl[3 * l] = node.size();
-      node_lvl[3 * l + 1] = firstq_l[l];
-      node_lvl[3 * l + 2] = nnode_l[l];
-      node.insert(node.end(), lnode[l].begin(), lnode[l].end());
+      node_lvl[3 * l] = tot;
+      node_lvl[3 * l + 1] = first_gt[l] < np ? lc[first_gt[l]] >> (Lm - l) : 0;
+      node_lvl[3 * l + 2] = nn[l];
+      tot += nn[l] + 1;  // with the sentinel
+      h->level_len[l] = S[np] - S[first_gt[l]];
     }
+    node.resize(tot);
+  }
+  std::vector<uint64_t> fill(Lw, 0);
+  for (size_t i = 0; i < np; i++) {
+    const uint64_t c = S[i + 1] - S[i];
+    for (int l = 0; l < ln[i]; l++) {
+      if (l >= lo[i]) node[node_lvl[3 * l] + fill[l]++] = S[i] - S[first_gt[l]];
+      zc[l] += ((lc[i] >> (Lm - 1 - l)) & 1u) ? 0 : c;
+    }
+  }
+  for (int l = 0; l < Lm; l++) {
+    node[node_lvl[3 * l] + nn[l]] = h->level_len[l];  // sentinel = level length
+    if (fill[l] != nn[l]) return WT_ERR_INVALID_ARG;   // not a prefix code
   }
   h->level_off.assign(Lm + 1, 0);
   for (int l = 0; l < Lm; l++) h->level_off[l + 1] = h->level_off[l] + level_words(h->level_len[l]);

@@ -73,68 +73,78 @@ uint32_t huffman_lengths(const uint64_t* hist, uint32_t sigma, uint32_t cap, uin
   // (weight, symbol) in one queue, internal nodes in creation order in a
   // second one (their weights never decrease, and every internal id exceeds
   // every leaf id, so both queues stay sorted by (weight, id) and the smaller
-  // head is exactly the heap's minimum).
+  // head is exactly the heap's minimum).  Nodes are numbered by queue
+  // position (sorted leaf rank, creation order), which keeps every array
+  // below sequential in memory.
   const size_t m = present.size();
-  std::vector<uint32_t> leaf(m);
+  std::vector<uint32_t> leaf(m);   // symbols by (weight, symbol)
+  std::vector<uint64_t> lw(m);     // their weights
   {
-    // leaves sorted by (weight, symbol): LSD radix sort of the packed keys
-    // weight * 2^24 + symbol (11-bit digits), or a comparison sort when the
-    // weights do not fit 40 bits
+    // `present` is in symbol order, so a stable sort on the weight alone
+    // gives (weight, symbol): LSD radix sort, 13-bit digits, on packed
+    // (weight << 24 | symbol) keys; a comparison sort when weights pass 40 bits
     uint64_t wmax = 0;
     for (uint32_t x : present) wmax = std::max(wmax, hist[x]);
     if (wmax < (1ull << 40)) {
       std::vector<uint64_t> key(m), tmp(m);
       for (size_t i = 0; i < m; i++) key[i] = (hist[present[i]] << 24) | present[i];
-      int bits = 24;
-      while (bits < 64 && (wmax >> (bits - 24))) bits++;
-      for (int sh = 0; sh < bits; sh += 11) {
-        std::vector<size_t> cnt(2049, 0);
-        for (uint64_t k : key) cnt[((k >> sh) & 2047) + 1]++;
-        for (int b = 0; b < 2048; b++) cnt[b + 1] += cnt[b];
-        for (uint64_t k : key) tmp[cnt[(k >> sh) & 2047]++] = k;
+      int wbits = 1;
+      while (wbits < 40 && (wmax >> wbits)) wbits++;
+      constexpr int D = 13;
+      std::vector<size_t> cnt((1u << D) + 1);
+      for (int sh = 24; sh < 24 + wbits; sh += D) {
+        std::fill(cnt.begin(), cnt.end(), 0);
+        for (uint64_t k : key) cnt[((k >> sh) & ((1u << D) - 1)) + 1]++;
+        for (uint32_t b = 0; b < (1u << D); b++) cnt[b + 1] += cnt[b];
+        for (uint64_t k : key) tmp[cnt[(k >> sh) & ((1u << D) - 1)]++] = k;
         key.swap(tmp);
       }
-      for (size_t i = 0; i < m; i++) leaf[i] = (uint32_t)(key[i] & 0xffffffu);
+      for (size_t i = 0; i < m; i++) {
+        leaf[i] = (uint32_t)(key[i] & 0xffffffu);
+        lw[i] = key[i] >> 24;
+      }
     } else {
       leaf = present;
-      std::sort(leaf.begin(), leaf.end(), [&](uint32_t a, uint32_t b) {
-        return hist[a] != hist[b] ? hist[a] < hist[b] : a < b;
-      });
+      std::stable_sort(leaf.begin(), leaf.end(),
+                       [&](uint32_t a, uint32_t b) { return hist[a] < hist[b]; });
+      for (size_t i = 0; i < m; i++) lw[i] = hist[leaf[i]];
     }
   }
-  std::vector<uint64_t> parent((size_t)sigma + m, 0);
-  std::vector<uint64_t> iw(m);  // weights of internal node sigma + k
+  // parents: of sorted leaf i at pl[i], of internal node k at pi[k]; an
+  // internal parent k is stored as k (leaves and internal nodes apart)
+  std::vector<uint32_t> pl(m), pi(m - 1);
+  std::vector<uint64_t> iw(m - 1);  // weight of internal node k
   size_t li = 0, qi = 0, nint = 0;
-  auto take = [&](uint64_t& w, uint64_t& id) {
-    const bool use_leaf =
-        li < m && (qi >= nint || hist[leaf[li]] <= iw[qi]);  // equal weight: leaf id is smaller
-    if (use_leaf) {
-      w = hist[leaf[li]];
-      id = leaf[li++];
+  // take the lighter head; equal weight: the leaf (its id is smaller)
+  auto take = [&](uint64_t& w, bool& is_leaf, size_t& idx) {
+    is_leaf = li < m && (qi >= nint || lw[li] <= iw[qi]);
+    if (is_leaf) {
+      w = lw[li];
+      idx = li++;
     } else {
       w = iw[qi];
-      id = sigma + qi++;
+      idx = qi++;
     }
   };
-  uint64_t next = sigma;
   for (size_t k = 0; k + 1 < m; k++) {
-    uint64_t wa, ida, wb, idb;
-    take(wa, ida);
-    take(wb, idb);
-    parent[ida] = next;
-    parent[idb] = next;
+    uint64_t wa, wb;
+    bool la, lb;
+    size_t ia, ib;
+    take(wa, la, ia);
+    take(wb, lb, ib);
+    (la ? pl[ia] : pi[ia]) = (uint32_t)k;
+    (lb ? pl[ib] : pi[ib]) = (uint32_t)k;
     iw[nint++] = wa + wb;
-    next++;
   }
-  // depths: internal nodes are created after their children, so walking ids
-  // downwards from the root gives every parent's depth before its children
-  const uint64_t root = next - 1;
-  std::vector<uint32_t> depth((size_t)sigma + present.size(), 0);
-  for (uint64_t v = root; v-- > sigma;) depth[v] = depth[parent[v]] + 1;
+  // depths: an internal node is created after its children, so walking the
+  // creation order downwards from the root gives every parent's depth first
+  std::vector<uint32_t> depth(m - 1, 0);
+  for (size_t v = m - 1; v-- > 0;)
+    if (v + 2 < m) depth[v] = depth[pi[v]] + 1;  // the root (m - 2) has depth 0
   uint32_t maxlen = 0;
-  for (uint32_t s : present) {
-    const uint32_t d = depth[parent[s]] + 1;
-    len[s] = (uint8_t)std::min<uint32_t>(d, 255);
+  for (size_t i = 0; i < m; i++) {
+    const uint32_t d = depth[pl[i]] + 1;
+    len[leaf[i]] = (uint8_t)std::min<uint32_t>(d, 255);
     maxlen = std::max(maxlen, d);
   }
   if (maxlen <= cap) return maxlen;

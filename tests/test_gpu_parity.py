@@ -125,6 +125,38 @@ def test_huffman_parity(wt, case):
     h.free()
 
 
+@pytest.mark.parametrize("kind", ["flat", "mixed", "deep"])
+def test_huffman_caller_lengths(wt, kind):
+    """Caller-given code lengths, incomplete codes included (Kraft sum < 1):
+    the tree follows the canonical codes of those lengths (Section 4.3 takes
+    the shape as codewords)."""
+    rng = np.random.default_rng({"flat": 1, "mixed": 2, "deep": 3}[kind])
+    sigma = 700
+    S = synth.zipf(50 + len(kind), 90001, sigma, 1.1, 2)
+    present = np.bincount(S.astype(np.int64), minlength=sigma) > 0
+    if kind == "flat":
+        ln = np.full(sigma, 11, np.uint8)            # Kraft 700/2048
+    elif kind == "mixed":
+        ln = rng.integers(10, 15, sigma).astype(np.uint8)
+    else:
+        ln = np.full(sigma, 14, np.uint8)            # 31/32 + 400/2^14 + 295/2^30 < 1
+        ln[:5] = [1, 2, 3, 4, 5]
+        ln[5:300] = 30                               # long codes: 30 levels
+    ln[~present & (rng.random(sigma) < 0.5)] = 0     # some absent symbols get no code
+    assert float(np.sum(np.ldexp(1.0, -ln[ln > 0].astype(int)))) <= 1.0
+    h = wt.huff_wt_build(to_dev(S), sigma, code_len=ln)
+    ex = h.export()
+    code = oracle.canonical_codes(ln)
+    assert np.array_equal(ex.code_len, ln) and np.array_equal(ex.code, code)
+    bits, woff, nl = oracle.huff_wt_build(S, ln, code)
+    assert ex.levels == int(ln.max()) and np.array_equal(ex.level_len, nl)
+    assert np.array_equal(ex.level_off, woff)
+    assert np.array_equal(ex.bits, bits)
+    levels = [bits[int(woff[l]):int(woff[l + 1])] for l in range(int(ln.max()))]
+    check_binary_dirs(ex, levels, [int(x) for x in nl])
+    h.free()
+
+
 @pytest.mark.parametrize("tau", [1, 2, 3, 4, 5, 6, 7, 8])
 def test_tau_invariance(wt, tau):
     S = synth.zipf(21, 30011, 3000, 1.1, 2)
