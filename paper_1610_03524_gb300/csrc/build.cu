@@ -272,9 +272,13 @@ static void launch_hist_digits_w(const void* seq, uint64_t n, uint32_t sigma, co
 }
 
 // Full symbol histogram (balanced / Huffman / 4-ary trees).
+// (large alphabets: block b adds into copy b % ncopy of the histogram, at
+// hist + (b % ncopy) * sigma, so that the frequent symbols of a skewed
+// alphabet spread their atomics over several addresses; the copies are
+// summed afterwards)
 template <int WB>
 __global__ void k_hist_full(const void* seq, uint64_t n, uint32_t sigma, uint64_t* hist,
-                            uint32_t* err, int use_smem) {
+                            uint32_t* err, int use_smem, uint32_t ncopy = 1) {
   extern __shared__ uint32_t shh[];
   if (use_smem) {
     for (uint32_t i = threadIdx.x; i < sigma; i += blockDim.x) shh[i] = 0;
@@ -312,7 +316,8 @@ __global__ void k_hist_full(const void* seq, uint64_t n, uint32_t sigma, uint64_
                           const uint32_t act = __activemask();
                           const uint32_t peers = __match_any_sync(act, x);
                           if (ok && lane == __ffs(peers) - 1)
-                            atomicAdd((unsigned long long*)&hist[x], (unsigned long long)__popc(peers));
+                            atomicAdd((unsigned long long*)&hist[(uint64_t)(blockIdx.x % ncopy) * sigma + x],
+                                      (unsigned long long)__popc(peers));
                         }
                       });
   if (bad) atomicOr(err, ERR_SYMBOL);
@@ -323,17 +328,44 @@ __global__ void k_hist_full(const void* seq, uint64_t n, uint32_t sigma, uint64_
   }
 }
 
+__global__ void k_hist_sum_copies(const uint64_t* copies, uint32_t sigma, uint32_t ncopy,
+                                  uint64_t* hist) {
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < sigma;
+       i += (uint64_t)gridDim.x * blockDim.x) {
+    uint64_t a = 0;
+    for (uint32_t c = 0; c < ncopy; c++) a += copies[(uint64_t)c * sigma + i];
+    hist[i] += a;
+  }
+}
+
 static wt_status launch_hist_full(const void* seq, int w, uint64_t n, uint32_t sigma,
                                   uint64_t* hist, uint32_t* err, cudaStream_t st) {
   if (n == 0) return WT_OK;
   const int use_smem = sigma <= 12288;
   const size_t shb = use_smem ? sigma * 4 : 0;
   const uint32_t blocks = std::min<uint64_t>(num_sms() * 4, (n + 4095) / 4096 + 1);
-  if (w == 1) k_hist_full<1><<<blocks, 512, shb, st>>>(seq, n, sigma, hist, err, use_smem);
-  else if (w == 2) k_hist_full<2><<<blocks, 512, shb, st>>>(seq, n, sigma, hist, err, use_smem);
-  else k_hist_full<4><<<blocks, 512, shb, st>>>(seq, n, sigma, hist, err, use_smem);
+  // global counters: 16 copies while they take at most 256 MB
+  uint32_t ncopy = 1;
+  uint64_t* dst = hist;
+  if (!use_smem && sigma > 8) {
+    ncopy = (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>(16, (256ull << 20) / (8ull * sigma)));
+    if (ncopy > 1) {
+      CK(dmalloc((void**)&dst, (size_t)ncopy * sigma * 8, st));
+      CK(cudaMemsetAsync(dst, 0, (size_t)ncopy * sigma * 8, st));
+    }
+  }
+  if (w == 1) k_hist_full<1><<<blocks, 512, shb, st>>>(seq, n, sigma, dst, err, use_smem, ncopy);
+  else if (w == 2) k_hist_full<2><<<blocks, 512, shb, st>>>(seq, n, sigma, dst, err, use_smem, ncopy);
+  else k_hist_full<4><<<blocks, 512, shb, st>>>(seq, n, sigma, dst, err, use_smem, ncopy);
   count_launch();
   CK(cudaGetLastError());
+  if (ncopy > 1) {
+    k_hist_sum_copies<<<(unsigned)std::min<uint64_t>((sigma + 255) / 256, (uint64_t)num_sms() * 8), 256, 0,
+                        st>>>(dst, sigma, ncopy, hist);
+    count_launch();
+    CK(cudaGetLastError());
+    dfree(dst, st);
+  }
   return WT_OK;
 }
 
@@ -1093,7 +1125,6 @@ wt_status build_huff(const void* d_seq, uint64_t n, uint32_t sigma, int w, const
   } else {
     maxlen = huffman_lengths(hh.data(), sigma, 32, h->code_len.data());
   }
-  canonical_codes(h->code_len.data(), sigma, h->code.data());
   h->max_code_len = maxlen;
   const int Lm = (int)maxlen;
   h->L = h->levels = (uint32_t)Lm;
@@ -1124,13 +1155,22 @@ wt_status build_huff(const void* d_seq, uint64_t n, uint32_t sigma, int w, const
   const int Lw = std::max(Lm, 1);
   std::vector<uint64_t> S(np + 1, 0), lc(np);
   std::vector<uint8_t> ln(np), lo(np);
-  for (size_t i = 0; i < np; i++) {
-    const uint32_t sy = order[i];
-    ln[i] = h->code_len[sy];
-    lc[i] = (uint64_t)h->code[sy] << (Lm - ln[i]);
-    S[i + 1] = S[i] + hh[sy];
-    // first level on which symbol i opens a node
-    lo[i] = i == 0 ? 0 : (uint8_t)(__builtin_clzll((lc[i - 1] ^ lc[i]) << (64 - Lm)) + 1);
+  std::vector<uint64_t> nn(Lw, 0);
+  {
+    // canonical codes along the order (consecutive values, shifted left
+    // when the length grows), with the per-symbol arrays above
+    uint64_t c = 0;
+    for (size_t i = 0; i < np; i++) {
+      const uint32_t sy = order[i];
+      ln[i] = h->code_len[sy];
+      if (i) c = (c + 1) << (ln[i] - ln[i - 1]);
+      h->code[sy] = (uint32_t)c;
+      lc[i] = c << (Lm - ln[i]);
+      S[i + 1] = S[i] + hh[sy];
+      // first level on which symbol i opens a node
+      lo[i] = i == 0 ? 0 : (uint8_t)(__builtin_clzll((lc[i - 1] ^ lc[i]) << (64 - Lm)) + 1);
+      for (int l = lo[i]; l < ln[i]; l++) nn[l]++;
+    }
   }
   std::vector<uint64_t> first_gt(Lw + 1, np);
   {
@@ -1143,9 +1183,7 @@ wt_status build_huff(const void* d_seq, uint64_t n, uint32_t sigma, int w, const
   }
   h->level_len.assign(Lm, 0);
   std::vector<uint64_t> node_lvl(3 * (size_t)Lw, 0);
-  std::vector<uint64_t> zc(Lw, 0), nn(Lw, 0);
-  for (size_t i = 0; i < np; i++)
-    for (int l = lo[i]; l < ln[i]; l++) nn[l]++;
+  std::vector<uint64_t> zc(Lw, 0);
   std::vector<uint64_t> node;
   {
     uint64_t tot = 0;
@@ -1158,15 +1196,29 @@ wt_status build_huff(const void* d_seq, uint64_t n, uint32_t sigma, int w, const
     }
     node.resize(tot);
   }
-  std::vector<uint64_t> fill(Lw, 0);
+  // node starts, and the ones of every level as runs: bit l of symbol i
+  // (the last bit of its (l+1)-bit prefix) can differ from symbol i-1's
+  // only where that prefix changes, i.e. from level lo[i] - 1 up
+  std::vector<uint64_t> fill(Lw, 0), ones(Lw, 0), run0(Lw, 0);
+  std::vector<uint8_t> cur(Lw, 0);
   for (size_t i = 0; i < np; i++) {
-    const uint64_t c = S[i + 1] - S[i];
-    for (int l = 0; l < ln[i]; l++) {
+    const int l0 = lo[i] > 0 ? lo[i] - 1 : 0;
+    for (int l = l0; l < ln[i]; l++) {
       if (l >= lo[i]) node[node_lvl[3 * l] + fill[l]++] = S[i] - S[first_gt[l]];
-      zc[l] += ((lc[i] >> (Lm - 1 - l)) & 1u) ? 0 : c;
+      const uint8_t b = (uint8_t)((lc[i] >> (Lm - 1 - l)) & 1u);
+      if (i == first_gt[l]) {
+        cur[l] = b;
+        run0[l] = S[i];
+      } else if (b != cur[l]) {
+        if (cur[l]) ones[l] += S[i] - run0[l];
+        cur[l] = b;
+        run0[l] = S[i];
+      }
     }
   }
   for (int l = 0; l < Lm; l++) {
+    if (cur[l]) ones[l] += S[np] - run0[l];
+    zc[l] = h->level_len[l] - ones[l];
     node[node_lvl[3 * l] + nn[l]] = h->level_len[l];  // sentinel = level length
     if (fill[l] != nn[l]) return WT_ERR_INVALID_ARG;   // not a prefix code
   }

@@ -81,11 +81,41 @@ uint32_t huffman_lengths(const uint64_t* hist, uint32_t sigma, uint32_t cap, uin
   std::vector<uint64_t> lw(m);     // their weights
   {
     // `present` is in symbol order, so a stable sort on the weight alone
-    // gives (weight, symbol): LSD radix sort, 13-bit digits, on packed
-    // (weight << 24 | symbol) keys; a comparison sort when weights pass 40 bits
+    // gives (weight, symbol): a counting sort when most weights are below
+    // 2^16, else an LSD radix sort (13-bit digits) on packed
+    // (weight << 24 | symbol) keys, or a comparison sort past 40-bit weights
     uint64_t wmax = 0;
-    for (uint32_t x : present) wmax = std::max(wmax, hist[x]);
-    if (wmax < (1ull << 40)) {
+    size_t nbig = 0;
+    constexpr uint64_t K = 1u << 16;
+    for (uint32_t x : present) {
+      wmax = std::max(wmax, hist[x]);
+      nbig += hist[x] >= K;
+    }
+    if (nbig <= m / 8) {
+      // mostly small weights: one counting pass below K, the few heavier
+      // leaves sorted apart and placed after them
+      std::vector<uint32_t> cnt(K + 1, 0);
+      std::vector<uint32_t> big;
+      big.reserve(nbig);
+      for (uint32_t x : present) {
+        if (hist[x] < K) cnt[hist[x] + 1]++;
+        else big.push_back(x);
+      }
+      for (uint64_t b = 0; b < K; b++) cnt[b + 1] += cnt[b];
+      for (uint32_t x : present)
+        if (hist[x] < K) {
+          const uint32_t at = cnt[hist[x]]++;
+          leaf[at] = x;
+          lw[at] = hist[x];
+        }
+      std::stable_sort(big.begin(), big.end(),
+                       [&](uint32_t a, uint32_t b) { return hist[a] < hist[b]; });
+      const size_t s0 = m - big.size();
+      for (size_t i = 0; i < big.size(); i++) {
+        leaf[s0 + i] = big[i];
+        lw[s0 + i] = hist[big[i]];
+      }
+    } else if (wmax < (1ull << 40)) {
       std::vector<uint64_t> key(m), tmp(m);
       for (size_t i = 0; i < m; i++) key[i] = (hist[present[i]] << 24) | present[i];
       int wbits = 1;

@@ -58,6 +58,8 @@ def check_binary_dirs(ex, bits_by_level, nbits_by_level):
         rec = oracle.rank_dir(bl, nb)
         got = ex.level_dir(l)
         assert np.array_equal(got, rec), f"rank directory of level {l}"
+        # the level's zero count: the oracle directory's total
+        assert int(ex.zeros[l]) == int(rec[-1, 0]), f"zeros of level {l}"
         for b in (0, 1):
             s = oracle.select_samples(bl, nb, b)
             assert np.array_equal(ex.samples(l, b), s), f"select samples level {l} bit {b}"
