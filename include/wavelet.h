@@ -13,8 +13,9 @@
  *  * `stream` is a cudaStream_t passed as void* (NULL = legacy default
  *    stream).  Every call only enqueues work on it and returns; results are
  *    final once the stream is synchronised.  Device-side errors found during
- *    a build (a symbol >= sigma, a bounded wait that ran out) are reported by
- *    wt_sync() or by the next call on the handle.
+ *    a build (a symbol >= sigma: WT_ERR_SYMBOL_GE_SIGMA; an internal table
+ *    that disagrees with the data, which leaves the affected bits unwritten:
+ *    WT_ERR_CUDA) are reported by wt_sync() or by the next call on the handle.
  *  * Symbol sequences are contiguous arrays of width_bytes = 1, 2 or 4
  *    (little-endian unsigned), read-only, borrowed for the duration of the
  *    call and never retained.
@@ -48,7 +49,7 @@ typedef enum {
   WT_ERR_SYMBOL_GE_SIGMA = 2,  /* the sequence holds a symbol >= sigma */
   WT_ERR_NO_MEMORY = 3,        /* device allocation failed */
   WT_ERR_CUDA = 4,             /* a CUDA runtime call failed */
-  WT_ERR_TIMEOUT = 5,          /* a bounded device-side wait ran out */
+  WT_ERR_TIMEOUT = 5,          /* a serving-loop request has not finished yet */
   WT_ERR_UNSUPPORTED = 6       /* valid but not supported (e.g. sigma too large) */
 } wt_status;
 

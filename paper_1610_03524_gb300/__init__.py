@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(_HERE, "libwavelet.so")
 
 WT_OK = 0
 STATUS = {0: "ok", 1: "invalid argument", 2: "symbol >= sigma", 3: "out of device memory",
-          4: "CUDA error", 5: "bounded device wait ran out", 6: "unsupported"}
+          4: "CUDA error", 5: "not finished yet", 6: "unsupported"}
 KIND_WT, KIND_WM, KIND_HUFF, KIND_MULTI, KIND_RS = range(5)
 FLAG_NO_DIRECTORY = 1
 FLAG_SELECT_O1 = 2

@@ -42,7 +42,6 @@ void free_arrays(wt_struct* h) {
   dfree(h->d_samp, st);
   dfree(h->d_zeros, st);
   dfree(h->d_err, st);
-  dfree(h->d_abort, st);
   dfree(h->d_meta, st);
   dfree(h->d_code, st);
   dfree(h->d_len, st);
@@ -62,14 +61,12 @@ wt_status new_handle(wt_stream stream, uint64_t n, uint32_t sigma, wt_struct** o
   h->n = n;
   h->sigma = sigma;
   cudaGetDevice(&h->device);
-  if (dmalloc((void**)&h->d_err, 8, h->stream) != cudaSuccess ||
-      dmalloc((void**)&h->d_abort, 8, h->stream) != cudaSuccess) {
+  if (dmalloc((void**)&h->d_err, 8, h->stream) != cudaSuccess) {
     free_arrays(h);
     delete h;
     return WT_ERR_NO_MEMORY;
   }
   cudaMemsetAsync(h->d_err, 0, 8, h->stream);
-  cudaMemsetAsync(h->d_abort, 0, 8, h->stream);
   *out = h;
   return WT_OK;
 }
@@ -99,15 +96,7 @@ wt_status sync_handle(wt_struct* h) {
   e = cudaMemcpy(&err, h->d_err, 4, cudaMemcpyDeviceToHost);
   if (e != cudaSuccess) return h->deferred = WT_ERR_CUDA;
   if (err & ERR_SYMBOL) return h->deferred = WT_ERR_SYMBOL_GE_SIGMA;
-  if (err & ERR_TIMEOUT) return h->deferred = WT_ERR_TIMEOUT;
-  if (err) return h->deferred = WT_ERR_CUDA;
-  if (h->arena) {
-    // a wait that ran out anywhere in the batch stopped every sequence
-    uint32_t ab = 0;
-    e = cudaMemcpy(&ab, h->d_abort, 4, cudaMemcpyDeviceToHost);
-    if (e != cudaSuccess) return h->deferred = WT_ERR_CUDA;
-    if (ab) return h->deferred = WT_ERR_TIMEOUT;
-  }
+  if (err) return h->deferred = WT_ERR_CUDA;  // ERR_INTERNAL: a table disagreed with a tile
   if (!h->zeros_valid) {
     h->zeros.assign(h->levels, 0);
     if (h->levels && h->bpe == 1) {
@@ -131,7 +120,8 @@ wt_status seq_build(int kind, const void* d_seq, uint64_t n, uint32_t sigma, uin
   wt_status s = check_opts(opts);
   if (s != WT_OK) return s;
   if (kind == WT_KIND_MULTI && degree != 4) return WT_ERR_UNSUPPORTED;
-  if (n >= ((uint64_t)1 << 40)) return WT_ERR_UNSUPPORTED;  // look-back counts are 40 bits
+  // the constant-time select directory packs 40-bit offsets; tile indices are 32-bit
+  if (n >= ((uint64_t)1 << 40)) return WT_ERR_UNSUPPORTED;
   if ((kind == WT_KIND_WT || kind == WT_KIND_MULTI || kind == WT_KIND_HUFF) && sigma > (1u << 24))
     return WT_ERR_UNSUPPORTED;
   wt_struct* h = nullptr;
@@ -293,7 +283,7 @@ const char* wt_status_str(wt_status s) {
     case WT_ERR_SYMBOL_GE_SIGMA: return "symbol >= sigma";
     case WT_ERR_NO_MEMORY: return "out of device memory";
     case WT_ERR_CUDA: return "CUDA error";
-    case WT_ERR_TIMEOUT: return "bounded device wait ran out";
+    case WT_ERR_TIMEOUT: return "not finished yet";
     case WT_ERR_UNSUPPORTED: return "unsupported";
   }
   return "unknown status";

@@ -187,13 +187,13 @@ wt_status batch_build_wm(const wt_batch_item* items, uint32_t m, const wt_build_
     nlev_tot += p.L;
     Gmax = std::max(Gmax, p.n ? p.G : 0);
   }
-  // ---- arena: bits | dir | samp | zeros | meta | err[m] + abort ----------
+  // ---- arena: bits | dir | samp | zeros | meta | err[m] -----------------
   const uint64_t off_dir = 8 * nbits;
   const uint64_t off_samp = off_dir + 8 * ndir;
   const uint64_t off_zeros = off_samp + 8 * nsamp;
   const uint64_t off_meta = up(off_zeros + 8 * nzeros, 256);
   const uint64_t off_err = up(off_meta + sizeof(LevelMeta) * nmeta, 256);
-  const uint64_t arena_bytes = off_err + up(4 * ((uint64_t)m + 1), 256);
+  const uint64_t arena_bytes = off_err + up(4 * (uint64_t)m, 256);
   Arena* ar = new Arena();
   ar->bytes = arena_bytes;
   {
@@ -210,7 +210,6 @@ wt_status batch_build_wm(const wt_batch_item* items, uint32_t m, const wt_build_
   uint64_t* a_zeros = (uint64_t*)(A + off_zeros);
   LevelMeta* a_meta = (LevelMeta*)(A + off_meta);
   uint32_t* a_err = (uint32_t*)(A + off_err);
-  uint32_t* a_abort = a_err + m;
   // handles own the arena from here on (a failure below frees it through them)
   for (uint32_t i = 0; i < m; i++) {
     wt_struct* h = hs[i];
@@ -230,7 +229,6 @@ wt_status batch_build_wm(const wt_batch_item* items, uint32_t m, const wt_build_
     h->d_zeros = a_zeros + p.zeros_base;
     h->d_meta = a_meta + p.meta_base;
     h->d_err = a_err + i;
-    h->d_abort = a_abort;
     h->level_len.assign(p.L, p.n);
     h->level_off.assign(p.L + 1, 0);
     h->dir_off.assign(p.L + 1, 0);
@@ -380,7 +378,7 @@ wt_status batch_build_wm(const wt_batch_item* items, uint32_t m, const wt_build_
   }
   // ---- uploads and launches -------------------------------------------------
   if (nbits) CK(cudaMemsetAsync(a_bits, 0, 8 * nbits, st));
-  CK(cudaMemsetAsync(a_err, 0, 4 * ((uint64_t)m + 1), st));
+  CK(cudaMemsetAsync(a_err, 0, 4 * (uint64_t)m, st));
   if (nzeros) CK(cudaMemsetAsync(a_zeros, 0, 8 * nzeros, st));  // empty sequences plan nothing
   if (nhist) CK(cudaMemsetAsync(d_hist, 0, 8 * nhist, st));
   CK(cudaMemsetAsync(d_tick, 0, 4 * 64, st));
@@ -397,7 +395,6 @@ wt_status batch_build_wm(const wt_batch_item* items, uint32_t m, const wt_build_
     P.shape = SHAPE_WM;
     P.ticket = d_tick + li;
     P.err = a_err;  // replaced per tile by the sequence's own word
-    P.abort_flag = a_abort;
     P.ntiles = L0.ntiles;
     P.segs = d_sseg + L0.first;
     P.nsegs = L0.nsegs;
@@ -414,16 +411,14 @@ wt_status batch_build_wm(const wt_batch_item* items, uint32_t m, const wt_build_
 }
 
 void batch_status(wt_handle* hs, uint32_t m, wt_status* st) {
-  // the batch's error words are consecutive in its arena, followed by the
-  // shared abort word
-  std::vector<uint32_t> err((size_t)m + 1, 0);
-  const bool ok = m && cudaMemcpy(err.data(), hs[0]->d_err, 4 * ((size_t)m + 1),
+  // the batch's error words are consecutive in its arena
+  std::vector<uint32_t> err((size_t)m, 0);
+  const bool ok = m && cudaMemcpy(err.data(), hs[0]->d_err, 4 * (size_t)m,
                                   cudaMemcpyDeviceToHost) == cudaSuccess;
   for (uint32_t i = 0; i < m; i++) {
     wt_status s = WT_OK;
     if (!ok) s = WT_ERR_CUDA;
     else if (err[i] & ERR_SYMBOL) s = WT_ERR_SYMBOL_GE_SIGMA;
-    else if ((err[i] & ERR_TIMEOUT) || err[m]) s = WT_ERR_TIMEOUT;
     else if (err[i]) s = WT_ERR_CUDA;
     if (s != WT_OK) hs[i]->deferred = s;
     st[i] = s;

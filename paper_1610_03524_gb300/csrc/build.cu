@@ -7,9 +7,9 @@
 //      integer sort; for the wavelet matrix one digit histogram per pass,
 //      since a histogram does not depend on the order of the elements);
 //   2. plan: node/class start offsets of every level by prefix sums
-//      (Section 4.2), zero counts z_l (Section 4.3), zeroing of the words
-//      that straddle two nodes, look-back reset;
-//   3. one partition pass per tau levels (k_pass.cuh);
+//      (Section 4.2), zero counts z_l (Section 4.3), tile ticket reset;
+//   3. one partition pass per tau levels (k_pass.cuh), each after the
+//      per-tile digit counts and their prefix sums across the tiles;
 //   4. rank/select directories on every level (dirq.cu).
 #include <algorithm>
 #include <cmath>
@@ -536,10 +536,9 @@ __device__ void plan_wm_classes(const uint64_t* hist, int L, int tau, int G, uin
 // Wavelet-matrix plan, one block: class starts and zero counts; reset of the
 // tile tickets.
 __global__ void k_plan_wm(const uint64_t* hist, int L, int tau, int G, uint64_t* cls,
-                          uint64_t* zeros, uint32_t* tickets, uint32_t* abort_flag) {
+                          uint64_t* zeros, uint32_t* tickets) {
   plan_wm_classes(hist, L, tau, G, cls, zeros);
   for (int g = threadIdx.x; g < 32; g += blockDim.x) tickets[g] = 0;
-  if (threadIdx.x == 0) *abort_flag = 0;
 }
 
 // Balanced-tree helpers over C (C[v] = number of symbols < v, v in [0, 2^L]).
@@ -583,9 +582,8 @@ __global__ void k_zero_padding(uint64_t* bits, const uint64_t* lvl_off, const ui
   for (uint64_t w = used + threadIdx.x; w < W; w += blockDim.x) bits[lvl_off[l] + w] = 0;
 }
 
-__global__ void k_reset_tickets(uint32_t* tickets, uint32_t* abort_flag) {
+__global__ void k_reset_tickets(uint32_t* tickets) {
   for (int g = threadIdx.x; g < 32; g += blockDim.x) tickets[g] = 0;
-  if (threadIdx.x == 0) *abort_flag = 0;
 }
 
 // Node-aligned tiles over T_a: node p spans [bnd[p*stride], bnd[(p+1)*stride]).
@@ -876,7 +874,6 @@ static PassParams base_params(wt_struct* h, Work& wk, uint32_t* tickets,
   P.lvl_len = d_lvl_len;
   P.ticket = tickets;
   P.err = h->d_err;
-  P.abort_flag = h->d_abort;
   (void)wk;
   return P;
 }
@@ -942,7 +939,7 @@ wt_status build_wm(const void* d_seq, uint64_t n, uint32_t sigma, int w, const w
     count_launch();
     CK(cudaGetLastError());
   }
-  k_plan_wm<<<1, 1024, 0, st>>>(hist, L, tau, G, cls, h->d_zeros, tickets, h->d_abort);
+  k_plan_wm<<<1, 1024, 0, st>>>(hist, L, tau, G, cls, h->d_zeros, tickets);
   count_launch();
   CK(cudaGetLastError());
   // intermediate sequences
@@ -1026,7 +1023,7 @@ wt_status build_wt(const void* d_seq, uint64_t n, uint32_t sigma, int w, const w
     count_launch();
     CK(cudaGetLastError());
   }
-  k_reset_tickets<<<1, 32, 0, st>>>(tickets, h->d_abort);
+  k_reset_tickets<<<1, 32, 0, st>>>(tickets);
   count_launch();
   CK(cudaGetLastError());
   void* seqbuf[2] = {nullptr, nullptr};
@@ -1285,7 +1282,7 @@ wt_status build_huff(const void* d_seq, uint64_t n, uint32_t sigma, int w, const
   TRY(wk.get(&d_ntiles, 1));
   CK(cudaMemcpyAsync(d_off, h->level_off.data(), (Lm + 1) * 8, cudaMemcpyHostToDevice, st));
   CK(cudaMemcpyAsync(d_len, h->level_len.data(), Lm * 8, cudaMemcpyHostToDevice, st));
-  k_reset_tickets<<<1, 32, 0, st>>>(tickets, h->d_abort);
+  k_reset_tickets<<<1, 32, 0, st>>>(tickets);
   count_launch();
   CK(cudaGetLastError());
   void* seqbuf[2] = {nullptr, nullptr};

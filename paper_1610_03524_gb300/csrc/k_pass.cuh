@@ -212,7 +212,6 @@ __global__ void __launch_bounds__(NT + 32, WT_PASS_MIN_CTAS) k_pass(const __grid
   for (;;) {
     if (tid == 0) {
       uint32_t ti = atomicAdd(P0.ticket, 1u);
-      if (ld_volatile_u32(P0.abort_flag)) ti = 0xffffffffu;
       s_tile = ti;
       if (BATCH && ti < ntiles) fill_seg(s_P, P0, ti);
     }

@@ -69,7 +69,6 @@ struct wt_struct {
   uint64_t* d_samp = nullptr;
   uint64_t* d_zeros = nullptr;   // [levels]
   uint32_t* d_err = nullptr;     // device error word
-  uint32_t* d_abort = nullptr;
   wtk::LevelMeta* d_meta = nullptr;
   // Huffman tables (device)
   uint32_t* d_code = nullptr;
@@ -93,7 +92,6 @@ struct wt_struct {
   wtk::ClarkMeta* d_cmeta = nullptr;
   std::vector<wtk::ClarkMeta> cmeta;
   // batched builds: the shared allocation holding every device array above
-  // (d_abort is then shared by the whole batch)
   wtk::Arena* arena = nullptr;
 };
 

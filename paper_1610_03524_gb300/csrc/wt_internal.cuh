@@ -11,7 +11,8 @@ constexpr int NCLS = 1 << (TAU_MAX + 1);    // class-tree slots: level j class k
 constexpr uint32_t FULL = 0xffffffffu;
 
 // device error word bits
-enum : uint32_t { ERR_SYMBOL = 1u, ERR_TIMEOUT = 2u, ERR_INTERNAL = 4u };
+// (ERR_INTERNAL: a prefix table disagreed with a tile; never for correct tables)
+enum : uint32_t { ERR_SYMBOL = 1u, ERR_INTERNAL = 4u };
 
 // structure shapes handled by the partition pass
 enum Shape : int { SHAPE_WM = 0, SHAPE_WT = 1, SHAPE_HUFF = 2 };
@@ -117,15 +118,10 @@ struct PassParams {
   uint32_t tcs;          // their stride (tc_stride of the largest digit width)
   uint32_t* ticket;      // tiles are taken in order from this counter
   uint32_t* err;
-  uint32_t* abort_flag;
 };
 
 __device__ __forceinline__ uint32_t rev_bits(uint32_t k, int j) {
   return j == 0 ? 0u : (__brev(k) >> (32 - j));
-}
-
-__device__ __forceinline__ uint32_t ld_volatile_u32(const uint32_t* p) {
-  return *(const volatile uint32_t*)p;
 }
 
 __device__ __forceinline__ uint32_t lanemask_lt() {
