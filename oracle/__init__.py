@@ -61,6 +61,10 @@ def _load():
             lib.orc_clark_build.argtypes = [U64P, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint64,
                                             ctypes.c_uint64, U64P, U64P, U64P, U64P, U32P, U32P,
                                             U64P]
+            lib.orc_clark_digits.restype = ctypes.c_int
+            lib.orc_clark_digits.argtypes = lib.orc_clark_build.argtypes
+            lib.orc_digit_samples.restype = ctypes.c_uint64
+            lib.orc_digit_samples.argtypes = [U64P, ctypes.c_uint64, ctypes.c_uint32, U64P]
             lib.orc_huffman_lengths.restype = ctypes.c_uint32
             lib.orc_huffman_lengths.argtypes = [U64P, ctypes.c_uint32, ctypes.c_uint32, U8P]
             lib.orc_canonical_codes.argtypes = [U8P, ctypes.c_uint32, U32P]
@@ -136,29 +140,44 @@ CLARK_HUGE_MIN = 1 << 32
 CLARK_SPARSE_MIN = 1 << 16
 
 
-def clark(bits_level: np.ndarray, nbits: int, b: int, huge_min: int = CLARK_HUGE_MIN,
-          sparse_min: int = CLARK_SPARSE_MIN):
-    """Constant-time select directory of one bit value (desc, sub, sparse, huge)."""
-    bl = np.ascontiguousarray(bits_level, dtype=np.uint64)
-    lib = _load()
-    cnt = np.zeros(3, dtype=np.uint64)
+def _clark(fn, words, n, v, huge_min, sparse_min):
+    bl = np.ascontiguousarray(words, dtype=np.uint64)
     null64 = ctypes.cast(None, U64P)
     null32 = ctypes.cast(None, U32P)
     c = [ctypes.c_uint64() for _ in range(3)]
-    if lib.orc_clark_build(_p(bl, U64P), nbits, b, huge_min, sparse_min, ctypes.byref(c[0]),
-                           ctypes.byref(c[1]), ctypes.byref(c[2]), null64, null32, null32, null64):
+    if fn(_p(bl, U64P), n, v, huge_min, sparse_min, ctypes.byref(c[0]),
+          ctypes.byref(c[1]), ctypes.byref(c[2]), null64, null32, null32, null64):
         raise MemoryError("oracle clark")
     R, H, S = (int(x.value) for x in c)
     desc = np.zeros(max(R, 1), dtype=np.uint64)
     sub = np.zeros(max(16 * R, 1), dtype=np.uint32)
     sparse = np.zeros(max(256 * S, 1), dtype=np.uint32)
     huge = np.zeros(max(4096 * H, 1), dtype=np.uint64)
-    if lib.orc_clark_build(_p(bl, U64P), nbits, b, huge_min, sparse_min, ctypes.byref(c[0]),
-                           ctypes.byref(c[1]), ctypes.byref(c[2]), _p(desc, U64P), _p(sub, U32P),
-                           _p(sparse, U32P), _p(huge, U64P)):
+    if fn(_p(bl, U64P), n, v, huge_min, sparse_min, ctypes.byref(c[0]),
+          ctypes.byref(c[1]), ctypes.byref(c[2]), _p(desc, U64P), _p(sub, U32P),
+          _p(sparse, U32P), _p(huge, U64P)):
         raise MemoryError("oracle clark")
-    del cnt
     return desc[:R], sub[:16 * R], sparse[:256 * S], huge[:4096 * H]
+
+
+def clark(bits_level: np.ndarray, nbits: int, b: int, huge_min: int = CLARK_HUGE_MIN,
+          sparse_min: int = CLARK_SPARSE_MIN):
+    """Constant-time select directory of one bit value (desc, sub, sparse, huge)."""
+    return _clark(_load().orc_clark_build, bits_level, nbits, b, huge_min, sparse_min)
+
+
+def clark_digits(dig_level: np.ndarray, ndig: int, d: int, huge_min: int = CLARK_HUGE_MIN,
+                 sparse_min: int = CLARK_SPARSE_MIN):
+    """The same for the occurrences of digit value d in a 4-ary digit level."""
+    return _clark(_load().orc_clark_digits, dig_level, ndig, d, huge_min, sparse_min)
+
+
+def digit_samples(dig_level: np.ndarray, ndig: int, d: int) -> np.ndarray:
+    """Position of every 4096th occurrence of digit value d (from occurrence 0)."""
+    dl = np.ascontiguousarray(dig_level, dtype=np.uint64)
+    out = np.zeros(ndig // 4096 + 2, dtype=np.uint64)
+    ns = _load().orc_digit_samples(_p(dl, U64P), ndig, d, _p(out, U64P))
+    return out[:ns].copy()
 
 
 def huffman_lengths(hist, cap: int = 32):

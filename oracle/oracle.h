@@ -79,6 +79,16 @@ int orc_clark_build(const uint64_t* bits, uint64_t nbits, uint32_t b, uint64_t h
                     uint64_t sparse_min, uint64_t* nranges, uint64_t* nhuge, uint64_t* nsparse,
                     uint64_t* desc, uint32_t* sub, uint32_t* sparse, uint64_t* huge);
 
+/* Generalized select for the digit levels of the 4-ary tree (§5.2: select
+ * per character, by the same ranges and sub-ranges as the binary case):
+ * the sampled and constant-time directories above, for the occurrences of
+ * digit value d (0..3) in a digit level of ndig 2-bit digits; positions and
+ * lengths count digits. */
+uint64_t orc_digit_samples(const uint64_t* dig, uint64_t ndig, uint32_t d, uint64_t* samp);
+int orc_clark_digits(const uint64_t* dig, uint64_t ndig, uint32_t d, uint64_t huge_min,
+                     uint64_t sparse_min, uint64_t* nranges, uint64_t* nhuge, uint64_t* nsparse,
+                     uint64_t* desc, uint32_t* sub, uint32_t* sparse, uint64_t* huge);
+
 /* Huffman code lengths (§4.3 arbitrary-shaped trees; Huffman shape).
  * Heap keyed (weight, id), leaf id = symbol, internal id = sigma + creation
  * index; symbols with count 0 get length 0; a single present symbol gets

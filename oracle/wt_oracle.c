@@ -129,11 +129,18 @@ void orc_rank_dir(const uint64_t* bits, uint64_t nbits, uint64_t* rec) {
 
 /* Sampled select (§5.1 select keeps the position of every (log n loglog n)- */
 /* th 1; here every 4096th occurrence of b, counting from occurrence 0).   */
-uint64_t orc_select_samples(const uint64_t* bits, uint64_t nbits, uint32_t b,
-                            uint64_t* samp) {
+/* element p of a sequence of width-bit values packed LSB first into u64
+   words (width 1: a bitvector; width 2: a digit level of the 4-ary tree) */
+static uint32_t elem(const uint64_t* w, uint64_t p, int width) {
+  uint64_t b = p * (uint64_t)width;
+  return (uint32_t)((w[b >> 6] >> (b & 63)) & ((1u << width) - 1u));
+}
+
+static uint64_t samples_w(const uint64_t* w, uint64_t n, int width, uint32_t v,
+                          uint64_t* samp) {
   uint64_t cnt = 0, ns = 0;
-  for (uint64_t p = 0; p < nbits; p++) {
-    if ((uint32_t)getbit(bits, p) == b) {
+  for (uint64_t p = 0; p < n; p++) {
+    if (elem(w, p, width) == v) {
       if (cnt % 4096 == 0) samp[ns++] = p;
       cnt++;
     }
@@ -141,22 +148,32 @@ uint64_t orc_select_samples(const uint64_t* bits, uint64_t nbits, uint32_t b,
   return ns;
 }
 
+uint64_t orc_select_samples(const uint64_t* bits, uint64_t nbits, uint32_t b,
+                            uint64_t* samp) {
+  return samples_w(bits, nbits, 1, b, samp);
+}
+
+uint64_t orc_digit_samples(const uint64_t* dig, uint64_t ndig, uint32_t d, uint64_t* samp) {
+  return samples_w(dig, ndig, 2, d, samp);
+}
+
 /* ---------------------------------------------------------------------- */
 /* Clark-style select directory (§5.1 select), as defined in oracle.h.      */
 /* ---------------------------------------------------------------------- */
-int orc_clark_build(const uint64_t* bits, uint64_t nbits, uint32_t b, uint64_t huge_min,
-                    uint64_t sparse_min, uint64_t* nranges, uint64_t* nhuge, uint64_t* nsparse,
-                    uint64_t* desc, uint32_t* sub, uint32_t* sparse, uint64_t* huge) {
+static int clark_w(const uint64_t* bits, uint64_t nbits, int width, uint32_t b,
+                   uint64_t huge_min, uint64_t sparse_min, uint64_t* nranges, uint64_t* nhuge,
+                   uint64_t* nsparse, uint64_t* desc, uint32_t* sub, uint32_t* sparse,
+                   uint64_t* huge) {
   /* pass 1: the positions of occurrences 0, 256, 512, ... */
   uint64_t cnt = 0;
   for (uint64_t p = 0; p < nbits; p++)
-    if ((uint32_t)getbit(bits, p) == b) cnt++;
+    if (elem(bits, p, width) == b) cnt++;
   uint64_t M = (cnt + 255) / 256, R = (cnt + 4095) / 4096;
   uint64_t* p256 = (uint64_t*)malloc((M + 1) * sizeof(uint64_t));
   if (!p256) return -1;
   uint64_t c = 0;
   for (uint64_t p = 0; p < nbits; p++) {
-    if ((uint32_t)getbit(bits, p) == b) {
+    if (elem(bits, p, width) == b) {
       if (c % 256 == 0) p256[c / 256] = p;
       c++;
     }
@@ -185,7 +202,7 @@ int orc_clark_build(const uint64_t* bits, uint64_t nbits, uint32_t b, uint64_t h
       if (huge) {
         uint64_t j = 0;
         for (uint64_t p = S1; p < e && j < 4096; p++)
-          if ((uint32_t)getbit(bits, p) == b) huge[4096 * nh + j++] = p;
+          if (elem(bits, p, width) == b) huge[4096 * nh + j++] = p;
         for (; j < 4096; j++) huge[4096 * nh + j] = NONE;
       }
       nh++;
@@ -195,7 +212,7 @@ int orc_clark_build(const uint64_t* bits, uint64_t nbits, uint32_t b, uint64_t h
         if (sparse) {
           uint64_t m = 16 * k + i, j = 0;
           for (uint64_t p = p256[m]; p < nbits && j < 256; p++)
-            if ((uint32_t)getbit(bits, p) == b) sparse[256 * ns + j++] = (uint32_t)(p - S1);
+            if (elem(bits, p, width) == b) sparse[256 * ns + j++] = (uint32_t)(p - S1);
           for (; j < 256; j++) sparse[256 * ns + j] = 0xffffffffu;
         }
         ns++;
@@ -207,6 +224,20 @@ int orc_clark_build(const uint64_t* bits, uint64_t nbits, uint32_t b, uint64_t h
   if (nhuge) *nhuge = nh;
   if (nsparse) *nsparse = ns;
   return 0;
+}
+
+int orc_clark_build(const uint64_t* bits, uint64_t nbits, uint32_t b, uint64_t huge_min,
+                    uint64_t sparse_min, uint64_t* nranges, uint64_t* nhuge, uint64_t* nsparse,
+                    uint64_t* desc, uint32_t* sub, uint32_t* sparse, uint64_t* huge) {
+  return clark_w(bits, nbits, 1, b, huge_min, sparse_min, nranges, nhuge, nsparse, desc, sub,
+                 sparse, huge);
+}
+
+int orc_clark_digits(const uint64_t* dig, uint64_t ndig, uint32_t d, uint64_t huge_min,
+                     uint64_t sparse_min, uint64_t* nranges, uint64_t* nhuge, uint64_t* nsparse,
+                     uint64_t* desc, uint32_t* sub, uint32_t* sparse, uint64_t* huge) {
+  return clark_w(dig, ndig, 2, d, huge_min, sparse_min, nranges, nhuge, nsparse, desc, sub,
+                 sparse, huge);
 }
 
 /* ---------------------------------------------------------------------- */

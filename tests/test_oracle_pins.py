@@ -369,7 +369,7 @@ def test_queries_definition():
 # position of every occurrence; small thresholds make all three kinds of
 # range and sub-range appear
 # ---------------------------------------------------------------------------
-def _clark_answer(desc, sub, sparse, huge, samp, bits, nbits, b, j):
+def _clark_answer(desc, sub, sparse, huge, samp, bits, nbits, b, j, width=1):
     k = j >> 12
     d = int(desc[k])
     if d >> 63:
@@ -383,7 +383,8 @@ def _clark_answer(desc, sub, sparse, huge, samp, bits, nbits, b, j):
     p = S1 + int(sub[16 * k + i])
     need = j & 255  # occurrences to skip after the sub-range's first one
     while True:
-        if ((int(bits[p >> 6]) >> (p & 63)) & 1) == b:
+        q = p * width
+        if ((int(bits[q >> 6]) >> (q & 63)) & ((1 << width) - 1)) == b:
             if need == 0:
                 return p
             need -= 1
@@ -429,3 +430,60 @@ def test_clark_select_answers_every_occurrence(seed, nbits, density, huge_min, s
             assert _clark_answer(desc, sub, sparse, huge, samp, words, nbits, b, j) == pos[j], (b, j)
     if seed in (2, 3, 5):
         assert "huge" in kinds or "sparse" in kinds
+
+
+# ---------------------------------------------------------------------------
+# generalized select on 4-ary digit levels (§5.2, select per character): the
+# same sampled and constant-time structures over the occurrences of each
+# digit value; brute force over the digit array
+# ---------------------------------------------------------------------------
+def _digit_words(x):
+    n = x.size
+    words = np.zeros(oracle.level_words(2 * n), dtype=np.uint64)
+    for v in range(4):
+        pos = np.nonzero(x == v)[0].astype(np.uint64) * np.uint64(2)
+        if v & 1:
+            np.bitwise_or.at(words, (pos >> np.uint64(6)).astype(np.int64),
+                             np.left_shift(np.uint64(1), pos & np.uint64(63)))
+        if v & 2:
+            q = pos + np.uint64(1)
+            np.bitwise_or.at(words, (q >> np.uint64(6)).astype(np.int64),
+                             np.left_shift(np.uint64(1), q & np.uint64(63)))
+    return words
+
+
+@pytest.mark.parametrize("seed,n,probs,huge_min,sparse_min", [
+    (1, 30000, (0.25, 0.25, 0.25, 0.25), 1 << 32, 1 << 16),
+    (2, 150000, (0.97, 0.01, 0.01, 0.01), 1 << 14, 1 << 11),
+    (3, 150000, (0.5, 0.499, 0.0005, 0.0005), 1 << 13, 1 << 10),
+    (4, 70000, (0.1, 0.2, 0.3, 0.4), 1 << 12, 1 << 9),
+    (5, 5000, (0.0, 1.0, 0.0, 0.0), 1 << 32, 1 << 16),
+])
+def test_digit_select_structures_answer_every_occurrence(seed, n, probs, huge_min, sparse_min):
+    rng = np.random.default_rng(100 + seed)
+    x = rng.choice(4, size=n, p=probs).astype(np.uint8)
+    # stretches where value 0 takes over, so long ranges appear for the others
+    x[(np.arange(n) // 9000) % 4 == 1] = 0
+    words = _digit_words(x)
+    # the packing itself against the oracle's 4-ary levels of a sigma-4 text
+    assert np.array_equal(words, oracle.mwt_build(x.astype(np.uint32), 4)[0])
+    kinds = set()
+    for d in range(4):
+        pos = np.nonzero(x == d)[0]
+        samp = oracle.digit_samples(words, n, d)
+        assert np.array_equal(samp, pos[::4096].astype(np.uint64))
+        desc, sub, sparse, huge = oracle.clark_digits(words, n, d, huge_min, sparse_min)
+        assert desc.size == (pos.size + 4095) // 4096
+        for k in range(desc.size):
+            dk = int(desc[k])
+            kinds.add("huge" if dk >> 63 else ("sparse" if (dk >> 40) & 0xFFFF else "dense"))
+        js = np.arange(pos.size)
+        if pos.size > 20000:
+            js = np.unique(np.concatenate([js[::256], js[255::256], js[-300:],
+                                           rng.integers(0, pos.size, 5000)]))
+        for j in js:
+            j = int(j)
+            got = _clark_answer(desc, sub, sparse, huge, samp, words, n, d, j, width=2)
+            assert got == pos[j], (d, j)
+    if seed in (2, 3, 4):
+        assert {"huge", "sparse"} & kinds
