@@ -69,7 +69,8 @@ typedef struct {
 
 #define WT_FLAG_NO_DIRECTORY 1u  /* skip rank/select directories (timing of the bitmap build) */
 #define WT_FLAG_SELECT_O1 2u     /* also build the constant-time select directory of every
-                                    binary level (wt/wm/Huffman/rs builds; not 4-ary, not batched) */
+                                    level: binary levels (wt/wm/Huffman/rs) and the digit
+                                    levels of 4-ary trees (per digit value); not batched */
 
 enum { WT_KIND_WT = 0, WT_KIND_WM = 1, WT_KIND_HUFF = 2, WT_KIND_MULTI = 3, WT_KIND_RS = 4 };
 
@@ -87,14 +88,17 @@ typedef struct {
   uint32_t max_code_len;    /* HUFF only */
   const uint64_t* bits;     /* device */
   const uint64_t* dir;      /* device */
-  const uint64_t* samp;     /* device (binary kinds) */
+  const uint64_t* samp;     /* device */
   const uint64_t* level_len;  /* host [levels]: elements on each level */
   const uint64_t* level_off;  /* host [levels+1]: word offset of each level in bits */
   const uint64_t* dir_off;    /* host [levels+1]: u64 offset of each level in dir */
-  const uint64_t* samp_off;   /* host [2*levels+1]: u64 offsets into samp; level l
-                                 holds ceil(zeros_l/4096) zero samples from
-                                 samp_off[2l] and ceil(ones_l/4096) one samples
-                                 from samp_off[2l+1] (offsets are capacities) */
+  const uint64_t* samp_off;   /* host [V*levels+1], V = 2 (binary) or 4 (MULTI): u64
+                                 offsets into samp; level l holds the positions of
+                                 occurrences 0, 4096, 8192, ... of value v from
+                                 samp_off[V*l+v] (ceil(count_v/4096) of them; the
+                                 offsets are capacities); v = bit value, or digit
+                                 value of a MULTI digit level (Section 5.2
+                                 generalized select) */
   const uint64_t* zeros;      /* host [levels]: 0 bits per level (binary kinds) */
   const uint8_t* code_len;    /* host [sigma] (HUFF) */
   const uint32_t* code;       /* host [sigma] (HUFF) */
@@ -272,8 +276,11 @@ wt_status wt_sync(wt_handle h);
 /* Fills *out with views of the handle's arrays (synchronises the stream). */
 wt_status wt_export(wt_handle h, wt_export_view* out);
 
-/* The constant-time select directory of one binary level and bit value
- * (after Clark, Section 5.1 select), built with WT_FLAG_SELECT_O1.  Ranges
+/* The constant-time select directory of one level and value (after Clark,
+ * Section 5.1 select; per digit value on the digit levels of a 4-ary tree,
+ * Section 5.2 generalized select, with positions and lengths counted in
+ * digits; bit = the bit value 0..1, or the digit value 0..3), built with
+ * WT_FLAG_SELECT_O1.  Ranges
  * of 4096 occurrences start at the select samples; a range of at least 2^32
  * bits keeps the positions of its occurrences ("huge"); the others keep the
  * offsets of occurrences 256i (i < 16) from the range's start ("sub"), and a

@@ -230,10 +230,16 @@ class Exported:
         return self.dir[int(self.dir_off[l]):int(self.dir_off[l + 1])].reshape(-1, w)
 
     def samples(self, l: int, b: int) -> np.ndarray:
-        n = int(self.level_len[l])
-        z = int(self.zeros[l])
-        cnt = z if b == 0 else n - z
-        s = int(self.samp_off[2 * l + b])
+        """Positions of occurrences 0, 4096, ... of value b on level l (bit
+        value; digit value on the digit levels of a 4-ary tree)."""
+        if self.bits_per_elem == 2:
+            cnt = int(self.level_dir(l)[-1, b])
+            s = int(self.samp_off[4 * l + b])
+        else:
+            n = int(self.level_len[l])
+            z = int(self.zeros[l])
+            cnt = z if b == 0 else n - z
+            s = int(self.samp_off[2 * l + b])
         return self.samp[s:s + (cnt + 4095) // 4096]
 
 
@@ -290,7 +296,7 @@ class Handle:
         level_len = host(v.level_len, L)
         level_off = host(v.level_off, L + 1)
         dir_off = host(v.dir_off, L + 1)
-        samp_off = host(v.samp_off, 2 * L + 1)
+        samp_off = host(v.samp_off, (4 if v.bits_per_elem == 2 else 2) * L + 1)
         zeros = host(v.zeros, L)
         nw = int(level_off[-1]) if L else 0
         bits = d2h(v.bits, nw * 8) if nw else np.zeros(0, np.uint64)

@@ -128,10 +128,6 @@ wt_status seq_build(int kind, const void* d_seq, uint64_t n, uint32_t sigma, uin
   s = new_handle(stream, n, sigma, &h);
   if (s != WT_OK) return s;
   h->flags = opts ? opts->flags : 0u;
-  if ((h->flags & WT_FLAG_SELECT_O1) && kind == WT_KIND_MULTI) {
-    finish(h, WT_ERR_UNSUPPORTED, out);
-    return WT_ERR_UNSUPPORTED;
-  }
   switch (kind) {
     case WT_KIND_WM: s = build_wm(d_seq, n, sigma, (int)width, opts, h); break;
     case WT_KIND_WT: s = build_wt(d_seq, n, sigma, (int)width, opts, h, false); break;
@@ -252,10 +248,10 @@ wt_status wt_free(wt_handle h) {
 }
 
 wt_status wt_export_select(wt_handle h, uint32_t level, uint32_t bit, wt_select_view* out) {
-  if (!h || !out || bit > 1) return WT_ERR_INVALID_ARG;
+  if (!h || !out || bit > 3) return WT_ERR_INVALID_ARG;
   wt_status s = sync_handle(h);
   if (s != WT_OK) return s;
-  if (!(h->flags & WT_FLAG_SELECT_O1) || h->bpe != 1 || level >= h->cmeta.size())
+  if (!(h->flags & WT_FLAG_SELECT_O1) || level >= h->cmeta.size() || bit > (h->bpe == 2 ? 3u : 1u))
     return WT_ERR_INVALID_ARG;
   const ClarkMeta& m = h->cmeta[level];
   memset(out, 0, sizeof(*out));

@@ -10,7 +10,9 @@
 // searches superblocks, blocks, words, then the bit inside the word.
 // Digit levels of the 4-ary tree (Section 5.2, per-value counts): one
 // 64-byte record per 1024 digits, {4 x u64 counts of each value before the
-// superblock, 4 blocks x 4 values u16 counts inside it}.
+// superblock, 4 blocks x 4 values u16 counts inside it}; select samples per
+// digit value (Section 5.2 generalized select: the position of every 4096th
+// occurrence of each value), four regions of n/4096 + 1 per level.
 #include <algorithm>
 #include <cstdio>
 #include <vector>
@@ -243,6 +245,44 @@ __global__ void k_mdir_finish(const LevelMeta* meta, int nlev, const uint64_t* s
   }
 }
 
+// position (inside digit superblock s, relative to its start) of the r-th
+// (0-based) occurrence of digit value d; the occurrence lies in s
+__device__ uint32_t find_in_dsb(const uint64_t* lbits, const uint64_t* ldir, uint64_t s, uint32_t d,
+                                uint32_t r) {
+  int b = 3;
+  for (; b > 0; b--)
+    if (((ldir[8 * s + 4 + b] >> (16 * d)) & 0xffffull) <= r) break;
+  r -= b ? (uint32_t)((ldir[8 * s + 4 + b] >> (16 * d)) & 0xffffull) : 0u;
+  for (uint64_t w = 32 * s + 8 * b; w < 32 * s + 32; w++) {
+    const uint64_t m = digit_match(lbits[w], d);
+    const uint32_t c = __popcll(m);
+    if (c > r) return (uint32_t)((w - 32 * s) * 32 + sel64(m, r) / 2);
+    r -= c;
+  }
+  return 1023;
+}
+
+// every 4096th occurrence of each digit value: one thread per superblock
+// (a superblock of 1024 digits holds at most one sample per value)
+__global__ void k_mdigit_samples(const uint64_t* bits, const LevelMeta* meta, int nlev,
+                                 const uint64_t* sb_first, uint64_t total_sb,
+                                 const uint64_t* dir, uint64_t* samp) {
+  const uint64_t g = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= total_sb) return;
+  const int l = find_level(sb_first, nlev, g);
+  const LevelMeta m = meta[l];
+  const uint64_t s = g - sb_first[l];
+  const uint64_t* ld = dir + m.dir_off;
+  const uint64_t* lb = bits + m.bit_off;
+  const uint64_t cap = m.n / 4096 + 1;
+  for (uint32_t d = 0; d < 4; d++) {
+    const uint64_t before = ld[8 * s + d], in = ld[8 * (s + 1) + d] - before;
+    const uint64_t k = (before + 4095) / 4096;
+    if (4096 * k < before + in)
+      samp[m.s0_off + d * cap + k] = 1024 * s + find_in_dsb(lb, ld, s, d, (uint32_t)(4096 * k - before));
+  }
+}
+
 wt_status upload_meta(wt_struct* h) {
   const size_t nb = std::max<size_t>(h->meta.size(), 1) * sizeof(LevelMeta);
   if (!h->d_meta) CK(dmalloc((void**)&h->d_meta, nb, h->stream));
@@ -308,25 +348,31 @@ wt_status dir_build_levels(const uint64_t* bits, const LevelMeta* d_meta, uint32
 constexpr uint64_t CK_HUGE_MIN = 1ull << 32;    // range length that keeps all positions
 constexpr uint64_t CK_SPARSE_MIN = 1ull << 16;  // sub-range length that keeps all offsets
 
-// occurrences of bit value b before superblock s of a level
+// occurrences of value b before superblock s of a level: bit values of a
+// binary level (2048-bit superblocks), digit values of a digit level (1024)
+template <bool DIG>
 __device__ __forceinline__ uint64_t occ_before(const uint64_t* ldir, int b, uint64_t s) {
+  if (DIG) return ldir[8 * s + b];
   const uint64_t z = ldir[2 * s];
   return b ? 2048 * s - z : z;
 }
 
-// position of occurrence q of bit value b, known to lie in superblocks
-// [lo, hi] of the level (q >= occurrences before lo)
+// position of occurrence q of value b, known to lie in superblocks [lo, hi]
+// of the level (q >= occurrences before lo)
+template <bool DIG>
 __device__ uint64_t dir_select(const uint64_t* lbits, const uint64_t* ldir, int b, uint64_t q,
                                uint64_t lo, uint64_t hi) {
   while (lo < hi) {
     const uint64_t mid = (lo + hi + 1) >> 1;
-    if (occ_before(ldir, b, mid) <= q) lo = mid;
+    if (occ_before<DIG>(ldir, b, mid) <= q) lo = mid;
     else hi = mid - 1;
   }
-  return 2048 * lo + find_in_sb(lbits, ldir, lo, b, (uint32_t)(q - occ_before(ldir, b, lo)));
+  const uint32_t r = (uint32_t)(q - occ_before<DIG>(ldir, b, lo));
+  if (DIG) return 1024 * lo + find_in_dsb(lbits, ldir, lo, (uint32_t)b, r);
+  return 2048 * lo + find_in_sb(lbits, ldir, lo, b, r);
 }
 
-// one (level, bit value) of the directory build
+// one (level, bit or digit value) of the directory build
 struct CkSeg {
   uint64_t g0;        // its first range in the global numbering
   uint64_t cnt;       // occurrences
@@ -345,6 +391,7 @@ __device__ __forceinline__ uint32_t ck_seg_of(const CkSeg* segs, uint32_t nseg, 
 }
 
 // per range: kind, sub-sample offsets, mask of long sub-ranges
+template <bool DIG>
 __global__ void k_ck_ranges(const uint64_t* bits, const uint64_t* dir, const uint64_t* samp,
                             const CkSeg* segs, uint32_t nseg, uint64_t G, uint32_t* sub,
                             uint64_t* mask_or_huge, uint64_t* nh, uint64_t* ns) {
@@ -361,11 +408,12 @@ __global__ void k_ck_ranges(const uint64_t* bits, const uint64_t* dir, const uin
   const bool huge = e - S1 >= CK_HUGE_MIN;
   uint32_t mask = 0;
   uint64_t prev = S1;  // start of sub-range i
-  const uint64_t lo_sb = S1 >> 11, hi_sb = (e - 1) >> 11;
+  constexpr int SBSH = DIG ? 10 : 11;
+  const uint64_t lo_sb = S1 >> SBSH, hi_sb = (e - 1) >> SBSH;
   for (int i = 0; i < 16; i++) {
     const uint64_t m = 16 * k + i;
     uint64_t start = 0;
-    if (!huge && m < M) start = i == 0 ? S1 : dir_select(lbits, ldir, sg.b, 256 * m, lo_sb, hi_sb);
+    if (!huge && m < M) start = i == 0 ? S1 : dir_select<DIG>(lbits, ldir, sg.b, 256 * m, lo_sb, hi_sb);
     sub[16 * g + i] = huge ? 0u : (m < M ? (uint32_t)(start - S1) : 0xffffffffu);
     if (!huge && i > 0 && m - 1 < M && m < M && start - prev >= CK_SPARSE_MIN) mask |= 1u << (i - 1);
     if (!huge && m < M) prev = start;
@@ -388,6 +436,7 @@ __global__ void k_ck_desc(const CkSeg* segs, uint32_t nseg, uint64_t G, const ui
 }
 
 // explicit answers: one block per range that keeps any
+template <bool DIG>
 __global__ void k_ck_fill(const uint64_t* bits, const uint64_t* dir, const uint64_t* samp,
                           const CkSeg* segs, uint32_t nseg, uint64_t G, const uint64_t* kind,
                           const uint64_t* gh, const uint64_t* gs, const uint32_t* sub,
@@ -401,11 +450,13 @@ __global__ void k_ck_fill(const uint64_t* bits, const uint64_t* dir, const uint6
     const uint64_t* ldir = dir + sg.dir_off;
     const uint64_t S1 = samp[sg.samp_off + k];
     const uint64_t e = (k + 1 < R) ? samp[sg.samp_off + k + 1] : sg.n;
-    const uint64_t lo_sb = S1 >> 11, hi_sb = (e - 1) >> 11;
+    constexpr int SBSH = DIG ? 10 : 11;
+    const uint64_t lo_sb = S1 >> SBSH, hi_sb = (e - 1) >> SBSH;
     if (kd >> 63) {
       for (uint32_t j = threadIdx.x; j < 4096; j += blockDim.x) {
         const uint64_t q = 4096 * k + j;
-        huge_all[4096 * gh[g] + j] = q < sg.cnt ? dir_select(lbits, ldir, sg.b, q, lo_sb, hi_sb) : ~0ull;
+        huge_all[4096 * gh[g] + j] =
+            q < sg.cnt ? dir_select<DIG>(lbits, ldir, sg.b, q, lo_sb, hi_sb) : ~0ull;
       }
     } else {
       uint32_t mask = (uint32_t)kd;
@@ -416,7 +467,8 @@ __global__ void k_ck_fill(const uint64_t* bits, const uint64_t* dir, const uint6
         for (uint32_t j = threadIdx.x; j < 256; j += blockDim.x) {
           const uint64_t q = 4096 * k + 256 * i + j;
           sparse_all[256 * s + j] =
-              q < sg.cnt ? (uint32_t)(dir_select(lbits, ldir, sg.b, q, lo_sb, hi_sb) - S1) : 0xffffffffu;
+              q < sg.cnt ? (uint32_t)(dir_select<DIG>(lbits, ldir, sg.b, q, lo_sb, hi_sb) - S1)
+                         : 0xffffffffu;
         }
         s++;
       }
@@ -429,27 +481,53 @@ __global__ void k_gather_u64(const uint64_t* src, const uint64_t* idx, uint64_t 
   if (i < n) out[i] = src[idx[i]];
 }
 
+// dig: digit levels (4 values; occurrence counts from the directory's
+// trailing records), else binary levels (2 values; counts from the zeros)
 static wt_status build_clark(wt_struct* h) {
   cudaStream_t st = h->stream;
   const uint32_t nlev = h->levels;
-  // occurrence counts per level need the zero counts on the host
-  std::vector<uint64_t> zeros(nlev, 0);
+  const bool dig = h->bpe == 2;
+  const int NV = dig ? 4 : 2;
+  // occurrence counts of every value on every level, on the host
+  std::vector<uint64_t> occ((size_t)NV * nlev, 0);
   if (nlev) {
-    CK(cudaMemcpyAsync(zeros.data(), h->d_zeros, nlev * 8, cudaMemcpyDeviceToHost, st));
-    CK(cudaStreamSynchronize(st));
+    if (dig) {
+      std::vector<uint64_t> idx(occ.size());
+      for (uint32_t l = 0; l < nlev; l++)
+        for (int d = 0; d < 4; d++) idx[4 * l + d] = h->meta[l].dir_off + 8 * h->meta[l].nsb + d;
+      uint64_t *d_idx, *d_got;
+      CK(dmalloc((void**)&d_idx, idx.size() * 8, st));
+      CK(dmalloc((void**)&d_got, idx.size() * 8, st));
+      CK(cudaMemcpyAsync(d_idx, idx.data(), idx.size() * 8, cudaMemcpyHostToDevice, st));
+      k_gather_u64<<<(unsigned)((idx.size() + 255) / 256), 256, 0, st>>>(h->d_dir, d_idx,
+                                                                         idx.size(), d_got);
+      count_launch();
+      CK(cudaMemcpyAsync(occ.data(), d_got, occ.size() * 8, cudaMemcpyDeviceToHost, st));
+      CK(cudaStreamSynchronize(st));
+      dfree(d_idx, st);
+      dfree(d_got, st);
+    } else {
+      std::vector<uint64_t> zeros(nlev, 0);
+      CK(cudaMemcpyAsync(zeros.data(), h->d_zeros, nlev * 8, cudaMemcpyDeviceToHost, st));
+      CK(cudaStreamSynchronize(st));
+      for (uint32_t l = 0; l < nlev; l++) {
+        occ[2 * l] = zeros[l];
+        occ[2 * l + 1] = h->meta[l].n - zeros[l];
+      }
+    }
   }
   std::vector<CkSeg> segs;
   h->cmeta.assign(nlev, ClarkMeta{});
   uint64_t G = 0;
   for (uint32_t l = 0; l < nlev; l++) {
     const LevelMeta& m = h->meta[l];
-    for (int b = 0; b < 2; b++) {
+    for (int b = 0; b < NV; b++) {
       CkSeg sg;
       sg.g0 = G;
-      sg.cnt = b ? m.n - zeros[l] : zeros[l];
+      sg.cnt = occ[(size_t)NV * l + b];
       sg.bit_off = m.bit_off;
       sg.dir_off = m.dir_off;
-      sg.samp_off = b ? m.s1_off : m.s0_off;
+      sg.samp_off = dig ? m.s0_off + (uint64_t)b * (m.n / 4096 + 1) : (b ? m.s1_off : m.s0_off);
       sg.n = m.n;
       sg.nsb = m.nsb;
       sg.b = b;
@@ -477,8 +555,12 @@ static wt_status build_clark(wt_struct* h) {
     CK(cudaMemcpyAsync(d_segs, segs.data(), nseg * sizeof(CkSeg), cudaMemcpyHostToDevice, st));
   const unsigned gg = (unsigned)((G + 255) / 256);
   if (G) {
-    k_ck_ranges<<<gg, 256, 0, st>>>(h->d_bits_ro, h->d_dir, h->d_samp, d_segs, nseg, G, d_sub,
-                                    d_kind, d_nh, d_ns);
+    if (dig)
+      k_ck_ranges<true><<<gg, 256, 0, st>>>(h->d_bits_ro, h->d_dir, h->d_samp, d_segs, nseg, G,
+                                            d_sub, d_kind, d_nh, d_ns);
+    else
+      k_ck_ranges<false><<<gg, 256, 0, st>>>(h->d_bits_ro, h->d_dir, h->d_samp, d_segs, nseg, G,
+                                             d_sub, d_kind, d_nh, d_ns);
     count_launch();
   }
   wt_status s = scan_excl_u64_pub(d_nh, d_gh, G, scr, st);
@@ -498,48 +580,48 @@ static wt_status build_clark(wt_struct* h) {
       k_ck_desc<<<gg, 256, 0, st>>>(d_segs, nseg, G, d_kind, d_gh, d_gs, h->d_ck64);
       count_launch();
       const unsigned fg = (unsigned)std::min<uint64_t>(G, (uint64_t)num_sms() * 16);
-      k_ck_fill<<<fg, 256, 0, st>>>(h->d_bits_ro, h->d_dir, h->d_samp, d_segs, nseg, G, d_kind,
-                                    d_gh, d_gs, d_sub, h->d_ck64 + G, h->d_ck32 + 16 * G);
+      if (dig)
+        k_ck_fill<true><<<fg, 256, 0, st>>>(h->d_bits_ro, h->d_dir, h->d_samp, d_segs, nseg, G,
+                                            d_kind, d_gh, d_gs, d_sub, h->d_ck64 + G,
+                                            h->d_ck32 + 16 * G);
+      else
+        k_ck_fill<false><<<fg, 256, 0, st>>>(h->d_bits_ro, h->d_dir, h->d_samp, d_segs, nseg, G,
+                                             d_kind, d_gh, d_gs, d_sub, h->d_ck64 + G,
+                                             h->d_ck32 + 16 * G);
       count_launch();
     }
-    // per (level, bit value): the scans at its first and one-past-last range
-    std::vector<uint64_t> idx(4 * (size_t)nlev, 0), got(4 * (size_t)nlev, 0);
+    // per (level, value): the scans at its first and one-past-last range
+    const size_t nv = (size_t)NV * nlev;
+    std::vector<uint64_t> idx(2 * nv, 0);
     for (uint32_t l = 0; l < nlev; l++)
-      for (int b = 0; b < 2; b++) {
-        idx[4 * l + 2 * b] = h->cmeta[l].desc[b];
-        idx[4 * l + 2 * b + 1] = h->cmeta[l].desc[b] + h->cmeta[l].nr[b];
+      for (int b = 0; b < NV; b++) {
+        idx[2 * (NV * l + b)] = h->cmeta[l].desc[b];
+        idx[2 * (NV * l + b) + 1] = h->cmeta[l].desc[b] + h->cmeta[l].nr[b];
       }
-    std::vector<uint64_t> gh_first(2 * nlev), gh_end(2 * nlev), gs_first(2 * nlev), gs_end(2 * nlev);
+    std::vector<uint64_t> both(2 * idx.size(), 0);
     if (nlev) {
       uint64_t *d_idx, *d_got;
       CK(dmalloc((void**)&d_idx, idx.size() * 8, st));
-      CK(dmalloc((void**)&d_got, 2 * idx.size() * 8, st));
+      CK(dmalloc((void**)&d_got, both.size() * 8, st));
       CK(cudaMemcpyAsync(d_idx, idx.data(), idx.size() * 8, cudaMemcpyHostToDevice, st));
       k_gather_u64<<<(unsigned)((idx.size() + 255) / 256), 256, 0, st>>>(d_gh, d_idx, idx.size(), d_got);
       count_launch();
       k_gather_u64<<<(unsigned)((idx.size() + 255) / 256), 256, 0, st>>>(d_gs, d_idx, idx.size(),
                                                                          d_got + idx.size());
       count_launch();
-      std::vector<uint64_t> both(2 * idx.size());
       CK(cudaMemcpyAsync(both.data(), d_got, both.size() * 8, cudaMemcpyDeviceToHost, st));
       CK(cudaStreamSynchronize(st));
       dfree(d_idx, st);
       dfree(d_got, st);
-      for (uint32_t l = 0; l < nlev; l++)
-        for (int b = 0; b < 2; b++) {
-          gh_first[2 * l + b] = both[4 * l + 2 * b];
-          gh_end[2 * l + b] = both[4 * l + 2 * b + 1];
-          gs_first[2 * l + b] = both[idx.size() + 4 * l + 2 * b];
-          gs_end[2 * l + b] = both[idx.size() + 4 * l + 2 * b + 1];
-        }
     }
     for (uint32_t l = 0; l < nlev; l++)
-      for (int b = 0; b < 2; b++) {
+      for (int b = 0; b < NV; b++) {
+        const size_t i = 2 * ((size_t)NV * l + b);
         ClarkMeta& cm = h->cmeta[l];
-        cm.nh[b] = gh_end[2 * l + b] - gh_first[2 * l + b];
-        cm.ns[b] = gs_end[2 * l + b] - gs_first[2 * l + b];
-        cm.huge[b] = G + 4096 * gh_first[2 * l + b];
-        cm.sparse[b] = 16 * G + 256 * gs_first[2 * l + b];
+        cm.nh[b] = both[i + 1] - both[i];
+        cm.ns[b] = both[idx.size() + i + 1] - both[idx.size() + i];
+        cm.huge[b] = G + 4096 * both[i];
+        cm.sparse[b] = 16 * G + 256 * both[idx.size() + i];
       }
     CK(dmalloc((void**)&h->d_cmeta, std::max<uint32_t>(nlev, 1) * sizeof(ClarkMeta), st));
     if (nlev)
@@ -566,9 +648,12 @@ wt_status build_directories(wt_struct* h) {
   const bool dig = h->bpe == 2;
   const uint64_t sbsz = dig ? 1024 : 2048;
   const uint64_t rec = dig ? 8 : 2;
+  // select samples: per level one region of n/4096 + 1 per value (2 bit
+  // values, or 4 digit values)
+  const uint32_t NV = dig ? 4 : 2;
   h->meta.assign(nlev, LevelMeta{});
   h->dir_off.assign(nlev + 1, 0);
-  h->samp_off.assign(2 * nlev + 1, 0);
+  h->samp_off.assign(NV * nlev + 1, 0);
   std::vector<uint64_t> sb_first(nlev + 1, 0);
   for (uint32_t l = 0; l < nlev; l++) {
     LevelMeta& m = h->meta[l];
@@ -578,15 +663,14 @@ wt_status build_directories(wt_struct* h) {
     m.dir_off = h->dir_off[l];
     h->dir_off[l + 1] = h->dir_off[l] + rec * (m.nsb + 1);
     sb_first[l + 1] = sb_first[l] + m.nsb;
-    const uint64_t cap = dig ? 0 : m.n / 4096 + 1;
-    m.s0_off = h->samp_off[2 * l];
-    h->samp_off[2 * l + 1] = m.s0_off + cap;
-    m.s1_off = h->samp_off[2 * l + 1];
-    h->samp_off[2 * l + 2] = m.s1_off + cap;
+    const uint64_t cap = m.n / 4096 + 1;
+    for (uint32_t v = 0; v < NV; v++) h->samp_off[NV * l + v + 1] = h->samp_off[NV * l + v] + cap;
+    m.s0_off = h->samp_off[NV * l];
+    m.s1_off = h->samp_off[NV * l + 1];
   }
   const uint64_t total_sb = sb_first[nlev];
   CK(dmalloc((void**)&h->d_dir, std::max<uint64_t>(h->dir_off[nlev], 1) * 8, st));
-  CK(dmalloc((void**)&h->d_samp, std::max<uint64_t>(h->samp_off[2 * nlev], 1) * 8, st));
+  CK(dmalloc((void**)&h->d_samp, std::max<uint64_t>(h->samp_off[NV * nlev], 1) * 8, st));
   wt_status s = upload_meta(h);
   if (s != WT_OK) return s;
   if (nlev == 0) return WT_OK;
@@ -616,6 +700,11 @@ wt_status build_directories(wt_struct* h) {
   if (s == WT_OK) {
     k_mdir_finish<<<fgrid, 256, 0, st>>>(h->d_meta, nlev, d_first, total_sb, sbx, h->d_dir);
     count_launch();
+    if (total_sb) {
+      k_mdigit_samples<<<(unsigned)((total_sb + 255) / 256), 256, 0, st>>>(
+          h->d_bits_ro, h->d_meta, nlev, d_first, total_sb, h->d_dir, h->d_samp);
+      count_launch();
+    }
   }
   cudaError_t e = cudaGetLastError();
   dfree(d_first, st);
@@ -624,6 +713,7 @@ wt_status build_directories(wt_struct* h) {
   dfree(scr, st);
   if (s != WT_OK) return s;
   if (e != cudaSuccess) return WT_ERR_CUDA;
+  if (h->flags & WT_FLAG_SELECT_O1) return build_clark(h);
   return WT_OK;
 }
 
@@ -711,7 +801,7 @@ __device__ uint64_t select_b(const BinLevel& v, int bv, uint64_t k) {
     if ((k & 255) == 0) return p0;
     uint64_t hi = (p0 + CK_SPARSE_MIN - 1) >> 11;
     if (hi >= v.nsb) hi = v.nsb - 1;
-    return dir_select(v.bits, v.dir, bv, k, p0 >> 11, hi);
+    return dir_select<false>(v.bits, v.dir, bv, k, p0 >> 11, hi);
   }
   const uint64_t cnt = bv ? v.n - v.zeros : v.zeros;
   const uint64_t ns = (cnt + 4095) / 4096;
@@ -916,7 +1006,11 @@ __device__ uint64_t q_huff(const QStruct& S, int op, uint32_t c, uint64_t x) {
 struct DigLevel {
   const uint64_t* bits;
   const uint64_t* dir;
+  const uint64_t* samp;  // 4 regions of n/4096 + 1: samples of values 0..3
   uint64_t n, nsb;
+  const ClarkMeta* cm;
+  const uint64_t* ck64;
+  const uint32_t* ck32;
 };
 
 __device__ __forceinline__ DigLevel dig_level(const QStruct& S, int l) {
@@ -924,8 +1018,12 @@ __device__ __forceinline__ DigLevel dig_level(const QStruct& S, int l) {
   DigLevel v;
   v.bits = S.bits + m.bit_off;
   v.dir = S.dir + m.dir_off;
+  v.samp = S.samp + m.s0_off;
   v.n = m.n;
   v.nsb = m.nsb;
+  v.cm = S.cmeta ? S.cmeta + l : nullptr;
+  v.ck64 = S.ck64;
+  v.ck32 = S.ck32;
   return v;
 }
 
@@ -945,26 +1043,35 @@ __device__ __forceinline__ uint32_t get_digit(const DigLevel& v, uint64_t i) {
   return (uint32_t)((v.bits[i >> 5] >> (2 * (i & 31))) & 3ull);
 }
 
-// position of the k-th (0-based) occurrence of digit d
+// position of the k-th (0-based) occurrence of digit d; k < its count
+// (Section 5.2 generalized select: the structures of the binary case per
+// digit value)
 __device__ uint64_t select_d(const DigLevel& v, uint32_t d, uint64_t k) {
-  uint64_t lo = 0, hi = v.nsb - 1;
-  while (lo < hi) {
-    const uint64_t mid = (lo + hi + 1) >> 1;
-    if (v.dir[8 * mid + d] <= k) lo = mid;
-    else hi = mid - 1;
+  const uint64_t* samp = v.samp + d * (v.n / 4096 + 1);
+  const uint64_t kk = k >> 12;
+  if (v.cm) {
+    // constant-time directory: stored answer, or a sub-range shorter than
+    // 2^16 digits to search
+    const uint64_t dsc = v.ck64[v.cm->desc[d] + kk];
+    if (dsc >> 63) return v.ck64[v.cm->huge[d] + (dsc & ((1ull << 63) - 1)) + (k & 4095)];
+    const uint32_t mask = (uint32_t)((dsc >> 40) & 0xffffu);
+    const int i = (int)((k >> 8) & 15);
+    const uint64_t S1 = samp[kk];
+    if ((mask >> i) & 1u) {
+      const uint64_t sidx = (dsc & ((1ull << 40) - 1)) + (uint64_t)__popc(mask & ((1u << i) - 1u));
+      return S1 + v.ck32[v.cm->sparse[d] + 256 * sidx + (k & 255)];
+    }
+    const uint64_t p0 = S1 + v.ck32[v.cm->sub[d] + 16 * kk + i];
+    if ((k & 255) == 0) return p0;
+    uint64_t hi = (p0 + CK_SPARSE_MIN - 1) >> 10;
+    if (hi >= v.nsb) hi = v.nsb - 1;
+    return dir_select<true>(v.bits, v.dir, (int)d, k, p0 >> 10, hi);
   }
-  uint64_t r = k - v.dir[8 * lo + d];
-  int b = 3;
-  for (; b > 0; b--)
-    if (((v.dir[8 * lo + 4 + b] >> (16 * d)) & 0xffffull) <= r) break;
-  r -= b ? ((v.dir[8 * lo + 4 + b] >> (16 * d)) & 0xffffull) : 0;
-  for (uint64_t w = 32 * lo + 8 * b; w < 32 * lo + 32; w++) {
-    const uint64_t m = digit_match(v.bits[w], d);
-    const uint32_t c = __popcll(m);
-    if (c > r) return w * 32 + sel64(m, (uint32_t)r) / 2;
-    r -= c;
-  }
-  return NONE;
+  // sampled: the search starts between two samples
+  const uint64_t ns = (v.dir[8 * v.nsb + d] + 4095) / 4096;
+  const uint64_t lo = samp[kk] >> 10;
+  const uint64_t hi = kk + 1 < ns ? samp[kk + 1] >> 10 : v.nsb - 1;
+  return dir_select<true>(v.bits, v.dir, (int)d, k, lo, hi);
 }
 
 __device__ uint64_t q_multi(const QStruct& S, int op, uint32_t c, uint64_t x) {

@@ -32,10 +32,12 @@ struct LevelMeta {
 // Constant-time select directory of one level (offsets, in elements, into
 // the handle's two arrays: ck64 = descriptors | long-range positions,
 // ck32 = sub-sample offsets | long-sub-range offsets), per bit value.
+// per level, per bit value (binary levels: 0, 1) or digit value (4-ary
+// digit levels: 0..3)
 struct ClarkMeta {
-  uint64_t nr[2], nh[2], ns[2];
-  uint64_t desc[2], huge[2];    // in ck64
-  uint64_t sub[2], sparse[2];   // in ck32
+  uint64_t nr[4], nh[4], ns[4];
+  uint64_t desc[4], huge[4];    // in ck64
+  uint64_t sub[4], sparse[4];   // in ck32
 };
 
 // Huffman query tables (device): symbols in canonical order, per length the

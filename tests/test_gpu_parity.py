@@ -105,6 +105,9 @@ def test_multiary_parity(wt, case):
     assert np.array_equal(ex.bits.reshape(od.shape), od)
     for b in range(od.shape[0]):
         assert np.array_equal(ex.level_dir(b), oracle.mwt_dir(od[b], S.size))
+        # select samples of every digit value (Section 5.2 generalized select)
+        for d in range(4):
+            assert np.array_equal(ex.samples(b, d), oracle.digit_samples(od[b], S.size, d)), (b, d)
     h.free()
 
 
