@@ -702,6 +702,32 @@ def run_select(args, wt):
         res[f"bitvector_{name}"] = {"build_ms": bms, "select_ms": qms,
                                     "queries_per_s": Q / qms * 1e3}
         h.free()
+    del dw
+    # 4-ary tree of the DNA-like text (n = 2^32, sigma 5): select per digit
+    # value on every digit level (generalized select)
+    ng = 1 << 32
+    gpin = torch.empty(ng, dtype=torch.uint8).pin_memory()
+    synth.genome(synth_seed(3), ng, addr=gpin.data_ptr())
+    dg = gpin.to("cuda")
+    del gpin
+    cnt = torch.zeros(5, dtype=torch.int64, device="cuda")
+    for o in range(0, ng, 1 << 28):
+        cnt += torch.bincount(dg[o:o + (1 << 28)].to(torch.int32), minlength=5)
+    cnt = cnt.cpu().numpy()
+    presg = np.nonzero(cnt)[0]
+    cg = presg[rng.integers(0, presg.size, Q)].astype(np.uint32)
+    kg = (rng.random(Q) * cnt[cg]).astype(np.uint64) + 1
+    dcg = torch.from_numpy(cg.view(np.int32)).cuda()
+    dkg = torch.from_numpy(kg.view(np.int64)).cuda()
+    for name, fl in (("sampled", 0), ("o1", wt.FLAG_SELECT_O1)):
+        bms = timed(lambda: wt.multiary_build(dg, 5, flags=fl).free(), 3)
+        h = wt.multiary_build(dg, 5, flags=fl)
+        h.sync()
+        qms = timed(lambda: h.select(dcg, dkg, out))
+        res[f"multiary_{name}"] = {"build_ms": bms, "select_ms": qms,
+                                   "queries_per_s": Q / qms * 1e3}
+        h.free()
+    del dg
     cpu = None
     if not args.no_cpu:
         import oracle
@@ -719,7 +745,8 @@ def run_select(args, wt):
     cfg = {"workload": f"2^22 select queries (c, k uniform over present symbols and their "
                        f"counts) on the wavelet matrix of n=2^30 uint16 Zipf(1.1), sigma 2^16; "
                        f"and 2^22 select-1 queries on a 2^32-bit bitvector of dense and 1-in-300 "
-                       f"stretches; sampled vs constant-time select directory",
+                       f"stretches; and 2^22 selects on the 4-ary tree of the n=2^32 DNA-like "
+                       f"text (sigma 5); sampled vs constant-time select directory",
            "queries": Q}
     _line(args, "select queries/s, constant-time directory (wavelet matrix n=2^30)",
           res["wm_o1"]["queries_per_s"], "queries/s", res["wm_o1"]["select_ms"], cfg, dtype="u16",

@@ -270,6 +270,19 @@ wt_status wt_rank(wt_handle h, const uint32_t* d_c, const uint64_t* d_i, uint64_
 wt_status wt_select(wt_handle h, const uint32_t* d_c, const uint64_t* d_k, uint64_t q,
                     uint64_t* d_out, wt_stream stream);
 
+/* Domain-decomposition merge (Section 4.2: the K sub-problems' levels are
+ * concatenated node by node, at offsets from prefix sums of the node sizes).
+ * parts[0..r-1] are wavelet matrices (all of them) or balanced wavelet trees
+ * (all of them) of consecutive pieces S_0, ..., S_{r-1} of one sequence,
+ * built with the same sigma and with directories; *out receives the
+ * structure of the concatenation S_0 S_1 ... S_{r-1}, bit for bit the one a
+ * single build of it gives, with its own directories (opts->flags may ask
+ * for WT_FLAG_SELECT_O1).  The parts are read (each is synchronised first)
+ * and stay valid.  Limits: ceil(log2 sigma) <= 20 and r * 2^ceil(log2
+ * sigma) <= 2^26 (WT_ERR_UNSUPPORTED otherwise). */
+wt_status wt_dd_merge(const wt_handle* parts, uint32_t r, const wt_build_opts* opts,
+                      wt_stream stream, wt_handle* out);
+
 /* Waits for the handle's build stream and returns its deferred status. */
 wt_status wt_sync(wt_handle h);
 

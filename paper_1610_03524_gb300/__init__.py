@@ -32,7 +32,7 @@ ABI_SYMBOLS = ("wt_build", "wm_build", "huff_wt_build", "multiary_build", "rs_bu
                "wm_batch_build", "wm_autotune", "wm_autotune_clear", "wt_query_multi",
                "wt_server_create", "wt_server_submit_build", "wt_server_submit_queries",
                "wt_server_poll", "wt_server_handle", "wt_server_release", "wt_server_stats",
-               "wt_server_destroy", "wt_export_select")
+               "wt_server_destroy", "wt_export_select", "wt_dd_merge")
 
 
 class WaveletError(RuntimeError):
@@ -138,6 +138,8 @@ def load_library(path: str = LIB_PATH):
     lib.rs_dir_build_static.argtypes = [vp, u64, vp, vp, vp, vp]
     lib.wt_export_select.restype = c.c_int
     lib.wt_export_select.argtypes = [vp, u32, u32, c.POINTER(SelectView)]
+    lib.wt_dd_merge.restype = c.c_int
+    lib.wt_dd_merge.argtypes = [hp, u32, c.POINTER(BuildOpts), vp, hp]
     lib.wm_batch_build.restype = c.c_int
     lib.wm_batch_build.argtypes = [c.POINTER(BatchItem), u32, c.POINTER(BuildOpts), vp, hp]
     lib.wm_autotune.restype = c.c_int
@@ -453,6 +455,21 @@ def wm_batch_build(seqs, sigmas, ns=None, tau: int = 0, flags: int = 0, stream=N
     _check(load_library().wm_batch_build(items, m, ctypes.byref(o), _stream_ptr(stream), outs),
            "wm_batch_build")
     return [Handle(ctypes.c_void_p(outs[i])) for i in range(m)]
+
+
+def dd_merge(parts, flags: int = 0, stream=None) -> Handle:
+    """The structure of the concatenation of consecutive pieces of one
+    sequence from the pieces' structures (all wavelet matrices or all
+    balanced wavelet trees, same sigma): domain-decomposition merge."""
+    r = len(parts)
+    arr = (ctypes.c_void_p * max(r, 1))()
+    for i, p in enumerate(parts):
+        arr[i] = p._live()
+    h = ctypes.c_void_p()
+    o = _opts(0, 0, flags)
+    _check(load_library().wt_dd_merge(arr, r, ctypes.byref(o), _stream_ptr(stream),
+                                       ctypes.byref(h)), "wt_dd_merge")
+    return Handle(h)
 
 
 def wm_autotune(seq, sigma: int, n: int | None = None, stream=None):

@@ -17,7 +17,8 @@ INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libwavelet.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["build.cu", "dirq.cu", "api.cu", "huffman.cpp", "noalloc.cu", "batch.cu", "server.cu"]
+SOURCES = ["build.cu", "dirq.cu", "api.cu", "huffman.cpp", "noalloc.cu", "batch.cu", "server.cu",
+           "ddmerge.cu"]
 
 
 def nvcc() -> str:

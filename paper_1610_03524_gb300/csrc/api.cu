@@ -187,6 +187,38 @@ wt_status rs_build(const uint64_t* d_bits, uint64_t nbits, const wt_build_opts* 
   return finish(h, s, out);
 }
 
+wt_status wt_dd_merge(const wt_handle* parts, uint32_t r, const wt_build_opts* opts,
+                      wt_stream stream, wt_handle* out) {
+  if (!out) return WT_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (!parts || r == 0) return WT_ERR_INVALID_ARG;
+  wt_status s = check_opts(opts);
+  if (s != WT_OK) return s;
+  const wt_struct* p0 = parts[0];
+  if (!p0 || (p0->kind != WT_KIND_WM && p0->kind != WT_KIND_WT)) return WT_ERR_INVALID_ARG;
+  uint64_t n = 0;
+  for (uint32_t p = 0; p < r; p++) {
+    wt_struct* q = parts[p];
+    if (!q || q->kind != p0->kind || q->sigma != p0->sigma || q->L != p0->L || q->bpe != 1 ||
+        (q->flags & WT_FLAG_NO_DIRECTORY))
+      return WT_ERR_INVALID_ARG;
+    s = sync_handle(q);  // the parts' bits, directories and zero counts are final
+    if (s != WT_OK) return s;
+    n += q->n;
+  }
+  // node tables of R x 2^L entries; 40-bit offsets as for every build
+  if (p0->L > 20 || ((uint64_t)r << p0->L) > ((uint64_t)1 << 26)) return WT_ERR_UNSUPPORTED;
+  if (n >= ((uint64_t)1 << 40)) return WT_ERR_UNSUPPORTED;
+  wt_struct* h = nullptr;
+  s = new_handle(stream, n, p0->sigma, &h);
+  if (s != WT_OK) return s;
+  h->flags = opts ? opts->flags : 0u;
+  h->kind = p0->kind;
+  h->L = h->levels = p0->L;
+  s = dd_merge(parts, r, h);
+  return finish(h, s, out);
+}
+
 wt_status wt_access(wt_handle h, const uint64_t* d_i, uint64_t q, uint64_t* d_out,
                     wt_stream stream) {
   if (!h || (q && (!d_i || !d_out))) return WT_ERR_INVALID_ARG;

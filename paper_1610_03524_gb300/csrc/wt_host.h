@@ -143,6 +143,9 @@ wt_status launch_query_multi(wt_struct* const* hs, uint32_t nh, const uint32_t* 
 int tuned_tau(uint32_t L, uint64_t n);
 // bytes a batched wavelet-matrix build keeps for one sequence
 uint64_t wm_resident_bytes(uint64_t n, uint32_t sigma);
+// domain-decomposition merge of the structures of consecutive parts into
+// h (kind, L, levels, n, sigma, flags set)
+wt_status dd_merge(wt_struct* const* parts, uint32_t R, wt_struct* h);
 // final status of the m handles of one batched build (after its stream is
 // synchronised), read with one copy of the batch's error words
 void batch_status(wt_handle* hs, uint32_t m, wt_status* st);
