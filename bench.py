@@ -51,7 +51,8 @@ def parse():
     ap.add_argument("--cpu-log2n", type=int, default=24, help="oracle sample length 2^k")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle baseline leg")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--workload", choices=["wm", "batch", "serve", "genome", "huff", "select"],
+    ap.add_argument("--workload", choices=["wm", "batch", "serve", "genome", "huff", "select",
+                                           "ddmerge"],
                     default="wm",
                     help="wm: the headline wavelet-matrix build (default); batch: 4096 "
                          "wavelet matrices, batched vs plain launches; serve: Poisson "
@@ -753,6 +754,68 @@ def run_select(args, wt):
           results=res, cpu_baseline=cpu)
 
 
+def run_ddmerge(args, wt):
+    """Domain decomposition (Section 4.2) of the headline sequence: the
+    wavelet matrix of n = 2^30 uint16 Zipf(1.1) over 2^16 built as 8
+    consecutive pieces and merged, against one build of the whole.  The merge
+    reads every piece's bits and writes the whole's once: 2 n L / 8 bytes."""
+    import numpy as np
+    import torch
+    import synth
+    n, R = 1 << args.log2n, 8
+    L = 16
+    pin = torch.empty(n, dtype=torch.int16).pin_memory()
+    synth.zipf(SEED, n, SIGMA, ZIPF_S, 2, addr=pin.data_ptr())
+    d = pin.to("cuda")
+    del pin
+    cut = [i * n // R for i in range(R + 1)]
+    pieces_t = [d[a:b] for a, b in zip(cut[:-1], cut[1:])]
+
+    def timed(fn, reps):
+        ts = []
+        for _ in range(reps):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            fn()
+            e1.record()
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return statistics.median(ts[args.warmup:]) if len(ts) > args.warmup else ts[-1]
+
+    reps = args.warmup + args.steps
+    single = timed(lambda: wt.wm_build(d, SIGMA).free(), reps)
+
+    def build_pieces():
+        return [wt.wm_build(x, SIGMA) for x in pieces_t]
+
+    piece_ms = timed(lambda: [h.free() for h in build_pieces()], reps)
+    parts = build_pieces()
+    for h in parts:
+        h.sync()
+    merge_nodir = timed(lambda: wt.dd_merge(parts, flags=wt.FLAG_NO_DIRECTORY).free(), reps)
+    merge_ms = timed(lambda: wt.dd_merge(parts).free(), reps)
+    for h in parts:
+        h.free()
+    alg = 2 * n * L / 8
+    peak, peak_kind = measured_peak_hbm()
+    ach = alg / (merge_nodir * 1e-3) / 1e9
+    tot = piece_ms + merge_ms
+    cfg = {"workload": f"wavelet matrix of n=2^{args.log2n} uint16 Zipf(1.1) sigma=2^16 as {R} "
+                       f"pieces built apart and merged (domain decomposition), vs one build",
+           "pieces": R, "l2": "inputs larger than L2; no flush needed"}
+    _line(args, "Gsymbol-levels/s (pieces + merge, with directories)", n * L / tot / 1e6,
+          "Gsymbol-levels/s", tot, cfg,
+          results={"single_build_ms": single, "pieces_build_ms": piece_ms,
+                   "merge_ms_with_directories": merge_ms, "merge_ms_bits_only": merge_nodir},
+          roofline={"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
+                    "frac": ach / peak, "traffic": None,
+                    "kernel": "wt_dd_merge without directories (node sizes, plan, k_dd_copy)",
+                    "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)"
+                    if peak_kind == "measured" else "fallback",
+                    "algorithmic_bytes_per_launch": alg})
+
+
 def synth_seed(k):
     import synth
     return synth.SEED_BASE + k
@@ -875,6 +938,8 @@ def run_other(args):
         run_serve(args, wt)
     elif args.workload == "select":
         run_select(args, wt)
+    elif args.workload == "ddmerge":
+        run_ddmerge(args, wt)
     else:
         run_tree(args, wt)
     return 0

@@ -277,7 +277,7 @@ wt_status wt_select(wt_handle h, const uint32_t* d_c, const uint64_t* d_k, uint6
  * built with the same sigma and with directories; *out receives the
  * structure of the concatenation S_0 S_1 ... S_{r-1}, bit for bit the one a
  * single build of it gives, with its own directories (opts->flags may ask
- * for WT_FLAG_SELECT_O1).  The parts are read (each is synchronised first)
+ * for WT_FLAG_SELECT_O1, or skip them with WT_FLAG_NO_DIRECTORY).  The parts are read (each is synchronised first)
  * and stay valid.  Limits: ceil(log2 sigma) <= 20 and r * 2^ceil(log2
  * sigma) <= 2^26 (WT_ERR_UNSUPPORTED otherwise). */
 wt_status wt_dd_merge(const wt_handle* parts, uint32_t r, const wt_build_opts* opts,

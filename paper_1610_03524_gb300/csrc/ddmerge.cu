@@ -14,9 +14,10 @@
 //      part's directory at the node's two ends);
 //   2. destination of every (part, node) run: exclusive scan of the node
 //      totals over the nodes of a level, plus the runs of the earlier parts;
-//   3. the runs cut into pieces of at most 2048 bits, one warp per piece:
-//      whole destination words are stored, words shared with a neighbouring
-//      run are ORed into the zeroed level buffer.
+//   3. the runs' destinations cut at multiples of 32768 bits, the run of
+//      every piece written out, then one warp per piece, 16 destination
+//      words per lane: whole words are stored, words shared with a
+//      neighbouring run are ORed into the zeroed level buffer.
 // On one GPU the parts' bits are read in place.  Across GPUs, a rank's runs
 // go to the rank owning their destination positions (the routing is planned
 // in paper_1610_03524_gb300/dist.py).
@@ -42,7 +43,7 @@ uint64_t scan_scratch_pub(uint64_t n);
     }                                                                           \
   } while (0)
 
-constexpr uint32_t DD_PIECE = 2048;  // bits per piece of a run
+constexpr uint32_t DD_PIECE = 32768;  // bits per piece of a run: 16 words per lane
 
 // one level of one part
 struct DdLevel {
@@ -62,6 +63,12 @@ __device__ uint64_t dd_rank0(const DdLevel& v, uint64_t x) {
   const uint32_t rem = (uint32_t)(x & 63);
   if (rem) r += rem - __popcll(v.bits[wend] & ((1ull << rem) - 1ull));
   return r;
+}
+
+// level 0 of every part: one node, the whole part
+__global__ void k_dd_init(const DdLevel* lv, int L, uint32_t R, uint64_t stride, uint64_t* cnt) {
+  const uint32_t p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p < R) cnt[(uint64_t)p * stride] = lv[(uint64_t)p * L].n;
 }
 
 // level l -> l + 1 of every part: sizes and starts of the children of every
@@ -113,51 +120,61 @@ __global__ void k_dd_dest(const uint64_t* cnt, const uint64_t* X, uint32_t R, ui
   for (uint32_t p = 0; p < R; p++) {
     const uint64_t g = (uint64_t)p * stride + i, k = cnt[g];
     dst[g] = d;
-    npc[g] = (k + DD_PIECE - 1) / DD_PIECE;
+    // pieces: the run's destination cut at multiples of DD_PIECE bits
+    npc[g] = k ? ((d % DD_PIECE) + k + DD_PIECE - 1) / DD_PIECE : 0;
     d += k;
   }
 }
 
-// one warp per piece
-__global__ void k_dd_copy(const DdLevel* lv, int L, uint64_t stride, uint64_t nseg,
+// run of every piece: one warp per run writes its index over its pieces
+__global__ void k_dd_map(const uint64_t* PS, uint64_t nseg, uint32_t* map) {
+  const int lane = threadIdx.x & 31;
+  const uint64_t g = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (g >= nseg) return;
+  const uint64_t a = PS[g], b = PS[g + 1];
+  for (uint64_t t = a + lane; t < b; t += 32) map[t] = (uint32_t)g;
+}
+
+// one warp per piece, the grid covering every piece: each warp's reads of
+// its run's table entries are independent of every other warp's
+__global__ void k_dd_copy(const DdLevel* lv, int L, uint64_t stride, const uint32_t* map,
                           const uint64_t* cnt, const uint64_t* cs, const uint64_t* dst,
                           const uint64_t* PS, uint64_t npieces, uint64_t* out,
                           uint64_t out_level_words, uint32_t* err) {
   const int lane = threadIdx.x & 31;
-  const uint64_t w0 = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
-  for (uint64_t j = w0; j < npieces; j += nw) {
-    // run holding piece j: the last g with PS[g] <= j
-    uint64_t lo = 0, hi = nseg - 1;
-    while (lo < hi) {
-      const uint64_t mid = (lo + hi + 1) >> 1;
-      if (PS[mid] <= j) lo = mid;
-      else hi = mid - 1;
-    }
-    const uint64_t g = lo, p = g / stride, i = g - p * stride;
+  const uint64_t j = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (j >= npieces) return;
+  const uint64_t g = map[j];
+  {
+    const uint64_t p = g / stride, i = g - p * stride;
     const int l = dd_level_of(i);
     const DdLevel v = lv[p * L + l];
-    const uint64_t off = (j - PS[g]) * DD_PIECE;
-    const uint64_t len = min((uint64_t)DD_PIECE, cnt[g] - off);
-    const uint64_t S = cs[g] + off;                       // first source bit
-    const uint64_t D = dst[g] + off;                      // first destination bit
+    // piece j - PS[g] of the run: destination bits [D, E) inside one aligned
+    // block of DD_PIECE bits, source bits from S
+    const uint64_t D0 = dst[g], E0 = D0 + cnt[g];
+    const uint64_t blk = (D0 / DD_PIECE + (j - PS[g])) * DD_PIECE;
+    const uint64_t D = max(blk, D0), E = min(blk + DD_PIECE, E0);
+    const uint64_t S = cs[g] + (D - D0);
     uint64_t* const ol = out + (uint64_t)l * out_level_words;
-    const uint64_t dw0 = D >> 6, dw1 = (D + len - 1) >> 6;
-    for (uint64_t w = dw0 + lane; w <= dw1; w += 32) {
-      const uint64_t a = max(w << 6, D), b = min((w << 6) + 64, D + len);
-      const uint64_t sp = S + (a - D), nb = b - a;
-      const uint64_t sw = sp >> 6;
-      const uint32_t sh = (uint32_t)(sp & 63);
-      if (sp + nb > v.n || w >= out_level_words) {  // never for consistent sizes
-        atomicOr(err, ERR_INTERNAL);
-        continue;
+#pragma unroll
+    for (int u = 0; u < (int)(DD_PIECE / 2048); u++) {
+      const uint64_t w = (blk >> 6) + 32 * u + lane;  // destination words, 32 apart
+      if ((w << 6) < E && (w << 6) + 64 > D) {
+        const uint64_t a = max(w << 6, D), b = min((w << 6) + 64, E);
+        const uint64_t sp = S + (a - D), nb = b - a;
+        const uint64_t sw = sp >> 6;
+        const uint32_t sh = (uint32_t)(sp & 63);
+        if (sp + nb > v.n || w >= out_level_words) {  // never for consistent sizes
+          atomicOr(err, ERR_INTERNAL);
+          continue;
+        }
+        uint64_t x = v.bits[sw] >> sh;
+        if (sh && ((sp + nb - 1) >> 6) > sw) x |= v.bits[sw + 1] << (64 - sh);
+        if (nb < 64) x &= (1ull << nb) - 1ull;
+        const uint32_t at = (uint32_t)(a - (w << 6));
+        if (nb == 64) ol[w] = x;
+        else atomicOr((unsigned long long*)(ol + w), (unsigned long long)(x << at));
       }
-      uint64_t x = v.bits[sw] >> sh;
-      if (sh && ((sp + nb - 1) >> 6) > sw) x |= v.bits[sw + 1] << (64 - sh);
-      if (nb < 64) x &= (1ull << nb) - 1ull;
-      const uint32_t at = (uint32_t)(a - (w << 6));
-      if (nb == 64) ol[w] = x;
-      else atomicOr((unsigned long long*)(ol + w), (unsigned long long)(x << at));
     }
   }
 }
@@ -206,14 +223,11 @@ wt_status dd_merge(wt_struct* const* parts, uint32_t R, wt_struct* h) {
   CK(dmalloc((void**)&PS, (nseg + 1) * 8, st));
   CK(dmalloc((void**)&scr, scan_scratch_pub(std::max(nseg, stride)) * 8, st));
   CK(cudaMemcpyAsync(d_lv, hl.data(), hl.size() * sizeof(DdLevel), cudaMemcpyHostToDevice, st));
-  // level 0: one node per part, the whole part
-  {
-    std::vector<uint64_t> c0(nseg, 0);
-    for (uint32_t p = 0; p < R; p++) c0[(size_t)p * stride] = parts[p]->n;
-    CK(cudaMemcpyAsync(cnt, c0.data(), nseg * 8, cudaMemcpyHostToDevice, st));
-    CK(cudaMemsetAsync(cs, 0, nseg * 8, st));
-    CK(cudaStreamSynchronize(st));  // c0 is pageable and local
-  }
+  // level 0: one node per part, the whole part (the part sizes ride in the
+  // level table)
+  CK(cudaMemsetAsync(cs, 0, nseg * 8, st));
+  k_dd_init<<<(R + 255) / 256, 256, 0, st>>>(d_lv, L, R, stride, cnt);
+  count_launch();
   for (int l = 0; l + 1 < L; l++) {
     const uint64_t th = (uint64_t)R << l;
     k_dd_children<<<(unsigned)((th + 255) / 256), 256, 0, st>>>(d_lv, L, l, R, wm, stride, cnt, cs);
@@ -233,10 +247,14 @@ wt_status dd_merge(wt_struct* const* parts, uint32_t R, wt_struct* h) {
     CK(cudaStreamSynchronize(st));
   }
   if (s == WT_OK && npieces) {
-    const uint64_t warps = std::min<uint64_t>(npieces, (uint64_t)num_sms() * 64);
-    k_dd_copy<<<(unsigned)((warps * 32 + 255) / 256), 256, 0, st>>>(
-        d_lv, L, stride, nseg, cnt, cs, dst, PS, npieces, h->d_bits, W, h->d_err);
+    uint32_t* map;
+    CK(dmalloc((void**)&map, npieces * 4, st));
+    k_dd_map<<<(unsigned)((nseg * 32 + 255) / 256), 256, 0, st>>>(PS, nseg, map);
     count_launch();
+    k_dd_copy<<<(unsigned)((npieces * 32 + 255) / 256), 256, 0, st>>>(
+        d_lv, L, stride, map, cnt, cs, dst, PS, npieces, h->d_bits, W, h->d_err);
+    count_launch();
+    dfree(map, st);
   }
   cudaError_t e = cudaGetLastError();
   dfree(d_lv, st);
@@ -250,6 +268,7 @@ wt_status dd_merge(wt_struct* const* parts, uint32_t R, wt_struct* h) {
   dfree(scr, st);
   if (s != WT_OK) return s;
   if (e != cudaSuccess) return WT_ERR_CUDA;
+  if (h->flags & WT_FLAG_NO_DIRECTORY) return WT_OK;
   return build_directories(h);
 }
 
