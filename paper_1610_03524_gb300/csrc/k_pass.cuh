@@ -131,7 +131,8 @@ struct PassSmem {
   static constexpr int TW = T / 32;
   static constexpr size_t off_buf = 0;                                        // 2 x T elements
   static constexpr size_t off_lbits = off_buf + 2 * (size_t)T * sizeof(E);   // row words per level
-  static constexpr size_t off_pb1 = off_lbits + (size_t)TAU_MAX * TW * 8;    // second digit bits
+  static constexpr int TWS = TW + 2;  // row words per level, two zero words after them
+  static constexpr size_t off_pb1 = off_lbits + (size_t)TAU_MAX * TWS * 8;   // second digit bits
   static constexpr size_t off_ccnt = off_pb1 + (DIG ? (size_t)(TAU_MAX / 2) * TW * 4 : 0);
   static constexpr size_t off_cstart = off_ccnt + (size_t)NCLS * 4;
   static constexpr size_t off_excnt = off_cstart + (size_t)NCLS * 4;  // 8-aligned
@@ -154,6 +155,7 @@ __global__ void __launch_bounds__(NT + 32, WT_PASS_MIN_CTAS) k_pass(const __grid
   __shared__ PassParams s_P;
   const PassParams& P = BATCH ? s_P : P0;
   constexpr int W = NT / 32, PW = T / W, EPW = PW / 32, TW = T / 32, NB = NT + 32, CW = W;
+  constexpr int TWS = TW + 2;
   static_assert(EPW >= 1 && EPW <= 32, "iterations per warp must fit a warp");
   static_assert(T % 64 == 0 && NT >= (1 << TAU_MAX), "tile geometry");
   using SM = PassSmem<E, T, NT, DIG>;
@@ -185,6 +187,9 @@ __global__ void __launch_bounds__(NT + 32, WT_PASS_MIN_CTAS) k_pass(const __grid
   if (BATCH && tid == 0) s_P = P0;
   const uint32_t lt = lanemask_lt();
   const int wbase = warp * PW;
+  // the two words after each level's rows stay zero (the writer reads past
+  // a level's last row without a bounds check)
+  for (int i = tid; i < 2 * TAU_MAX; i += NB) rowq[(i >> 1) * TWS + TW + (i & 1)] = make_uint2(0u, 0u);
 
   auto bar_workers = [&]() { asm volatile("bar.sync 1, %0;" ::"n"(NT) : "memory"); };
   // block-wide exclusive scan of one int per thread
@@ -355,7 +360,7 @@ __global__ void __launch_bounds__(NT + 32, WT_PASS_MIN_CTAS) k_pass(const __grid
           E* dst = (j & 1) ? bufA : bufB;
           const uint32_t m = 1u << (P.rbits - 1 - j);
           const bool two = DIG && (((P.a + j) & 1) == 0) && (P.a + j + 1 < P.L);
-          uint2* const Rw = rowq + j * TW + warp * EPW;
+          uint2* const Rw = rowq + j * TWS + warp * EPW;
 #if WT_PASS_KEEP_X
           uint32_t xr[EPW];
 #endif
@@ -413,12 +418,15 @@ __global__ void __launch_bounds__(NT + 32, WT_PASS_MIN_CTAS) k_pass(const __grid
     // 64 local bits of level j starting at local bit position bp
     auto get64 = [&](int j, int bp) -> uint64_t {
       if (!DIG) {
-        const uint32_t lo = get32q<TW>(rowq + j * TW, bp);
-        const uint32_t hi = get32q<TW>(rowq + j * TW, bp + 32);
+        // bp >= 0 and bp < T: words bp/32 .. bp/32 + 2 exist (zero pads)
+        const uint2* r = rowq + j * TWS + (bp >> 5);
+        const int o = bp & 31;
+        const uint32_t w0 = r[0].x, w1 = r[1].x, w2 = r[2].x;
+        const uint32_t lo = __funnelshift_r(w0, w1, o), hi = __funnelshift_r(w1, w2, o);
         return ((uint64_t)hi << 32) | lo;
       }
       const int e = bp >> 1;
-      const uint32_t b0 = get32q<TW>(rowq + j * TW, e);
+      const uint32_t b0 = get32q<TW>(rowq + j * TWS, e);
       if (P.a + j + 1 < P.L) {
         const uint32_t b1 = get32<TW>(pb1 + (j >> 1) * TW, e);
         return (spread32(b0) << 1) | spread32(b1);
@@ -450,37 +458,56 @@ __global__ void __launch_bounds__(NT + 32, WT_PASS_MIN_CTAS) k_pass(const __grid
     const int wex = block_scan(nw, wtot);
     if (tid < ntl) wst[tid] = wex;
     __syncthreads();
-    // first word of each level (classes of level j are 2^j-1 .. 2^(j+1)-2)
-    int lvw[TAU_MAX];
-#pragma unroll
-    for (int j = 1; j < TAU_MAX; j++) lvw[j] = j < t ? wst[(1 << j) - 1] : 0x7fffffff;
-    for (int x = tid; x < wtot; x += NB) {
-      int j = 0;
-#pragma unroll
-      for (int j2 = 1; j2 < TAU_MAX; j2++) j += lvw[j2] <= x ? 1 : 0;
-      int lo = (1 << j) - 1, hi = (2 << j) - 2;
-      while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (wst[mid] <= x) lo = mid;
-        else hi = mid - 1;
+    // each thread takes consecutive words of the flattened list: the class of
+    // its first word by a search, the next classes by stepping (classes
+    // without words have empty ranges and are stepped over)
+    {
+      const int per = (wtot + NB - 1) / NB;
+      const int x0 = tid * per, x1 = min(wtot, x0 + per);
+      int ci = 0;
+      if (x0 < x1) {
+        int lo = 0, hi = ntl - 1;
+        while (lo < hi) {
+          const int mid = (lo + hi + 1) >> 1;
+          if (wst[mid] <= x0) lo = mid;
+          else hi = mid - 1;
+        }
+        ci = lo;
       }
-      const int ci = lo;
-      const uint64_t nlb = s_lvl_bits[j];
-      uint64_t* const lb = s_lvl_ptr[j];
-      const uint64_t G0 = cls_g0[ci];
-      const uint64_t G1 = G0 + (uint64_t)ccnt[ci] * bpe;
-      const uint64_t w = (G0 >> 6) + (uint64_t)(x - wst[ci]);
-      const uint64_t wb = w << 6;
-      const uint64_t lo2 = wb > G0 ? wb : G0;
-      const uint64_t hi2 = (wb + 64 < G1) ? wb + 64 : G1;
-      uint64_t v = get64(j, (int)cstart[ci] * bpe + (int)(lo2 - G0));
-      const int nb = (int)(hi2 - lo2);
-      if (nb < 64) v &= (1ull << nb) - 1ull;
-      v <<= (int)(lo2 - wb);
-      const uint64_t wend = (wb + 64 < nlb) ? wb + 64 : nlb;
-      if (wb >= nlb) atomicOr(P.err, ERR_INTERNAL);  // never for consistent tables
-      else if (G0 <= wb && G1 >= wend) lb[w] = v;
-      else atomicOr((unsigned long long*)(lb + w), (unsigned long long)v);
+      int nxt = ci + 1 < ntl ? wst[ci + 1] : wtot;
+      int k = x0 - wst[ci];  // word of the run
+      // the run: level j, first global bit G0, length nbits, first tile bit lb0
+      int j = 31 - __clz(ci + 1);
+      uint64_t G0 = cls_g0[ci];
+      int nbits = (int)ccnt[ci] * bpe, lb0 = (int)cstart[ci] * bpe;
+      for (int x = x0; x < x1; x++, k++) {
+        if (x >= nxt) {
+          do {
+            ci++;
+            nxt = ci + 1 < ntl ? wst[ci + 1] : wtot;
+          } while (x >= nxt);
+          k = 0;
+          j = 31 - __clz(ci + 1);
+          G0 = cls_g0[ci];
+          nbits = (int)ccnt[ci] * bpe;
+          lb0 = (int)cstart[ci] * bpe;
+        }
+        const int g0 = (int)(G0 & 63);
+        const int lo = k ? 0 : g0;            // first bit of the word that is the run's
+        const int r0 = 64 * k + lo - g0;      // its index in the run
+        const int nb = min(64 - lo, nbits - r0);
+        uint64_t v = get64(j, lb0 + r0);
+        if (nb < 64) v &= (1ull << nb) - 1ull;
+        v <<= lo;
+        const uint64_t w = (G0 >> 6) + (uint64_t)k;
+        const uint64_t nlb = s_lvl_bits[j];
+        uint64_t* const lb = s_lvl_ptr[j];
+        // stored when the run holds the whole word, or its start and the
+        // level's end; else shared with another run
+        if ((w << 6) >= nlb) atomicOr(P.err, ERR_INTERNAL);  // never for consistent tables
+        else if (lo == 0 && (nb == 64 || (w << 6) + nb == nlb)) lb[w] = v;
+        else atomicOr((unsigned long long*)(lb + w), (unsigned long long)v);
+      }
     }
     __syncthreads();
 
