@@ -120,81 +120,23 @@ __device__ __forceinline__ void for_each_symbol(const void* seq, uint64_t n, uin
   for (uint64_t i = nvec * PER + gtid; i < n; i += gstride) f((uint32_t)s[i]);
 }
 
-// Per-pass digit histograms (wavelet matrix).  Pass g covers levels
-// a = g*tau .. a+t-1; its digit is the t bits below level a.  The counts are
-// kept by digit value d; the plan reads them by the reversed digit (Section
-// 4.3: the sort key of a pass is the reverse of its tau bits).
-struct HistGeom {
-  int shf[32];
-  uint32_t mask[32];
-  int off[33];
-  int G;
-};
-
-__host__ HistGeom hist_geom(int L, int tau) {
-  HistGeom g;
-  memset(&g, 0, sizeof(g));
-  int o = 0;
-  for (int a = 0; a < L && g.G < 32; a += tau, g.G++) {
-    const int t = std::min(tau, L - a);
-    g.shf[g.G] = L - a - t;
-    g.mask[g.G] = (1u << t) - 1u;
-    g.off[g.G] = o;
-    o += 1 << t;
-  }
-  g.off[g.G] = o;
-  return g;
-}
-
-// NG > 0: the pass count is a compile-time constant and the geometry stays in
-// registers; NG == 0: any pass count, geometry read from shared memory.
-template <int WB, int NG>
-__global__ void k_hist_digits(const void* seq, uint64_t n, uint32_t sigma,
-                              const __grid_constant__ HistGeom geo, uint64_t* hist, uint32_t* err) {
-  // at most 1024 bins in total: G passes of 2^t bins, G*2^tau <= 1024 for tau <= 8
-  __shared__ uint32_t sh[1024];
-  const int tot = geo.off[geo.G];
-  for (int i = threadIdx.x; i < tot; i += blockDim.x) sh[i] = 0;
-  __syncthreads();
-  bool bad = false;
-  for_each_symbol<WB>(seq, n, (uint64_t)blockIdx.x * blockDim.x + threadIdx.x,
-                      (uint64_t)gridDim.x * blockDim.x, [&](uint32_t x) {
-                        bad |= x >= sigma;
-                        if (NG > 0) {
-#pragma unroll
-                          for (int g = 0; g < NG; g++)
-                            atomicAdd(&sh[geo.off[g] + ((x >> geo.shf[g]) & geo.mask[g])], 1u);
-                        } else {
-                          for (int g = 0; g < geo.G; g++)
-                            atomicAdd(&sh[geo.off[g] + ((x >> geo.shf[g]) & geo.mask[g])], 1u);
-                        }
-                      });
-  if (bad) atomicOr(err, ERR_SYMBOL);
-  __syncthreads();
-  for (int i = threadIdx.x; i < tot; i += blockDim.x)
-    if (sh[i]) atomicAdd((unsigned long long*)&hist[i], (unsigned long long)sh[i]);
-}
-
-// The same histograms, walked tile by tile (tiles of PASS_T symbols, as the
-// first partition pass sees them), also writing each tile's counts of the
-// first pass's reversed digit: the first pass's per-tile counts come with
-// the one read of the sequence.
-template <int WB, int NG>
+// Digit counts of the wavelet matrix's passes: pass g covers levels
+// a = g*tau .. a+t-1; its digit is the t bits below level a, its sort key the
+// digit reversed (Section 4.3: the reverse of the tau bits).
+// Validation and the first pass's digit counts, walked tile by tile (tiles
+// of PASS_T symbols, as the first partition pass sees them): each tile's
+// counts of the first pass's reversed digit, and their sums, the first
+// pass's histogram, from the one read of the sequence.  The later passes
+// take their counts from their own tiles (k_tile_counts).
+template <int WB>
 __global__ void __launch_bounds__(256) k_hist_digits_tiles(const void* seq, uint64_t n,
-                                                           uint32_t sigma,
-                                                           const __grid_constant__ HistGeom geo,
-                                                           int L, int t0, uint64_t* hist,
-                                                           uint32_t* err, uint32_t* tcnt,
-                                                           uint32_t tcs) {
+                                                           uint32_t sigma, int L, int t0,
+                                                           uint64_t* hist, uint32_t* err,
+                                                           uint32_t* tcnt, uint32_t tcs) {
   using T = typename std::conditional<WB == 1, uint8_t,
                                       typename std::conditional<WB == 2, uint16_t, uint32_t>::type>::type;
-  // the first pass's digits are counted per tile only (its global counts
-  // are the sums of the tile counts); the other passes' in sh
-  __shared__ uint32_t sh[1024];
   __shared__ uint32_t th[2][TC_STRIDE];
-  const int tot = geo.off[geo.G];
   const int tid = threadIdx.x;
-  for (int i = tid; i < tot; i += blockDim.x) sh[i] = 0;
   th[0][tid] = 0;
   th[1][tid] = 0;
   uint32_t own = 0;  // this thread's reversed digit, summed over the block's tiles
@@ -208,13 +150,6 @@ __global__ void __launch_bounds__(256) k_hist_digits_tiles(const void* seq, uint
   int buf = 0;
   auto count = [&](uint32_t x) {
     bad |= x >= sigma;
-    if (NG > 0) {
-#pragma unroll
-      for (int g = 1; g < NG; g++) atomicAdd(&sh[geo.off[g] + ((x >> geo.shf[g]) & geo.mask[g])], 1u);
-    } else {
-      for (int g = 1; g < geo.G; g++)
-        atomicAdd(&sh[geo.off[g] + ((x >> geo.shf[g]) & geo.mask[g])], 1u);
-    }
     atomicAdd(&th[buf][(__brev(x) >> rsh) & rmask], 1u);
   };
   for (uint64_t ti = blockIdx.x; ti < ntiles; ti += gridDim.x) {
@@ -254,22 +189,8 @@ __global__ void __launch_bounds__(256) k_hist_digits_tiles(const void* seq, uint
   // first pass: digit value = the reverse of this thread's t0-bit key
   if (tid <= (int)rmask && own)
     atomicAdd((unsigned long long*)&hist[__brev((uint32_t)tid) >> (32 - t0)], (unsigned long long)own);
-  __syncthreads();
-  for (int i = geo.off[1]; i < tot; i += blockDim.x)
-    if (i + tid < tot && sh[i + tid]) atomicAdd((unsigned long long*)&hist[i + tid], (unsigned long long)sh[i + tid]);
 }
 
-template <int WB>
-static void launch_hist_digits_w(const void* seq, uint64_t n, uint32_t sigma, const HistGeom& geo,
-                                 uint64_t* hist, uint32_t* err, uint32_t blocks, cudaStream_t st) {
-  switch (geo.G) {
-    case 1: k_hist_digits<WB, 1><<<blocks, 512, 0, st>>>(seq, n, sigma, geo, hist, err); break;
-    case 2: k_hist_digits<WB, 2><<<blocks, 512, 0, st>>>(seq, n, sigma, geo, hist, err); break;
-    case 3: k_hist_digits<WB, 3><<<blocks, 512, 0, st>>>(seq, n, sigma, geo, hist, err); break;
-    case 4: k_hist_digits<WB, 4><<<blocks, 512, 0, st>>>(seq, n, sigma, geo, hist, err); break;
-    default: k_hist_digits<WB, 0><<<blocks, 512, 0, st>>>(seq, n, sigma, geo, hist, err); break;
-  }
-}
 
 // Full symbol histogram (balanced / Huffman / 4-ary trees).
 // (large alphabets: block b adds into copy b % ncopy of the histogram, at
@@ -499,38 +420,52 @@ static std::vector<PassGeom> make_passes(int L, int tau, int first_w) {
 // reversed digit r: prefix sums over the histogram, read at digit rev(r),
 // folded mod 2^j), and
 // the zero count of every level (the class-0 size after its split).
-__device__ void plan_wm_classes(const uint64_t* hist, int L, int tau, int G, uint64_t* cls,
-                                uint64_t* zeros) {
+// One pass (levels a .. a+t-1): counts of the t-bit digits, given by digit
+// value (by_key = 0) or by reversed digit, the key of the splits (by_key = 1).
+__device__ void plan_wm_pass(const uint64_t* h, int by_key, int a, int t, uint64_t* cls,
+                             uint64_t* zeros) {
   __shared__ uint64_t cnt[512];
   __shared__ uint64_t st[512];
+  for (int j = 0; j <= t; j++) {
+    const int nk = 1 << j;
+    for (int k = threadIdx.x; k < nk; k += blockDim.x) {
+      uint64_t s = 0;
+      for (int r = k; r < (1 << t); r += nk) s += h[by_key ? r : rev_bits((uint32_t)r, t)];
+      cnt[k] = s;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      uint64_t acc = 0;
+      for (int k = 0; k < nk; k++) {
+        st[k] = acc;
+        acc += cnt[k];
+      }
+      st[nk] = acc;
+    }
+    __syncthreads();
+    uint64_t* c = cls + (nk - 1 + j);
+    for (int k = threadIdx.x; k <= nk; k += blockDim.x) c[k] = st[k];
+    if (j >= 1 && threadIdx.x == 0) zeros[a + j - 1] = st[nk >> 1];
+    __syncthreads();
+  }
+}
+
+__device__ void plan_wm_classes(const uint64_t* hist, int L, int tau, int G, uint64_t* cls,
+                                uint64_t* zeros) {
   int hoff = 0, coff = 0;
   for (int g = 0; g < G; g++) {
     const int a = g * tau, t = min(tau, L - a);
-    for (int j = 0; j <= t; j++) {
-      const int nk = 1 << j;
-      for (int k = threadIdx.x; k < nk; k += blockDim.x) {
-        uint64_t s = 0;
-        for (int r = k; r < (1 << t); r += nk) s += hist[hoff + rev_bits((uint32_t)r, t)];
-        cnt[k] = s;
-      }
-      __syncthreads();
-      if (threadIdx.x == 0) {
-        uint64_t acc = 0;
-        for (int k = 0; k < nk; k++) {
-          st[k] = acc;
-          acc += cnt[k];
-        }
-        st[nk] = acc;
-      }
-      __syncthreads();
-      uint64_t* c = cls + coff + (nk - 1 + j);
-      for (int k = threadIdx.x; k <= nk; k += blockDim.x) c[k] = st[k];
-      if (j >= 1 && threadIdx.x == 0) zeros[a + j - 1] = st[nk >> 1];
-      __syncthreads();
-    }
+    plan_wm_pass(hist + hoff, 0, a, t, cls + coff, zeros);
     hoff += 1 << t;
     coff += (2 << t) + t + 1;
   }
+}
+
+// the plan of one later pass from the totals of its tiles' digit counts
+// (indexed by reversed digit: the last row of the scanned chunk table)
+__global__ void k_plan_wm_pass(const uint64_t* totals, int a, int t, uint64_t* cls,
+                               uint64_t* zeros) {
+  plan_wm_pass(totals, 1, a, t, cls, zeros);
 }
 
 // Wavelet-matrix plan, one block: class starts and zero counts; reset of the
@@ -737,10 +672,19 @@ __global__ void __launch_bounds__(32) k_tile_scan_top(uint64_t* tchunk, uint32_t
   if (lane == 0) tchunk[(uint64_t)nchunk * S + r] = carry;
 }
 
-// tcnt_pre: the tiles' digit counts when already taken (else counted here)
+// A wavelet-matrix pass planned from its own tiles' digit counts: class
+// starts of its levels into cls, their zero counts into zeros.
+struct PassPlan {
+  uint64_t* cls;
+  uint64_t* zeros;
+};
+
+// tcnt_pre: the tiles' digit counts when already taken (else counted here);
+// plan: the pass's plan, made here from the totals of those counts
 template <typename E, bool DIG, bool BATCH = false>
 static wt_status launch_pass_t(const PassParams& P, uint64_t max_tiles, const wt_build_opts* o,
-                               cudaStream_t st, uint32_t* tcnt_pre = nullptr) {
+                               cudaStream_t st, uint32_t* tcnt_pre = nullptr,
+                               const PassPlan* plan = nullptr) {
   using SM = PassSmem<E, PT, PNT, DIG>;
   auto kern = k_pass<E, PT, PNT, DIG, BATCH>;
   static bool attr = false;
@@ -774,6 +718,11 @@ static wt_status launch_pass_t(const PassParams& P, uint64_t max_tiles, const wt
   count_launch();
   k_tile_scan_top<<<Q.tcs, 32, 0, st>>>(tchunk, nchunk);
   count_launch();
+  if (plan) {
+    k_plan_wm_pass<<<1, 256, 0, st>>>(tchunk + (uint64_t)nchunk * Q.tcs, P.a, P.t, plan->cls,
+                                      plan->zeros);
+    count_launch();
+  }
   Q.tcnt = tcnt;
   Q.tchunk = tchunk;
   Prof& pf = prof();
@@ -799,11 +748,11 @@ static wt_status launch_pass_t(const PassParams& P, uint64_t max_tiles, const wt
 
 static wt_status launch_pass(const PassParams& P, bool wide, bool dig, uint64_t max_tiles,
                              const wt_build_opts* o, cudaStream_t st,
-                             uint32_t* tcnt_pre = nullptr) {
-  if (dig) return wide ? launch_pass_t<uint32_t, true>(P, max_tiles, o, st, tcnt_pre)
-                       : launch_pass_t<uint16_t, true>(P, max_tiles, o, st, tcnt_pre);
-  return wide ? launch_pass_t<uint32_t, false>(P, max_tiles, o, st, tcnt_pre)
-              : launch_pass_t<uint16_t, false>(P, max_tiles, o, st, tcnt_pre);
+                             uint32_t* tcnt_pre = nullptr, const PassPlan* plan = nullptr) {
+  if (dig) return wide ? launch_pass_t<uint32_t, true>(P, max_tiles, o, st, tcnt_pre, plan)
+                       : launch_pass_t<uint16_t, true>(P, max_tiles, o, st, tcnt_pre, plan);
+  return wide ? launch_pass_t<uint32_t, false>(P, max_tiles, o, st, tcnt_pre, plan)
+              : launch_pass_t<uint16_t, false>(P, max_tiles, o, st, tcnt_pre, plan);
 }
 
 // Batched wavelet matrices: one launch over the tiles of every sequence in
@@ -912,34 +861,28 @@ wt_status build_wm(const void* d_seq, uint64_t n, uint32_t sigma, int w, const w
   CK(cudaMemcpyAsync(d_off, h->level_off.data(), (L + 1) * 8, cudaMemcpyHostToDevice, st));
   CK(cudaMemcpyAsync(d_len, h->level_len.data(), L * 8, cudaMemcpyHostToDevice, st));
   CK(cudaMemsetAsync(hist, 0, nh * 8, st));
-  // digit histograms of every pass, and the first pass's per-tile counts
+  // the first pass's digit histogram and per-tile counts (with validation)
   uint32_t* tcnt0;
   const uint64_t ntiles0 = (n + PASS_T - 1) / PASS_T;
   TRY(wk.get(&tcnt0, (size_t)ntiles0 * tc_stride(ps[0].t)));
   {
     const uint32_t blocks = (uint32_t)std::min<uint64_t>((uint64_t)num_sms() * 8, ntiles0);
-    const HistGeom geo = hist_geom(L, tau);
     const int t0 = ps[0].t;
-#define WT_HT(WB, NG)                                                                       \
-  k_hist_digits_tiles<WB, NG><<<blocks, 256, 0, st>>>(d_seq, n, sigma, geo, L, t0, hist, \
-                                                      h->d_err, tcnt0, tc_stride(t0))
-#define WT_HTW(WB)                                 \
-  switch (geo.G) {                                 \
-    case 1: WT_HT(WB, 1); break;                   \
-    case 2: WT_HT(WB, 2); break;                   \
-    case 3: WT_HT(WB, 3); break;                   \
-    case 4: WT_HT(WB, 4); break;                   \
-    default: WT_HT(WB, 0); break;                  \
-  }
-    if (w == 1) { WT_HTW(1) }
-    else if (w == 2) { WT_HTW(2) }
-    else { WT_HTW(4) }
-#undef WT_HTW
-#undef WT_HT
+    if (w == 1)
+      k_hist_digits_tiles<1><<<blocks, 256, 0, st>>>(d_seq, n, sigma, L, t0, hist, h->d_err, tcnt0,
+                                                     tc_stride(t0));
+    else if (w == 2)
+      k_hist_digits_tiles<2><<<blocks, 256, 0, st>>>(d_seq, n, sigma, L, t0, hist, h->d_err, tcnt0,
+                                                     tc_stride(t0));
+    else
+      k_hist_digits_tiles<4><<<blocks, 256, 0, st>>>(d_seq, n, sigma, L, t0, hist, h->d_err, tcnt0,
+                                                     tc_stride(t0));
     count_launch();
     CK(cudaGetLastError());
   }
-  k_plan_wm<<<1, 1024, 0, st>>>(hist, L, tau, G, cls, h->d_zeros, tickets);
+  // pass 0 planned from the histogram; the later passes from their own
+  // tiles' digit counts, just before they run
+  k_plan_wm<<<1, 1024, 0, st>>>(hist, L, tau, 1, cls, h->d_zeros, tickets);
   count_launch();
   CK(cudaGetLastError());
   // intermediate sequences
@@ -969,7 +912,9 @@ wt_status build_wm(const void* d_seq, uint64_t n, uint32_t sigma, int w, const w
     P.wm_cls = cls + coff;
     P.ntiles = (uint32_t)ntiles;
     P.n_in = n;
-    TRY(launch_pass(P, pg.wide, false, ntiles, o, st, g == 0 ? tcnt0 : nullptr));
+    const PassPlan plan{cls + coff, h->d_zeros};
+    TRY(launch_pass(P, pg.wide, false, ntiles, o, st, g == 0 ? tcnt0 : nullptr,
+                    g == 0 ? nullptr : &plan));
     coff += (2 << pg.t) + pg.t + 1;
     in = P.out;
   }

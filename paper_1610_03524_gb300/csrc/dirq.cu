@@ -64,7 +64,10 @@ __device__ __forceinline__ uint32_t sel64(uint64_t v, uint32_t r) {
 // One block covers DIR_SB_PER_BLOCK superblocks of one level (blk_first[l]:
 // first block of level l), so the level is found once per block; each warp
 // counts DIR_SB_PER_WARP superblocks with their words loaded together.
-constexpr int DIR_SB_PER_WARP = 4;
+#ifndef WT_DIR_SB_PER_WARP
+#define WT_DIR_SB_PER_WARP 4
+#endif
+constexpr int DIR_SB_PER_WARP = WT_DIR_SB_PER_WARP;
 constexpr int DIR_SB_PER_BLOCK = 8 * DIR_SB_PER_WARP;  // 256 threads
 
 __global__ void __launch_bounds__(256) k_dir_count(const uint64_t* bits, const LevelMeta* meta,
