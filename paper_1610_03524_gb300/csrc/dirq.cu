@@ -800,11 +800,16 @@ __device__ uint64_t select_b(const BinLevel& v, int bv, uint64_t k) {
       const uint64_t sidx = (d & ((1ull << 40) - 1)) + (uint64_t)__popc(mask & ((1u << i) - 1u));
       return S1 + v.ck32[v.cm->sparse[bv] + 256 * sidx + (k & 255)];
     }
-    const uint64_t p0 = S1 + v.ck32[v.cm->sub[bv] + 16 * kk + i];
+    const uint32_t* sb = v.ck32 + v.cm->sub[bv] + 16 * kk;
+    const uint64_t p0 = S1 + sb[i];
     if ((k & 255) == 0) return p0;
-    uint64_t hi = (p0 + CK_SPARSE_MIN - 1) >> 11;
-    if (hi >= v.nsb) hi = v.nsb - 1;
-    return dir_select<false>(v.bits, v.dir, bv, k, p0 >> 11, hi);
+    // the sub-range ends at the next sub-sample, or at the range's end
+    uint64_t p1 = (i + 1 < 16 && sb[i + 1] != 0xffffffffu) ? S1 + sb[i + 1] : 0;
+    if (!p1) {
+      const uint64_t ns = ((bv ? v.n - v.zeros : v.zeros) + 4095) / 4096;
+      p1 = kk + 1 < ns ? samp[kk + 1] : v.n;
+    }
+    return dir_select<false>(v.bits, v.dir, bv, k, p0 >> 11, (p1 - 1) >> 11);
   }
   const uint64_t cnt = bv ? v.n - v.zeros : v.zeros;
   const uint64_t ns = (cnt + 4095) / 4096;
@@ -1064,11 +1069,16 @@ __device__ uint64_t select_d(const DigLevel& v, uint32_t d, uint64_t k) {
       const uint64_t sidx = (dsc & ((1ull << 40) - 1)) + (uint64_t)__popc(mask & ((1u << i) - 1u));
       return S1 + v.ck32[v.cm->sparse[d] + 256 * sidx + (k & 255)];
     }
-    const uint64_t p0 = S1 + v.ck32[v.cm->sub[d] + 16 * kk + i];
+    const uint32_t* sb = v.ck32 + v.cm->sub[d] + 16 * kk;
+    const uint64_t p0 = S1 + sb[i];
     if ((k & 255) == 0) return p0;
-    uint64_t hi = (p0 + CK_SPARSE_MIN - 1) >> 10;
-    if (hi >= v.nsb) hi = v.nsb - 1;
-    return dir_select<true>(v.bits, v.dir, (int)d, k, p0 >> 10, hi);
+    // the sub-range ends at the next sub-sample, or at the range's end
+    uint64_t p1 = (i + 1 < 16 && sb[i + 1] != 0xffffffffu) ? S1 + sb[i + 1] : 0;
+    if (!p1) {
+      const uint64_t ns = (v.dir[8 * v.nsb + d] + 4095) / 4096;
+      p1 = kk + 1 < ns ? samp[kk + 1] : v.n;
+    }
+    return dir_select<true>(v.bits, v.dir, (int)d, k, p0 >> 10, (p1 - 1) >> 10);
   }
   // sampled: the search starts between two samples
   const uint64_t ns = (v.dir[8 * v.nsb + d] + 4095) / 4096;
