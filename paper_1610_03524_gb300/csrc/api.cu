@@ -92,15 +92,20 @@ wt_status sync_handle(wt_struct* h) {
   if (h->deferred != WT_OK) return h->deferred;
   cudaError_t e = cudaStreamSynchronize(h->stream);
   if (e != cudaSuccess) return h->deferred = WT_ERR_CUDA;
+  // small reads on the handle's own stream (not the legacy stream, which
+  // would wait for every other blocking stream of the device)
   uint32_t err = 0;
-  e = cudaMemcpy(&err, h->d_err, 4, cudaMemcpyDeviceToHost);
+  e = cudaMemcpyAsync(&err, h->d_err, 4, cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
   if (e != cudaSuccess) return h->deferred = WT_ERR_CUDA;
   if (err & ERR_SYMBOL) return h->deferred = WT_ERR_SYMBOL_GE_SIGMA;
   if (err) return h->deferred = WT_ERR_CUDA;  // ERR_INTERNAL: a table disagreed with a tile
   if (!h->zeros_valid) {
     h->zeros.assign(h->levels, 0);
     if (h->levels && h->bpe == 1) {
-      e = cudaMemcpy(h->zeros.data(), h->d_zeros, h->levels * 8, cudaMemcpyDeviceToHost);
+      e = cudaMemcpyAsync(h->zeros.data(), h->d_zeros, h->levels * 8, cudaMemcpyDeviceToHost,
+                          h->stream);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
       if (e != cudaSuccess) return h->deferred = WT_ERR_CUDA;
     }
     h->zeros_valid = true;

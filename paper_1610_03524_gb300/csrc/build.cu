@@ -827,6 +827,30 @@ static PassParams base_params(wt_struct* h, Work& wk, uint32_t* tickets,
   return P;
 }
 
+// small host tables reach the device as kernel parameters
+constexpr size_t UPLOAD_MAX = 3968;
+struct UploadBlock {
+  uint8_t b[UPLOAD_MAX];
+};
+
+__global__ void k_upload(uint8_t* dst, const __grid_constant__ UploadBlock blk, uint32_t bytes) {
+  for (uint32_t i = threadIdx.x; i < bytes; i += blockDim.x) dst[i] = blk.b[i];
+}
+
+wt_status upload(void* d_dst, const void* h_src, size_t bytes, cudaStream_t st) {
+  if (bytes == 0) return WT_OK;
+  if (bytes > UPLOAD_MAX) {
+    CK(cudaMemcpyAsync(d_dst, h_src, bytes, cudaMemcpyHostToDevice, st));
+    return WT_OK;
+  }
+  UploadBlock blk;
+  memcpy(blk.b, h_src, bytes);
+  k_upload<<<1, 256, 0, st>>>((uint8_t*)d_dst, blk, (uint32_t)bytes);
+  count_launch();
+  CK(cudaGetLastError());
+  return WT_OK;
+}
+
 // ---------------------------------------------------------------------------
 // wavelet matrix
 // ---------------------------------------------------------------------------
@@ -858,8 +882,8 @@ wt_status build_wm(const void* d_seq, uint64_t n, uint32_t sigma, int w, const w
   TRY(wk.get(&tickets, 32));
   TRY(wk.get(&d_off, L + 1));
   TRY(wk.get(&d_len, L));
-  CK(cudaMemcpyAsync(d_off, h->level_off.data(), (L + 1) * 8, cudaMemcpyHostToDevice, st));
-  CK(cudaMemcpyAsync(d_len, h->level_len.data(), L * 8, cudaMemcpyHostToDevice, st));
+  TRY(upload(d_off, h->level_off.data(), (L + 1) * 8, st));
+  TRY(upload(d_len, h->level_len.data(), L * 8, st));
   CK(cudaMemsetAsync(hist, 0, nh * 8, st));
   // the first pass's digit histogram and per-tile counts (with validation)
   uint32_t* tcnt0;
@@ -958,8 +982,8 @@ wt_status build_wt(const void* d_seq, uint64_t n, uint32_t sigma, int w, const w
   TRY(wk.get(&toff, max_nodes + 1));
   TRY(wk.get(&tiles, max_tiles));
   TRY(wk.get(&d_ntiles, 1));
-  CK(cudaMemcpyAsync(d_off, h->level_off.data(), (h->levels + 1) * 8, cudaMemcpyHostToDevice, st));
-  CK(cudaMemcpyAsync(d_len, h->level_len.data(), h->levels * 8, cudaMemcpyHostToDevice, st));
+  TRY(upload(d_off, h->level_off.data(), (h->levels + 1) * 8, st));
+  TRY(upload(d_len, h->level_len.data(), h->levels * 8, st));
   CK(cudaMemsetAsync(hist, 0, V * 8, st));
   TRY(launch_hist_full(d_seq, w, n, sigma, hist, h->d_err, st));
   TRY(scan_excl_u64(hist, C, V, scr, st));
@@ -1225,8 +1249,8 @@ wt_status build_huff(const void* d_seq, uint64_t n, uint32_t sigma, int w, const
   TRY(wk.get(&toff, max_nodes + 1));
   TRY(wk.get(&tiles, max_tiles));
   TRY(wk.get(&d_ntiles, 1));
-  CK(cudaMemcpyAsync(d_off, h->level_off.data(), (Lm + 1) * 8, cudaMemcpyHostToDevice, st));
-  CK(cudaMemcpyAsync(d_len, h->level_len.data(), Lm * 8, cudaMemcpyHostToDevice, st));
+  TRY(upload(d_off, h->level_off.data(), (Lm + 1) * 8, st));
+  TRY(upload(d_len, h->level_len.data(), Lm * 8, st));
   k_reset_tickets<<<1, 32, 0, st>>>(tickets);
   count_launch();
   CK(cudaGetLastError());

@@ -289,9 +289,7 @@ __global__ void k_mdigit_samples(const uint64_t* bits, const LevelMeta* meta, in
 wt_status upload_meta(wt_struct* h) {
   const size_t nb = std::max<size_t>(h->meta.size(), 1) * sizeof(LevelMeta);
   if (!h->d_meta) CK(dmalloc((void**)&h->d_meta, nb, h->stream));
-  if (!h->meta.empty())
-    CK(cudaMemcpyAsync(h->d_meta, h->meta.data(), h->meta.size() * sizeof(LevelMeta),
-                       cudaMemcpyHostToDevice, h->stream));
+  if (!h->meta.empty()) return upload(h->d_meta, h->meta.data(), h->meta.size() * sizeof(LevelMeta), h->stream);
   return WT_OK;
 }
 
@@ -318,7 +316,10 @@ wt_status dir_build_levels(const uint64_t* bits, const LevelMeta* d_meta, uint32
   CK(dmalloc((void**)&sbz, std::max<uint64_t>(total_sb, 1) * 8, st));
   CK(dmalloc((void**)&sbx, (total_sb + 1) * 8, st));
   CK(dmalloc((void**)&scr, scan_scratch_pub(total_sb) * 8, st));
-  CK(cudaMemcpyAsync(d_first, firsts.data(), firsts.size() * 8, cudaMemcpyHostToDevice, st));
+  {
+    const wt_status us = upload(d_first, firsts.data(), firsts.size() * 8, st);
+    if (us != WT_OK) return us;
+  }
   const unsigned fgrid = (unsigned)((total_sb + nlev + 255) / 256);
   if (total_sb) {
     k_dir_count<<<(unsigned)nblk, 256, 0, st>>>(bits, d_meta, (int)nlev, d_first, d_first + nlev + 1,
@@ -688,7 +689,10 @@ wt_status build_directories(wt_struct* h) {
   CK(dmalloc((void**)&sbz, std::max<uint64_t>(total_sb, 1) * 8 * 4, st));
   CK(dmalloc((void**)&sbx, (total_sb + 1) * 8 * 4, st));
   CK(dmalloc((void**)&scr, scan_scratch_pub(total_sb) * 8, st));
-  CK(cudaMemcpyAsync(d_first, sb_first.data(), (nlev + 1) * 8, cudaMemcpyHostToDevice, st));
+  {
+    const wt_status us = upload(d_first, sb_first.data(), (nlev + 1) * 8, st);
+    if (us != WT_OK) return us;
+  }
   // one warp per superblock: enough loads in flight to stream the bitmaps
   const unsigned cgrid = (unsigned)std::min<uint64_t>((total_sb * 32 + 255) / 256 + 1, 1u << 24);
   const unsigned fgrid = (unsigned)((total_sb + nlev + 255) / 256);
@@ -1254,7 +1258,10 @@ wt_status launch_query_multi(wt_struct* const* hs, uint32_t nh, const uint32_t* 
   for (uint32_t i = 0; i < nh; i++) fill_qstruct(hs[i], tab[i]);
   QStruct* d_tab = nullptr;
   CK(dmalloc((void**)&d_tab, tab.size() * sizeof(QStruct), st));
-  CK(cudaMemcpyAsync(d_tab, tab.data(), tab.size() * sizeof(QStruct), cudaMemcpyHostToDevice, st));
+  {
+    const wt_status us = upload(d_tab, tab.data(), tab.size() * sizeof(QStruct), st);
+    if (us != WT_OK) return us;
+  }
   k_query_multi<<<(unsigned)((q + 127) / 128), 128, 0, st>>>(d_tab, nh, sid, op, c, x, q, out);
   count_launch();
   cudaError_t e = cudaGetLastError();

@@ -112,6 +112,11 @@ wt_status upload_meta(wt_struct* h);
 
 uint32_t num_sms();
 
+// Host -> device copy of a small table through a kernel's parameters (no
+// copy engine: a small copy would otherwise queue behind large transfers of
+// other streams); larger tables by cudaMemcpyAsync.
+wt_status upload(void* d_dst, const void* h_src, size_t bytes, cudaStream_t st);
+
 // Launch accounting (all kernels of the library) and optional CUDA-event
 // timing of the partition-pass launches, for the benchmark's roofline.
 struct Prof {
