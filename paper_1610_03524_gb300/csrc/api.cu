@@ -27,16 +27,23 @@ wt_status check_opts(const wt_build_opts* o) {
   return WT_OK;
 }
 
-void free_arrays(wt_struct* h) {
+// sync: first wait for the work queued on the handle's stream (queries on
+// other streams included, through the caller's ordering), as wt_free does
+void free_arrays(wt_struct* h, bool sync = false) {
   cudaStream_t st = h->stream;
   if (h->arena) {
+    // the last handle of a batch returns the shared allocation
     if (h->arena->refs.fetch_sub(1) == 1) {
+      if (sync) cudaStreamSynchronize(st);
       dfree(h->arena->base, st);
       delete h->arena;
+      // the memory is back in the pool, for allocations on any stream
+      if (sync) cudaStreamSynchronize(st);
     }
     h->arena = nullptr;
     return;
   }
+  if (sync) cudaStreamSynchronize(st);
   dfree(h->d_bits, st);
   dfree(h->d_dir, st);
   dfree(h->d_samp, st);
@@ -277,9 +284,13 @@ wt_status wt_export(wt_handle h, wt_export_view* out) {
 
 wt_status wt_free(wt_handle h) {
   if (!h) return WT_ERR_INVALID_ARG;
-  cudaStreamSynchronize(h->stream);
-  free_arrays(h);
-  cudaError_t e = cudaStreamSynchronize(h->stream);
+  // memory goes back in stream order after the handle's queued work; a
+  // handle of a batch that is not the last one frees nothing and waits for
+  // nothing
+  const bool owner = !h->arena;
+  free_arrays(h, true);
+  // the memory is back in the pool, for allocations on any stream
+  const cudaError_t e = owner ? cudaStreamSynchronize(h->stream) : cudaGetLastError();
   delete h;
   return e == cudaSuccess ? WT_OK : WT_ERR_CUDA;
 }

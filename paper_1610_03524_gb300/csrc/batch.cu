@@ -382,11 +382,9 @@ wt_status batch_build_wm(const wt_batch_item* items, uint32_t m, const wt_build_
   if (nzeros) CK(cudaMemsetAsync(a_zeros, 0, 8 * nzeros, st));  // empty sequences plan nothing
   if (nhist) CK(cudaMemsetAsync(d_hist, 0, 8 * nhist, st));
   CK(cudaMemsetAsync(d_tick, 0, 4 * 64, st));
-  if (nmeta)
-    CK(cudaMemcpyAsync(a_meta, h_meta_all.data(), sizeof(LevelMeta) * nmeta,
-                       cudaMemcpyHostToDevice, st));
-  CK(cudaMemcpyAsync(Wd + w_lvl, img.data(), img.size(), cudaMemcpyHostToDevice, st));
-  wt_status s = launch_hist_batch(d_hseg, nh, nchunks, d_hist, st);
+  wt_status s = nmeta ? upload(a_meta, h_meta_all.data(), sizeof(LevelMeta) * nmeta, st) : WT_OK;
+  if (s == WT_OK) s = upload(Wd + w_lvl, img.data(), img.size(), st);
+  if (s == WT_OK) s = launch_hist_batch(d_hseg, nh, nchunks, d_hist, st);
   if (s == WT_OK) s = launch_plan_batch(d_pseg, m, st);
   for (size_t li = 0; li < launches.size() && s == WT_OK; li++) {
     const Launch& L0 = launches[li];
