@@ -204,7 +204,27 @@ def cpu_baseline(log2n_sample):
     return {"value": n * 16 / dt / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": f"first 2^{log2n_sample} symbols of the workload's distribution (same seed); "
                       f"single-threaded C oracle: WM levels + rank directory + select samples; "
-                      f"{dt:.2f} s"}
+                      f"{dt:.2f} s",
+            "parallel": cpu_parallel_baseline(S)}
+
+
+def cpu_parallel_baseline(S):
+    """The same sample through the multi-threaded CPU construction
+    (cpu_baseline/: levelwise stable splits over chunks, prefix-summed
+    offsets), on every host core; median of three runs."""
+    import cpu_baseline as cb
+    threads = os.cpu_count() or 1
+    cb.wm_build(S[:4096], 16, threads)  # warm-up: threads, pages
+    ts = []
+    for _ in range(3):
+        t0 = time.perf_counter()
+        cb.wm_build(S, 16, threads)
+        ts.append(time.perf_counter() - t0)
+    dt = statistics.median(ts)
+    return {"value": S.size * 16 / dt / 1e9, "unit": UNIT, "cores": threads,
+            "kind": "multi-threaded CPU build (cpu_baseline/)",
+            "sample": f"the same 2^{int(S.size).bit_length() - 1} symbols; WM levels + rank "
+                      f"directory + select samples; {dt:.3f} s"}
 
 
 def run_reference(args):
