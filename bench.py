@@ -337,10 +337,12 @@ def run_native(args):
             else "fallback 6800 GB/s",
             "algorithmic_bytes_per_launch": alg_bytes / max(pass_launches, 1),
             "avg_launch_ms": pass_ms / max(pass_launches, 1),
-            "pass_share_of_step": (pass_ms / args.steps) / ms if ms > 0 else None,
-            "whole_step_frac_of_Bmin": None}
-    # whole-step model B(tau=8) ~ 10.16 n bytes (histogram 2n, passes 6n, directory 2.16n)
+            "pass_share_of_step": (pass_ms / args.steps) / ms if ms > 0 else None}
+    # whole-step byte models: B(tau=8) ~ 10.16 n (histogram 2n, passes 6n,
+    # directory 2.16n); B_min = n w + L n / 8 + directory writes (L n / 128 +
+    # L n / 512 select samples) = 4.156 n, a single ideal pass
     roof["whole_step_frac_of_B_tau8"] = (10.16 * n / (ms * 1e-3) / 1e9) / peak
+    roof["whole_step_frac_of_Bmin"] = ((2 + 2 + 16 / 128 + 16 / 512) * n / (ms * 1e-3) / 1e9) / peak
 
     # end to end through the C ABI: every step copies its input from pinned
     # host memory, builds, and reads its zero counts back on the host.  Two
