@@ -31,7 +31,8 @@ wt_status launch_hist_batch(const HistSeg* d_segs, uint32_t nsegs, uint64_t nchu
 wt_status launch_plan_batch(const PlanSeg* d_ps, uint32_t m, cudaStream_t st);
 wt_status dir_build_levels(const uint64_t* bits, const LevelMeta* d_meta, uint32_t nlev,
                            const std::vector<uint64_t>& sb_first, uint64_t* dir, uint64_t* samp,
-                           uint64_t* zeros, int write_zeros, cudaStream_t st);
+                           uint64_t* zeros, int write_zeros, cudaStream_t st,
+                           const LevelMeta* h_meta = nullptr);
 
 #define CK(x)                                                   \
   do {                                                          \

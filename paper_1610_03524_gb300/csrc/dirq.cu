@@ -70,21 +70,46 @@ __device__ __forceinline__ uint32_t sel64(uint64_t v, uint32_t r) {
 constexpr int DIR_SB_PER_WARP = WT_DIR_SB_PER_WARP;
 constexpr int DIR_SB_PER_BLOCK = 8 * DIR_SB_PER_WARP;  // 256 threads
 
+// Up to DIR_SMALL levels: their first blocks, first superblocks and
+// metadata ride in the kernel parameters, so a block finds its level without
+// a dependent load (else the tables are searched in global memory).
+constexpr int DIR_SMALL = 32;
+struct DirLevels {
+  int nlev;
+  uint64_t blk_first[DIR_SMALL + 1];
+  uint64_t sb_first[DIR_SMALL + 1];
+  LevelMeta meta[DIR_SMALL];
+};
+
+template <bool SMALL>
 __global__ void __launch_bounds__(256) k_dir_count(const uint64_t* bits, const LevelMeta* meta,
                                                    int nlev, const uint64_t* sb_first,
                                                    const uint64_t* blk_first, uint64_t* dir,
-                                                   uint64_t* sbz) {
-  __shared__ LevelMeta m;
+                                                   uint64_t* sbz, const __grid_constant__ DirLevels dl) {
+  __shared__ LevelMeta sm;
   __shared__ uint64_t s_sb0, s_g0;
-  if (threadIdx.x == 0) {
-    const int l = find_level(blk_first, nlev, blockIdx.x);
-    m = meta[l];
-    s_sb0 = (blockIdx.x - blk_first[l]) * DIR_SB_PER_BLOCK;
-    s_g0 = sb_first[l];
+  LevelMeta m;
+  uint64_t sb0, g0;
+  if (SMALL) {
+    int l = 0;
+    while (l + 1 < dl.nlev && dl.blk_first[l + 1] <= blockIdx.x) l++;
+    m = dl.meta[l];
+    sb0 = (blockIdx.x - dl.blk_first[l]) * DIR_SB_PER_BLOCK;
+    g0 = dl.sb_first[l];
+  } else {
+    if (threadIdx.x == 0) {
+      const int l = find_level(blk_first, nlev, blockIdx.x);
+      sm = meta[l];
+      s_sb0 = (blockIdx.x - blk_first[l]) * DIR_SB_PER_BLOCK;
+      s_g0 = sb_first[l];
+    }
+    __syncthreads();
+    m = sm;
+    sb0 = s_sb0;
+    g0 = s_g0;
   }
-  __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const uint64_t s0 = s_sb0 + (uint64_t)warp * DIR_SB_PER_WARP;
+  const uint64_t s0 = sb0 + (uint64_t)warp * DIR_SB_PER_WARP;
   uint64_t w[DIR_SB_PER_WARP];
   int valid[DIR_SB_PER_WARP];
 #pragma unroll
@@ -110,7 +135,7 @@ __global__ void __launch_bounds__(256) k_dir_count(const uint64_t* bits, const L
     const uint64_t r2 = (uint64_t)__shfl_sync(FULL, zi, 15);
     const uint64_t r3 = (uint64_t)__shfl_sync(FULL, zi, 23);
     if (lane == 0) dir[m.dir_off + 2 * s + 1] = (r1 << 16) | (r2 << 32) | (r3 << 48);
-    if (lane == 31) sbz[s_g0 + s] = (uint64_t)zi;
+    if (lane == 31) sbz[g0 + s] = (uint64_t)zi;
   }
 }
 
@@ -155,14 +180,25 @@ __device__ uint32_t find_in_sb(const uint64_t* lbits, const uint64_t* ldir, uint
   return 2047;
 }
 
+template <bool SMALL>
 __global__ void k_select_samples(const uint64_t* bits, const LevelMeta* meta, int nlev,
                                  const uint64_t* sb_first, uint64_t total_sb,
-                                 const uint64_t* dir, uint64_t* samp) {
+                                 const uint64_t* dir, uint64_t* samp,
+                                 const __grid_constant__ DirLevels dl) {
   const uint64_t g = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= total_sb) return;
-  const int l = find_level(sb_first, nlev, g);
-  const LevelMeta m = meta[l];
-  const uint64_t s = g - sb_first[l];
+  LevelMeta m;
+  uint64_t s;
+  if (SMALL) {
+    int l = 0;
+    while (l + 1 < dl.nlev && dl.sb_first[l + 1] <= g) l++;
+    m = dl.meta[l];
+    s = g - dl.sb_first[l];
+  } else {
+    const int l = find_level(sb_first, nlev, g);
+    m = meta[l];
+    s = g - sb_first[l];
+  }
   const uint64_t* ld = dir + m.dir_off;
   const uint64_t* lb = bits + m.bit_off;
   const uint64_t zb = ld[2 * s], ze = ld[2 * s + 2];
@@ -299,7 +335,8 @@ wt_status upload_meta(wt_struct* h) {
 // level's zero count in zeros[l].
 wt_status dir_build_levels(const uint64_t* bits, const LevelMeta* d_meta, uint32_t nlev,
                            const std::vector<uint64_t>& sb_first, uint64_t* dir, uint64_t* samp,
-                           uint64_t* zeros, int write_zeros, cudaStream_t st) {
+                           uint64_t* zeros, int write_zeros, cudaStream_t st,
+                           const LevelMeta* h_meta) {
   if (nlev == 0) return WT_OK;
   const uint64_t total_sb = sb_first[nlev];
   // blocks of the counting kernel: DIR_SB_PER_BLOCK superblocks of one level each
@@ -321,9 +358,25 @@ wt_status dir_build_levels(const uint64_t* bits, const LevelMeta* d_meta, uint32
     if (us != WT_OK) return us;
   }
   const unsigned fgrid = (unsigned)((total_sb + nlev + 255) / 256);
+  // few levels with host metadata: the level tables go in the parameters
+  const bool small = h_meta && nlev <= (uint32_t)DIR_SMALL;
+  DirLevels dl;
+  memset(&dl, 0, sizeof(dl));
+  if (small) {
+    dl.nlev = (int)nlev;
+    for (uint32_t l = 0; l <= nlev; l++) {
+      dl.blk_first[l] = blk_first[l];
+      dl.sb_first[l] = sb_first[l];
+    }
+    for (uint32_t l = 0; l < nlev; l++) dl.meta[l] = h_meta[l];
+  }
   if (total_sb) {
-    k_dir_count<<<(unsigned)nblk, 256, 0, st>>>(bits, d_meta, (int)nlev, d_first, d_first + nlev + 1,
-                                               dir, sbz);
+    if (small)
+      k_dir_count<true><<<(unsigned)nblk, 256, 0, st>>>(bits, d_meta, (int)nlev, d_first,
+                                                       d_first + nlev + 1, dir, sbz, dl);
+    else
+      k_dir_count<false><<<(unsigned)nblk, 256, 0, st>>>(bits, d_meta, (int)nlev, d_first,
+                                                        d_first + nlev + 1, dir, sbz, dl);
     count_launch();
   }
   wt_status s = scan_excl_u64_pub(sbz, sbx, total_sb, scr, st);
@@ -332,8 +385,12 @@ wt_status dir_build_levels(const uint64_t* bits, const LevelMeta* d_meta, uint32
                                         write_zeros);
     count_launch();
     if (total_sb) {
-      k_select_samples<<<(unsigned)((total_sb + 255) / 256), 256, 0, st>>>(
-          bits, d_meta, (int)nlev, d_first, total_sb, dir, samp);
+      if (small)
+        k_select_samples<true><<<(unsigned)((total_sb + 255) / 256), 256, 0, st>>>(
+            bits, d_meta, (int)nlev, d_first, total_sb, dir, samp, dl);
+      else
+        k_select_samples<false><<<(unsigned)((total_sb + 255) / 256), 256, 0, st>>>(
+            bits, d_meta, (int)nlev, d_first, total_sb, dir, samp, dl);
       count_launch();
     }
   }
@@ -680,7 +737,7 @@ wt_status build_directories(wt_struct* h) {
   if (nlev == 0) return WT_OK;
   if (!dig) {
     s = dir_build_levels(h->d_bits_ro, h->d_meta, nlev, sb_first, h->d_dir, h->d_samp,
-                         h->d_zeros, h->kind == WT_KIND_RS ? 1 : 0, st);
+                         h->d_zeros, h->kind == WT_KIND_RS ? 1 : 0, st, h->meta.data());
     if (s == WT_OK && (h->flags & WT_FLAG_SELECT_O1)) s = build_clark(h);
     return s;
   }
