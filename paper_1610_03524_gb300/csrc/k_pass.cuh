@@ -1,24 +1,25 @@
 // k_pass.cuh -- the level-group partition kernel (one pass = t levels).
 //
-// One CTA processes one tile of T_a at a time (tiles taken in order from an
-// atomic ticket, so every wait below is on a tile that is already running).
-// For a tile it computes, in shared memory:
+// One CTA processes one tile of T_a at a time (tiles taken from an atomic
+// ticket; no CTA waits on another).  For a tile it computes, in shared
+// memory:
 //   * the tile's bits of levels a..a+t-1, each in the order that level has
 //     inside the tile, by t stable 1-bit splits of the tile (Section 4.1: the
 //     descendants' sub-sequences are a stable integer sort on the next tau
 //     bits; Section 4.3: for the wavelet matrix the key is the reversed
 //     digit, i.e. the splits run from the level-a bit up).  Level j's bits
 //     are the ballot words of b_j in the order after j splits;
-//   * the element count of every class (node) of every level, from the
-//     tile's digit histogram (prefix sums, Section 2).
-// The count of every class in the earlier tiles of the tile's sequence or
-// node comes from prefix sums, taken before the pass, of every tile's digit
+//   * the element count of every class (node) of every level, folded from
+//     the tile's digit counts.
+// The tile's digit counts and those of all earlier tiles of its sequence or
+// node come from prefix sums, taken before the pass, of every tile's digit
 // counts: the domain decomposition of Section 4.2 with K = number of tiles
-// and per-node offsets by prefix sums across the K sub-problems.  Words copied whole are stored;
-// the "boundary" words that several tiles or nodes share (Section 4.2) are
-// merged with atomicOr into the level buffer, which the build zeroes first.
-// Finally the tile scatters its elements, narrowed to the bits still needed,
-// to T_{a+t}: the stable partition on the t-bit digit (big nodes, Section 3).
+// and per-node offsets by prefix sums across the K sub-problems.  Words
+// copied whole are stored; the "boundary" words that several tiles or nodes
+// share (Section 4.2) are merged with atomicOr into the level buffer, which
+// the build zeroes first.  Finally the tile scatters its elements, narrowed
+// to the bits still needed, to T_{a+t}: the stable partition on the t-bit
+// digit (big nodes, Section 3).
 #pragma once
 #include <type_traits>
 
