@@ -43,12 +43,6 @@ wt_status dir_build_levels(const uint64_t* bits, const LevelMeta* d_meta, uint32
     }                                                           \
   } while (0)
 
-#define TRY(x)                     \
-  do {                             \
-    wt_status s_ = (x);            \
-    if (s_ != WT_OK) return s_;    \
-  } while (0)
-
 // ---------------------------------------------------------------------------
 // autotuner table: (L, ceil(log2 n)) -> levels per pass
 // ---------------------------------------------------------------------------

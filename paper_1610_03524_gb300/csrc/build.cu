@@ -268,10 +268,11 @@ static wt_status launch_hist_full(const void* seq, int w, uint64_t n, uint32_t s
   // global counters: 16 copies while they take at most 256 MB
   uint32_t ncopy = 1;
   uint64_t* dst = hist;
+  Work wk{st, {}};
   if (!use_smem && sigma > 8) {
     ncopy = (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>(16, (256ull << 20) / (8ull * sigma)));
     if (ncopy > 1) {
-      CK(dmalloc((void**)&dst, (size_t)ncopy * sigma * 8, st));
+      TRY(wk.get(&dst, (size_t)ncopy * sigma));
       CK(cudaMemsetAsync(dst, 0, (size_t)ncopy * sigma * 8, st));
     }
   }
@@ -285,7 +286,6 @@ static wt_status launch_hist_full(const void* seq, int w, uint64_t n, uint32_t s
                         st>>>(dst, sigma, ncopy, hist);
     count_launch();
     CK(cudaGetLastError());
-    dfree(dst, st);
   }
   return WT_OK;
 }
@@ -704,15 +704,16 @@ static wt_status launch_pass_t(const PassParams& P, uint64_t max_tiles, const wt
   const uint32_t nchunk = (uint32_t)((mt + TCHUNK - 1) / TCHUNK);
   PassParams Q = P;
   Q.tcs = P.tcs ? P.tcs : tc_stride(P.t);  // batched passes give the widest digit's
+  Work wk{st, {}};
   uint32_t* tcnt = tcnt_pre;
   uint64_t* tchunk = nullptr;
   if (!tcnt) {
-    CK(dmalloc((void**)&tcnt, mt * Q.tcs * 4, st));
+    TRY(wk.get(&tcnt, mt * Q.tcs));
     k_tile_counts<E, BATCH><<<(unsigned)std::min<uint64_t>(mt, (uint64_t)num_sms() * 16), 256, 0,
                               st>>>(Q, tcnt);
     count_launch();
   }
-  CK(dmalloc((void**)&tchunk, ((uint64_t)nchunk + 1) * Q.tcs * 8, st));
+  TRY(wk.get(&tchunk, ((uint64_t)nchunk + 1) * Q.tcs));
   k_tile_scan_chunk<<<nchunk, Q.tcs, 0, st>>>(tcnt, P.tiles ? P.ntiles_dev : nullptr, P.ntiles,
                                               tchunk);
   count_launch();
@@ -735,8 +736,6 @@ static wt_status launch_pass_t(const PassParams& P, uint64_t max_tiles, const wt
   kern<<<(unsigned)grid, PNT + 32, SM::bytes, st>>>(Q);
   CK(cudaGetLastError());
   count_launch();
-  if (!tcnt_pre) dfree(tcnt, st);
-  dfree(tchunk, st);
   if (pf.on) {
     cudaEventRecord(e1, st);
     pf.ev.push_back(e0);
@@ -773,28 +772,6 @@ static int pick_tau(const wt_build_opts* o, int L, bool even, uint64_t n = 0) {
 }
 
 // common workspace of a build
-struct Work {
-  cudaStream_t st;
-  std::vector<void*> bufs;
-  ~Work() {
-    for (void* p : bufs) dfree(p, st);
-  }
-  template <typename T>
-  wt_status get(T** p, size_t count) {
-    void* q = nullptr;
-    cudaError_t e = dmalloc(&q, count * sizeof(T), st);
-    if (e != cudaSuccess) return WT_ERR_NO_MEMORY;
-    bufs.push_back(q);
-    *p = (T*)q;
-    return WT_OK;
-  }
-};
-
-#define TRY(x)                     \
-  do {                             \
-    wt_status s_ = (x);            \
-    if (s_ != WT_OK) return s_;    \
-  } while (0)
 
 static wt_status alloc_outputs(wt_struct* h, uint64_t total_words) {
   CK(dmalloc((void**)&h->d_bits, total_words * 8, h->stream));

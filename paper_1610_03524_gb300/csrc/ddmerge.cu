@@ -200,7 +200,7 @@ wt_status dd_merge(wt_struct* const* parts, uint32_t R, wt_struct* h) {
   for (uint32_t p = 0; p < R; p++)
     for (int l = 0; l < L; l++) h->zeros[l] += parts[p]->zeros[l];
   h->zeros_valid = true;
-  CK(cudaMemcpyAsync(h->d_zeros, h->zeros.data(), L * 8, cudaMemcpyHostToDevice, st));
+  TRY(upload(h->d_zeros, h->zeros.data(), L * 8, st));
   // the parts' levels
   std::vector<DdLevel> hl((size_t)R * L);
   for (uint32_t p = 0; p < R; p++)
@@ -211,18 +211,19 @@ wt_status dd_merge(wt_struct* const* parts, uint32_t R, wt_struct* h) {
     }
   const uint64_t stride = ((uint64_t)1 << L) - 1;  // nodes of levels 0 .. L-1
   const uint64_t nseg = (uint64_t)R * stride;
+  Work wk{st, {}};
   DdLevel* d_lv;
   uint64_t *cnt, *cs, *dst, *npc, *tot, *X, *PS, *scr;
-  CK(dmalloc((void**)&d_lv, hl.size() * sizeof(DdLevel), st));
-  CK(dmalloc((void**)&cnt, nseg * 8, st));
-  CK(dmalloc((void**)&cs, nseg * 8, st));
-  CK(dmalloc((void**)&dst, nseg * 8, st));
-  CK(dmalloc((void**)&npc, nseg * 8, st));
-  CK(dmalloc((void**)&tot, stride * 8, st));
-  CK(dmalloc((void**)&X, (stride + 1) * 8, st));
-  CK(dmalloc((void**)&PS, (nseg + 1) * 8, st));
-  CK(dmalloc((void**)&scr, scan_scratch_pub(std::max(nseg, stride)) * 8, st));
-  CK(cudaMemcpyAsync(d_lv, hl.data(), hl.size() * sizeof(DdLevel), cudaMemcpyHostToDevice, st));
+  TRY(wk.get(&d_lv, hl.size()));
+  TRY(wk.get(&cnt, nseg));
+  TRY(wk.get(&cs, nseg));
+  TRY(wk.get(&dst, nseg));
+  TRY(wk.get(&npc, nseg));
+  TRY(wk.get(&tot, stride));
+  TRY(wk.get(&X, stride + 1));
+  TRY(wk.get(&PS, nseg + 1));
+  TRY(wk.get(&scr, scan_scratch_pub(std::max(nseg, stride))));
+  TRY(upload(d_lv, hl.data(), hl.size() * sizeof(DdLevel), st));
   // level 0: one node per part, the whole part (the part sizes ride in the
   // level table)
   CK(cudaMemsetAsync(cs, 0, nseg * 8, st));
@@ -248,24 +249,14 @@ wt_status dd_merge(wt_struct* const* parts, uint32_t R, wt_struct* h) {
   }
   if (s == WT_OK && npieces) {
     uint32_t* map;
-    CK(dmalloc((void**)&map, npieces * 4, st));
+    TRY(wk.get(&map, npieces));
     k_dd_map<<<(unsigned)((nseg * 32 + 255) / 256), 256, 0, st>>>(PS, nseg, map);
     count_launch();
     k_dd_copy<<<(unsigned)((npieces * 32 + 255) / 256), 256, 0, st>>>(
         d_lv, L, stride, map, cnt, cs, dst, PS, npieces, h->d_bits, W, h->d_err);
     count_launch();
-    dfree(map, st);
   }
   cudaError_t e = cudaGetLastError();
-  dfree(d_lv, st);
-  dfree(cnt, st);
-  dfree(cs, st);
-  dfree(dst, st);
-  dfree(npc, st);
-  dfree(tot, st);
-  dfree(X, st);
-  dfree(PS, st);
-  dfree(scr, st);
   if (s != WT_OK) return s;
   if (e != cudaSuccess) return WT_ERR_CUDA;
   if (h->flags & WT_FLAG_NO_DIRECTORY) return WT_OK;

@@ -348,15 +348,13 @@ wt_status dir_build_levels(const uint64_t* bits, const LevelMeta* d_meta, uint32
     blk_first[l + 1] = blk_first[l] + (nsb + DIR_SB_PER_BLOCK - 1) / DIR_SB_PER_BLOCK;
   }
   const uint64_t nblk = blk_first[nlev];
+  Work wk{st, {}};
   uint64_t *d_first, *sbz, *sbx, *scr;
-  CK(dmalloc((void**)&d_first, 2 * ((size_t)nlev + 1) * 8, st));
-  CK(dmalloc((void**)&sbz, std::max<uint64_t>(total_sb, 1) * 8, st));
-  CK(dmalloc((void**)&sbx, (total_sb + 1) * 8, st));
-  CK(dmalloc((void**)&scr, scan_scratch_pub(total_sb) * 8, st));
-  {
-    const wt_status us = upload(d_first, firsts.data(), firsts.size() * 8, st);
-    if (us != WT_OK) return us;
-  }
+  TRY(wk.get(&d_first, 2 * ((size_t)nlev + 1)));
+  TRY(wk.get(&sbz, std::max<uint64_t>(total_sb, 1)));
+  TRY(wk.get(&sbx, total_sb + 1));
+  TRY(wk.get(&scr, scan_scratch_pub(total_sb)));
+  TRY(upload(d_first, firsts.data(), firsts.size() * 8, st));
   const unsigned fgrid = (unsigned)((total_sb + nlev + 255) / 256);
   // few levels with host metadata: the level tables go in the parameters
   const bool small = h_meta && nlev <= (uint32_t)DIR_SMALL;
@@ -395,10 +393,6 @@ wt_status dir_build_levels(const uint64_t* bits, const LevelMeta* d_meta, uint32
     }
   }
   cudaError_t e = cudaGetLastError();
-  dfree(d_first, st);
-  dfree(sbz, st);
-  dfree(sbx, st);
-  dfree(scr, st);
   if (s != WT_OK) return s;
   return e == cudaSuccess ? WT_OK : WT_ERR_CUDA;
 }
@@ -556,17 +550,16 @@ static wt_status build_clark(wt_struct* h) {
       std::vector<uint64_t> idx(occ.size());
       for (uint32_t l = 0; l < nlev; l++)
         for (int d = 0; d < 4; d++) idx[4 * l + d] = h->meta[l].dir_off + 8 * h->meta[l].nsb + d;
+      Work wk0{st, {}};
       uint64_t *d_idx, *d_got;
-      CK(dmalloc((void**)&d_idx, idx.size() * 8, st));
-      CK(dmalloc((void**)&d_got, idx.size() * 8, st));
-      CK(cudaMemcpyAsync(d_idx, idx.data(), idx.size() * 8, cudaMemcpyHostToDevice, st));
+      TRY(wk0.get(&d_idx, idx.size()));
+      TRY(wk0.get(&d_got, idx.size()));
+      TRY(upload(d_idx, idx.data(), idx.size() * 8, st));
       k_gather_u64<<<(unsigned)((idx.size() + 255) / 256), 256, 0, st>>>(h->d_dir, d_idx,
                                                                          idx.size(), d_got);
       count_launch();
       CK(cudaMemcpyAsync(occ.data(), d_got, occ.size() * 8, cudaMemcpyDeviceToHost, st));
       CK(cudaStreamSynchronize(st));
-      dfree(d_idx, st);
-      dfree(d_got, st);
     } else {
       std::vector<uint64_t> zeros(nlev, 0);
       CK(cudaMemcpyAsync(zeros.data(), h->d_zeros, nlev * 8, cudaMemcpyDeviceToHost, st));
@@ -601,19 +594,19 @@ static wt_status build_clark(wt_struct* h) {
     }
   }
   const uint32_t nseg = (uint32_t)segs.size();
+  Work wk{st, {}};
   uint64_t *d_kind, *d_nh, *d_ns, *d_gh, *d_gs, *scr;
   CkSeg* d_segs;
   uint32_t* d_sub;
-  CK(dmalloc((void**)&d_sub, std::max<uint64_t>(16 * G, 1) * 4, st));
-  CK(dmalloc((void**)&d_kind, std::max<uint64_t>(G, 1) * 8, st));
-  CK(dmalloc((void**)&d_nh, std::max<uint64_t>(G, 1) * 8, st));
-  CK(dmalloc((void**)&d_ns, std::max<uint64_t>(G, 1) * 8, st));
-  CK(dmalloc((void**)&d_gh, (G + 1) * 8, st));
-  CK(dmalloc((void**)&d_gs, (G + 1) * 8, st));
-  CK(dmalloc((void**)&scr, scan_scratch_pub(G) * 8, st));
-  CK(dmalloc((void**)&d_segs, std::max<uint32_t>(nseg, 1) * sizeof(CkSeg), st));
-  if (nseg)
-    CK(cudaMemcpyAsync(d_segs, segs.data(), nseg * sizeof(CkSeg), cudaMemcpyHostToDevice, st));
+  TRY(wk.get(&d_sub, std::max<uint64_t>(16 * G, 1)));
+  TRY(wk.get(&d_kind, std::max<uint64_t>(G, 1)));
+  TRY(wk.get(&d_nh, std::max<uint64_t>(G, 1)));
+  TRY(wk.get(&d_ns, std::max<uint64_t>(G, 1)));
+  TRY(wk.get(&d_gh, G + 1));
+  TRY(wk.get(&d_gs, G + 1));
+  TRY(wk.get(&scr, scan_scratch_pub(G)));
+  TRY(wk.get(&d_segs, std::max<uint32_t>(nseg, 1)));
+  if (nseg) TRY(upload(d_segs, segs.data(), nseg * sizeof(CkSeg), st));
   const unsigned gg = (unsigned)((G + 255) / 256);
   if (G) {
     if (dig)
@@ -662,9 +655,9 @@ static wt_status build_clark(wt_struct* h) {
     std::vector<uint64_t> both(2 * idx.size(), 0);
     if (nlev) {
       uint64_t *d_idx, *d_got;
-      CK(dmalloc((void**)&d_idx, idx.size() * 8, st));
-      CK(dmalloc((void**)&d_got, both.size() * 8, st));
-      CK(cudaMemcpyAsync(d_idx, idx.data(), idx.size() * 8, cudaMemcpyHostToDevice, st));
+      TRY(wk.get(&d_idx, idx.size()));
+      TRY(wk.get(&d_got, both.size()));
+      TRY(upload(d_idx, idx.data(), idx.size() * 8, st));
       k_gather_u64<<<(unsigned)((idx.size() + 255) / 256), 256, 0, st>>>(d_gh, d_idx, idx.size(), d_got);
       count_launch();
       k_gather_u64<<<(unsigned)((idx.size() + 255) / 256), 256, 0, st>>>(d_gs, d_idx, idx.size(),
@@ -672,8 +665,6 @@ static wt_status build_clark(wt_struct* h) {
       count_launch();
       CK(cudaMemcpyAsync(both.data(), d_got, both.size() * 8, cudaMemcpyDeviceToHost, st));
       CK(cudaStreamSynchronize(st));
-      dfree(d_idx, st);
-      dfree(d_got, st);
     }
     for (uint32_t l = 0; l < nlev; l++)
       for (int b = 0; b < NV; b++) {
@@ -691,14 +682,6 @@ static wt_status build_clark(wt_struct* h) {
     CK(cudaStreamSynchronize(st));  // host vectors above are pageable and local
   }
   cudaError_t e = cudaGetLastError();
-  dfree(d_sub, st);
-  dfree(d_kind, st);
-  dfree(d_nh, st);
-  dfree(d_ns, st);
-  dfree(d_gh, st);
-  dfree(d_gs, st);
-  dfree(scr, st);
-  dfree(d_segs, st);
   if (s != WT_OK) return s;
   return e == cudaSuccess ? WT_OK : WT_ERR_CUDA;
 }
@@ -741,15 +724,13 @@ wt_status build_directories(wt_struct* h) {
     if (s == WT_OK && (h->flags & WT_FLAG_SELECT_O1)) s = build_clark(h);
     return s;
   }
+  Work wk{st, {}};
   uint64_t *d_first, *sbz, *sbx, *scr;
-  CK(dmalloc((void**)&d_first, (nlev + 1) * 8, st));
-  CK(dmalloc((void**)&sbz, std::max<uint64_t>(total_sb, 1) * 8 * 4, st));
-  CK(dmalloc((void**)&sbx, (total_sb + 1) * 8 * 4, st));
-  CK(dmalloc((void**)&scr, scan_scratch_pub(total_sb) * 8, st));
-  {
-    const wt_status us = upload(d_first, sb_first.data(), (nlev + 1) * 8, st);
-    if (us != WT_OK) return us;
-  }
+  TRY(wk.get(&d_first, nlev + 1));
+  TRY(wk.get(&sbz, std::max<uint64_t>(total_sb, 1) * 4));
+  TRY(wk.get(&sbx, (total_sb + 1) * 4));
+  TRY(wk.get(&scr, scan_scratch_pub(total_sb)));
+  TRY(upload(d_first, sb_first.data(), (nlev + 1) * 8, st));
   // one warp per superblock: enough loads in flight to stream the bitmaps
   const unsigned cgrid = (unsigned)std::min<uint64_t>((total_sb * 32 + 255) / 256 + 1, 1u << 24);
   const unsigned fgrid = (unsigned)((total_sb + nlev + 255) / 256);
@@ -771,10 +752,6 @@ wt_status build_directories(wt_struct* h) {
     }
   }
   cudaError_t e = cudaGetLastError();
-  dfree(d_first, st);
-  dfree(sbz, st);
-  dfree(sbx, st);
-  dfree(scr, st);
   if (s != WT_OK) return s;
   if (e != cudaSuccess) return WT_ERR_CUDA;
   if (h->flags & WT_FLAG_SELECT_O1) return build_clark(h);
@@ -1313,17 +1290,13 @@ wt_status launch_query_multi(wt_struct* const* hs, uint32_t nh, const uint32_t* 
   if (q == 0) return WT_OK;
   std::vector<QStruct> tab(std::max<uint32_t>(nh, 1));
   for (uint32_t i = 0; i < nh; i++) fill_qstruct(hs[i], tab[i]);
+  Work wk{st, {}};
   QStruct* d_tab = nullptr;
-  CK(dmalloc((void**)&d_tab, tab.size() * sizeof(QStruct), st));
-  {
-    const wt_status us = upload(d_tab, tab.data(), tab.size() * sizeof(QStruct), st);
-    if (us != WT_OK) return us;
-  }
+  TRY(wk.get(&d_tab, tab.size()));
+  TRY(upload(d_tab, tab.data(), tab.size() * sizeof(QStruct), st));
   k_query_multi<<<(unsigned)((q + 127) / 128), 128, 0, st>>>(d_tab, nh, sid, op, c, x, q, out);
   count_launch();
-  cudaError_t e = cudaGetLastError();
-  dfree(d_tab, st);
-  CK(e);
+  CK(cudaGetLastError());
   return WT_OK;
 }
 

@@ -112,6 +112,31 @@ wt_status upload_meta(wt_struct* h);
 
 uint32_t num_sms();
 
+// Temporary device buffers of one call, returned to the pool (in stream
+// order) when the call ends, on every path.
+struct Work {
+  cudaStream_t st;
+  std::vector<void*> bufs;
+  ~Work() {
+    for (void* p : bufs) dfree(p, st);
+  }
+  template <typename T>
+  wt_status get(T** p, size_t count) {
+    void* q = nullptr;
+    cudaError_t e = dmalloc(&q, count * sizeof(T), st);
+    if (e != cudaSuccess) return WT_ERR_NO_MEMORY;
+    bufs.push_back(q);
+    *p = (T*)q;
+    return WT_OK;
+  }
+};
+
+#define TRY(x)                     \
+  do {                             \
+    wt_status s_ = (x);            \
+    if (s_ != WT_OK) return s_;    \
+  } while (0)
+
 // Host -> device copy of a small table through a kernel's parameters (no
 // copy engine: a small copy would otherwise queue behind large transfers of
 // other streams); larger tables by cudaMemcpyAsync.
