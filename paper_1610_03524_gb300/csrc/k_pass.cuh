@@ -14,12 +14,14 @@
 // The tile's digit counts and those of all earlier tiles of its sequence or
 // node come from prefix sums, taken before the pass, of every tile's digit
 // counts: the domain decomposition of Section 4.2 with K = number of tiles
-// and per-node offsets by prefix sums across the K sub-problems.  Words
-// copied whole are stored; the "boundary" words that several tiles or nodes
-// share (Section 4.2) are merged with atomicOr into the level buffer, which
-// the build zeroes first.  Finally the tile scatters its elements, narrowed
-// to the bits still needed, to T_{a+t}: the stable partition on the t-bit
-// digit (big nodes, Section 3).
+// and per-node offsets by prefix sums across the K sub-problems.  The
+// tile's level bits leave as runs, one per (level, class); the runs' output
+// words form one list, written by lanes in windows of 32 consecutive
+// entries.  Words copied whole are stored; the "boundary" words that several
+// tiles or nodes share (Section 4.2) are merged with atomicOr into the level
+// buffer, which the build zeroes first.  Finally the tile scatters its
+// elements, narrowed to the bits still needed, to T_{a+t}: the stable
+// partition on the t-bit digit (big nodes, Section 3).
 #pragma once
 #include <type_traits>
 
@@ -178,9 +180,14 @@ __global__ void __launch_bounds__(NT + 32, WT_PASS_MIN_CTAS) k_pass(const __grid
   __shared__ int s_scan[W + 1];
   __shared__ int wst[1 << TAU_MAX];
   __shared__ uint32_t s_dead[(1 << TAU_MAX) / 32];
-  __shared__ uint64_t s_lvl_bits[TAU_MAX];
-  __shared__ uint64_t* s_lvl_ptr[TAU_MAX];
   __shared__ int s_bad;
+  // the writer's flattened list of run words, in windows of 32 entries
+  constexpr int WMAX = TAU_MAX * (2 * T / 64) + 2 * (1 << TAU_MAX);
+  constexpr int WWIN = (WMAX + 31) / 32;
+  __shared__ uint8_t s_g0[1 << TAU_MAX];
+  __shared__ uint32_t s_wstart[WWIN];
+  __shared__ uint8_t s_runid[WWIN * 32];
+  __shared__ uint8_t s_winrun[WWIN];
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int bpe = DIG ? 2 : 1;
@@ -434,8 +441,9 @@ __global__ void __launch_bounds__(NT + 32, WT_PASS_MIN_CTAS) k_pass(const __grid
       }
       return spread32(b0);
     };
-    // words of every (level, class) of this tile, one flattened loop
-    uint64_t* const cls_g0 = cls_cs;  // first global bit of each class run
+    // words of every (level, class) of this tile, one flattened list: per
+    // run its output word pointer, first bit in that word and word count
+    uint64_t* const cls_wp = cls_cs;
     int nw = 0;
     if (tid < ntl) {
       const int j = 31 - __clz(tid + 1);
@@ -445,69 +453,53 @@ __global__ void __launch_bounds__(NT + 32, WT_PASS_MIN_CTAS) k_pass(const __grid
       if (!dead) {
         const uint64_t G0 = (cs + ex_cnt[tid]) * bpe;
         const uint64_t G1 = G0 + (uint64_t)ccnt[tid] * bpe;
-        nw = (int)(((G1 - 1) >> 6) - (G0 >> 6) + 1);
-        cls_g0[tid] = G0;
+        const int lo_ = DIG ? ((P.a + j) >> 1) : (P.a + j);
+        if (G1 > P.lvl_len[lo_] * (uint64_t)bpe) {
+          atomicOr(P.err, ERR_INTERNAL);  // never for consistent tables
+        } else {
+          nw = (int)(((G1 - 1) >> 6) - (G0 >> 6) + 1);
+          cls_wp[tid] = (uint64_t)(P.bits + P.lvl_off[lo_] + (G0 >> 6));
+          s_g0[tid] = (uint8_t)(G0 & 63);
+        }
       }
-    } else if (tid >= NT && tid - NT < t) {
-      // the control warp: output level of each level of the pass
-      const int j = tid - NT;
-      const int lo_ = DIG ? ((P.a + j) >> 1) : (P.a + j);
-      s_lvl_bits[j] = P.lvl_len[lo_] * (uint64_t)bpe;
-      s_lvl_ptr[j] = P.bits + P.lvl_off[lo_];
     }
+    // the list in windows of 32 entries: a bit per run start, the run of
+    // each start, and the run in force at each window's first entry
+    if (tid < WWIN) s_wstart[tid] = 0u;
     int wtot;
-    const int wex = block_scan(nw, wtot);
-    if (tid < ntl) wst[tid] = wex;
-    __syncthreads();
-    // each thread takes consecutive words of the flattened list: the class of
-    // its first word by a search, the next classes by stepping (classes
-    // without words have empty ranges and are stepped over)
-    {
-      const int per = (wtot + NB - 1) / NB;
-      const int x0 = tid * per, x1 = min(wtot, x0 + per);
-      int ci = 0;
-      if (x0 < x1) {
-        int lo = 0, hi = ntl - 1;
-        while (lo < hi) {
-          const int mid = (lo + hi + 1) >> 1;
-          if (wst[mid] <= x0) lo = mid;
-          else hi = mid - 1;
-        }
-        ci = lo;
+    const int wex = block_scan(nw, wtot);  // its barriers order the zeroing
+    if (tid < ntl) {
+      wst[tid] = wex;
+      if (nw > 0 && wex + nw <= WMAX) {
+        atomicOr(&s_wstart[wex >> 5], 1u << (wex & 31));
+        s_runid[wex] = (uint8_t)tid;
+        for (int w = (wex + 31) >> 5; (w << 5) < wex + nw; w++) s_winrun[w] = (uint8_t)tid;
       }
-      int nxt = ci + 1 < ntl ? wst[ci + 1] : wtot;
-      int k = x0 - wst[ci];  // word of the run
-      // the run: level j, first global bit G0, length nbits, first tile bit lb0
-      int j = 31 - __clz(ci + 1);
-      uint64_t G0 = cls_g0[ci];
-      int nbits = (int)ccnt[ci] * bpe, lb0 = (int)cstart[ci] * bpe;
-      for (int x = x0; x < x1; x++, k++) {
-        if (x >= nxt) {
-          do {
-            ci++;
-            nxt = ci + 1 < ntl ? wst[ci + 1] : wtot;
-          } while (x >= nxt);
-          k = 0;
-          j = 31 - __clz(ci + 1);
-          G0 = cls_g0[ci];
-          nbits = (int)ccnt[ci] * bpe;
-          lb0 = (int)cstart[ci] * bpe;
+    }
+    __syncthreads();
+    if (wtot > WMAX) {
+      if (tid == 0) atomicOr(P.err, ERR_INTERNAL);  // never: bounded by the tile geometry
+    } else {
+      const uint32_t le = lt | (1u << lane);
+      for (int win = warp; (win << 5) < wtot; win += NB / 32) {
+        const int x = (win << 5) + lane;
+        const uint32_t mb = s_wstart[win] & le;
+        const int ci = mb ? (int)s_runid[(win << 5) + 31 - __clz(mb)] : (int)s_winrun[win];
+        if (x < wtot) {
+          const int k = x - wst[ci];  // word of the run
+          const int j = 31 - __clz(ci + 1);
+          uint64_t* const wp = (uint64_t*)cls_wp[ci];
+          const int g0 = s_g0[ci];
+          const int nbits = (int)ccnt[ci] * bpe, lb0 = (int)cstart[ci] * bpe;
+          const int lo = k ? 0 : g0;           // first bit of the word that is the run's
+          const int r0 = k ? 64 * k - g0 : 0;  // its index in the run
+          const int nb = min(64 - lo, nbits - r0);
+          uint64_t v = get64(j, lb0 + r0);
+          if (nb < 64) v &= (1ull << nb) - 1ull;
+          // stored when the run holds the whole word, else ORed
+          if (nb == 64) wp[k] = v;
+          else atomicOr((unsigned long long*)(wp + k), (unsigned long long)(v << lo));
         }
-        const int g0 = (int)(G0 & 63);
-        const int lo = k ? 0 : g0;            // first bit of the word that is the run's
-        const int r0 = 64 * k + lo - g0;      // its index in the run
-        const int nb = min(64 - lo, nbits - r0);
-        uint64_t v = get64(j, lb0 + r0);
-        if (nb < 64) v &= (1ull << nb) - 1ull;
-        v <<= lo;
-        const uint64_t w = (G0 >> 6) + (uint64_t)k;
-        const uint64_t nlb = s_lvl_bits[j];
-        uint64_t* const lb = s_lvl_ptr[j];
-        // stored when the run holds the whole word, or its start and the
-        // level's end; else shared with another run
-        if ((w << 6) >= nlb) atomicOr(P.err, ERR_INTERNAL);  // never for consistent tables
-        else if (lo == 0 && (nb == 64 || (w << 6) + nb == nlb)) lb[w] = v;
-        else atomicOr((unsigned long long*)(lb + w), (unsigned long long)v);
       }
     }
     __syncthreads();
