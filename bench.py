@@ -346,22 +346,27 @@ def run_native(args):
 
     # end to end through the C ABI: every step copies its input from pinned
     # host memory, builds, and reads its zero counts back on the host.  Two
-    # device buffers and two streams: the copy of step i + 1 runs while step
-    # i builds (the copy into a buffer waits for the build that last read it)
+    # device buffers, one copy stream and two build streams taken in turn:
+    # the copy of step i + 1 runs while step i builds (the copy into a buffer
+    # waits for the build that last read it), and step i + 1's build is
+    # queued before the host waits for step i's result, so the GPU never
+    # waits for the host between builds
     e2e = None
     if not args.no_e2e:
         dbufs = [torch.empty_like(d), torch.empty_like(d)]
         hz = torch.empty(L, dtype=torch.int64).pin_memory()
-        k = max(1, min(args.steps, 10))
-        sc, sb = torch.cuda.Stream(), torch.cuda.Stream()
+        k = max(1, args.steps)
+        sc = torch.cuda.Stream()
+        sbs = [torch.cuda.Stream(), torch.cuda.Stream()]
         copied = [torch.cuda.Event(), torch.cuda.Event()]
         built = [torch.cuda.Event(), torch.cuda.Event()]
         barrier()
         torch.cuda.synchronize()
         f0 = torch.cuda.Event(enable_timing=True)
         f1 = torch.cuda.Event(enable_timing=True)
-        f0.record(sb)
-        sc.wait_stream(sb)
+        f0.record(sbs[0])
+        sc.wait_stream(sbs[0])
+        sbs[1].wait_stream(sbs[0])
         lib = wt.load_library()
         view = wt.ExportView()
 
@@ -373,21 +378,30 @@ def run_native(args):
                 dbufs[b].copy_(pin, non_blocking=True)
                 copied[b].record(sc)
 
+        def finish(h):
+            # the step's result read on the host: wt_export waits for the
+            # build (its own stream only) and copies the 16 per-level zero
+            # counts device -> host; then the structure is released (its
+            # memory returns to the pool)
+            wt._check(lib.wt_export(h.raw, ctypes.byref(view)), "wt_export")
+            hz.numpy()[:] = np.ctypeslib.as_array(view.zeros, shape=(L,)).view(np.int64)
+            h.free()
+
         copy_in(0)
+        prev = None
         for i in range(k):
             if i + 1 < k:
                 copy_in(i + 1)
             b = i % 2
-            sb.wait_event(copied[b])
-            h = wt.wm_build(dbufs[b], SIGMA, stream=sb)
-            built[b].record(sb)
-            # the step's result read on the host: wt_export waits for the
-            # build and copies the 16 per-level zero counts device -> host;
-            # then the structure is released (its memory returns to the pool)
-            wt._check(lib.wt_export(h.raw, ctypes.byref(view)), "wt_export")
-            hz.numpy()[:] = np.ctypeslib.as_array(view.zeros, shape=(L,)).view(np.int64)
-            h.free()
-        f1.record(sb)
+            sbs[b].wait_event(copied[b])
+            h = wt.wm_build(dbufs[b], SIGMA, stream=sbs[b])
+            built[b].record(sbs[b])
+            if prev is not None:
+                finish(prev)
+            prev = h
+        finish(prev)
+        sbs[0].wait_stream(sbs[1])
+        f1.record(sbs[0])
         torch.cuda.synchronize()
         barrier()
         e_ms = f0.elapsed_time(f1) / k
