@@ -159,28 +159,33 @@ def kernel_hash():
     return h.hexdigest()[:16]
 
 
-def profiled_traffic():
-    """Per-launch DRAM bytes of the pass kernel from the committed ncu summary,
-    if it was taken on the current kernel source (else None)."""
+def profiled_fields():
+    """Machine-readable figures of the committed ncu summary of the pass
+    kernel (per-launch DRAM traffic at full size, issue-slot use, IPC), if it
+    was taken on the current kernel source (else an empty dict)."""
     try:
         txt = open(PROFILE_TXT).read()
     except OSError:
-        return None
-    kh = ts = None
+        return {}
+    kh, out = None, {}
     for ln in txt.splitlines():
-        if ln.startswith("kernel_source_sha256_16:"):
-            kh = ln.split(":", 1)[1].strip()
-        if ln.startswith("traffic_bytes_per_launch_full_size:"):
+        key, _, val = ln.partition(":")
+        if key == "kernel_source_sha256_16":
+            kh = val.strip()
+        elif key in ("traffic_bytes_per_launch_full_size", "issue_active_frac", "inst_per_cycle_per_sm"):
             try:
-                ts = float(ln.split(":", 1)[1].strip())
+                out[key] = float(val.strip())
             except ValueError:
-                ts = None
-    return ts if (kh == kernel_hash() and ts) else None
+                pass
+    return out if kh == kernel_hash() else {}
 
 
-# --------------------------------------------------------------------------
-# CPU oracle baseline (test infrastructure, timed as it stands)
-# --------------------------------------------------------------------------
+def profiled_traffic():
+    """Per-launch DRAM bytes of the pass kernel from the committed ncu summary,
+    if it was taken on the current kernel source (else None)."""
+    return profiled_fields().get("traffic_bytes_per_launch_full_size")
+
+
 def oracle_step(S_sample, sigma):
     import oracle
     import numpy as np
@@ -338,6 +343,15 @@ def run_native(args):
             "algorithmic_bytes_per_launch": alg_bytes / max(pass_launches, 1),
             "avg_launch_ms": pass_ms / max(pass_launches, 1),
             "pass_share_of_step": (pass_ms / args.steps) / ms if ms > 0 else None}
+    # what bounds the kernel in practice: instruction issue (from the same
+    # ncu summary; a diagnostic beside the HBM roofline, 4 issue slots per SM
+    # and cycle)
+    pf = profiled_fields()
+    if "issue_active_frac" in pf:
+        roof["issue_diagnostic"] = {"issue_slots_used_frac": pf["issue_active_frac"],
+                                    "inst_per_cycle_per_sm": pf.get("inst_per_cycle_per_sm"),
+                                    "peak_inst_per_cycle_per_sm": 4.0,
+                                    "source": "ncu --set full, 2^26 symbols (profiles/)"}
     # whole-step byte models: B(tau=8) ~ 10.16 n (histogram 2n, passes 6n,
     # directory 2.16n); B_min = n w + L n / 8 + directory writes (L n / 128 +
     # L n / 512 select samples) = 4.156 n, a single ideal pass
