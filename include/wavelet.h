@@ -59,8 +59,11 @@ typedef void* wt_stream;
 /* Build options; a zero field means "choose automatically".
  *  tau           levels per partition pass (1..8); the paper's tau (Sections 3, 4.1).
  *  tile_symbols  symbols per tile; the paper's sub-sequence size n/K (Section 4.2).
- *  ctas_per_sm   resident CTAs per SM for the persistent partition kernel.
- *  k_chunks      number of tiles K; overrides tile_symbols when set.
+ *                Only 0 or 4096 (the partition kernel's tile) is supported; other
+ *                values return WT_ERR_UNSUPPORTED.
+ *  ctas_per_sm   resident CTAs per SM for the persistent partition kernel (capped
+ *                at the kernel's occupancy).
+ *  k_chunks      number of tiles K; only 0 (K = ceil(n / 4096)) is supported.
  *  select_sample sampling period of the select directory; only 4096 is supported.
  *  flags         WT_FLAG_* below. */
 typedef struct {

@@ -14,15 +14,12 @@ namespace {
 
 bool valid_width(uint32_t w) { return w == 1 || w == 2 || w == 4; }
 
-bool sigma_fits_width(uint32_t sigma, uint32_t w) {
-  return w == 4 || (uint64_t)sigma <= ((uint64_t)1 << (8 * w));
-}
-
 wt_status check_opts(const wt_build_opts* o) {
   if (!o) return WT_OK;
   if (o->tau > 8) return WT_ERR_INVALID_ARG;
   if (o->select_sample != 0 && o->select_sample != 4096) return WT_ERR_UNSUPPORTED;
-  if (o->tile_symbols != 0 && o->tile_symbols != 8192) return WT_ERR_UNSUPPORTED;
+  // the partition kernel's tile is fixed at PASS_T symbols; K follows from n
+  if (o->tile_symbols != 0 && o->tile_symbols != (uint32_t)PASS_T) return WT_ERR_UNSUPPORTED;
   if (o->k_chunks != 0) return WT_ERR_UNSUPPORTED;
   return WT_OK;
 }
@@ -126,9 +123,6 @@ wt_status seq_build(int kind, const void* d_seq, uint64_t n, uint32_t sigma, uin
   if (!out) return WT_ERR_INVALID_ARG;
   *out = nullptr;
   if ((!d_seq && n) || sigma == 0 || !valid_width(width)) return WT_ERR_INVALID_ARG;
-  if (!sigma_fits_width(sigma, width) && width < 4) {
-    // symbols >= sigma cannot be stored anyway; sigma above the width range is allowed
-  }
   wt_status s = check_opts(opts);
   if (s != WT_OK) return s;
   if (kind == WT_KIND_MULTI && degree != 4) return WT_ERR_UNSUPPORTED;

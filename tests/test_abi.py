@@ -89,3 +89,24 @@ def test_library_huffman_ties_match_oracle(lib, seed, sigma, hi):
     lo, mo = oracle.huffman_lengths(hist, 32)
     assert ma == mo and np.array_equal(la, lo)
     assert np.array_equal(lib.canonical_codes(la), oracle.canonical_codes(lo))
+
+
+def test_unsupported_options_are_rejected_before_device_work(lib):
+    # options are checked before any allocation or launch, so this runs on
+    # the host alone: an empty sequence with each unsupported option
+    so = lib.load_library()
+    bad = [dict(tau=9, status=1), dict(tile_symbols=8192, status=6), dict(tile_symbols=100, status=6),
+           dict(k_chunks=5, status=6), dict(select_sample=1000, status=6)]
+    for b in bad:
+        o = lib.BuildOpts()
+        for f in ("tau", "tile_symbols", "k_chunks", "select_sample"):
+            setattr(o, f, b.get(f, 0))
+        h = ctypes.c_void_p()
+        for fn in (so.wm_build, so.wt_build):
+            assert fn(None, 0, 4, 2, ctypes.byref(o), None, ctypes.byref(h)) == b["status"], b
+            assert not h.value
+    # invalid widths and sigma are rejected the same way
+    h = ctypes.c_void_p()
+    assert so.wm_build(None, 0, 4, 3, None, None, ctypes.byref(h)) == 1
+    assert so.wm_build(None, 0, 0, 2, None, None, ctypes.byref(h)) == 1
+    assert so.wm_build(None, 5, 4, 2, None, None, ctypes.byref(h)) == 1

@@ -3,7 +3,7 @@ CPU oracle on the same seeded inputs.  All arithmetic is integer, so every
 bitmap word, directory record, select sample, zero count and query answer
 must be bit-exact (tolerance 0).
 
-Sizes span several 8192-symbol tiles with ragged tails; edge cases cover
+Sizes span several 4096-symbol tiles with ragged tails; edge cases cover
 empty, single-symbol, sigma in {1, 2, 3, 5, 2^k, 2^k+1}, constant and sorted
 inputs, every tau, and a symbol >= sigma."""
 import numpy as np
