@@ -181,9 +181,11 @@ typedef struct {
  * outs[i] receives the handle of items[i], exactly the structure wm_build
  * returns for it; the m handles share one device allocation, released when
  * the last of them is freed.  opts->tau == 0 takes each sequence's levels
- * per pass from the autotuner's table (8 when not tuned).  A symbol >= sigma
- * is reported on that sequence's handle only; a device wait that ran out is
- * reported on every handle of the batch.  On error every outs[i] is NULL. */
+ * per pass from the autotuner's table (8 when not tuned).  Each sequence has
+ * its own error word: a symbol >= sigma (WT_ERR_SYMBOL_GE_SIGMA), or a failed
+ * internal consistency check of its tiles (WT_ERR_CUDA; never for consistent
+ * tables), is reported on that sequence's handle only.  A failed call
+ * (invalid argument, no memory, a CUDA error) sets every outs[i] to NULL. */
 wt_status wm_batch_build(const wt_batch_item* items, uint32_t m, const wt_build_opts* opts,
                          wt_stream stream, wt_handle* outs);
 
