@@ -11,14 +11,18 @@
  *  * Pointers named d_* are device pointers (CUDA global memory of the
  *    current device); h_* are host pointers.  Sizes are element counts.
  *  * `stream` is a cudaStream_t passed as void* (NULL = legacy default
- *    stream).  Every call only enqueues work on it and returns; results are
- *    final once the stream is synchronised.  Device-side errors found during
+ *    stream).  Builds and queries enqueue their work on it and return
+ *    (huff_wt_build synchronises once, as stated there); results are final
+ *    once the stream is synchronised.  Calls that hand results to the host
+ *    (wt_sync, wt_export, wt_export_select, wt_dd_merge for its parts,
+ *    wt_free, wm_autotune) synchronise the handle's stream themselves.  Device-side errors found during
  *    a build (a symbol >= sigma: WT_ERR_SYMBOL_GE_SIGMA; an internal table
  *    that disagrees with the data, which leaves the affected bits unwritten:
  *    WT_ERR_CUDA) are reported by wt_sync() or by the next call on the handle.
  *  * Symbol sequences are contiguous arrays of width_bytes = 1, 2 or 4
  *    (little-endian unsigned), read-only, borrowed for the duration of the
- *    call and never retained.
+ *    call and never retained.  n must be below 2^40; longer sequences return
+ *    WT_ERR_UNSUPPORTED.
  *  * A build returns WT_OK and a handle in *out, or an error status and
  *    leaves *out == NULL.  The handle owns every array it exports (except
  *    the caller's bitvector for rs_build) until wt_free().
