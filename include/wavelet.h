@@ -286,9 +286,10 @@ wt_status wt_select(wt_handle h, const uint32_t* d_c, const uint64_t* d_k, uint6
  * built with the same sigma and with directories; *out receives the
  * structure of the concatenation S_0 S_1 ... S_{r-1}, bit for bit the one a
  * single build of it gives, with its own directories (opts->flags may ask
- * for WT_FLAG_SELECT_O1, or skip them with WT_FLAG_NO_DIRECTORY).  The parts are read (each is synchronised first)
- * and stay valid.  Limits: ceil(log2 sigma) <= 20 and r * 2^ceil(log2
- * sigma) <= 2^26 (WT_ERR_UNSUPPORTED otherwise). */
+ * for WT_FLAG_SELECT_O1, or skip them with WT_FLAG_NO_DIRECTORY).  The parts
+ * are read (each is synchronised first) and stay valid.  Limits:
+ * ceil(log2 sigma) <= 20 and r * 2^ceil(log2 sigma) <= 2^26
+ * (WT_ERR_UNSUPPORTED otherwise). */
 wt_status wt_dd_merge(const wt_handle* parts, uint32_t r, const wt_build_opts* opts,
                       wt_stream stream, wt_handle* out);
 
@@ -345,10 +346,12 @@ wt_status wt_memcpy_d2h(void* h_dst, const void* d_src, uint64_t bytes);
 void wt_prof_enable(int on);
 wt_status wt_prof_read(uint64_t* launches, uint64_t* pass_launches, double* pass_ms);
 
-/* Host-side helpers (no GPU needed): Huffman code lengths (heap keyed by
- * (weight, id), leaf id = symbol, internal id = sigma + creation order;
- * package-merge when longer than cap) and canonical codes.  Return the
- * longest length.  Used by huff_wt_build; exported for testing. */
+/* Host-side helpers (no GPU needed): Huffman code lengths and canonical
+ * codes.  The lengths are those of Huffman's merge with ties broken by
+ * (weight, id), leaf id = symbol and internal id = sigma + creation order
+ * (computed by a two-queue merge over the leaves sorted by weight), or of
+ * package-merge when that code is longer than cap.  wt_huffman_lengths
+ * returns the longest length.  Used by huff_wt_build; exported for testing. */
 uint32_t wt_huffman_lengths(const uint64_t* h_hist, uint32_t sigma, uint32_t cap,
                             uint8_t* h_len);
 void wt_canonical_codes(const uint8_t* h_len, uint32_t sigma, uint32_t* h_code);
