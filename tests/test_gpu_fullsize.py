@@ -1,7 +1,8 @@
 """GPU checks beyond the small parity sizes.
 
-* Parity with the oracle, bit-exact, at 2^25 symbols: more tiles than the
-  look-back ring has slots, so every slot is reused within a pass.
+* Parity with the oracle, bit-exact, at 2^25 symbols: 8192 tiles, so the
+  per-tile prefix tables span many 256-tile chunks and the chunk prefixes
+  carry counts across them.
 * The headline workload at full size, in the launch configuration the
   benchmark times (wavelet matrix of n = 2^30 uint16 Zipf(1.1) symbols over
   2^16): properties that hold at any size.  Each level of a wavelet matrix
