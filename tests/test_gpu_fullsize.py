@@ -35,7 +35,7 @@ def wt():
 
 
 @pytest.mark.parametrize("kind", ["wm", "wt"])
-def test_parity_beyond_the_ring(wt, kind):
+def test_parity_across_prefix_chunks(wt, kind):
     n, sigma = 1 << 25, 4096
     S = synth.zipf(77, n, sigma, 1.1, 2)
     fn = wt.wm_build if kind == "wm" else wt.wt_build
@@ -47,7 +47,7 @@ def test_parity_beyond_the_ring(wt, kind):
     h.free()
 
 
-def test_batch_parity_beyond_the_ring(wt):
+def test_batch_parity_across_prefix_chunks(wt):
     seqs = [(synth.uniform(80 + i, n, s, 2), s) for i, (n, s) in
             enumerate([(1 << 23, 256), (3 << 22, 65536), (1 << 22, 4), (5 << 21, 4096)])]
     hs = wt.wm_batch_build([to_dev(S) for S, _ in seqs], [s for _, s in seqs])
