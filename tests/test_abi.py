@@ -110,3 +110,28 @@ def test_unsupported_options_are_rejected_before_device_work(lib):
     assert so.wm_build(None, 0, 4, 3, None, None, ctypes.byref(h)) == 1
     assert so.wm_build(None, 0, 0, 2, None, None, ctypes.byref(h)) == 1
     assert so.wm_build(None, 5, 4, 2, None, None, ctypes.byref(h)) == 1
+
+
+@pytest.mark.parametrize("compiler,std", [("gcc", "-std=c99"), ("g++", "-std=c++17")])
+def test_c_client_compiles_and_links(lib, tmp_path, compiler, std):
+    # the boundary is plain C: a C99 (and a C++) program using only the
+    # header and the CUDA runtime compiles warning-free and links against the
+    # library, every call it makes resolving (it is not run without a GPU)
+    import shutil
+    import subprocess
+    cc = shutil.which(compiler)
+    if cc is None:
+        pytest.skip(f"{compiler} not found")
+    cuda = os.environ.get("CUDA_HOME", "/usr/local/cuda")
+    if not os.path.exists(os.path.join(cuda, "include", "cuda_runtime_api.h")):
+        pytest.skip("CUDA headers not found")
+    src = os.path.join(ROOT, "tests", "abi_client.c")
+    libdir = os.path.dirname(lib.LIB_PATH)
+    cmd = [cc, std, "-Wall", "-Wextra", "-Werror", "-pedantic"]
+    if compiler == "g++":
+        cmd += ["-x", "c++"]
+    cmd += [src, "-I", os.path.join(ROOT, "include"), "-isystem", os.path.join(cuda, "include"),
+            "-o", str(tmp_path / "abi_client"), "-L", libdir, "-l:" + os.path.basename(lib.LIB_PATH),
+            "-L", os.path.join(cuda, "lib64"), "-lcudart", "-Wl,-rpath," + libdir]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
