@@ -351,7 +351,9 @@ wt_status wt_prof_read(uint64_t* launches, uint64_t* pass_launches, double* pass
  * (weight, id), leaf id = symbol and internal id = sigma + creation order
  * (computed by a two-queue merge over the leaves sorted by weight), or of
  * package-merge when that code is longer than cap.  wt_huffman_lengths
- * returns the longest length.  Used by huff_wt_build; exported for testing. */
+ * returns the longest length, or 0 with every length 0 when no code exists
+ * (no symbol present, or more than 2^cap present symbols).  Used by
+ * huff_wt_build (cap 32); exported for testing. */
 uint32_t wt_huffman_lengths(const uint64_t* h_hist, uint32_t sigma, uint32_t cap,
                             uint8_t* h_len);
 void wt_canonical_codes(const uint8_t* h_len, uint32_t sigma, uint32_t* h_code);

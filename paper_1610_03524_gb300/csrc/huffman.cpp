@@ -59,9 +59,24 @@ void limited_lengths(const std::vector<uint64_t>& w, const std::vector<uint32_t>
 
 }  // namespace
 
+// Scratch arrays of one call.  A thread keeps them between calls for
+// alphabets of up to KEEP_MAX symbols (under ~80 MB): on a 2^20 alphabet the
+// first touch of freshly allocated arrays cost more than the merge itself.
+// Larger alphabets allocate per call.
+struct HuffScratch {
+  std::vector<uint32_t> present, leaf, big, cnt, pl, pi, depth;
+  std::vector<uint64_t> lw, iw, key, tmp;
+};
+constexpr uint32_t KEEP_MAX = 1u << 21;
+
 uint32_t huffman_lengths(const uint64_t* hist, uint32_t sigma, uint32_t cap, uint8_t* len) {
   std::fill(len, len + sigma, (uint8_t)0);
-  std::vector<uint32_t> present;
+  thread_local HuffScratch kept;
+  HuffScratch fresh;
+  HuffScratch& sc = sigma <= KEEP_MAX ? kept : fresh;
+  std::vector<uint32_t>& present = sc.present;
+  present.clear();
+  present.reserve(sigma);
   for (uint32_t s = 0; s < sigma; s++)
     if (hist[s]) present.push_back(s);
   if (present.empty()) return 0;
@@ -77,8 +92,10 @@ uint32_t huffman_lengths(const uint64_t* hist, uint32_t sigma, uint32_t cap, uin
   // position (sorted leaf rank, creation order), which keeps every array
   // below sequential in memory.
   const size_t m = present.size();
-  std::vector<uint32_t> leaf(m);   // symbols by (weight, symbol)
-  std::vector<uint64_t> lw(m);     // their weights
+  std::vector<uint32_t>& leaf = sc.leaf;  // symbols by (weight, symbol)
+  std::vector<uint64_t>& lw = sc.lw;      // their weights
+  leaf.resize(m);
+  lw.resize(m);
   {
     // `present` is in symbol order, so a stable sort on the weight alone
     // gives (weight, symbol): a counting sort when most weights are below
@@ -94,8 +111,10 @@ uint32_t huffman_lengths(const uint64_t* hist, uint32_t sigma, uint32_t cap, uin
     if (nbig <= m / 8) {
       // mostly small weights: one counting pass below K, the few heavier
       // leaves sorted apart and placed after them
-      std::vector<uint32_t> cnt(K + 1, 0);
-      std::vector<uint32_t> big;
+      std::vector<uint32_t>& cnt = sc.cnt;
+      std::vector<uint32_t>& big = sc.big;
+      cnt.assign(K + 1, 0);
+      big.clear();
       big.reserve(nbig);
       for (uint32_t x : present) {
         if (hist[x] < K) cnt[hist[x] + 1]++;
@@ -116,7 +135,10 @@ uint32_t huffman_lengths(const uint64_t* hist, uint32_t sigma, uint32_t cap, uin
         lw[s0 + i] = hist[big[i]];
       }
     } else if (wmax < (1ull << 40)) {
-      std::vector<uint64_t> key(m), tmp(m);
+      std::vector<uint64_t>& key = sc.key;
+      std::vector<uint64_t>& tmp = sc.tmp;
+      key.resize(m);
+      tmp.resize(m);
       for (size_t i = 0; i < m; i++) key[i] = (hist[present[i]] << 24) | present[i];
       int wbits = 1;
       while (wbits < 40 && (wmax >> wbits)) wbits++;
@@ -134,7 +156,7 @@ uint32_t huffman_lengths(const uint64_t* hist, uint32_t sigma, uint32_t cap, uin
         lw[i] = key[i] >> 24;
       }
     } else {
-      leaf = present;
+      leaf.assign(present.begin(), present.end());
       std::stable_sort(leaf.begin(), leaf.end(),
                        [&](uint32_t a, uint32_t b) { return hist[a] < hist[b]; });
       for (size_t i = 0; i < m; i++) lw[i] = hist[leaf[i]];
@@ -142,8 +164,12 @@ uint32_t huffman_lengths(const uint64_t* hist, uint32_t sigma, uint32_t cap, uin
   }
   // parents: of sorted leaf i at pl[i], of internal node k at pi[k]; an
   // internal parent k is stored as k (leaves and internal nodes apart)
-  std::vector<uint32_t> pl(m), pi(m - 1);
-  std::vector<uint64_t> iw(m - 1);  // weight of internal node k
+  std::vector<uint32_t>& pl = sc.pl;
+  std::vector<uint32_t>& pi = sc.pi;
+  std::vector<uint64_t>& iw = sc.iw;  // weight of internal node k
+  pl.resize(m);
+  pi.resize(m - 1);
+  iw.resize(m - 1);
   size_t li = 0, qi = 0, nint = 0;
   // take the lighter head; equal weight: the leaf (its id is smaller)
   auto take = [&](uint64_t& w, bool& is_leaf, size_t& idx) {
@@ -168,9 +194,10 @@ uint32_t huffman_lengths(const uint64_t* hist, uint32_t sigma, uint32_t cap, uin
   }
   // depths: an internal node is created after its children, so walking the
   // creation order downwards from the root gives every parent's depth first
-  std::vector<uint32_t> depth(m - 1, 0);
-  for (size_t v = m - 1; v-- > 0;)
-    if (v + 2 < m) depth[v] = depth[pi[v]] + 1;  // the root (m - 2) has depth 0
+  std::vector<uint32_t>& depth = sc.depth;
+  depth.resize(m - 1);
+  depth[m - 2] = 0;  // the root
+  for (size_t v = m - 2; v-- > 0;) depth[v] = depth[pi[v]] + 1;
   uint32_t maxlen = 0;
   for (size_t i = 0; i < m; i++) {
     const uint32_t d = depth[pl[i]] + 1;
@@ -178,6 +205,11 @@ uint32_t huffman_lengths(const uint64_t* hist, uint32_t sigma, uint32_t cap, uin
     maxlen = std::max(maxlen, d);
   }
   if (maxlen <= cap) return maxlen;
+  if (cap < 32 && m > ((size_t)1 << cap)) {
+    // no prefix code of at most cap bits has m codewords
+    std::fill(len, len + sigma, (uint8_t)0);
+    return 0;
+  }
   std::vector<uint32_t> sym = present;
   std::sort(sym.begin(), sym.end(), [&](uint32_t a, uint32_t b) {
     return hist[a] != hist[b] ? hist[a] < hist[b] : a < b;

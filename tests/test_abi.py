@@ -135,3 +135,17 @@ def test_c_client_compiles_and_links(lib, tmp_path, compiler, std):
             "-L", os.path.join(cuda, "lib64"), "-lcudart", "-Wl,-rpath," + libdir]
     r = subprocess.run(cmd, capture_output=True, text=True)
     assert r.returncode == 0, r.stderr
+
+
+def test_library_huffman_cap_feasibility(lib):
+    # 2^cap codewords at most: exactly 2^cap symbols fit (all of length cap);
+    # one more symbol has no code, reported as 0 with every length 0
+    hist = np.array([1, 2, 3, 4, 5, 6, 7, 1000], dtype=np.uint64)
+    la, ma = lib.huffman_lengths(hist, 3)
+    assert ma == 3 and np.array_equal(la, np.full(8, 3, np.uint8))
+    lo, mo = oracle.huffman_lengths(hist, 3)
+    assert mo == 3 and np.array_equal(la, lo)
+    la, ma = lib.huffman_lengths(np.append(hist, np.uint64(9)), 3)
+    assert ma == 0 and not la.any()
+    la, ma = lib.huffman_lengths(np.zeros(5, np.uint64), 3)
+    assert ma == 0 and not la.any()
