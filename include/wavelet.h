@@ -162,11 +162,15 @@ wt_status rs_build(const uint64_t* d_bits, uint64_t nbits, const wt_build_opts* 
  * Outputs, allocated by the caller: d_dir, 2*(ceil(nbits/2048)+1) u64 in the
  * rs_build record layout; d_samp0 / d_samp1, nbits/4096+1 u64 each, receiving
  * the positions of the 0-based 4096k-th zero / one (as rs_build's samples).
- * nbits must be <= 2^30; larger sizes return WT_ERR_UNSUPPORTED.  The first
- * call on a device looks up the array's device address; issue that first call
- * before any stream capture.  All calls share the scratch array, so calls
- * whose kernels overlap on the GPU race: order them (e.g. one stream).
- * Asynchronous on `stream` like every other call. */
+ * nbits must be <= 2^30; larger sizes return WT_ERR_UNSUPPORTED.  Each call
+ * outside stream capture looks up the array's device address on the current
+ * device (so the address stays right after cudaDeviceReset); a call during
+ * capture reuses the address of the last call outside capture, so issue a
+ * first call on each device before any stream capture.  All calls share the
+ * scratch array, so calls whose kernels overlap on the GPU race: order them
+ * (e.g. one stream).  WT_ERR_CUDA reports only this call's own launch errors;
+ * an error left pending by an earlier, unrelated CUDA call is neither
+ * reported nor cleared.  Asynchronous on `stream` like every other call. */
 wt_status rs_dir_build_static(const uint64_t* d_bits, uint64_t nbits, uint64_t* d_dir,
                               uint64_t* d_samp0, uint64_t* d_samp1, wt_stream stream);
 
@@ -352,8 +356,11 @@ wt_status wt_prof_read(uint64_t* launches, uint64_t* pass_launches, double* pass
  * (computed by a two-queue merge over the leaves sorted by weight), or of
  * package-merge when that code is longer than cap.  wt_huffman_lengths
  * returns the longest length, or 0 with every length 0 when no code exists
- * (no symbol present, or more than 2^cap present symbols).  Used by
- * huff_wt_build (cap 32); exported for testing. */
+ * (no symbol present, or more than 2^cap present symbols); it returns 0
+ * without writing h_len when the arguments are out of range (a NULL pointer,
+ * cap not in 1..64, sigma > 2^24: the alphabet limit of huff_wt_build).  Used by huff_wt_build (cap 32); exported for
+ * testing.  A calling thread keeps its scratch arrays (at most about 126 MB,
+ * for alphabets of up to 2^21 symbols) between calls until it exits. */
 uint32_t wt_huffman_lengths(const uint64_t* h_hist, uint32_t sigma, uint32_t cap,
                             uint8_t* h_len);
 void wt_canonical_codes(const uint8_t* h_len, uint32_t sigma, uint32_t* h_code);

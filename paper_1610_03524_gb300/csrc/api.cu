@@ -364,7 +364,9 @@ wt_status wt_prof_read(uint64_t* launches, uint64_t* pass_launches, double* pass
 
 uint32_t wt_huffman_lengths(const uint64_t* h_hist, uint32_t sigma, uint32_t cap,
                             uint8_t* h_len) {
-  if (!h_hist || !h_len || cap == 0 || cap > 64) return 0;
+  // the radix path packs (weight << 24 | symbol): the alphabet limit of
+  // huff_wt_build keeps every symbol within 24 bits
+  if (!h_hist || !h_len || cap == 0 || cap > 64 || sigma > (1u << 24)) return 0;
   return huffman_lengths(h_hist, sigma, cap, h_len);
 }
 

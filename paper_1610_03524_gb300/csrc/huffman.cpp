@@ -60,9 +60,11 @@ void limited_lengths(const std::vector<uint64_t>& w, const std::vector<uint32_t>
 }  // namespace
 
 // Scratch arrays of one call.  A thread keeps them between calls for
-// alphabets of up to KEEP_MAX symbols (under ~80 MB): on a 2^20 alphabet the
-// first touch of freshly allocated arrays cost more than the merge itself.
-// Larger alphabets allocate per call.
+// alphabets of up to KEEP_MAX symbols: on a 2^20 alphabet the first touch of
+// freshly allocated arrays cost more than the merge itself.  Seven u32 and
+// four u64 arrays of at most KEEP_MAX entries each: at most about 126 MB per
+// calling thread, kept until the thread exits.  Larger alphabets allocate
+// per call.
 struct HuffScratch {
   std::vector<uint32_t> present, leaf, big, cnt, pl, pi, depth;
   std::vector<uint64_t> lw, iw, key, tmp;

@@ -23,23 +23,26 @@
 
 namespace wtk {
 
-wt_status scan_excl_u64_pub(const uint64_t* in, uint64_t* out, uint64_t n, uint64_t* scratch,
-                            cudaStream_t st);
-
 // Largest bitvector accepted: 2^30 bits (2^19 superblocks of 2048 bits).
 constexpr uint64_t NOALLOC_MAX_BITS = 1ull << 30;
 constexpr uint64_t NOALLOC_MAX_SB = NOALLOC_MAX_BITS / 2048;
+// the scan below: 1024 threads x 4 counts per block
+constexpr int NA_BT = 1024, NA_PER = 4, NA_CH = NA_BT * NA_PER;
 // superblock zero counts, scanned in place (+1 total), then the scan's block
-// sums (n/4096 + 2 entries)
-constexpr uint64_t NOALLOC_SCRATCH = (NOALLOC_MAX_SB + 1) + (NOALLOC_MAX_SB / 4096 + 2);
+// sums (one per block of NA_CH counts, + total)
+constexpr uint64_t NOALLOC_SCRATCH = (NOALLOC_MAX_SB + 1) + (NOALLOC_MAX_SB / NA_CH + 2);
 
 static __device__ __align__(256) uint64_t g_noalloc_scratch[NOALLOC_SCRATCH];
 
 namespace {
 
-// Host-side device address of g_noalloc_scratch, looked up once per device
-// with that device current (the symbol name itself is only a host stand-in).
-uint64_t* scratch_ptr(int dev, cudaError_t* err) {
+// Host-side device address of g_noalloc_scratch on device `dev` (the symbol
+// name itself is only a host stand-in).  Looked up with that device current
+// on every call outside stream capture, so the address stays right after a
+// cudaDeviceReset reloads the module; during capture the address from the
+// last call outside capture is used (the lookup may load the module, which
+// capture does not allow).
+uint64_t* scratch_ptr(int dev, bool capturing, cudaError_t* err) {
   static std::mutex mu;
   static uint64_t* ptrs[64] = {nullptr};
   std::lock_guard<std::mutex> lock(mu);
@@ -48,16 +51,87 @@ uint64_t* scratch_ptr(int dev, cudaError_t* err) {
     *err = cudaErrorInvalidDevice;
     return nullptr;
   }
-  if (!ptrs[dev]) {
+  if (!capturing) {
     void* p = nullptr;
     cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
     if (e != cudaSuccess) {
       *err = e;
+      ptrs[dev] = nullptr;
       return nullptr;
     }
     ptrs[dev] = (uint64_t*)p;
+  } else if (!ptrs[dev]) {
+    *err = cudaErrorStreamCaptureUnsupported;
   }
   return ptrs[dev];
+}
+
+// exclusive scan of n u64 in place (out[n] = total): per-block sums, a scan
+// of the sums in one block, then each block's scan from its offset
+__device__ uint64_t na_block_scan(uint64_t v, uint64_t* total) {
+  __shared__ uint64_t ws[32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint64_t x = v;
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint64_t y = __shfl_up_sync(FULL, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) ws[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    const int nw = blockDim.x >> 5;
+    uint64_t t = lane < nw ? ws[lane] : 0;
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint64_t y = __shfl_up_sync(FULL, t, o);
+      if (lane >= o) t += y;
+    }
+    if (lane < nw) ws[lane] = t;
+  }
+  __syncthreads();
+  const uint64_t base = warp ? ws[warp - 1] : 0;
+  if (total) *total = ws[(blockDim.x >> 5) - 1];
+  __syncthreads();
+  return base + x - v;
+}
+
+__global__ void k_na_scan_sums(const uint64_t* a, uint64_t n, uint64_t* bsum) {
+  const uint64_t i0 = (uint64_t)blockIdx.x * NA_CH + (uint64_t)threadIdx.x * NA_PER;
+  uint64_t s = 0;
+  for (int k = 0; k < NA_PER; k++) s += i0 + k < n ? a[i0 + k] : 0;
+  uint64_t tot;
+  na_block_scan(s, &tot);
+  if (threadIdx.x == 0) bsum[blockIdx.x] = tot;
+}
+
+__global__ void k_na_scan_top(uint64_t* bsum, uint64_t nb) {
+  __shared__ uint64_t carry;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  for (uint64_t c0 = 0; c0 < nb; c0 += blockDim.x) {
+    const uint64_t i = c0 + threadIdx.x;
+    uint64_t tot;
+    const uint64_t ex = na_block_scan(i < nb ? bsum[i] : 0, &tot);
+    if (i < nb) bsum[i] = carry + ex;
+    __syncthreads();
+    if (threadIdx.x == 0) carry += tot;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) bsum[nb] = carry;
+}
+
+__global__ void k_na_scan_down(uint64_t* a, uint64_t n, const uint64_t* bsum) {
+  const uint64_t i0 = (uint64_t)blockIdx.x * NA_CH + (uint64_t)threadIdx.x * NA_PER;
+  uint64_t v[NA_PER], s = 0;
+  for (int k = 0; k < NA_PER; k++) {
+    v[k] = i0 + k < n ? a[i0 + k] : 0;
+    s += v[k];
+  }
+  uint64_t ex = na_block_scan(s, nullptr) + bsum[blockIdx.x];
+  for (int k = 0; k < NA_PER; k++) {
+    if (i0 + k < n) a[i0 + k] = ex;
+    ex += v[k];
+  }
+  if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) a[n] = bsum[gridDim.x];
 }
 
 __global__ void k_rs_count_static(const uint64_t* bits, uint64_t nbits, uint64_t nsb,
@@ -139,6 +213,22 @@ __global__ void k_rs_select_static(const uint64_t* bits, uint64_t nbits, uint64_
 
 using namespace wtk;
 
+// One launch with its own return code: the error of this launch only (an
+// error an earlier, unrelated call left pending is neither reported as this
+// call's nor cleared).
+template <class T>
+struct same_type {
+  using type = T;
+};
+template <typename... A>
+static cudaError_t launch(void (*k)(A...), unsigned grid, unsigned block, cudaStream_t st,
+                          typename same_type<A>::type... args) {
+  void* pa[] = {(void*)&args...};
+  const cudaError_t e = cudaLaunchKernel((const void*)k, dim3(grid), dim3(block), pa, 0, st);
+  if (e == cudaSuccess) count_launch();
+  return e;
+}
+
 extern "C" wt_status rs_dir_build_static(const uint64_t* d_bits, uint64_t nbits, uint64_t* d_dir,
                                          uint64_t* d_samp0, uint64_t* d_samp1,
                                          wt_stream stream) {
@@ -150,31 +240,42 @@ extern "C" wt_status rs_dir_build_static(const uint64_t* d_bits, uint64_t nbits,
   if (!d_dir || (nbits && (!d_bits || !d_samp0 || !d_samp1))) return WT_ERR_INVALID_ARG;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return WT_ERR_CUDA;
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cap) != cudaSuccess) return WT_ERR_CUDA;
   cudaError_t err;
-  uint64_t* scr = scratch_ptr(dev, &err);
+  uint64_t* scr = scratch_ptr(dev, cap != cudaStreamCaptureStatusNone, &err);
   if (!scr) {
-    fprintf(stderr, "rs_dir_build_static: cudaGetSymbolAddress failed: %s\n",
+    fprintf(stderr, "rs_dir_build_static: no device address of the scratch array: %s\n",
             cudaGetErrorString(err));
     return WT_ERR_CUDA;
   }
-  cudaStream_t st = (cudaStream_t)stream;
   const uint64_t nsb = (nbits + 2047) / 2048;
   uint64_t* sbz = scr;                 // nsb + 1 entries, scanned in place
   uint64_t* bsum = scr + NOALLOC_MAX_SB + 1;
-  if (nsb) {
-    const unsigned grid = (unsigned)((nsb * 32 + 255) / 256);
-    k_rs_count_static<<<grid, 256, 0, st>>>(d_bits, nbits, nsb, d_dir, sbz);
-    count_launch();
-  }
   // every scratch entry read below is written first by this call
-  wt_status s = scan_excl_u64_pub(sbz, sbz, nsb, bsum, st);
-  if (s != WT_OK) return s;
-  k_rs_finish_static<<<(unsigned)((nsb + 1 + 255) / 256), 256, 0, st>>>(nsb, sbz, d_dir);
-  count_launch();
+  cudaError_t e = cudaSuccess;
+  const uint64_t nb = (nsb + NA_CH - 1) / NA_CH;
   if (nsb) {
-    k_rs_select_static<<<(unsigned)((nsb + 255) / 256), 256, 0, st>>>(d_bits, nbits, nsb, d_dir,
-                                                                       d_samp0, d_samp1);
-    count_launch();
+    e = launch(k_rs_count_static, (unsigned)((nsb * 32 + 255) / 256), 256u, st, d_bits, nbits,
+               nsb, d_dir, sbz);
+    if (e == cudaSuccess) e = launch(k_na_scan_sums, (unsigned)nb, (unsigned)NA_BT, st,
+                                     sbz, nsb, bsum);
+    if (e == cudaSuccess) e = launch(k_na_scan_top, 1u, (unsigned)NA_BT, st, bsum, nb);
+    if (e == cudaSuccess) e = launch(k_na_scan_down, (unsigned)nb, (unsigned)NA_BT, st, sbz, nsb,
+                                     bsum);
+  } else {
+    e = cudaMemsetAsync(sbz, 0, sizeof(uint64_t), st);
   }
-  return cudaGetLastError() == cudaSuccess ? WT_OK : WT_ERR_CUDA;
+  if (e == cudaSuccess) e = launch(k_rs_finish_static, (unsigned)((nsb + 1 + 255) / 256), 256u,
+                                   st, nsb, sbz, d_dir);
+  if (e == cudaSuccess && nsb)
+    e = launch(k_rs_select_static, (unsigned)((nsb + 255) / 256), 256u, st, d_bits, nbits, nsb,
+               d_dir, d_samp0, d_samp1);
+  if (e != cudaSuccess) {
+    cudaGetLastError();  // this call's own launch error, returned as the status
+    fprintf(stderr, "rs_dir_build_static: %s\n", cudaGetErrorString(e));
+    return WT_ERR_CUDA;
+  }
+  return WT_OK;
 }

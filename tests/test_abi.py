@@ -149,3 +149,41 @@ def test_library_huffman_cap_feasibility(lib):
     assert ma == 0 and not la.any()
     la, ma = lib.huffman_lengths(np.zeros(5, np.uint64), 3)
     assert ma == 0 and not la.any()
+
+
+@pytest.mark.parametrize("kind", ["powers", "steep", "noisy"])
+def test_library_length_limited_cost_is_optimal(lib, kind):
+    """The library's length-limited lengths, pinned without the oracle's
+    package-merge: for caps that bind, the cost sum(w * len) equals the
+    optimum of an independent dynamic program over depths, every length is
+    at most the cap and the code is complete (Kraft sum exactly 1)."""
+    from test_oracle_pins import limited_cost_dp
+    rng = np.random.default_rng({"powers": 1, "steep": 2, "noisy": 3}[kind])
+    if kind == "powers":
+        w = [2 ** i for i in range(26)]
+    elif kind == "steep":
+        w = [int(1.8 ** i) + i for i in range(28)]
+    else:
+        w = [int(2.1 ** i * rng.uniform(0.6, 1.4)) + 1 for i in range(24)] + [1, 1, 2, 3]
+    order = rng.permutation(len(w))
+    hist = np.array([w[i] for i in order], dtype=np.uint64)
+    _, free_max = lib.huffman_lengths(hist, 64)
+    for cap in (free_max - 1, 16, 10, 6):
+        if (1 << cap) < len(w):
+            continue
+        assert cap < free_max  # the cap binds
+        ln, mx = lib.huffman_lengths(hist, cap)
+        assert 0 < mx <= cap and int(ln.max()) == mx
+        assert sum(2.0 ** -int(x) for x in ln) == 1.0
+        assert int((hist * ln.astype(np.uint64)).sum()) == limited_cost_dp([int(x) for x in hist],
+                                                                          cap)
+
+
+def test_library_huffman_rejects_out_of_range(lib):
+    hist = np.ones(4, dtype=np.uint64)
+    ln = np.full(4, 7, dtype=np.uint8)
+    so = lib.load_library()
+    assert so.wt_huffman_lengths(hist.ctypes.data, (1 << 24) + 1, 32, ln.ctypes.data) == 0
+    assert so.wt_huffman_lengths(hist.ctypes.data, 4, 0, ln.ctypes.data) == 0
+    assert so.wt_huffman_lengths(hist.ctypes.data, 4, 65, ln.ctypes.data) == 0
+    assert (ln == 7).all()  # not written
