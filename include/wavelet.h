@@ -15,7 +15,7 @@
  *    (huff_wt_build synchronises once, as stated there); results are final
  *    once the stream is synchronised.  Calls that hand results to the host
  *    (wt_sync, wt_export, wt_export_select, wt_dd_merge for its parts,
- *    wt_free, wm_autotune) synchronise the handle's stream themselves.  Device-side errors found during
+ *    wt_free, wm_autotune, wm_autotune_config) synchronise the handle's stream themselves.  Device-side errors found during
  *    a build (a symbol >= sigma: WT_ERR_SYMBOL_GE_SIGMA; an internal table
  *    that disagrees with the data, which leaves the affected bits unwritten:
  *    WT_ERR_CUDA) are reported by wt_sync() or by the next call on the handle.
@@ -63,11 +63,15 @@ typedef void* wt_stream;
 /* Build options; a zero field means "choose automatically".
  *  tau           levels per partition pass (1..8); the paper's tau (Sections 3, 4.1).
  *  tile_symbols  symbols per tile; the paper's sub-sequence size n/K (Section 4.2).
- *                Only 0 or 4096 (the partition kernel's tile) is supported; other
- *                values return WT_ERR_UNSUPPORTED.
+ *                wm_build: 2048, 4096 or 8192; the trees, 4-ary trees and batched
+ *                builds: 4096 only.  Other values return WT_ERR_UNSUPPORTED.
  *  ctas_per_sm   resident CTAs per SM for the persistent partition kernel (capped
  *                at the kernel's occupancy).
- *  k_chunks      number of tiles K; only 0 (K = ceil(n / 4096)) is supported.
+ *  k_chunks      number of tiles K; only 0 (K = ceil(n / tile_symbols)) is
+ *                supported.
+ *  wm_build fills tau, tile_symbols and ctas_per_sm left at 0 from the
+ *  autotuner's record for the sequence's (L, ceil(log2 n)), if any (see
+ *  wm_autotune_config), else tau 8, 4096 symbols and the occupancy limit.
  *  select_sample sampling period of the select directory; only 4096 is supported.
  *  flags         WT_FLAG_* below. */
 typedef struct {
@@ -197,16 +201,60 @@ typedef struct {
 wt_status wm_batch_build(const wt_batch_item* items, uint32_t m, const wt_build_opts* opts,
                          wt_stream stream, wt_handle* outs);
 
+/* The same batched build behind one object (Section 4.2's decomposition
+ * across sub-problems, as wm_batch_build): a caller that builds and releases
+ * many sequences per step handles one object instead of m.  *out receives
+ * the batch, or NULL on a failed call (the statuses of wm_batch_build).
+ * wt_batch_handle(b, i) returns the structure of items[i] (borrowed: valid
+ * until wt_batch_free, never passed to wt_free; NULL for i >= m).
+ * wt_batch_sync waits for the batch's stream once and writes the status of
+ * every sequence into st[0..m) (st may be NULL); it returns WT_OK when every
+ * sequence built, else the first failing status.  wt_batch_free releases
+ * every structure of the batch (waiting for the work queued on its stream)
+ * and the object. */
+typedef struct wt_batch_s* wt_batch;
+wt_status wm_batch_build_one(const wt_batch_item* items, uint32_t m, const wt_build_opts* opts,
+                             wt_stream stream, wt_batch* out);
+wt_handle wt_batch_handle(wt_batch b, uint32_t i);
+wt_status wt_batch_sync(wt_batch b, wt_status* st);
+wt_status wt_batch_free(wt_batch b);
+
 /* Autotuner for the levels per pass tau (Section 4.2: fewer, wider passes
  * against more work per pass).  Times wavelet-matrix builds of d_seq
  * (without directories; one untimed and the best of two timed builds) for
  * tau = 1 .. min(8, L), writes the fastest to *best_tau and the times to
- * ms_out[tau-1] (ms_out may be NULL; 0 where not tried), and records it for
- * every later wm_build / wm_batch_build with opts->tau == 0 of a sequence
- * with the same L and ceil(log2 n).  Synchronises the stream. */
+ * ms_out[tau-1] (ms_out may be NULL; 0 where not tried), and records it (with
+ * the default tile and occupancy) for every later wm_build / wm_batch_build
+ * with opts->tau == 0 of a sequence with the same L and ceil(log2 n).
+ * Synchronises the stream. */
 wt_status wm_autotune(const void* d_seq, uint64_t n, uint32_t sigma, uint32_t width_bytes,
                       wt_stream stream, uint32_t* best_tau, float* ms_out);
-/* Forgets every recorded tau. */
+/* A tuned wavelet-matrix configuration. */
+typedef struct {
+  uint32_t tau;           /* levels per partition pass */
+  uint32_t tile_symbols;  /* symbols per tile: 2048, 4096 or 8192 */
+  uint32_t ctas_per_sm;   /* resident partition CTAs per SM, 0 = as many as fit */
+  uint32_t reserved;
+  uint64_t k_chunks;      /* K = ceil(n / tile_symbols), the number of sub-problems */
+  float ms;               /* best measured build time (no directories), ms */
+} wt_tuning;
+
+/* Autotuner of the whole configuration (Section 4.2: the number of
+ * sub-problems K against the per-sub-problem work, and tau against the
+ * number of passes).  Times wavelet-matrix builds of d_seq (without
+ * directories; one untimed and the best of two timed builds per
+ * configuration): first tau = 1 .. min(8, L) at 4096-symbol tiles and full
+ * occupancy, then, for the two fastest tau, tiles of 2048 / 4096 / 8192
+ * symbols at full occupancy and at 4 and 3 CTAs per SM.  Writes the fastest
+ * to *out and records it for every later wm_build with zero options (and the
+ * tau for wm_batch_build) of a sequence with the same L and ceil(log2 n).
+ * Synchronises the stream. */
+wt_status wm_autotune_config(const void* d_seq, uint64_t n, uint32_t sigma,
+                             uint32_t width_bytes, wt_stream stream, wt_tuning* out);
+/* The configuration a wm_build with zero options takes for a sequence of n
+ * symbols over sigma (ms = 0). */
+wt_status wm_tuning(uint64_t n, uint32_t sigma, wt_tuning* out);
+/* Forgets every recorded configuration. */
 void wm_autotune_clear(void);
 
 /* Queries over several structures in one launch: query i applies d_op[i]

@@ -32,7 +32,9 @@ ABI_SYMBOLS = ("wt_build", "wm_build", "huff_wt_build", "multiary_build", "rs_bu
                "wm_batch_build", "wm_autotune", "wm_autotune_clear", "wt_query_multi",
                "wt_server_create", "wt_server_submit_build", "wt_server_submit_queries",
                "wt_server_poll", "wt_server_handle", "wt_server_release", "wt_server_stats",
-               "wt_server_destroy", "wt_export_select", "wt_dd_merge")
+               "wt_server_destroy", "wt_export_select", "wt_dd_merge", "wm_autotune_config",
+               "wm_tuning", "wm_batch_build_one", "wt_batch_handle", "wt_batch_sync",
+               "wt_batch_free")
 
 
 class WaveletError(RuntimeError):
@@ -65,6 +67,17 @@ class SelectView(ctypes.Structure):
     _fields_ = [("nranges", ctypes.c_uint64), ("nhuge", ctypes.c_uint64),
                 ("nsparse", ctypes.c_uint64), ("desc", ctypes.c_void_p), ("sub", ctypes.c_void_p),
                 ("sparse", ctypes.c_void_p), ("huge", ctypes.c_void_p)]
+
+
+class Tuning(ctypes.Structure):
+    _fields_ = [("tau", ctypes.c_uint32), ("tile_symbols", ctypes.c_uint32),
+                ("ctas_per_sm", ctypes.c_uint32), ("reserved", ctypes.c_uint32),
+                ("k_chunks", ctypes.c_uint64), ("ms", ctypes.c_float)]
+
+    def as_dict(self):
+        return {"tau": int(self.tau), "tile_symbols": int(self.tile_symbols),
+                "ctas_per_sm": int(self.ctas_per_sm), "k_chunks": int(self.k_chunks),
+                "ms": float(self.ms)}
 
 
 class BatchItem(ctypes.Structure):
@@ -144,6 +157,18 @@ def load_library(path: str = LIB_PATH):
     lib.wm_batch_build.argtypes = [c.POINTER(BatchItem), u32, c.POINTER(BuildOpts), vp, hp]
     lib.wm_autotune.restype = c.c_int
     lib.wm_autotune.argtypes = [vp, u64, u32, u32, vp, c.POINTER(u32), c.POINTER(c.c_float)]
+    lib.wm_batch_build_one.restype = c.c_int
+    lib.wm_batch_build_one.argtypes = [c.POINTER(BatchItem), u32, c.POINTER(BuildOpts), vp, hp]
+    lib.wt_batch_handle.restype = vp
+    lib.wt_batch_handle.argtypes = [vp, u32]
+    lib.wt_batch_sync.restype = c.c_int
+    lib.wt_batch_sync.argtypes = [vp, vp]
+    lib.wt_batch_free.restype = c.c_int
+    lib.wt_batch_free.argtypes = [vp]
+    lib.wm_autotune_config.restype = c.c_int
+    lib.wm_autotune_config.argtypes = [vp, u64, u32, u32, vp, c.POINTER(Tuning)]
+    lib.wm_tuning.restype = c.c_int
+    lib.wm_tuning.argtypes = [u64, u32, c.POINTER(Tuning)]
     lib.wm_autotune_clear.restype = None
     lib.wm_autotune_clear.argtypes = []
     lib.wt_query_multi.restype = c.c_int
@@ -186,9 +211,9 @@ def _stream_ptr(stream):
     return ctypes.c_void_p(stream.cuda_stream)
 
 
-def _opts(tau=0, ctas_per_sm=0, flags=0):
+def _opts(tau=0, ctas_per_sm=0, flags=0, tile_symbols=0):
     o = BuildOpts()
-    o.tau, o.ctas_per_sm, o.flags = tau, ctas_per_sm, flags
+    o.tau, o.ctas_per_sm, o.flags, o.tile_symbols = tau, ctas_per_sm, flags, tile_symbols
     return o
 
 
@@ -349,10 +374,10 @@ def _build(fn, what, *args):
 
 
 def wm_build(seq, sigma: int, n: int | None = None, tau: int = 0, ctas_per_sm: int = 0,
-             flags: int = 0, stream=None) -> Handle:
+             flags: int = 0, stream=None, tile_symbols: int = 0) -> Handle:
     """Wavelet matrix of a device tensor of uint8/int16/int32 symbols."""
     n = seq.numel() if n is None else n
-    o = _opts(tau, ctas_per_sm, flags)
+    o = _opts(tau, ctas_per_sm, flags, tile_symbols)
     return _build(load_library().wm_build, "wm_build", _ptr(seq), n, sigma, _width(seq),
                   ctypes.byref(o), _stream_ptr(stream))
 
@@ -457,6 +482,70 @@ def wm_batch_build(seqs, sigmas, ns=None, tau: int = 0, flags: int = 0, stream=N
     return [Handle(ctypes.c_void_p(outs[i])) for i in range(m)]
 
 
+class _BatchMember(Handle):
+    """A structure of a Batch: usable like a Handle, released with its batch."""
+
+    def free(self):
+        self._h = None
+
+    def __del__(self):
+        pass
+
+
+class Batch:
+    """The structures of one batched build behind one object (wm_batch_build_one)."""
+
+    def __init__(self, raw: ctypes.c_void_p, m: int):
+        self._b = raw
+        self._m = m
+
+    def __len__(self):
+        return self._m
+
+    def handle(self, i: int) -> Handle:
+        if not self._b:
+            raise WaveletError(1, "batch already freed")
+        h = load_library().wt_batch_handle(self._b, i)
+        if not h:
+            raise WaveletError(1, "wt_batch_handle")
+        return _BatchMember(ctypes.c_void_p(h))
+
+    def sync(self) -> np.ndarray:
+        """Wait once; the status of every sequence (0 = built)."""
+        st = np.zeros(max(self._m, 1), dtype=np.int32)
+        load_library().wt_batch_sync(self._b, st.ctypes.data)
+        return st[:self._m]
+
+    def free(self):
+        if self._b:
+            _check(load_library().wt_batch_free(self._b), "wt_batch_free")
+            self._b = None
+
+    def __del__(self):
+        try:
+            if self._b and _lib is not None:
+                _lib.wt_batch_free(self._b)
+        except Exception:
+            pass
+
+
+def wm_batch_build_one(seqs, sigmas, ns=None, tau: int = 0, flags: int = 0,
+                       stream=None) -> Batch:
+    """wm_batch_build as one Batch object (one object per step instead of m)."""
+    m = len(seqs)
+    items = (BatchItem * max(m, 1))()
+    for i, (sq, sg) in enumerate(zip(seqs, sigmas)):
+        items[i].d_seq = _ptr(sq) if sq is not None else 0
+        items[i].n = sq.numel() if ns is None else int(ns[i])
+        items[i].sigma = int(sg)
+        items[i].width_bytes = _width(sq) if sq is not None else 2
+    b = ctypes.c_void_p()
+    o = _opts(tau, 0, flags)
+    _check(load_library().wm_batch_build_one(items, m, ctypes.byref(o), _stream_ptr(stream),
+                                              ctypes.byref(b)), "wm_batch_build_one")
+    return Batch(b, m)
+
+
 def dd_merge(parts, flags: int = 0, stream=None) -> Handle:
     """The structure of the concatenation of consecutive pieces of one
     sequence from the pieces' structures (all wavelet matrices or all
@@ -481,6 +570,25 @@ def wm_autotune(seq, sigma: int, n: int | None = None, stream=None):
     _check(load_library().wm_autotune(_ptr(seq), n, sigma, _width(seq), _stream_ptr(stream),
                                        ctypes.byref(best), ms), "wm_autotune")
     return int(best.value), [float(v) for v in ms]
+
+
+def wm_autotune_config(seq, sigma: int, n: int | None = None, stream=None) -> dict:
+    """Tune (tau, tile size, CTAs per SM) on this sequence; returns the
+    fastest configuration (with K and its build time) and records it for
+    later builds with zero options."""
+    n = seq.numel() if n is None else n
+    t = Tuning()
+    _check(load_library().wm_autotune_config(_ptr(seq), n, sigma, _width(seq),
+                                              _stream_ptr(stream), ctypes.byref(t)),
+           "wm_autotune_config")
+    return t.as_dict()
+
+
+def wm_tuning(n: int, sigma: int) -> dict:
+    """The configuration a wm_build with zero options takes."""
+    t = Tuning()
+    _check(load_library().wm_tuning(n, sigma, ctypes.byref(t)), "wm_tuning")
+    return t.as_dict()
 
 
 def wm_autotune_clear():

@@ -18,8 +18,11 @@ wt_status check_opts(const wt_build_opts* o) {
   if (!o) return WT_OK;
   if (o->tau > 8) return WT_ERR_INVALID_ARG;
   if (o->select_sample != 0 && o->select_sample != 4096) return WT_ERR_UNSUPPORTED;
-  // the partition kernel's tile is fixed at PASS_T symbols; K follows from n
-  if (o->tile_symbols != 0 && o->tile_symbols != (uint32_t)PASS_T) return WT_ERR_UNSUPPORTED;
+  // tiles of 2048, 4096 or 8192 symbols (wavelet matrix; the trees take
+  // PASS_T only, checked by the caller); K = ceil(n / tile) follows from n
+  if (o->tile_symbols != 0 && o->tile_symbols != 2048 && o->tile_symbols != 4096 &&
+      o->tile_symbols != 8192)
+    return WT_ERR_UNSUPPORTED;
   if (o->k_chunks != 0) return WT_ERR_UNSUPPORTED;
   return WT_OK;
 }
@@ -126,6 +129,9 @@ wt_status seq_build(int kind, const void* d_seq, uint64_t n, uint32_t sigma, uin
   wt_status s = check_opts(opts);
   if (s != WT_OK) return s;
   if (kind == WT_KIND_MULTI && degree != 4) return WT_ERR_UNSUPPORTED;
+  if (kind != WT_KIND_WM && opts && opts->tile_symbols != 0 &&
+      opts->tile_symbols != (uint32_t)PASS_T)
+    return WT_ERR_UNSUPPORTED;
   // the constant-time select directory packs 40-bit offsets; tile indices are 32-bit
   if (n >= ((uint64_t)1 << 40)) return WT_ERR_UNSUPPORTED;
   if ((kind == WT_KIND_WT || kind == WT_KIND_MULTI || kind == WT_KIND_HUFF) && sigma > (1u << 24))

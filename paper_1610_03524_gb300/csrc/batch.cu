@@ -44,11 +44,16 @@ wt_status dir_build_levels(const uint64_t* bits, const LevelMeta* d_meta, uint32
   } while (0)
 
 // ---------------------------------------------------------------------------
-// autotuner table: (L, ceil(log2 n)) -> levels per pass
+// autotuner table: (L, ceil(log2 n)) -> levels per pass, tile, CTAs per SM
 // ---------------------------------------------------------------------------
 namespace {
+struct TuneEntry {
+  uint8_t tau;      // 0 = not tuned
+  uint8_t tile_lg;  // log2 of the tile's symbols, 0 = default
+  uint8_t ctas;     // 0 = as many as fit
+};
 std::mutex g_tune_mu;
-uint8_t g_tune[33][65];  // 0 = not tuned
+TuneEntry g_tune[33][65];
 
 int log2_ceil(uint64_t n) {
   int k = 0;
@@ -67,17 +72,23 @@ int width_for_bits_b(int b) { return b <= 8 ? 1 : (b <= 16 ? 2 : 4); }
 uint64_t up(uint64_t x, uint64_t a) { return (x + a - 1) / a * a; }
 }  // namespace
 
-int tuned_tau(uint32_t L, uint64_t n) {
+TuneConfig tuned_config(uint32_t L, uint64_t n) {
   std::lock_guard<std::mutex> g(g_tune_mu);
   const int k = log2_ceil(n);
-  const int v = (L <= 32 && k <= 64) ? g_tune[L][k] : 0;
-  return v ? v : TAU_MAX;
+  const TuneEntry e = (L <= 32 && k <= 64) ? g_tune[L][k] : TuneEntry{0, 0, 0};
+  return TuneConfig{e.tau ? (int)e.tau : TAU_MAX, e.tile_lg ? 1u << e.tile_lg : (uint32_t)PASS_T,
+                    (uint32_t)e.ctas};
 }
 
-static void record_tau(uint32_t L, uint64_t n, int tau) {
+int tuned_tau(uint32_t L, uint64_t n) { return tuned_config(L, n).tau; }
+
+static void record_config(uint32_t L, uint64_t n, int tau, uint32_t tile, uint32_t ctas) {
   std::lock_guard<std::mutex> g(g_tune_mu);
   const int k = log2_ceil(n);
-  if (L <= 32 && k <= 64) g_tune[L][k] = (uint8_t)tau;
+  int lg = 0;
+  while (tile > 1u && (1u << lg) < tile) lg++;
+  if (L <= 32 && k <= 64)
+    g_tune[L][k] = TuneEntry{(uint8_t)tau, (uint8_t)(tile ? lg : 0), (uint8_t)ctas};
 }
 
 // ---------------------------------------------------------------------------
@@ -484,6 +495,66 @@ extern "C" wt_status wm_batch_build(const wt_batch_item* items, uint32_t m,
   return WT_OK;
 }
 
+struct wt_batch_s {
+  std::vector<wt_handle> hs;
+  cudaStream_t st = nullptr;
+};
+
+extern "C" wt_status wm_batch_build_one(const wt_batch_item* items, uint32_t m,
+                                        const wt_build_opts* opts, wt_stream stream,
+                                        wt_batch* out) {
+  if (!out) return WT_ERR_INVALID_ARG;
+  *out = nullptr;
+  wt_batch b = new (std::nothrow) wt_batch_s();
+  if (!b) return WT_ERR_NO_MEMORY;
+  b->hs.assign(m, nullptr);
+  b->st = (cudaStream_t)stream;
+  const wt_status s = wm_batch_build(items, m, opts, stream, b->hs.data());
+  if (s != WT_OK) {
+    delete b;
+    return s;
+  }
+  *out = b;
+  return WT_OK;
+}
+
+extern "C" wt_handle wt_batch_handle(wt_batch b, uint32_t i) {
+  return (b && i < b->hs.size()) ? b->hs[i] : nullptr;
+}
+
+extern "C" wt_status wt_batch_sync(wt_batch b, wt_status* st) {
+  if (!b) return WT_ERR_INVALID_ARG;
+  if (cudaStreamSynchronize(b->st) != cudaSuccess) return WT_ERR_CUDA;
+  const uint32_t m = (uint32_t)b->hs.size();
+  std::vector<wt_status> s(m, WT_OK);
+  if (m) batch_status(b->hs.data(), m, s.data());
+  wt_status first = WT_OK;
+  for (uint32_t i = 0; i < m; i++) {
+    if (st) st[i] = s[i];
+    if (first == WT_OK) first = s[i];
+  }
+  return first;
+}
+
+extern "C" wt_status wt_batch_free(wt_batch b) {
+  if (!b) return WT_ERR_INVALID_ARG;
+  // one wait for the batch's queued work, then every handle's reference to
+  // the shared arena is dropped; the last returns it to the pool
+  cudaError_t e = cudaStreamSynchronize(b->st);
+  for (wt_handle h : b->hs) {
+    if (!h) continue;
+    if (h->arena && h->arena->refs.fetch_sub(1) == 1) {
+      dfree(h->arena->base, b->st);
+      delete h->arena;
+    }
+    h->arena = nullptr;
+    delete h;
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->st);
+  delete b;
+  return e == cudaSuccess ? WT_OK : WT_ERR_CUDA;
+}
+
 extern "C" wt_status wm_autotune(const void* d_seq, uint64_t n, uint32_t sigma,
                                  uint32_t width_bytes, wt_stream stream, uint32_t* best_tau,
                                  float* ms_out) {
@@ -529,7 +600,99 @@ extern "C" wt_status wm_autotune(const void* d_seq, uint64_t n, uint32_t sigma,
   cudaEventDestroy(e1);
   if (s != WT_OK) return s;
   *best_tau = bt;
-  record_tau(L, n, (int)bt);
+  record_config(L, n, (int)bt, 0, 0);
+  return WT_OK;
+}
+
+namespace {
+// one untimed build, then the best of two timed ones (no directories)
+wt_status time_wm(const void* d_seq, uint64_t n, uint32_t sigma, uint32_t width,
+                  cudaStream_t st, uint32_t tau, uint32_t tile, uint32_t ctas, cudaEvent_t e0,
+                  cudaEvent_t e1, float* best) {
+  *best = 0.f;
+  for (int r = 0; r < 3; r++) {
+    wt_build_opts o{};
+    o.tau = tau;
+    o.tile_symbols = tile;
+    o.ctas_per_sm = ctas;
+    o.flags = WT_FLAG_NO_DIRECTORY;
+    wt_handle h = nullptr;
+    cudaEventRecord(e0, st);
+    wt_status s = wm_build(d_seq, n, sigma, width, &o, (wt_stream)st, &h);
+    cudaEventRecord(e1, st);
+    if (s != WT_OK) return s;
+    s = wt_sync(h);
+    wt_free(h);
+    if (s != WT_OK) return s;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (r > 0 && (*best == 0.f || ms < *best)) *best = ms;
+  }
+  return WT_OK;
+}
+}  // namespace
+
+extern "C" wt_status wm_autotune_config(const void* d_seq, uint64_t n, uint32_t sigma,
+                                        uint32_t width_bytes, wt_stream stream, wt_tuning* out) {
+  if ((!d_seq && n) || sigma == 0 || !out) return WT_ERR_INVALID_ARG;
+  if (width_bytes != 1 && width_bytes != 2 && width_bytes != 4) return WT_ERR_INVALID_ARG;
+  if (n >= ((uint64_t)1 << 40)) return WT_ERR_UNSUPPORTED;
+  cudaStream_t st = (cudaStream_t)stream;
+  const uint32_t L = levels_of_b(sigma);
+  const uint32_t tmax = std::min<uint32_t>(L, TAU_MAX);
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  wt_status s = WT_OK;
+  // levels per pass first, at the default tile and occupancy; then tile
+  // size and CTAs per SM at the best two of them
+  float tms[TAU_MAX + 1] = {0};
+  for (uint32_t tau = 1; tau <= tmax && s == WT_OK; tau++)
+    s = time_wm(d_seq, n, sigma, width_bytes, st, tau, 0, 0, e0, e1, &tms[tau]);
+  uint32_t t1 = tmax, t2 = 0;
+  for (uint32_t tau = 1; tau <= tmax; tau++)
+    if (tms[tau] < tms[t1]) t1 = tau;
+  for (uint32_t tau = 1; tau <= tmax; tau++)
+    if (tau != t1 && (t2 == 0 || tms[tau] < tms[t2])) t2 = tau;
+  wt_tuning best{};
+  best.tau = t1;
+  best.tile_symbols = (uint32_t)PASS_T;
+  best.ms = tms[t1];
+  const uint32_t tiles[3] = {2048, 4096, 8192};
+  const uint32_t ctas[3] = {0, 4, 3};
+  for (uint32_t tau : {t1, t2}) {
+    if (tau == 0) continue;
+    for (uint32_t tile : tiles)
+      for (uint32_t c : ctas) {
+        if (s != WT_OK) break;
+        if (tile == (uint32_t)PASS_T && c == 0) continue;  // timed above
+        float ms = 0.f;
+        s = time_wm(d_seq, n, sigma, width_bytes, st, tau, tile, c, e0, e1, &ms);
+        if (s == WT_OK && ms < best.ms) {
+          best.tau = tau;
+          best.tile_symbols = tile;
+          best.ctas_per_sm = c;
+          best.ms = ms;
+        }
+      }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (s != WT_OK) return s;
+  best.k_chunks = (n + best.tile_symbols - 1) / best.tile_symbols;
+  *out = best;
+  record_config(L, n, (int)best.tau, best.tile_symbols, best.ctas_per_sm);
+  return WT_OK;
+}
+
+extern "C" wt_status wm_tuning(uint64_t n, uint32_t sigma, wt_tuning* out) {
+  if (!out || sigma == 0) return WT_ERR_INVALID_ARG;
+  const TuneConfig c = tuned_config(levels_of_b(sigma), n);
+  *out = wt_tuning{};
+  out->tau = std::min<uint32_t>((uint32_t)c.tau, levels_of_b(sigma));
+  out->tile_symbols = c.tile;
+  out->ctas_per_sm = c.ctas;
+  out->k_chunks = (n + c.tile - 1) / c.tile;
   return WT_OK;
 }
 

@@ -124,7 +124,7 @@ __device__ __forceinline__ void for_each_symbol(const void* seq, uint64_t n, uin
 // a = g*tau .. a+t-1; its digit is the t bits below level a, its sort key the
 // digit reversed (Section 4.3: the reverse of the tau bits).
 // Validation and the first pass's digit counts, walked tile by tile (tiles
-// of PASS_T symbols, as the first partition pass sees them): each tile's
+// of `tile` symbols, as the first partition pass sees them): each tile's
 // counts of the first pass's reversed digit, and their sums, the first
 // pass's histogram, from the one read of the sequence.  The later passes
 // take their counts from their own tiles (k_tile_counts).
@@ -132,7 +132,10 @@ template <int WB>
 __global__ void __launch_bounds__(256) k_hist_digits_tiles(const void* seq, uint64_t n,
                                                            uint32_t sigma, int L, int t0,
                                                            uint64_t* hist, uint32_t* err,
-                                                           uint32_t* tcnt, uint32_t tcs) {
+                                                           uint32_t* tcnt, uint32_t tcs,
+                                                           uint32_t tile, uint4* clear,
+                                                           uint64_t clear_units,
+                                                           uint64_t clear_per) {
   using T = typename std::conditional<WB == 1, uint8_t,
                                       typename std::conditional<WB == 2, uint16_t, uint32_t>::type>::type;
   __shared__ uint32_t th[2][TC_STRIDE];
@@ -143,7 +146,7 @@ __global__ void __launch_bounds__(256) k_hist_digits_tiles(const void* seq, uint
   __syncthreads();
   const uint32_t rmask = (1u << t0) - 1u;
   const int rsh = 32 - L;
-  const uint64_t ntiles = (n + PASS_T - 1) / PASS_T;
+  const uint64_t ntiles = (n + tile - 1) / tile;
   const T* s = (const T*)seq;
   const bool vec = (((uintptr_t)seq) & 15) == 0;
   bool bad = false;
@@ -153,12 +156,14 @@ __global__ void __launch_bounds__(256) k_hist_digits_tiles(const void* seq, uint
     atomicAdd(&th[buf][(__brev(x) >> rsh) & rmask], 1u);
   };
   for (uint64_t ti = blockIdx.x; ti < ntiles; ti += gridDim.x) {
-    const uint64_t i0 = ti * PASS_T;
-    const uint64_t i1 = i0 + PASS_T < n ? i0 + PASS_T : n;
-    if (vec && i1 - i0 == PASS_T) {
+    // the first pass's levels start at zero: this tile's share of them
+    if (clear) clear_share(clear, clear_units, clear_per, ti, tid, blockDim.x);
+    const uint64_t i0 = ti * tile;
+    const uint64_t i1 = i0 + tile < n ? i0 + tile : n;
+    if (vec && i1 - i0 == tile) {
       constexpr int PER = 16 / WB;
       const uint4* v = (const uint4*)(s + i0);
-      for (int k = tid; k < PASS_T / PER; k += blockDim.x) {
+      for (int k = tid; k < (int)(tile / PER); k += blockDim.x) {
         const uint4 q = __ldcs(v + k);
         const uint32_t w[4] = {q.x, q.y, q.z, q.w};
 #pragma unroll
@@ -569,7 +574,7 @@ constexpr int PT = PASS_T, PNT = WT_PASS_NT;
 // of Section 4.2): one block per tile, the same tiles and digits as k_pass.
 template <typename E, bool BATCH>
 __global__ void __launch_bounds__(256) k_tile_counts(const __grid_constant__ PassParams P0,
-                                                     uint32_t* tcnt) {
+                                                     uint32_t* tcnt, uint32_t tile) {
   __shared__ uint32_t h[TC_STRIDE];
   __shared__ PassParams s_P;
   const PassParams& P = BATCH ? s_P : P0;
@@ -587,9 +592,9 @@ __global__ void __launch_bounds__(256) k_tile_counts(const __grid_constant__ Pas
       ts = d.start;
       cnt = (int)d.count;
     } else {
-      ts = (uint64_t)(ti - P.tile0) * PASS_T;
+      ts = (uint64_t)(ti - P.tile0) * tile;
       const uint64_t rem = P.n_in - ts;
-      cnt = (int)(rem < (uint64_t)PASS_T ? rem : (uint64_t)PASS_T);
+      cnt = (int)(rem < (uint64_t)tile ? rem : (uint64_t)tile);
     }
     const uint32_t rmask = (1u << P.t) - 1u;
     const int rsh = 32 - P.rbits;
@@ -597,9 +602,9 @@ __global__ void __launch_bounds__(256) k_tile_counts(const __grid_constant__ Pas
     const uintptr_t a = (uintptr_t)P.in + ts * (uint64_t)P.in_w;
     if (P.code_map) {
       for (int i = tid; i < cnt; i += 256) count(P.code_map[load_elem(P.in, P.in_w, ts + i)]);
-    } else if (P.in_w == 2 && cnt == PASS_T && (a & 15) == 0) {
+    } else if (P.in_w == 2 && cnt == (int)tile && (a & 15) == 0) {
       const uint4* src = (const uint4*)a;
-      for (int i = tid; i < PASS_T / 8; i += 256) {
+      for (int i = tid; i < (int)tile / 8; i += 256) {
         const uint4 q = __ldcs(src + i);
         const uint32_t w4[4] = {q.x, q.y, q.z, q.w};
 #pragma unroll
@@ -608,9 +613,9 @@ __global__ void __launch_bounds__(256) k_tile_counts(const __grid_constant__ Pas
           count(w4[k] >> 16);
         }
       }
-    } else if (P.in_w == 1 && cnt == PASS_T && (a & 15) == 0) {
+    } else if (P.in_w == 1 && cnt == (int)tile && (a & 15) == 0) {
       const uint4* src = (const uint4*)a;
-      for (int i = tid; i < PASS_T / 16; i += 256) {
+      for (int i = tid; i < (int)tile / 16; i += 256) {
         const uint4 q = __ldcs(src + i);
         const uint32_t w4[4] = {q.x, q.y, q.z, q.w};
 #pragma unroll
@@ -681,17 +686,17 @@ struct PassPlan {
 
 // tcnt_pre: the tiles' digit counts when already taken (else counted here);
 // plan: the pass's plan, made here from the totals of those counts
-template <typename E, bool DIG, bool BATCH = false>
+template <typename E, bool DIG, bool BATCH = false, int TT = PT, int TNT = PNT>
 static wt_status launch_pass_t(const PassParams& P, uint64_t max_tiles, const wt_build_opts* o,
                                cudaStream_t st, uint32_t* tcnt_pre = nullptr,
                                const PassPlan* plan = nullptr) {
-  using SM = PassSmem<E, PT, PNT, DIG>;
-  auto kern = k_pass<E, PT, PNT, DIG, BATCH>;
+  using SM = PassSmem<E, TT, TNT, DIG>;
+  auto kern = k_pass<E, TT, TNT, DIG, BATCH>;
   static bool attr = false;
   static int occ = 0;
   if (!attr) {
     CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM::bytes));
-    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, PNT + 32, SM::bytes));
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, TNT + 32, SM::bytes));
     if (occ < 1) occ = 1;
     attr = true;
   }
@@ -710,7 +715,7 @@ static wt_status launch_pass_t(const PassParams& P, uint64_t max_tiles, const wt
   if (!tcnt) {
     TRY(wk.get(&tcnt, mt * Q.tcs));
     k_tile_counts<E, BATCH><<<(unsigned)std::min<uint64_t>(mt, (uint64_t)num_sms() * 16), 256, 0,
-                              st>>>(Q, tcnt);
+                              st>>>(Q, tcnt, (uint32_t)TT);
     count_launch();
   }
   TRY(wk.get(&tchunk, ((uint64_t)nchunk + 1) * Q.tcs));
@@ -733,7 +738,7 @@ static wt_status launch_pass_t(const PassParams& P, uint64_t max_tiles, const wt
     cudaEventCreate(&e1);
     cudaEventRecord(e0, st);
   }
-  kern<<<(unsigned)grid, PNT + 32, SM::bytes, st>>>(Q);
+  kern<<<(unsigned)grid, TNT + 32, SM::bytes, st>>>(Q);
   CK(cudaGetLastError());
   count_launch();
   if (pf.on) {
@@ -745,11 +750,20 @@ static wt_status launch_pass_t(const PassParams& P, uint64_t max_tiles, const wt
   return WT_OK;
 }
 
+// tile: symbols per tile (PT for the trees; 2048, 4096 or 8192 for the
+// wavelet matrix, the 8192-symbol tile with 512 worker threads)
 static wt_status launch_pass(const PassParams& P, bool wide, bool dig, uint64_t max_tiles,
                              const wt_build_opts* o, cudaStream_t st,
-                             uint32_t* tcnt_pre = nullptr, const PassPlan* plan = nullptr) {
+                             uint32_t* tcnt_pre = nullptr, const PassPlan* plan = nullptr,
+                             uint32_t tile = PT) {
   if (dig) return wide ? launch_pass_t<uint32_t, true>(P, max_tiles, o, st, tcnt_pre, plan)
                        : launch_pass_t<uint16_t, true>(P, max_tiles, o, st, tcnt_pre, plan);
+  if (tile == 2048)
+    return wide ? launch_pass_t<uint32_t, false, false, 2048, 256>(P, max_tiles, o, st, tcnt_pre, plan)
+                : launch_pass_t<uint16_t, false, false, 2048, 256>(P, max_tiles, o, st, tcnt_pre, plan);
+  if (tile == 8192)
+    return wide ? launch_pass_t<uint32_t, false, false, 8192, 512>(P, max_tiles, o, st, tcnt_pre, plan)
+                : launch_pass_t<uint16_t, false, false, 8192, 512>(P, max_tiles, o, st, tcnt_pre, plan);
   return wide ? launch_pass_t<uint32_t, false>(P, max_tiles, o, st, tcnt_pre, plan)
               : launch_pass_t<uint16_t, false>(P, max_tiles, o, st, tcnt_pre, plan);
 }
@@ -773,12 +787,13 @@ static int pick_tau(const wt_build_opts* o, int L, bool even, uint64_t n = 0) {
 
 // common workspace of a build
 
-static wt_status alloc_outputs(wt_struct* h, uint64_t total_words) {
+// zero_bits: false when the build's own kernels zero the level buffer
+static wt_status alloc_outputs(wt_struct* h, uint64_t total_words, bool zero_bits = true) {
   CK(dmalloc((void**)&h->d_bits, total_words * 8, h->stream));
   h->d_bits_ro = h->d_bits;
   // the partition passes store whole words and OR the words shared by
   // several tiles or nodes, so the level buffer starts at zero
-  CK(cudaMemsetAsync(h->d_bits, 0, total_words * 8, h->stream));
+  if (zero_bits) CK(cudaMemsetAsync(h->d_bits, 0, total_words * 8, h->stream));
   CK(dmalloc((void**)&h->d_zeros, std::max<uint32_t>(h->levels, 1) * 8, h->stream));
   CK(cudaMemsetAsync(h->d_zeros, 0, std::max<uint32_t>(h->levels, 1) * 8, h->stream));
   return WT_OK;
@@ -840,13 +855,23 @@ wt_status build_wm(const void* d_seq, uint64_t n, uint32_t sigma, int w, const w
   h->bpe = 1;
   set_uniform_levels(h, n);
   const uint64_t W = level_words(n);
-  TRY(alloc_outputs(h, W * L));
+  // the level buffer is zeroed by the build's kernels (the histogram kernel
+  // the first pass's levels, each pass the next pass's), not by a memset
+  TRY(alloc_outputs(h, W * L, n == 0));
   Work wk{st, {}};
   if (n == 0) return build_directories(h);
+  // levels per pass, symbols per tile and CTAs per SM: the caller's, else
+  // the autotuner's for (L, ceil(log2 n)), else 8 / 4096 / the occupancy limit
+  const TuneConfig tc = tuned_config((uint32_t)L, n);
+  wt_build_opts eo = o ? *o : wt_build_opts{};
+  if (!eo.tau) eo.tau = (uint32_t)tc.tau;
+  if (!eo.tile_symbols) eo.tile_symbols = tc.tile;
+  if (!eo.ctas_per_sm) eo.ctas_per_sm = tc.ctas;
+  o = &eo;
   const int tau = pick_tau(o, L, false, n);
   std::vector<PassGeom> ps = make_passes(L, tau, w);
   const int G = (int)ps.size();
-  uint32_t T = PT;
+  const uint32_t T = o->tile_symbols;
   uint64_t *hist, *cls, *d_off, *d_len;
   uint32_t* tickets;
   int nh = 0, ncls = 0;
@@ -864,20 +889,23 @@ wt_status build_wm(const void* d_seq, uint64_t n, uint32_t sigma, int w, const w
   CK(cudaMemsetAsync(hist, 0, nh * 8, st));
   // the first pass's digit histogram and per-tile counts (with validation)
   uint32_t* tcnt0;
-  const uint64_t ntiles0 = (n + PASS_T - 1) / PASS_T;
+  const uint64_t ntiles0 = (n + T - 1) / T;
   TRY(wk.get(&tcnt0, (size_t)ntiles0 * tc_stride(ps[0].t)));
   {
     const uint32_t blocks = (uint32_t)std::min<uint64_t>((uint64_t)num_sms() * 8, ntiles0);
     const int t0 = ps[0].t;
+    // the first pass's levels: W * t0 words, a share per tile
+    uint4* const cl0 = (uint4*)h->d_bits;
+    const uint64_t cu0 = W * (uint64_t)t0 / 2, cp0 = (cu0 + ntiles0 - 1) / ntiles0;
     if (w == 1)
       k_hist_digits_tiles<1><<<blocks, 256, 0, st>>>(d_seq, n, sigma, L, t0, hist, h->d_err, tcnt0,
-                                                     tc_stride(t0));
+                                                     tc_stride(t0), T, cl0, cu0, cp0);
     else if (w == 2)
       k_hist_digits_tiles<2><<<blocks, 256, 0, st>>>(d_seq, n, sigma, L, t0, hist, h->d_err, tcnt0,
-                                                     tc_stride(t0));
+                                                     tc_stride(t0), T, cl0, cu0, cp0);
     else
       k_hist_digits_tiles<4><<<blocks, 256, 0, st>>>(d_seq, n, sigma, L, t0, hist, h->d_err, tcnt0,
-                                                     tc_stride(t0));
+                                                     tc_stride(t0), T, cl0, cu0, cp0);
     count_launch();
     CK(cudaGetLastError());
   }
@@ -913,9 +941,14 @@ wt_status build_wm(const void* d_seq, uint64_t n, uint32_t sigma, int w, const w
     P.wm_cls = cls + coff;
     P.ntiles = (uint32_t)ntiles;
     P.n_in = n;
+    if (g + 1 < G) {
+      P.clear = (uint4*)(h->d_bits + W * (uint64_t)ps[g + 1].a);
+      P.clear_units = W * (uint64_t)ps[g + 1].t / 2;
+      P.clear_per = (P.clear_units + ntiles - 1) / ntiles;
+    }
     const PassPlan plan{cls + coff, h->d_zeros};
     TRY(launch_pass(P, pg.wide, false, ntiles, o, st, g == 0 ? tcnt0 : nullptr,
-                    g == 0 ? nullptr : &plan));
+                    g == 0 ? nullptr : &plan, T));
     coff += (2 << pg.t) + pg.t + 1;
     in = P.out;
   }

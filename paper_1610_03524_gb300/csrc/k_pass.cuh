@@ -143,18 +143,24 @@ struct PassSmem {
   static constexpr size_t bytes = off_clscs + (size_t)(1 << TAU_MAX) * 8;
 };
 
-// resident CTAs per SM the register budget is sized for, and whether a
-// split keeps its 16 elements in registers between its two phases (else it
-// reads them from shared memory again)
+// resident CTAs per SM the register budget is sized for (40 registers a
+// thread at 288 threads a CTA; the 8192-symbol tile runs 544 threads a CTA,
+// 2 CTAs an SM at 60 registers),
+// and whether a split keeps its elements in registers between its two
+// phases (else it reads them from shared memory again)
 #ifndef WT_PASS_MIN_CTAS
 #define WT_PASS_MIN_CTAS 5
 #endif
+template <int T, int NT>
+struct PassCtas {
+  static constexpr int value = T >= 8192 ? 2 : WT_PASS_MIN_CTAS;
+};
 #ifndef WT_PASS_KEEP_X
 #define WT_PASS_KEEP_X 1
 #endif
 
 template <typename E, int T, int NT, bool DIG, bool BATCH>
-__global__ void __launch_bounds__(NT + 32, WT_PASS_MIN_CTAS) k_pass(const __grid_constant__ PassParams P0) {
+__global__ void __launch_bounds__(NT + 32, PassCtas<T, NT>::value) k_pass(const __grid_constant__ PassParams P0) {
   __shared__ PassParams s_P;
   const PassParams& P = BATCH ? s_P : P0;
   constexpr int W = NT / 32, PW = T / W, EPW = PW / 32, TW = T / 32, NB = NT + 32, CW = W;
@@ -181,6 +187,7 @@ __global__ void __launch_bounds__(NT + 32, WT_PASS_MIN_CTAS) k_pass(const __grid
   __shared__ int wst[1 << TAU_MAX];
   __shared__ uint32_t s_dead[(1 << TAU_MAX) / 32];
   __shared__ int s_bad;
+  __shared__ int s_oob;
   // the writer's flattened list of run words, in windows of 32 entries
   constexpr int WMAX = TAU_MAX * (2 * T / 64) + 2 * (1 << TAU_MAX);
   constexpr int WWIN = (WMAX + 31) / 32;
@@ -231,6 +238,9 @@ __global__ void __launch_bounds__(NT + 32, WT_PASS_MIN_CTAS) k_pass(const __grid
     __syncthreads();
     const uint32_t ti = s_tile;
     if (ti >= ntiles) break;
+    // this tile's share of the zeroing of a later pass's levels (stores that
+    // use the DRAM bandwidth the tile's compute leaves idle)
+    if (!BATCH && P0.clear) clear_share(P0.clear, P0.clear_units, P0.clear_per, ti, tid, NB);
     const int t = P.t;
     const int ntl = (1 << t) - 1;
     uint64_t ts;
@@ -508,21 +518,26 @@ __global__ void __launch_bounds__(NT + 32, WT_PASS_MIN_CTAS) k_pass(const __grid
     if (P.out) {
       const E* fin = cur ? bufB : bufA;
       if (tid < 8) s_dead[tid] = 0;
+      if (tid == 0) s_oob = 0;
       __syncthreads();
+      // per digit value d (the t bits above the ones still needed, i.e. the
+      // class key reversed): the output index of the tile's first element
+      // minus the tile-local start of its class (modular: may wrap)
       for (int r = tid; r < (1 << t); r += NB) {
         uint64_t cs, ce;
         bool dead;
         class_range(P, t, (uint32_t)r, node, cs, ce, dead);
         const int ci = cls_idx(t, r);
-        // modular base: cs + ex - cstart may wrap; dead classes are flagged apart
-        sbase[r] = cs + ex_cnt[ci] - cstart[ci];
-        if (dead) atomicOr(&s_dead[r >> 5], 1u << (r & 31));
+        const uint32_t d = rev_bits((uint32_t)r, t);
+        const uint64_t b0 = cs + ex_cnt[ci];
+        sbase[d] = b0 - cstart[ci];
+        if (dead) atomicOr(&s_dead[d >> 5], 1u << (d & 31));
+        else if (ccnt[ci] && b0 + ccnt[ci] > P.n_in) s_oob = 1;  // never for consistent tables
       }
       __syncthreads();
       const int nb = P.rbits - t;
       const uint32_t mask = nb >= 32 ? 0xffffffffu : ((1u << nb) - 1u);
-      const uint32_t rmask = (1u << t) - 1u;
-      const int rsh = 32 - P.rbits;
+      const uint32_t dmask = (1u << t) - 1u;
       // only Huffman trees have dead classes (elements leaving the tree)
       auto scatter = [&](auto out_t, auto huff_c) {
         using O = decltype(out_t);
@@ -530,14 +545,14 @@ __global__ void __launch_bounds__(NT + 32, WT_PASS_MIN_CTAS) k_pass(const __grid
         O* const out = (O*)P.out;
         for (int p = tid; p < cnt; p += NB) {
           const uint32_t x = fin[p];
-          const uint32_t r = (__brev(x) >> rsh) & rmask;
-          if (HF && ((s_dead[r >> 5] >> (r & 31)) & 1u)) continue;
-          const uint64_t o = sbase[r] + p;
-          if (o < P.n_in) out[o] = (O)(x & mask);
-          else atomicOr(P.err, ERR_INTERNAL);  // never for consistent tables
+          const uint32_t d = (x >> nb) & dmask;
+          if (HF && ((s_dead[d >> 5] >> (d & 31)) & 1u)) continue;
+          out[sbase[d] + (uint64_t)p] = (O)(x & mask);
         }
       };
-      if (P.shape == SHAPE_HUFF) {
+      if (s_oob) {
+        if (tid == 0) atomicOr(P.err, ERR_INTERNAL);
+      } else if (P.shape == SHAPE_HUFF) {
         if (P.out_w == 1) scatter(uint8_t{}, std::true_type{});
         else if (P.out_w == 2) scatter(uint16_t{}, std::true_type{});
         else scatter(uint32_t{}, std::true_type{});

@@ -169,7 +169,15 @@ void canonical_codes(const uint8_t* len, uint32_t sigma, uint32_t* code);
 wt_status launch_query_multi(wt_struct* const* hs, uint32_t nh, const uint32_t* sid,
                              const uint8_t* op, const uint32_t* c, const uint64_t* x, uint64_t q,
                              uint64_t* out, cudaStream_t st);
-// levels per pass recorded by the autotuner for (L, ceil(log2 n)); 8 if none
+// configuration of a wavelet-matrix build recorded by the autotuner for
+// (L, ceil(log2 n)): levels per pass (8 if none), symbols per tile (PASS_T if
+// none) and CTAs per SM (0 = as many as fit)
+struct TuneConfig {
+  int tau;
+  uint32_t tile;
+  uint32_t ctas;
+};
+TuneConfig tuned_config(uint32_t L, uint64_t n);
 int tuned_tau(uint32_t L, uint64_t n);
 // bytes a batched wavelet-matrix build keeps for one sequence
 uint64_t wm_resident_bytes(uint64_t n, uint32_t sigma);

@@ -118,7 +118,21 @@ struct PassParams {
   uint32_t tcs;          // their stride (tc_stride of the largest digit width)
   uint32_t* ticket;      // tiles are taken in order from this counter
   uint32_t* err;
+  // 16-byte units of a later pass's levels to zero, `clear_per` of them per
+  // tile (nullptr: none); see clear_share
+  uint4* clear;
+  uint64_t clear_units, clear_per;
 };
+
+// Zero tile ti's share of `units` 16-byte units at `p`: units
+// [ti * per, (ti + 1) * per), per = ceil(units / tiles) taken on the host.
+__device__ __forceinline__ void clear_share(uint4* p, uint64_t units, uint64_t per, uint64_t ti,
+                                            int tid, int nthreads) {
+  const uint64_t b = ti * per;
+  const uint64_t e = b + per < units ? b + per : units;
+  for (uint64_t i = b + (uint64_t)tid; i < e; i += (uint64_t)nthreads)
+    __stcs(p + i, make_uint4(0u, 0u, 0u, 0u));
+}
 
 __device__ __forceinline__ uint32_t rev_bits(uint32_t k, int j) {
   return j == 0 ? 0u : (__brev(k) >> (32 - j));

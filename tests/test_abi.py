@@ -95,16 +95,25 @@ def test_unsupported_options_are_rejected_before_device_work(lib):
     # options are checked before any allocation or launch, so this runs on
     # the host alone: an empty sequence with each unsupported option
     so = lib.load_library()
-    bad = [dict(tau=9, status=1), dict(tile_symbols=8192, status=6), dict(tile_symbols=100, status=6),
-           dict(k_chunks=5, status=6), dict(select_sample=1000, status=6)]
-    for b in bad:
+    bad = [dict(tau=9, status=1), dict(tile_symbols=100, status=6), dict(tile_symbols=1000, status=6),
+           dict(tile_symbols=16384, status=6), dict(k_chunks=5, status=6),
+           dict(select_sample=1000, status=6)]
+    # tiles of 2048 and 8192 symbols are for the wavelet matrix only
+    tree_bad = [dict(tile_symbols=2048, status=6), dict(tile_symbols=8192, status=6)]
+    for b in bad + tree_bad:
         o = lib.BuildOpts()
         for f in ("tau", "tile_symbols", "k_chunks", "select_sample"):
             setattr(o, f, b.get(f, 0))
         h = ctypes.c_void_p()
-        for fn in (so.wm_build, so.wt_build):
+        fns = [so.wt_build] if b in tree_bad else [so.wm_build, so.wt_build]
+        for fn in fns:
             assert fn(None, 0, 4, 2, ctypes.byref(o), None, ctypes.byref(h)) == b["status"], b
             assert not h.value
+        if b in tree_bad:
+            assert so.multiary_build(None, 0, 4, 2, 4, ctypes.byref(o), None,
+                                     ctypes.byref(h)) == b["status"]
+            assert so.huff_wt_build(None, 0, 4, 2, None, ctypes.byref(o), None,
+                                    ctypes.byref(h)) == b["status"]
     # invalid widths and sigma are rejected the same way
     h = ctypes.c_void_p()
     assert so.wm_build(None, 0, 4, 3, None, None, ctypes.byref(h)) == 1

@@ -154,6 +154,55 @@ def test_autotune(wt):
         wt.wm_autotune_clear()
 
 
+def test_batch_object(wt):
+    """One object for a whole batched build: its structures equal the
+    oracle's, answer queries, report per-sequence statuses (a symbol >= sigma
+    in one sequence fails that one only), and are released together."""
+    seqs = [(synth.zipf(90 + i, n, s, 1.1, 2), s) for i, (n, s) in
+            enumerate([(50001, 4096), (7, 4), (300000, 65536), (0, 256), (8192, 2)])]
+    bad = synth.uniform(99, 5000, 300, 2)
+    bad[17] = 299
+    ds = [to_dev(S) for S, _ in seqs] + [to_dev(bad)]
+    b = wt.wm_batch_build_one(ds, [s for _, s in seqs] + [200])
+    assert len(b) == 6
+    st = b.sync()
+    assert list(st[:5]) == [0] * 5 and st[5] == 2
+    for i, (S, sigma) in enumerate(seqs):
+        h = b.handle(i)
+        check_wm(h.export(), S, sigma)
+        if S.size:
+            q = 1000
+            op, c, arg = synth.queries(100 + i, S, sigma, q)
+            assert np.array_equal(queries_on(h, S, sigma, op, c, arg),
+                                  oracle_queries(S, sigma, op, c, arg))
+        h.free()  # a member's free only drops the view
+    b.free()
+    b.free()
+
+
+def test_autotune_config(wt):
+    """The whole-configuration tuner: (tau, tile size, CTAs per SM) and K;
+    builds with zero options then take the recorded triple (wm_tuning reports
+    it), and the result does not depend on it."""
+    n = (1 << 20) + 4097
+    S = synth.zipf(52, n, 65536, 1.1, 2)
+    d = to_dev(S)
+    try:
+        t = wt.wm_autotune_config(d, 65536)
+        assert 1 <= t["tau"] <= 8 and t["tile_symbols"] in (2048, 4096, 8192)
+        assert t["ctas_per_sm"] in (0, 3, 4) and t["ms"] > 0
+        assert t["k_chunks"] == (n + t["tile_symbols"] - 1) // t["tile_symbols"]
+        u = wt.wm_tuning(n, 65536)
+        assert (u["tau"], u["tile_symbols"], u["ctas_per_sm"], u["k_chunks"]) == \
+            (t["tau"], t["tile_symbols"], t["ctas_per_sm"], t["k_chunks"])
+        h = wt.wm_build(d, 65536)
+        check_wm(h.export(), S, 65536)
+        h.free()
+    finally:
+        wt.wm_autotune_clear()
+    assert wt.wm_tuning(n, 65536)["tile_symbols"] == 4096
+
+
 def _alone_answers(wt, seqs, qs):
     """Each request on its own: one plain build per sequence, one query call
     per op and structure.  qs hold sequence indices (-1: no structure)."""

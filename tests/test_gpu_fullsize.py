@@ -24,12 +24,14 @@ def wt():
     return m
 
 
-@pytest.mark.parametrize("kind", ["wm", "wt"])
-def test_parity_across_prefix_chunks(wt, kind):
+@pytest.mark.parametrize("kind,tile", [("wm", 0), ("wt", 0), ("wm", 2048), ("wm", 8192)])
+def test_parity_across_prefix_chunks(wt, kind, tile):
     n, sigma = 1 << 25, 4096
     S = synth.zipf(77, n, sigma, 1.1, 2)
-    fn = wt.wm_build if kind == "wm" else wt.wt_build
-    h = fn(to_dev(S), sigma)
+    if kind == "wm":
+        h = wt.wm_build(to_dev(S), sigma, tile_symbols=tile)
+    else:
+        h = wt.wt_build(to_dev(S), sigma)
     ex = h.export()
     ob = oracle.wm_build(S, sigma)[0] if kind == "wm" else oracle.wt_build(S, sigma)
     assert np.array_equal(ex.bits.reshape(ob.shape), ob)

@@ -183,6 +183,25 @@ def test_tau_invariance(wt, tau):
     h.free()
 
 
+@pytest.mark.parametrize("tile", [2048, 4096, 8192])
+@pytest.mark.parametrize("ctas", [0, 1, 3])
+def test_tile_sizes(wt, tile, ctas):
+    """Wavelet matrices at every supported tile size (the paper's K = n / tile
+    sub-problems, Section 4.2) and CTA count: bits, zero counts, directories
+    and samples equal the oracle's; sizes span several tiles with a ragged
+    tail, one pass and two passes."""
+    for (seed, n, sigma, tau) in [(61, 100003, 65536, 8), (62, 3 * 8192 + 5, 300, 0),
+                                  (63, (1 << 20) + 17, 256, 3), (64, 1000, 1 << 20, 5)]:
+        S = synth.zipf(seed, n, sigma, 1.1, 2 if sigma <= 65536 else 4)
+        ob, oz = oracle.wm_build(S, sigma)
+        h = wt.wm_build(to_dev(S), sigma, tau=tau, ctas_per_sm=ctas, tile_symbols=tile)
+        ex = h.export()
+        assert np.array_equal(ex.bits.reshape(ob.shape), ob), (seed, tile, ctas)
+        assert np.array_equal(ex.zeros, oz)
+        check_binary_dirs(ex, list(ob), [n] * ob.shape[0])
+        h.free()
+
+
 @pytest.mark.parametrize("ctas", [1, 2])
 def test_ctas_invariance(wt, ctas):
     S = synth.uniform(31, 200001, 65536, 2)
