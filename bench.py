@@ -65,6 +65,12 @@ def parse():
     ap.add_argument("--qlam", type=float, default=50.0,
                     help="serve: query batches (2^16 queries) per second")
     ap.add_argument("--duration", type=float, default=10.0, help="serve: seconds of arrivals")
+    ap.add_argument("--no-batch", action="store_true",
+                    help="headline: skip the batched-vs-plain sub-measurement")
+    ap.add_argument("--no-serve", action="store_true",
+                    help="headline: skip the serving-loop sub-measurement")
+    ap.add_argument("--no-tune", action="store_true",
+                    help="headline: skip the autotuner (default configuration)")
     return ap.parse_args()
 
 
@@ -81,6 +87,32 @@ def workload_config(n_log2):
             "n": 1 << n_log2, "sigma": SIGMA, "levels": 16, "width_bytes": 2, "tau": 8,
             "tile_symbols": 4096, "l2": "inputs (2 GiB) larger than L2; no flush needed",
             "seed": SEED}
+
+
+def width_for_bits(b):
+    return 1 if b <= 8 else (2 if b <= 16 else 4)
+
+
+def pass_bytes(n, L, w, tau):
+    """Algorithmic bytes of each partition pass of a wavelet-matrix build:
+    read its input (w bytes on the first pass, the narrowed intermediate
+    after), write the next intermediate (not on the last pass), write t
+    levels of n bits."""
+    out, a = [], 0
+    while a < L:
+        t = min(tau, L - a)
+        in_w = w if a == 0 else width_for_bits(L - a)
+        out_w = width_for_bits(L - a - t) if a + t < L else 0
+        out.append(n * (in_w + out_w) + n * t / 8)
+        a += t
+    return out
+
+
+def step_bytes(n, L, w, tau):
+    """B(tau): the whole build's algorithmic bytes -- validation/histogram
+    read, the passes, and the directory pass (read the levels, write 16-byte
+    records per 2048 bits and the select samples)."""
+    return n * w + sum(pass_bytes(n, L, w, tau)) + L * n / 8 + L * n / 128 + L * n / 512
 
 
 # --------------------------------------------------------------------------
@@ -290,6 +322,13 @@ def run_native(args):
         if ws > 1:
             dist.barrier()
 
+    # the autotuner's configuration (tau, tile size, CTAs per SM), recorded
+    # for every later build with zero options; untimed
+    if args.no_tune:
+        tuning = wt.wm_tuning(n, SIGMA)
+    else:
+        tuning = wt.wm_autotune_config(d, SIGMA)
+    tau = tuning["tau"]
     # warm-up (also builds the pool and the kernel attributes)
     for _ in range(args.warmup):
         h = wt.wm_build(d, SIGMA)
@@ -329,9 +368,9 @@ def run_native(args):
     value = ws * n * L / (ms_max * 1e-3) / 1e9
 
     # roofline of the partition-pass kernel: algorithmic bytes per launch
-    # pass 0: read 2 B + write 1 B (next sequence, 8 bits left) + 8 levels/8 B
-    # pass 1: read 1 B + 8 levels/8 B
-    alg_bytes = args.steps * (4 * n + 2 * n)
+    # (tau = 8: pass 0 reads 2 B, writes 1 B of the next sequence and 8 levels
+    # = 1 B; pass 1 reads 1 B and writes 1 B of levels)
+    alg_bytes = args.steps * sum(pass_bytes(n, L, 2, tau))
     achieved = alg_bytes / (pass_ms * 1e-3) / 1e9 if pass_ms > 0 else None
     peak, peak_kind = measured_peak_hbm()
     traffic = profiled_traffic()
@@ -352,10 +391,10 @@ def run_native(args):
                                     "inst_per_cycle_per_sm": pf.get("inst_per_cycle_per_sm"),
                                     "peak_inst_per_cycle_per_sm": 4.0,
                                     "source": "ncu --set full, 2^26 symbols (profiles/)"}
-    # whole-step byte models: B(tau=8) ~ 10.16 n (histogram 2n, passes 6n,
-    # directory 2.16n); B_min = n w + L n / 8 + directory writes (L n / 128 +
-    # L n / 512 select samples) = 4.156 n, a single ideal pass
-    roof["whole_step_frac_of_B_tau8"] = (10.16 * n / (ms * 1e-3) / 1e9) / peak
+    # whole-step byte models: B(tau) (tau = 8: ~10.16 n = histogram 2n,
+    # passes 6n, directory 2.16n); B_min = n w + L n / 8 + directory writes
+    # (L n / 128 + L n / 512 select samples) = 4.156 n, a single ideal pass
+    roof["whole_step_frac_of_B_tau"] = (step_bytes(n, L, 2, tau) / (ms * 1e-3) / 1e9) / peak
     roof["whole_step_frac_of_Bmin"] = ((2 + 2 + 16 / 128 + 16 / 512) * n / (ms * 1e-3) / 1e9) / peak
 
     # end to end through the C ABI: every step copies its input from pinned
@@ -384,12 +423,19 @@ def run_native(args):
         lib = wt.load_library()
         view = wt.ExportView()
 
+        # per-step events: the copy on the copy stream, the build on its stream
+        ev = lambda: torch.cuda.Event(enable_timing=True)
+        cs, ce = [ev() for _ in range(k)], [ev() for _ in range(k)]
+        bs, be = [ev() for _ in range(k)], [ev() for _ in range(k)]
+
         def copy_in(i):
             b = i % 2
             with torch.cuda.stream(sc):
                 if i >= 2:
                     sc.wait_event(built[b])
+                cs[i].record(sc)
                 dbufs[b].copy_(pin, non_blocking=True)
+                ce[i].record(sc)
                 copied[b].record(sc)
 
         def finish(h):
@@ -408,7 +454,9 @@ def run_native(args):
                 copy_in(i + 1)
             b = i % 2
             sbs[b].wait_event(copied[b])
+            bs[i].record(sbs[b])
             h = wt.wm_build(dbufs[b], SIGMA, stream=sbs[b])
+            be[i].record(sbs[b])
             built[b].record(sbs[b])
             if prev is not None:
                 finish(prev)
@@ -422,20 +470,54 @@ def run_native(args):
         te = torch.tensor([e_ms], dtype=torch.float64, device=dev)
         if ws > 1:
             dist.all_reduce(te, op=dist.ReduceOp.MAX)
+        cms = [cs[i].elapsed_time(ce[i]) for i in range(k)]
+        bms = [bs[i].elapsed_time(be[i]) for i in range(k)]
+        # overlap of step i+1's copy with step i's build
+        ov = []
+        for i in range(k - 1):
+            a0, a1 = f0.elapsed_time(cs[i + 1]), f0.elapsed_time(ce[i + 1])
+            b0, b1 = f0.elapsed_time(bs[i]), f0.elapsed_time(be[i])
+            ov.append(max(0.0, min(a1, b1) - max(a0, b0)) / max(a1 - a0, 1e-9))
         e2e = {"value": ws * n * L / (float(te.item()) * 1e-3) / 1e9, "unit": UNIT,
-               "h2d_bytes_per_step": 2 * n, "d2h_bytes_per_step": 8 * L, "steps": k}
+               "h2d_bytes_per_step": 2 * n, "d2h_bytes_per_step": 8 * L, "steps": k,
+               "ms_per_step": e_ms,
+               "timeline": {"copy_ms_median": statistics.median(cms), "copy_ms_max": max(cms),
+                            "h2d_GBps_median": 2 * n / (statistics.median(cms) * 1e-3) / 1e9,
+                            "build_ms_median": statistics.median(bms),
+                            "copy_overlapped_with_build_frac": statistics.median(ov) if ov else None,
+                            "exposed_ms_per_step": e_ms - ms}}
+
+    # the batched and the serving workloads, bounded, beside the headline
+    # (rank 0 at one GPU; --workload batch / serve run them in full)
+    batch = serve = None
+    if ws == 1 and not (args.no_batch and args.no_serve):
+        pinb, offs, ln, sig, zf, total = _batch_workload()
+        if not args.no_batch:
+            batch = batch_measure(wt, pinb, offs, ln, sig, total, reps=3, e2e_steps=4)
+        if not args.no_serve:
+            serve = serve_measure(wt, pinb, offs, ln, sig, lam=20.0, qlam=50.0, duration=3.0,
+                                  with_cpu=False)
+        del pinb
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu:
         cpu = cpu_baseline(args.cpu_log2n)
 
     if rank == 0:
+        cfg = workload_config(args.log2n)
+        cfg["tau"] = tau
+        cfg["tile_symbols"] = tuning["tile_symbols"]
+        cfg["tuning"] = {"tau": tau, "tile_symbols": tuning["tile_symbols"],
+                         "ctas_per_sm": tuning["ctas_per_sm"], "k_chunks": tuning["k_chunks"],
+                         "source": "default (--no-tune)" if args.no_tune
+                         else "wm_autotune_config on this sequence, untimed"}
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "u16", "data": "synthetic",
-                "config": workload_config(args.log2n), "roofline": roof, "cpu_baseline": cpu,
+                "config": cfg, "roofline": roof, "cpu_baseline": cpu,
                 "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
-                "parallelism": f"replicas x{ws} (independent builds, no collective)"}
+                "parallelism": f"replicas x{ws} (independent builds, no collective)",
+                "batch": batch, "serve": serve}
         print(json.dumps(line), flush=True)
     if ws > 1:
         dist.barrier()
@@ -489,6 +571,204 @@ def _batch_workload(m=4096, world=1, rank=0):
     with ThreadPoolExecutor(8) as ex:
         list(ex.map(gen, range(m)))
     return pin, offs, [int(x) for x in ln], [int(x) for x in sig], zf, int(total)
+
+
+def batch_measure(wt, pin, offs, ln, sig, total, reps=3, e2e_steps=4):
+    """The batched workload at one GPU: one batched build (the batch object,
+    wm_batch_build_one) against 4096 plain wm_build calls, wall clock with
+    the inputs resident; then end to end through the batch object: each step
+    copies the 4 GiB input from pinned host memory, builds the batch and reads
+    every sequence's status back, with the next step's copy on a second
+    stream overlapping this step's build."""
+    import numpy as np
+    import torch
+    m = len(ln)
+    d = pin.to("cuda")
+    seqs = [d[int(offs[i]):int(offs[i]) + ln[i]] for i in range(m)]
+    items = wt.batch_items(d.data_ptr(), 2 * offs[:m], ln, sig)
+    torch.cuda.synchronize()
+
+    def batched():
+        b = wt.wm_batch_build_one(items=items)
+        st = b.sync()
+        assert not st.any(), "batched build failed"
+        return b
+
+    def plain():
+        hs = [wt.wm_build(seqs[i], sig[i]) for i in range(m)]
+        for h in hs:
+            h.sync()
+        return hs
+
+    def timed(fn, k):
+        out = []
+        for _ in range(k):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            r = fn()
+            torch.cuda.synchronize()
+            out.append(time.perf_counter() - t0)
+            if isinstance(r, list):
+                for h in r:
+                    h.free()
+            else:
+                r.free()
+        return out
+
+    timed(batched, 1)
+    wt.prof_enable(True)
+    tb = timed(batched, reps)
+    launches, _, _ = wt.prof_read()
+    wt.prof_enable(False)
+    b = wt.wm_batch_build_one(items=items)
+    b.sync()
+    sl = sum(b.handle(i).symbol_levels() for i in range(m))
+    b.free()
+    timed(plain, 1)
+    wt.prof_enable(True)
+    tp = timed(plain, 1)
+    plain_launches, _, _ = wt.prof_read()
+    wt.prof_enable(False)
+    mb, mp = statistics.median(tb), statistics.median(tp)
+    out = {"workload": "4096 wavelet matrices with directories, lengths log-uniform in "
+                       "[2^10, 2^24] (total 2^31 symbols), sigma from {4,256,4096,65536}, "
+                       "uniform or Zipf(1.1), uint16",
+           "sequences": m, "symbols": int(total), "symbol_levels": int(sl),
+           "batched": {"value": sl / mb / 1e9, "unit": UNIT, "ms": 1e3 * mb,
+                       "gpu_launches": launches // len(tb), "reps": len(tb)},
+           "plain": {"value": sl / mp / 1e9, "unit": UNIT, "ms": 1e3 * mp,
+                     "gpu_launches": plain_launches // len(tp), "reps": len(tp)},
+           "batched_over_plain": mp / mb,
+           "timing": "wall clock around each build (host waits for the results), inputs resident"}
+    if e2e_steps:
+        dbufs = [torch.empty_like(d), torch.empty_like(d)]
+        its = [wt.batch_items(x.data_ptr(), 2 * offs[:m], ln, sig) for x in dbufs]
+        sc = torch.cuda.Stream()
+        sbs = [torch.cuda.Stream(), torch.cuda.Stream()]
+        copied = [torch.cuda.Event(), torch.cuda.Event()]
+        built = [torch.cuda.Event(), torch.cuda.Event()]
+        torch.cuda.synchronize()
+
+        def copy_in(i):
+            with torch.cuda.stream(sc):
+                if i >= 2:
+                    sc.wait_event(built[i % 2])
+                dbufs[i % 2].copy_(pin, non_blocking=True)
+                copied[i % 2].record(sc)
+
+        k = e2e_steps
+        t0 = time.perf_counter()
+        copy_in(0)
+        prev = None
+        for i in range(k):
+            if i + 1 < k:
+                copy_in(i + 1)
+            sbs[i % 2].wait_event(copied[i % 2])
+            cur = wt.wm_batch_build_one(items=its[i % 2], stream=sbs[i % 2])
+            built[i % 2].record(sbs[i % 2])
+            if prev is not None:
+                assert not prev.sync().any()
+                prev.free()
+            prev = cur
+        assert not prev.sync().any()
+        prev.free()
+        torch.cuda.synchronize()
+        te = (time.perf_counter() - t0) / k
+        out["e2e"] = {"value": sl / te / 1e9, "unit": UNIT, "ms_per_step": 1e3 * te,
+                      "h2d_bytes_per_step": int(2 * offs[-1]), "d2h_bytes_per_step": 4 * m,
+                      "steps": k}
+        del dbufs
+    del d, seqs
+    torch.cuda.empty_cache()
+    return out
+
+
+def serve_measure(wt, pin, offs, ln, sig, lam, qlam, duration, with_cpu=True, seed=None):
+    """The serving loop: builds of the batched workload's sequences arriving
+    Poisson at lam/s and batches of 2^16 uniform (structure, op, argument)
+    queries at qlam/s for `duration` seconds, under a 64 GB admission budget;
+    latency from submission to results in host memory."""
+    import numpy as np
+    host = pin.numpy().view(np.uint16)
+    rng = np.random.Generator(np.random.PCG64((synth_seed(5) ^ 0x5e7e) if seed is None else seed))
+    srv = wt.Server(budget_bytes=64 << 30)
+    D = duration
+    tb_arr = np.cumsum(rng.exponential(1.0 / lam, size=int(lam * D * 2) + 10))
+    tq_arr = np.cumsum(rng.exponential(1.0 / qlam, size=int(qlam * D * 2) + 10))
+    events = sorted([(t, 0) for t in tb_arr if t < D] + [(t, 1) for t in tq_arr if t < D])
+    Q = 1 << 16
+    # every query batch is drawn before the clock starts: uniform over the
+    # builds submitted before it (by submission index), op, and argument
+    pre = []
+    nsub = 0
+    for t, kind in events:
+        if kind == 0 and nsub < len(ln):
+            nsub += 1
+            pre.append(None)
+        elif kind == 1 and nsub:
+            k = rng.integers(0, nsub, size=Q)
+            ns = np.array(ln[:nsub], np.uint64)[k]
+            ss = np.array(sig[:nsub], np.uint32)[k]
+            op = rng.integers(0, 3, size=Q).astype(np.uint8)
+            c = (rng.random(Q) * ss).astype(np.uint32)
+            x = (rng.random(Q) * ns).astype(np.uint64)
+            x[op == 2] += 1  # select takes k >= 1
+            pre.append((k, op, c, x))
+        else:
+            pre.append(False)
+    builds, queries = [], []
+    nb = 0
+    t0 = time.perf_counter()
+    for (t, kind), item in zip(events, pre):
+        while time.perf_counter() - t0 < t:
+            time.sleep(0.0002)
+        if item is None:
+            i = nb
+            nb += 1
+            builds.append(srv.submit_build(host[int(offs[i]):int(offs[i]) + ln[i]], sig[i]))
+        elif item:
+            k, op, c, x = item
+            queries.append(srv.submit_queries(np.array(builds, np.uint64)[k], op, c, x))
+    lat_b, lat_q = [], []
+    for r in queries:
+        st, a, b, _ = srv.poll(r, 0)
+        lat_q.append((b - a) * 1e-6)
+    for r in builds:
+        st, a, b, _ = srv.poll(r)
+        lat_b.append((b - a) * 1e-6)
+    wall = time.perf_counter() - t0
+    srv.close()
+    pct = lambda v, p: float(np.percentile(v, p)) if v else None
+    out = {"workload": f"serving loop: wavelet-matrix builds of the batched configuration's "
+                       f"sequences arriving Poisson at {lam}/s, query batches of 2^16 uniform "
+                       f"(structure, op, argument) at {qlam}/s, {D} s of arrivals, 64 GB "
+                       f"admission budget",
+           "builds": len(builds), "query_batches": len(queries), "queries_per_batch": Q,
+           "queries_per_s": len(queries) * Q / wall, "wall_ms": 1e3 * wall,
+           "latency_ms": {"query_p50": pct(lat_q, 50), "query_p99": pct(lat_q, 99),
+                          "build_p50": pct(lat_b, 50), "build_p99": pct(lat_b, 99)}}
+    if with_cpu:
+        # the oracle answering queries of the same mix on one sequence of the
+        # median length (each answer by definition over the sequence)
+        import oracle
+        i = int(np.argsort(np.array(ln))[len(ln) // 2])
+        S = host[int(offs[i]):int(offs[i]) + ln[i]]
+        qn = 256
+        op = rng.integers(0, 3, size=qn).astype(np.uint8)
+        c = (rng.random(qn) * sig[i]).astype(np.uint32)
+        x = (rng.random(qn) * ln[i]).astype(np.uint64)
+        x[op == 2] += 1
+        t0c = time.perf_counter()
+        oracle.access(S, x[op == 0])
+        oracle.rank(S, sig[i], c[op == 1], x[op == 1])
+        oracle.select(S, sig[i], c[op == 2], x[op == 2])
+        dtc = time.perf_counter() - t0c
+        out["cpu_baseline"] = {"value": qn / dtc, "unit": "queries/s", "cores": 1,
+                               "kind": "oracle",
+                               "sample": f"{qn} queries of the same mix on one sequence of "
+                                         f"{ln[i]} symbols (the median length), single-threaded "
+                                         f"C oracle; {dtc:.3f} s"}
+    return out
 
 
 def run_batch(args, wt):
@@ -611,94 +891,14 @@ def _cpu_batch(pin, offs, ln, sig, target=1 << 24):
 
 
 def run_serve(args, wt):
-    import numpy as np
     pin, offs, ln, sig, zf, total = _batch_workload()
-    host = pin.numpy().view(np.uint16)
-    rng = np.random.Generator(np.random.PCG64(synth_seed(5) ^ 0x5e7e))
-    srv = wt.Server(budget_bytes=64 << 30)
-    # arrivals: builds (Poisson, lam/s, sequences in plan order) and query
-    # batches (Poisson, qlam/s, 2^16 uniform (structure, op, argument) over the
-    # structures already submitted)
-    D = args.duration
-    tb_arr = np.cumsum(rng.exponential(1.0 / args.lam, size=int(args.lam * D * 2) + 10))
-    tq_arr = np.cumsum(rng.exponential(1.0 / args.qlam, size=int(args.qlam * D * 2) + 10))
-    events = sorted([(t, 0) for t in tb_arr if t < D] + [(t, 1) for t in tq_arr if t < D])
-    Q = 1 << 16
-    # every query batch is drawn before the clock starts: uniform over the
-    # builds submitted before it (by submission index), op, and argument
-    pre = []
-    nsub = 0
-    for t, kind in events:
-        if kind == 0 and nsub < len(ln):
-            nsub += 1
-            pre.append(None)
-        elif kind == 1 and nsub:
-            k = rng.integers(0, nsub, size=Q)
-            ns = np.array(ln[:nsub], np.uint64)[k]
-            ss = np.array(sig[:nsub], np.uint32)[k]
-            op = rng.integers(0, 3, size=Q).astype(np.uint8)
-            c = (rng.random(Q) * ss).astype(np.uint32)
-            x = (rng.random(Q) * ns).astype(np.uint64)
-            x[op == 2] += 1  # select takes k >= 1
-            pre.append((k, op, c, x))
-        else:
-            pre.append(False)
-    builds, queries = [], []
-    nb = 0
-    t0 = time.perf_counter()
-    for (t, kind), item in zip(events, pre):
-        while time.perf_counter() - t0 < t:
-            time.sleep(0.0002)
-        if item is None:
-            i = nb
-            nb += 1
-            builds.append(srv.submit_build(host[int(offs[i]):int(offs[i]) + ln[i]], sig[i]))
-        elif item:
-            k, op, c, x = item
-            queries.append(srv.submit_queries(np.array(builds, np.uint64)[k], op, c, x))
-    lat_b, lat_q, done_q = [], [], []
-    for r in queries:
-        st, a, b, _ = srv.poll(r, 0)
-        lat_q.append((b - a) * 1e-6)
-        done_q.append(b)
-    for r in builds:
-        st, a, b, _ = srv.poll(r)
-        lat_b.append((b - a) * 1e-6)
-    wall = time.perf_counter() - t0
-    stats = srv.stats()
-    srv.close()
-    pct = lambda v, p: float(np.percentile(v, p)) if v else None
-    qps = len(queries) * Q / wall
-    cfg = {"workload": f"serving loop: wavelet-matrix builds of the batched configuration's "
-                       f"sequences arriving Poisson at {args.lam}/s, query batches of 2^16 "
-                       f"uniform (structure, op, argument) at {args.qlam}/s, {D} s of arrivals, "
-                       f"64 GB admission budget",
-           "builds": len(builds), "query_batches": len(queries), "queries_per_batch": Q}
-    cpu = None
-    if not args.no_cpu:
-        # the oracle answering queries of the same mix on one sequence of the
-        # median length (each answer by definition over the sequence)
-        import oracle
-        i = int(np.argsort(np.array(ln))[len(ln) // 2])
-        S = host[int(offs[i]):int(offs[i]) + ln[i]]
-        qn = 256
-        op = rng.integers(0, 3, size=qn).astype(np.uint8)
-        c = (rng.random(qn) * sig[i]).astype(np.uint32)
-        x = (rng.random(qn) * ln[i]).astype(np.uint64)
-        x[op == 2] += 1
-        t0c = time.perf_counter()
-        oracle.access(S, x[op == 0])
-        oracle.rank(S, sig[i], c[op == 1], x[op == 1])
-        oracle.select(S, sig[i], c[op == 2], x[op == 2])
-        dtc = time.perf_counter() - t0c
-        cpu = {"value": qn / dtc, "unit": "queries/s", "cores": 1, "kind": "oracle",
-               "sample": f"{qn} queries of the same mix on one sequence of {ln[i]} symbols "
-                         f"(the median length), single-threaded C oracle; {dtc:.3f} s"}
-    _line(args, "queries/s through the serving loop (arrival -> answers on host)", qps,
-          "queries/s", 1e3 * wall, cfg, cpu_baseline=cpu,
-          latency_ms={"query_p50": pct(lat_q, 50), "query_p99": pct(lat_q, 99),
-                      "build_p50": pct(lat_b, 50), "build_p99": pct(lat_b, 99)},
-          server=stats)
+    r = serve_measure(wt, pin, offs, ln, sig, args.lam, args.qlam, args.duration,
+                      with_cpu=not args.no_cpu)
+    cfg = {"workload": r["workload"], "builds": r["builds"], "query_batches": r["query_batches"],
+           "queries_per_batch": r["queries_per_batch"]}
+    _line(args, "queries/s through the serving loop (arrival -> answers on host)",
+          r["queries_per_s"], "queries/s", r["wall_ms"], cfg, cpu_baseline=r.get("cpu_baseline"),
+          latency_ms=r["latency_ms"])
 
 
 def run_select(args, wt):

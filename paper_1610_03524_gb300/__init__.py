@@ -529,19 +529,39 @@ class Batch:
             pass
 
 
-def wm_batch_build_one(seqs, sigmas, ns=None, tau: int = 0, flags: int = 0,
-                       stream=None) -> Batch:
-    """wm_batch_build as one Batch object (one object per step instead of m)."""
-    m = len(seqs)
-    items = (BatchItem * max(m, 1))()
-    for i, (sq, sg) in enumerate(zip(seqs, sigmas)):
-        items[i].d_seq = _ptr(sq) if sq is not None else 0
-        items[i].n = sq.numel() if ns is None else int(ns[i])
-        items[i].sigma = int(sg)
-        items[i].width_bytes = _width(sq) if sq is not None else 2
+_ITEM_DT = np.dtype([("d_seq", np.uint64), ("n", np.uint64), ("sigma", np.uint32),
+                     ("width_bytes", np.uint32)])
+
+
+def batch_items(base_ptr: int, byte_offsets, ns, sigmas, width: int = 2):
+    """wt_batch_item array for sequences at base_ptr + byte_offsets[i] (device
+    addresses), filled with numpy (no per-sequence Python work)."""
+    m = len(ns)
+    a = np.zeros(max(m, 1), dtype=_ITEM_DT)
+    a["d_seq"][:m] = np.uint64(base_ptr) + np.asarray(byte_offsets, dtype=np.uint64)[:m]
+    a["n"][:m] = np.asarray(ns, dtype=np.uint64)
+    a["sigma"][:m] = np.asarray(sigmas, dtype=np.uint32)
+    a["width_bytes"][:m] = width
+    return a
+
+
+def wm_batch_build_one(seqs=None, sigmas=None, ns=None, tau: int = 0, flags: int = 0,
+                       stream=None, items=None) -> Batch:
+    """wm_batch_build as one Batch object (one object per step instead of m).
+    Either device tensors and sigmas, or a prebuilt batch_items() array."""
+    if items is None:
+        m = len(seqs)
+        items = np.zeros(max(m, 1), dtype=_ITEM_DT)
+        for i, (sq, sg) in enumerate(zip(seqs, sigmas)):
+            items[i] = (_ptr(sq) if sq is not None else 0,
+                        sq.numel() if ns is None else int(ns[i]), int(sg),
+                        _width(sq) if sq is not None else 2)
+    else:
+        m = int(np.count_nonzero(items["sigma"])) if ns is None else int(ns)
     b = ctypes.c_void_p()
     o = _opts(tau, 0, flags)
-    _check(load_library().wm_batch_build_one(items, m, ctypes.byref(o), _stream_ptr(stream),
+    ip = ctypes.cast(items.ctypes.data, ctypes.POINTER(BatchItem))
+    _check(load_library().wm_batch_build_one(ip, m, ctypes.byref(o), _stream_ptr(stream),
                                               ctypes.byref(b)), "wm_batch_build_one")
     return Batch(b, m)
 

@@ -416,9 +416,13 @@ wt_status batch_build_wm(const wt_batch_item* items, uint32_t m, const wt_build_
 
 void batch_status(wt_handle* hs, uint32_t m, wt_status* st) {
   // the batch's error words are consecutive in its arena
+  // on the batch's own stream (the legacy stream would wait for every other
+  // blocking stream, e.g. a caller's copy of the next input)
   std::vector<uint32_t> err((size_t)m, 0);
-  const bool ok = m && cudaMemcpy(err.data(), hs[0]->d_err, 4 * (size_t)m,
-                                  cudaMemcpyDeviceToHost) == cudaSuccess;
+  const bool ok = m &&
+                  cudaMemcpyAsync(err.data(), hs[0]->d_err, 4 * (size_t)m, cudaMemcpyDeviceToHost,
+                                  hs[0]->stream) == cudaSuccess &&
+                  cudaStreamSynchronize(hs[0]->stream) == cudaSuccess;
   for (uint32_t i = 0; i < m; i++) {
     wt_status s = WT_OK;
     if (!ok) s = WT_ERR_CUDA;

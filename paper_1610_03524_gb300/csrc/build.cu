@@ -819,25 +819,100 @@ static PassParams base_params(wt_struct* h, Work& wk, uint32_t* tickets,
   return P;
 }
 
-// small host tables reach the device as kernel parameters
-constexpr size_t UPLOAD_MAX = 3968;
+// Host tables reach the device without a copy engine: a host-to-device copy
+// would queue behind whatever large copy the caller has in flight (the next
+// input, in a pipelined loop) and stall the build.  Tables up to 32 KB go as
+// kernel parameters.
+constexpr size_t UPLOAD_MAX = 3968, UPLOAD_BIG = 32000;
 struct UploadBlock {
   uint8_t b[UPLOAD_MAX];
+};
+struct UploadBigBlock {
+  uint8_t b[UPLOAD_BIG];
 };
 
 __global__ void k_upload(uint8_t* dst, const __grid_constant__ UploadBlock blk, uint32_t bytes) {
   for (uint32_t i = threadIdx.x; i < bytes; i += blockDim.x) dst[i] = blk.b[i];
 }
 
+__global__ void k_upload_big(uint8_t* dst, const __grid_constant__ UploadBigBlock blk,
+                             uint32_t bytes) {
+  for (uint32_t i = threadIdx.x; i < bytes; i += blockDim.x) dst[i] = blk.b[i];
+}
+
+// Larger tables: a pinned, device-mapped staging buffer that the host fills
+// and a kernel copies into device memory, reading it over the host link (no
+// copy engine).  Buffers are kept per device and reused once the event
+// recorded after their copy kernel has completed.
+struct Stage {
+  uint8_t* p = nullptr;
+  size_t bytes = 0;
+  cudaEvent_t ev = nullptr;
+};
+constexpr size_t STAGE_MIN = 8u << 20;
+
+__global__ void k_gather_host(uint8_t* dst, const uint8_t* src, size_t bytes) {
+  const size_t i0 = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  if ((((uintptr_t)dst | (uintptr_t)src) & 15) == 0) {
+    const size_t nv = bytes / 16;
+    for (size_t i = i0; i < nv; i += stride) ((uint4*)dst)[i] = ((const uint4*)src)[i];
+    for (size_t i = nv * 16 + i0; i < bytes; i += stride) dst[i] = src[i];
+  } else {
+    for (size_t i = i0; i < bytes; i += stride) dst[i] = src[i];
+  }
+}
+
+static wt_status upload_staged(void* d_dst, const void* h_src, size_t bytes, cudaStream_t st) {
+  static std::mutex mu;
+  static std::vector<Stage> stages[64];
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) return WT_ERR_CUDA;
+  std::lock_guard<std::mutex> g(mu);
+  std::vector<Stage>& v = stages[dev];
+  Stage* s = nullptr;
+  for (Stage& x : v)
+    if (x.bytes >= bytes && cudaEventQuery(x.ev) == cudaSuccess) {
+      s = &x;
+      break;
+    }
+  // a busy buffer answers cudaErrorNotReady: a status, not an error to keep
+  if (cudaPeekAtLastError() == cudaErrorNotReady) cudaGetLastError();
+  if (!s) {
+    Stage n;
+    n.bytes = std::max(bytes, STAGE_MIN);
+    CK(cudaHostAlloc((void**)&n.p, n.bytes, cudaHostAllocMapped | cudaHostAllocPortable));
+    if (cudaEventCreateWithFlags(&n.ev, cudaEventDisableTiming) != cudaSuccess) {
+      cudaFreeHost(n.p);
+      return WT_ERR_CUDA;
+    }
+    v.push_back(n);
+    s = &v.back();
+  }
+  memcpy(s->p, h_src, bytes);
+  const unsigned grid = (unsigned)std::min<size_t>((bytes / 16 + 255) / 256 + 1, 4 * (size_t)num_sms());
+  k_gather_host<<<grid, 256, 0, st>>>((uint8_t*)d_dst, s->p, bytes);
+  count_launch();
+  CK(cudaGetLastError());
+  CK(cudaEventRecord(s->ev, st));
+  return WT_OK;
+}
+
 wt_status upload(void* d_dst, const void* h_src, size_t bytes, cudaStream_t st) {
   if (bytes == 0) return WT_OK;
-  if (bytes > UPLOAD_MAX) {
-    CK(cudaMemcpyAsync(d_dst, h_src, bytes, cudaMemcpyHostToDevice, st));
+  if (bytes > UPLOAD_BIG) return upload_staged(d_dst, h_src, bytes, st);
+  if (bytes <= UPLOAD_MAX) {
+    UploadBlock blk;
+    memcpy(blk.b, h_src, bytes);
+    k_upload<<<1, 256, 0, st>>>((uint8_t*)d_dst, blk, (uint32_t)bytes);
+    count_launch();
+    CK(cudaGetLastError());
     return WT_OK;
   }
-  UploadBlock blk;
-  memcpy(blk.b, h_src, bytes);
-  k_upload<<<1, 256, 0, st>>>((uint8_t*)d_dst, blk, (uint32_t)bytes);
+  static thread_local UploadBigBlock big;
+  memcpy(big.b, h_src, bytes);
+  k_upload_big<<<1, 1024, 0, st>>>((uint8_t*)d_dst, big, (uint32_t)bytes);
   count_launch();
   CK(cudaGetLastError());
   return WT_OK;
