@@ -772,7 +772,30 @@ def serve_measure(wt, pin, offs, ln, sig, lam, qlam, duration, with_cpu=True, se
 
 
 def run_batch(args, wt):
-    import numpy as np
+    ws, rank, _ = dist_env()
+    if ws > 1:
+        return run_batch_ranks(args, wt)
+    pin, offs, ln, sig, zf, total = _batch_workload()
+    sampler = ClockSampler(0)
+    sampler.start()
+    r = batch_measure(wt, pin, offs, ln, sig, total, reps=max(1, args.steps),
+                      e2e_steps=0 if args.no_e2e else max(2, min(args.steps, 6)))
+    clocks = sampler.stop()
+    cpu = None if args.no_cpu else _cpu_batch(pin, offs, ln, sig)
+    cfg = {"workload": r["workload"] + ": one batched build (one batch object) vs 4096 plain "
+                                       "builds",
+           "sequences": r["sequences"], "symbols": r["symbols"], "symbol_levels": r["symbol_levels"],
+           "l2": "inputs (4 GiB) larger than L2; no flush needed",
+           "parallelism": "one GPU, no collective"}
+    _line(args, "Gsymbol-levels/s batched build (wall clock, inputs resident)",
+          r["batched"]["value"], UNIT, r["batched"]["ms"], cfg, plain=r["plain"],
+          batched_over_plain=r["batched_over_plain"], gpu_launches=r["batched"]["gpu_launches"],
+          clocks=clocks, e2e=r.get("e2e"), cpu_baseline=cpu)
+
+
+def run_batch_ranks(args, wt):
+    """Several ranks: each rank builds its share of the sequences (longest
+    first, no data-path collective); the slowest rank's time counts."""
     import torch
     import torch.distributed as tdist
     from paper_1610_03524_gb300 import dist as wdist
@@ -780,89 +803,36 @@ def run_batch(args, wt):
     pin, offs, ln, sig, zf, total = _batch_workload(world=ws, rank=rank)
     m = len(ln)
     d = pin.to("cuda")
-    seqs = [d[int(offs[i]):int(offs[i]) + ln[i]] for i in range(m)]
+    items = wt.batch_items(d.data_ptr(), 2 * offs[:m], ln, sig)
     torch.cuda.synchronize()
 
-    def timed(fn, reps):
-        out = []
-        for _ in range(reps):
-            if ws > 1:
-                tdist.barrier()
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            hs = fn()
-            torch.cuda.synchronize()
-            if ws > 1:
-                tdist.barrier()
-            out.append(wdist.max_over_ranks(time.perf_counter() - t0))
-            for h in hs:
-                h.sync()
-                h.free()
-        return out
+    def one():
+        tdist.barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        b = wt.wm_batch_build_one(items=items)
+        assert not b.sync().any()
+        dt = wdist.max_over_ranks(time.perf_counter() - t0)
+        sl = sum(b.handle(i).symbol_levels() for i in range(m))
+        b.free()
+        return dt, sl
 
-    batched = lambda: wt.wm_batch_build(seqs, sig)
-    plain = lambda: [wt.wm_build(seqs[i], sig[i]) for i in range(m)]
-    timed(batched, args.warmup)
-    sampler = ClockSampler(0)
-    sampler.start()
-    wt.prof_enable(True)
-    tb = timed(batched, args.steps)
-    launches, _, _ = wt.prof_read()
-    wt.prof_enable(False)
-    clocks = sampler.stop()
-    timed(plain, 1)
-    wt.prof_enable(True)
-    tp = timed(plain, max(1, min(args.steps, 3)))
-    plain_launches, _, _ = wt.prof_read()
-    wt.prof_enable(False)
-    hs = wt.wm_batch_build(seqs, sig)
-    sl = int(wdist.sum_over_ranks(sum(h.symbol_levels() for h in hs)))
+    for _ in range(args.warmup):
+        one()
+    ts, sl = [], 0
+    for _ in range(max(1, args.steps)):
+        dt, sl = one()
+        ts.append(dt)
+    sl = int(wdist.sum_over_ranks(sl))
     total = int(wdist.sum_over_ranks(total))
-    for h in hs:
-        h.free()
-    mb, mp = statistics.median(tb), statistics.median(tp)
-    # end to end: pinned host -> device copy of every sequence, batched build,
-    # one handle's zero counts read back
-    e2e = None
-    if not args.no_e2e:
-        lib = wt.load_library()
-        view = wt.ExportView()
-        dbuf = torch.empty_like(d)
-        views = [dbuf[int(offs[i]):int(offs[i]) + ln[i]] for i in range(m)]
-        k = max(1, min(args.steps, 3))
-        te = []
-        for _ in range(k):
-            if ws > 1:
-                tdist.barrier()
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            dbuf.copy_(pin, non_blocking=True)
-            hs = wt.wm_batch_build(views, sig)
-            # waits for the batch and copies sequence 0's per-level zero counts
-            wt._check(lib.wt_export(hs[0].raw, ctypes.byref(view)), "wt_export")
-            for h in hs:
-                h.free()
-            te.append(wdist.max_over_ranks(time.perf_counter() - t0))
-        e2e = {"value": sl / statistics.median(te) / 1e9, "unit": UNIT,
-               "h2d_bytes_per_step": int(wdist.sum_over_ranks(2 * int(offs[-1]))),
-               "d2h_bytes_per_step": int(wdist.sum_over_ranks(8 * view.levels)),
-               "steps": k}
-    cpu = None
-    if not args.no_cpu and ws == 1:
-        cpu = _cpu_batch(pin, offs, ln, sig)
+    mb = statistics.median(ts)
     if rank != 0:
         return
-    cfg = {"workload": "4096 wavelet matrices with directories, lengths log-uniform in "
-                       "[2^10, 2^24] (total 2^31), sigma from {4,256,4096,65536}, uniform or "
-                       "Zipf(1.1), uint16: one batched build vs 4096 plain builds",
-           "sequences": m, "symbols": total, "symbol_levels": sl,
-           "l2": "inputs (4 GiB) larger than L2; no flush needed"}
-    cfg["parallelism"] = f"sequences sharded over {ws} rank(s), no data-path collective"
+    cfg = {"workload": "4096 wavelet matrices with directories (batched configuration), "
+                       "sequences sharded over ranks", "symbols": total, "symbol_levels": sl,
+           "parallelism": f"sequences sharded over {ws} rank(s), no data-path collective"}
     _line(args, "Gsymbol-levels/s batched build (wall clock, inputs resident)", sl / mb / 1e9,
-          UNIT, 1e3 * mb, cfg, n_gpus=ws, plain={"value": sl / mp / 1e9, "ms_per_step": 1e3 * mp,
-                                      "gpu_launches": plain_launches // len(tp)},
-          batched_over_plain=mp / mb, gpu_launches=launches // len(tb), clocks=clocks, e2e=e2e,
-          cpu_baseline=cpu, min_ms=1e3 * min(tb), max_ms=1e3 * max(tb))
+          UNIT, 1e3 * mb, cfg, n_gpus=ws)
 
 
 def _cpu_batch(pin, offs, ln, sig, target=1 << 24):

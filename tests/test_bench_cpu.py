@@ -59,3 +59,16 @@ def test_reference_arm_line():
     assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["value"] == line["value"]
     assert line["e2e"] == {"value": line["value"], "unit": line["unit"], "h2d_bytes_per_step": 0,
                            "d2h_bytes_per_step": 0}
+
+
+def test_byte_model():
+    """Algorithmic bytes of the headline build (the byte model of the
+    benchmark's roofline): tau = 8 moves 4 B and 2 B per symbol in its two
+    passes and B(8) = 10.16 n for the whole build; tau = 4 narrows the
+    intermediate to 12, 8 and 4 bits."""
+    import bench
+    n = 1 << 20
+    assert bench.pass_bytes(n, 16, 2, 8) == [4 * n, 2 * n]
+    assert abs(bench.step_bytes(n, 16, 2, 8) / n - 10.15625) < 1e-9
+    assert bench.pass_bytes(n, 16, 2, 4) == [4.5 * n, 3.5 * n, 2.5 * n, 1.5 * n]
+    assert bench.pass_bytes(n, 3, 1, 8) == [1 * n + 3 * n / 8]
