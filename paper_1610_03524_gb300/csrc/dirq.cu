@@ -65,7 +65,7 @@ __device__ __forceinline__ uint32_t sel64(uint64_t v, uint32_t r) {
 // first block of level l), so the level is found once per block; each warp
 // counts DIR_SB_PER_WARP superblocks with their words loaded together.
 #ifndef WT_DIR_SB_PER_WARP
-#define WT_DIR_SB_PER_WARP 4
+#define WT_DIR_SB_PER_WARP 8
 #endif
 constexpr int DIR_SB_PER_WARP = WT_DIR_SB_PER_WARP;
 constexpr int DIR_SB_PER_BLOCK = 8 * DIR_SB_PER_WARP;  // 256 threads
@@ -108,34 +108,52 @@ __global__ void __launch_bounds__(256) k_dir_count(const uint64_t* bits, const L
     sb0 = s_sb0;
     g0 = s_g0;
   }
+  // two superblocks at a time: lanes 0-15 the first, 16-31 the second, each
+  // lane two consecutive words (one 16-byte load where aligned)
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int hl = lane & 15, half = lane >> 4;
   const uint64_t s0 = sb0 + (uint64_t)warp * DIR_SB_PER_WARP;
-  uint64_t w[DIR_SB_PER_WARP];
-  int valid[DIR_SB_PER_WARP];
+  const uint64_t* lb = bits + m.bit_off;
+  const bool vec = (((uintptr_t)lb) & 15) == 0;
+  constexpr int NP = DIR_SB_PER_WARP / 2;
+  uint64_t w0[NP], w1[NP];
+  int v0[NP], v1[NP];
 #pragma unroll
-  for (int u = 0; u < DIR_SB_PER_WARP; u++) {
-    const uint64_t s = s0 + u;
-    const int64_t rem = (int64_t)m.n - (int64_t)(2048 * s + 64 * (uint64_t)lane);
-    valid[u] = (s >= m.nsb || rem <= 0) ? 0 : (rem >= 64 ? 64 : (int)rem);
+  for (int u = 0; u < NP; u++) {
+    const uint64_t s = s0 + 2 * u + half;
+    const int64_t rem = (int64_t)m.n - (int64_t)(2048 * s + 128 * (uint64_t)hl);
+    const bool live = s < m.nsb && rem > 0;
+    v0[u] = !live ? 0 : (rem >= 64 ? 64 : (int)rem);
+    v1[u] = (!live || rem <= 64) ? 0 : (rem >= 128 ? 64 : (int)(rem - 64));
+    const uint64_t* p = lb + 32 * s + 2 * hl;
     // words past the last valid bit are not read (a caller bitvector may end there)
-    w[u] = valid[u] ? __ldcs(bits + m.bit_off + 32 * s + lane) : 0ull;
+    if (v1[u] && vec) {
+      const ulonglong2 q = __ldcs((const ulonglong2*)p);
+      w0[u] = q.x;
+      w1[u] = q.y;
+    } else {
+      w0[u] = v0[u] ? __ldcs(p) : 0ull;
+      w1[u] = v1[u] ? __ldcs(p + 1) : 0ull;
+    }
   }
 #pragma unroll
-  for (int u = 0; u < DIR_SB_PER_WARP; u++) {
-    const uint64_t s = s0 + u;
-    if (s >= m.nsb) break;
-    const int z = valid[u] - __popcll(w[u]);
+  for (int u = 0; u < NP; u++) {
+    const uint64_t s = s0 + 2 * u + half;
+    const int z = v0[u] + v1[u] - __popcll(w0[u]) - __popcll(w1[u]);
     int zi = z;
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const int y = __shfl_up_sync(FULL, zi, o);
-      if (lane >= o) zi += y;
+    for (int o = 1; o < 16; o <<= 1) {
+      const int y = __shfl_up_sync(FULL, zi, o, 16);
+      if (hl >= o) zi += y;
     }
-    const uint64_t r1 = (uint64_t)__shfl_sync(FULL, zi, 7);
-    const uint64_t r2 = (uint64_t)__shfl_sync(FULL, zi, 15);
-    const uint64_t r3 = (uint64_t)__shfl_sync(FULL, zi, 23);
-    if (lane == 0) dir[m.dir_off + 2 * s + 1] = (r1 << 16) | (r2 << 32) | (r3 << 48);
-    if (lane == 31) sbz[g0 + s] = (uint64_t)zi;
+    // zeros of 512-bit blocks 0, 1, 2 of the superblock: lanes 3, 7, 11 of its half
+    const uint64_t r1 = (uint64_t)__shfl_sync(FULL, zi, 3, 16);
+    const uint64_t r2 = (uint64_t)__shfl_sync(FULL, zi, 7, 16);
+    const uint64_t r3 = (uint64_t)__shfl_sync(FULL, zi, 11, 16);
+    if (s < m.nsb) {
+      if (hl == 0) dir[m.dir_off + 2 * s + 1] = (r1 << 16) | (r2 << 32) | (r3 << 48);
+      if (hl == 15) sbz[g0 + s] = (uint64_t)zi;
+    }
   }
 }
 
