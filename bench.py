@@ -245,23 +245,29 @@ def cpu_baseline(log2n_sample):
             "parallel": cpu_parallel_baseline(S)}
 
 
-def cpu_parallel_baseline(S):
-    """The same sample through the multi-threaded CPU construction
-    (cpu_baseline/: levelwise stable splits over chunks, prefix-summed
-    offsets), on every host core; median of three runs."""
+def cpu_parallel_baseline(S, short_lists=False):
+    """The same sample through a multi-threaded CPU construction
+    (cpu_baseline/: levelwise stable splits over chunks with prefix-summed
+    offsets, or big levels every 4 levels with table-driven short lists in
+    between), on every host core; median of three runs."""
     import cpu_baseline as cb
     threads = os.cpu_count() or 1
-    cb.wm_build(S[:4096], 16, threads)  # warm-up: threads, pages
+    cb.wm_build(S[:4096], 16, threads, short_lists=short_lists)  # warm-up: threads, pages
     ts = []
     for _ in range(3):
         t0 = time.perf_counter()
-        cb.wm_build(S, 16, threads)
+        cb.wm_build(S, 16, threads, short_lists=short_lists)
         ts.append(time.perf_counter() - t0)
     dt = statistics.median(ts)
-    return {"value": S.size * 16 / dt / 1e9, "unit": UNIT, "cores": threads,
-            "kind": "multi-threaded CPU build (cpu_baseline/)",
-            "sample": f"the same 2^{int(S.size).bit_length() - 1} symbols; WM levels + rank "
-                      f"directory + select samples; {dt:.3f} s"}
+    kind = ("multi-threaded CPU build, big levels + packed short lists split by table lookup "
+            "(cpu_baseline/)" if short_lists else "multi-threaded CPU build, levelwise splits "
+            "(cpu_baseline/)")
+    out = {"value": S.size * 16 / dt / 1e9, "unit": UNIT, "cores": threads, "kind": kind,
+           "sample": f"the same 2^{int(S.size).bit_length() - 1} symbols; WM levels + rank "
+                     f"directory + select samples; {dt:.3f} s"}
+    if not short_lists:
+        out["short_lists"] = cpu_parallel_baseline(S, short_lists=True)
+    return out
 
 
 def run_reference(args):

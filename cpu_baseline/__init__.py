@@ -1,6 +1,7 @@
-"""Multi-threaded CPU construction of the wavelet matrix with its rank
-directories and select samples (wm_cpu.cpp): the benchmark's timed CPU
-comparison.  Not used by the library."""
+"""Multi-threaded CPU constructions of the wavelet matrix with its rank
+directories and select samples (wm_cpu.cpp): levelwise splits, and big
+levels with table-driven packed short lists (Section 3, Theorem 4.1); the
+benchmark's timed CPU comparisons.  Not used by the library."""
 from __future__ import annotations
 
 import ctypes
@@ -31,13 +32,17 @@ def _load():
         lib.cpu_wm_build.argtypes = [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int, ctypes.c_int,
                                      ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                      ctypes.c_void_p]
+        lib.cpu_wm_build_short.restype = ctypes.c_int
+        lib.cpu_wm_build_short.argtypes = lib.cpu_wm_build.argtypes
         _lib = lib
     return _lib
 
 
-def wm_build(S: np.ndarray, L: int, threads: int):
+def wm_build(S: np.ndarray, L: int, threads: int, short_lists: bool = False):
     """Level words (L, W), zero counts (L,), rank records (L, nsb+1, 2) and
-    select samples (L, 2, n/4096 + 1) of the wavelet matrix of uint16 S."""
+    select samples (L, 2, n/4096 + 1) of the wavelet matrix of uint16 S.
+    short_lists: big levels every 4 levels and table-driven short lists in
+    between (Section 3, Theorem 4.1) instead of one split per level."""
     S = np.ascontiguousarray(S, dtype=np.uint16)
     n = S.size
     W = ((n + 2047) // 2048) * 32
@@ -47,6 +52,7 @@ def wm_build(S: np.ndarray, L: int, threads: int):
     zeros = np.zeros(L, dtype=np.uint64)
     dirs = np.zeros((L, nsb + 1, 2), dtype=np.uint64)
     samp = np.zeros((L, 2, cap), dtype=np.uint64)
-    _load().cpu_wm_build(S.ctypes.data, n, L, threads, bits.ctypes.data, zeros.ctypes.data,
-                         dirs.ctypes.data, samp.ctypes.data)
+    fn = _load().cpu_wm_build_short if short_lists else _load().cpu_wm_build
+    fn(S.ctypes.data, n, L, threads, bits.ctypes.data, zeros.ctypes.data, dirs.ctypes.data,
+       samp.ctypes.data)
     return bits, zeros, dirs, samp
