@@ -12,8 +12,9 @@
  *    current device); h_* are host pointers.  Sizes are element counts.
  *  * `stream` is a cudaStream_t passed as void* (NULL = legacy default
  *    stream).  Builds and queries enqueue their work on it and return
- *    (huff_wt_build synchronises once, as stated there); results are final
- *    once the stream is synchronised.  Calls that hand results to the host
+ *    (huff_wt_build finishes its build from a library thread, as stated
+ *    there); results are final once the stream is synchronised.  Calls that
+ *    hand results to the host
  *    (wt_sync, wt_export, wt_export_select, wt_dd_merge for its parts,
  *    wt_free, wm_autotune, wm_autotune_config) synchronise the handle's stream themselves.  Device-side errors found during
  *    a build (a symbol >= sigma: WT_ERR_SYMBOL_GE_SIGMA; an internal table
@@ -132,9 +133,18 @@ wt_status wm_build(const void* d_seq, uint64_t n, uint32_t sigma, uint32_t width
  * trees).  h_code_len: sigma code lengths (0 = absent symbol), or NULL to
  * derive Huffman lengths from the sequence's histogram, limited to 32 bits.
  * Codes are canonical.  Level l holds the elements with code length > l,
- * ordered by their l-bit code prefix; its bit is code bit l.  This call
- * synchronises the stream once (the code is built on the host from the
- * histogram).  sigma in [1, 2^24]. */
+ * ordered by their l-bit code prefix; its bit is code bit l.  sigma in
+ * [1, 2^24].  The code is built on the host from the sequence's histogram,
+ * so this build is asynchronous in a different way from the others: the call
+ * enqueues a copy of d_seq on `stream` (d_seq may be released once the
+ * stream has passed that point) and returns; a library thread then builds the
+ * histogram, the code and the tree on the handle's own stream, which starts
+ * after the copy.  Every later call on the handle (queries, wt_sync,
+ * wt_export, wt_export_select, wt_query_multi, wt_free, wt_symbol_levels)
+ * first waits for that thread and orders its own stream after the build.
+ * Errors of the build itself (a symbol >= sigma, caller lengths that leave a
+ * present symbol without a code or whose Kraft sum exceeds 1, no memory) are
+ * reported by the next call on the handle, as device-side errors are. */
 wt_status huff_wt_build(const void* d_seq, uint64_t n, uint32_t sigma, uint32_t width_bytes,
                         const uint8_t* h_code_len, const wt_build_opts* opts,
                         wt_stream stream, wt_handle* out);
@@ -390,7 +400,7 @@ const char* wt_status_str(wt_status s);
  * a utility for reading exported arrays). */
 wt_status wt_memcpy_d2h(void* h_dst, const void* d_src, uint64_t bytes);
 
-/* Measurement hooks (process-wide, not thread-safe): wt_prof_enable(1)
+/* Measurement hooks (process-wide; library threads record too): wt_prof_enable(1)
  * starts counting every kernel this library launches and recording CUDA
  * events around each partition-pass launch on its stream; wt_prof_read()
  * waits for those events and returns the kernel count, the number of pass

@@ -120,6 +120,91 @@ wt_status sync_handle(wt_struct* h) {
   return WT_OK;
 }
 
+// A handle built asynchronously: wait for its library thread, then (with
+// st given) order st after everything the build enqueued.  Returns the
+// handle's deferred status.
+wt_status join_build_impl(wt_struct* h, cudaStream_t st, bool order) {
+  if (h->worker) {
+    h->worker->join();
+    delete h->worker;
+    h->worker = nullptr;
+  }
+  if (order && h->built && st != h->stream) cudaStreamWaitEvent(st, h->built, 0);
+  return h->deferred;
+}
+
+__global__ void k_copy_bytes(uint8_t* dst, const uint8_t* src, uint64_t bytes) {
+  const uint64_t i0 = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  if ((((uintptr_t)dst | (uintptr_t)src) & 15) == 0) {
+    const uint64_t nv = bytes / 16;
+    for (uint64_t i = i0; i < nv; i += stride) ((uint4*)dst)[i] = ((const uint4*)src)[i];
+    for (uint64_t i = nv * 16 + i0; i < bytes; i += stride) dst[i] = src[i];
+  } else {
+    for (uint64_t i = i0; i < bytes; i += stride) dst[i] = src[i];
+  }
+}
+
+// Huffman-shaped tree, asynchronous: the call enqueues a copy of the input on
+// the caller's stream (the input is borrowed only until that stream reaches
+// the copy) and returns; a library thread builds the code on the host from
+// the histogram and enqueues the build on the handle's own stream, which
+// starts after the copy.  Every later call on the handle first waits for
+// that thread and orders its own stream after the build (join_build).
+wt_status huff_async(const void* d_seq, uint64_t n, uint32_t sigma, uint32_t width,
+                     const uint8_t* h_len, const wt_build_opts* opts, wt_stream stream,
+                     wt_handle* out) {
+  cudaStream_t cs = (cudaStream_t)stream;
+  wt_struct* h = nullptr;
+  wt_status s = new_handle(stream, n, sigma, &h);
+  if (s != WT_OK) return s;
+  h->flags = opts ? opts->flags : 0u;
+  h->kind = WT_KIND_HUFF;
+  cudaStream_t own = nullptr;
+  cudaEvent_t ready = nullptr;
+  void* copy = nullptr;
+  const uint64_t bytes = n * (uint64_t)width;
+  bool ok = cudaStreamCreateWithFlags(&own, cudaStreamNonBlocking) == cudaSuccess &&
+            cudaEventCreateWithFlags(&h->built, cudaEventDisableTiming) == cudaSuccess &&
+            cudaEventCreateWithFlags(&ready, cudaEventDisableTiming) == cudaSuccess &&
+            dmalloc(&copy, bytes, cs) == cudaSuccess;
+  if (ok && bytes) {
+    const unsigned grid = (unsigned)std::min<uint64_t>((bytes / 16 + 255) / 256 + 1, 4096);
+    k_copy_bytes<<<grid, 256, 0, cs>>>((uint8_t*)copy, (const uint8_t*)d_seq, bytes);
+    count_launch();
+  }
+  ok = ok && cudaEventRecord(ready, cs) == cudaSuccess &&
+       cudaStreamWaitEvent(own, ready, 0) == cudaSuccess && cudaGetLastError() == cudaSuccess;
+  if (ready) cudaEventDestroy(ready);
+  if (!ok) {
+    if (copy) dfree(copy, cs);
+    cudaStreamSynchronize(cs);
+    free_arrays(h);
+    cudaStreamSynchronize(cs);
+    if (h->built) cudaEventDestroy(h->built);
+    if (own) cudaStreamDestroy(own);
+    delete h;
+    return WT_ERR_CUDA;
+  }
+  h->stream = own;
+  h->own_stream = true;
+  std::vector<uint8_t> lens;
+  if (h_len) lens.assign(h_len, h_len + sigma);
+  const wt_build_opts oc = opts ? *opts : wt_build_opts{};
+  const int dev = h->device;
+  h->worker = new std::thread([h, copy, n, sigma, width, lens, oc, dev]() {
+    cudaSetDevice(dev);
+    wt_status st = build_huff(copy, n, sigma, (int)width, lens.empty() ? nullptr : lens.data(),
+                              &oc, h);
+    dfree(copy, h->stream);
+    if (st == WT_OK && cudaGetLastError() != cudaSuccess) st = WT_ERR_CUDA;
+    if (st != WT_OK) h->deferred = st;
+    cudaEventRecord(h->built, h->stream);
+  });
+  *out = h;
+  return WT_OK;
+}
+
 wt_status seq_build(int kind, const void* d_seq, uint64_t n, uint32_t sigma, uint32_t width,
                     const uint8_t* h_len, uint32_t degree, const wt_build_opts* opts,
                     wt_stream stream, wt_handle* out) {
@@ -136,6 +221,7 @@ wt_status seq_build(int kind, const void* d_seq, uint64_t n, uint32_t sigma, uin
   if (n >= ((uint64_t)1 << 40)) return WT_ERR_UNSUPPORTED;
   if ((kind == WT_KIND_WT || kind == WT_KIND_MULTI || kind == WT_KIND_HUFF) && sigma > (1u << 24))
     return WT_ERR_UNSUPPORTED;
+  if (kind == WT_KIND_HUFF) return huff_async(d_seq, n, sigma, width, h_len, opts, stream, out);
   wt_struct* h = nullptr;
   s = new_handle(stream, n, sigma, &h);
   if (s != WT_OK) return s;
@@ -150,6 +236,12 @@ wt_status seq_build(int kind, const void* d_seq, uint64_t n, uint32_t sigma, uin
 }
 
 }  // namespace
+
+namespace wtk {
+wt_status join_build(wt_struct* h, cudaStream_t st, bool order) {
+  return join_build_impl(h, st, order);
+}
+}  // namespace wtk
 
 extern "C" {
 
@@ -206,6 +298,8 @@ wt_status wt_dd_merge(const wt_handle* parts, uint32_t r, const wt_build_opts* o
   if (!parts || r == 0) return WT_ERR_INVALID_ARG;
   wt_status s = check_opts(opts);
   if (s != WT_OK) return s;
+  for (uint32_t p = 0; p < r; p++)
+    if (parts[p]) join_build(parts[p], parts[p]->stream, false);
   const wt_struct* p0 = parts[0];
   if (!p0 || (p0->kind != WT_KIND_WM && p0->kind != WT_KIND_WT)) return WT_ERR_INVALID_ARG;
   uint64_t n = 0;
@@ -234,31 +328,36 @@ wt_status wt_dd_merge(const wt_handle* parts, uint32_t r, const wt_build_opts* o
 wt_status wt_access(wt_handle h, const uint64_t* d_i, uint64_t q, uint64_t* d_out,
                     wt_stream stream) {
   if (!h || (q && (!d_i || !d_out))) return WT_ERR_INVALID_ARG;
-  if (h->deferred != WT_OK) return h->deferred;
+  const wt_status s = join_build(h, (cudaStream_t)stream, true);
+  if (s != WT_OK) return s;
   return launch_query(h, 0, nullptr, d_i, q, d_out, (cudaStream_t)stream);
 }
 
 wt_status wt_rank(wt_handle h, const uint32_t* d_c, const uint64_t* d_i, uint64_t q,
                   uint64_t* d_out, wt_stream stream) {
   if (!h || (q && (!d_c || !d_i || !d_out))) return WT_ERR_INVALID_ARG;
-  if (h->deferred != WT_OK) return h->deferred;
+  const wt_status s = join_build(h, (cudaStream_t)stream, true);
+  if (s != WT_OK) return s;
   return launch_query(h, 1, d_c, d_i, q, d_out, (cudaStream_t)stream);
 }
 
 wt_status wt_select(wt_handle h, const uint32_t* d_c, const uint64_t* d_k, uint64_t q,
                     uint64_t* d_out, wt_stream stream) {
   if (!h || (q && (!d_c || !d_k || !d_out))) return WT_ERR_INVALID_ARG;
-  if (h->deferred != WT_OK) return h->deferred;
+  const wt_status s = join_build(h, (cudaStream_t)stream, true);
+  if (s != WT_OK) return s;
   return launch_query(h, 2, d_c, d_k, q, d_out, (cudaStream_t)stream);
 }
 
 wt_status wt_sync(wt_handle h) {
   if (!h) return WT_ERR_INVALID_ARG;
+  join_build(h, h->stream, false);
   return sync_handle(h);
 }
 
 wt_status wt_export(wt_handle h, wt_export_view* out) {
   if (!h || !out) return WT_ERR_INVALID_ARG;
+  join_build(h, h->stream, false);
   wt_status s = sync_handle(h);
   if (s != WT_OK) return s;
   memset(out, 0, sizeof(*out));
@@ -287,16 +386,20 @@ wt_status wt_free(wt_handle h) {
   // memory goes back in stream order after the handle's queued work; a
   // handle of a batch that is not the last one frees nothing and waits for
   // nothing
+  join_build(h, h->stream, false);
   const bool owner = !h->arena;
   free_arrays(h, true);
   // the memory is back in the pool, for allocations on any stream
   const cudaError_t e = owner ? cudaStreamSynchronize(h->stream) : cudaGetLastError();
+  if (h->built) cudaEventDestroy(h->built);
+  if (h->own_stream) cudaStreamDestroy(h->stream);
   delete h;
   return e == cudaSuccess ? WT_OK : WT_ERR_CUDA;
 }
 
 wt_status wt_export_select(wt_handle h, uint32_t level, uint32_t bit, wt_select_view* out) {
   if (!h || !out || bit > 3) return WT_ERR_INVALID_ARG;
+  join_build(h, h->stream, false);
   wt_status s = sync_handle(h);
   if (s != WT_OK) return s;
   if (!(h->flags & WT_FLAG_SELECT_O1) || level >= h->cmeta.size() || bit > (h->bpe == 2 ? 3u : 1u))
@@ -315,6 +418,7 @@ wt_status wt_export_select(wt_handle h, uint32_t level, uint32_t bit, wt_select_
 
 uint64_t wt_symbol_levels(wt_handle h) {
   if (!h) return 0;
+  join_build(h, h->stream, false);
   uint64_t s = 0;
   for (uint64_t v : h->level_len) s += v;
   return h->bpe == 2 ? s * 2 : s;
@@ -342,6 +446,7 @@ wt_status wt_memcpy_d2h(void* h_dst, const void* d_src, uint64_t bytes) {
 
 void wt_prof_enable(int on) {
   Prof& p = prof();
+  std::lock_guard<std::mutex> g(p.mu);
   p.on = on != 0;
   p.launches = 0;
   p.pass_launches = 0;
@@ -351,6 +456,7 @@ void wt_prof_enable(int on) {
 
 wt_status wt_prof_read(uint64_t* launches, uint64_t* pass_launches, double* pass_ms) {
   Prof& p = prof();
+  std::lock_guard<std::mutex> g(p.mu);
   double ms = 0;
   wt_status s = WT_OK;
   for (size_t i = 0; i + 1 < p.ev.size(); i += 2) {

@@ -712,7 +712,8 @@ extern "C" wt_status wt_query_multi(const wt_handle* hs, uint32_t nh, const uint
   if ((nh && !hs) || (q && (!d_sid || !d_op || !d_c || !d_x || !d_out))) return WT_ERR_INVALID_ARG;
   for (uint32_t i = 0; i < nh; i++) {
     if (!hs[i]) return WT_ERR_INVALID_ARG;
-    if (hs[i]->deferred != WT_OK) return hs[i]->deferred;
+    const wt_status s = join_build(hs[i], (cudaStream_t)stream, true);
+    if (s != WT_OK) return s;
   }
   return launch_query_multi(hs, nh, d_sid, d_op, d_c, d_x, q, d_out, (cudaStream_t)stream);
 }

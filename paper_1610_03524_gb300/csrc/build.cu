@@ -743,6 +743,7 @@ static wt_status launch_pass_t(const PassParams& P, uint64_t max_tiles, const wt
   count_launch();
   if (pf.on) {
     cudaEventRecord(e1, st);
+    std::lock_guard<std::mutex> g(pf.mu);
     pf.ev.push_back(e0);
     pf.ev.push_back(e1);
     pf.pass_launches++;

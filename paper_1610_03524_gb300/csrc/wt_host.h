@@ -5,6 +5,8 @@
 #include <stdint.h>
 
 #include <atomic>
+#include <mutex>
+#include <thread>
 #include <vector>
 
 #include "../../include/wavelet.h"
@@ -95,9 +97,20 @@ struct wt_struct {
   std::vector<wtk::ClarkMeta> cmeta;
   // batched builds: the shared allocation holding every device array above
   wtk::Arena* arena = nullptr;
+  // asynchronous builds (huff_wt_build): the library thread that builds the
+  // code on the host and enqueues the rest of the build on `stream` (then
+  // the handle's own stream), and the event recorded after its last work
+  std::thread* worker = nullptr;
+  cudaEvent_t built = nullptr;
+  bool own_stream = false;
 };
 
 namespace wtk {
+
+// a handle built asynchronously (huff_wt_build): wait for its library thread
+// and, with order, make st wait for everything the build enqueued; returns
+// the handle's deferred status
+wt_status join_build(wt_struct* h, cudaStream_t st, bool order);
 
 // device memory helpers (stream-ordered pools)
 cudaError_t dmalloc(void** p, size_t bytes, cudaStream_t s);
@@ -145,9 +158,10 @@ wt_status upload(void* d_dst, const void* h_src, size_t bytes, cudaStream_t st);
 // Launch accounting (all kernels of the library) and optional CUDA-event
 // timing of the partition-pass launches, for the benchmark's roofline.
 struct Prof {
-  bool on = false;
+  std::atomic<bool> on{false};
   std::atomic<uint64_t> launches{0};
-  uint64_t pass_launches = 0;
+  std::atomic<uint64_t> pass_launches{0};
+  std::mutex mu;                 // guards ev (library threads record too)
   std::vector<cudaEvent_t> ev;  // pairs: before, after each pass launch
 };
 Prof& prof();

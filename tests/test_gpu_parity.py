@@ -256,15 +256,57 @@ def test_rs_parity(wt, nbits, seed):
 def test_symbol_out_of_range(wt):
     S = synth.uniform(51, 10000, 100, 1)
     S[1234] = 200
-    for fn in (wt.wm_build, wt.wt_build, wt.multiary_build):
+    for fn in (wt.wm_build, wt.wt_build, wt.multiary_build, wt.huff_wt_build):
         h = fn(to_dev(S), 100)
         with pytest.raises(wt.WaveletError) as ei:
             h.sync()
         assert ei.value.status == 2
         h.free()
+
+
+def test_huffman_build_is_asynchronous(wt):
+    """huff_wt_build returns once the input's copy is enqueued: the caller may
+    overwrite its input right after the stream passes the copy, several
+    builds may be in flight, and each handle's first use waits for its build
+    (queries on another stream are ordered after it)."""
+    import torch
+    seqs = [synth.zipf(60 + i, 200003 + 31 * i, 5000, 1.0, 4) for i in range(3)]
+    d = torch.empty(max(S.size for S in seqs), dtype=torch.int32, device="cuda")
+    hs = []
+    for S in seqs:
+        d[:S.size].copy_(torch.from_numpy(S.view(np.int32)).to("cuda"))
+        hs.append(wt.huff_wt_build(d[:S.size], 5000))   # d is overwritten by the next copy
+    other = torch.cuda.Stream()
+    for S, h in zip(seqs, hs):
+        hist = np.bincount(S.astype(np.int64), minlength=5000).astype(np.uint64)
+        ln, _ = oracle.huffman_lengths(hist, 32)
+        bits, woff, nl = oracle.huff_wt_build(S, ln, oracle.canonical_codes(ln))
+        q = 2000
+        op, c, arg = synth.queries(7, S, 5000, q)
+        m = op == 1
+        out = torch.empty(int(m.sum()), dtype=torch.int64, device="cuda")
+        h.rank(to_dev(c[m]), to_dev(arg[m]), out, stream=other)
+        other.synchronize()
+        assert np.array_equal(from_dev_u64(out), oracle.rank(S, 5000, c[m], arg[m]))
+        assert np.array_equal(h.export().bits, bits)
+        h.free()
+
+
+def test_huffman_invalid_caller_lengths_reported_on_use(wt):
+    S = synth.uniform(52, 5000, 50, 1)
+    ln = np.full(50, 6, np.uint8)
+    ln[S[0]] = 0  # a present symbol without a code
+    h = wt.huff_wt_build(to_dev(S), 50, code_len=ln)
     with pytest.raises(wt.WaveletError) as ei:
-        wt.huff_wt_build(to_dev(S), 100)
-    assert ei.value.status == 2
+        h.sync()
+    assert ei.value.status == 1
+    h.free()
+    ln = np.full(50, 2, np.uint8)  # Kraft sum 50/4 > 1
+    h = wt.huff_wt_build(to_dev(S), 50, code_len=ln)
+    with pytest.raises(wt.WaveletError) as ei:
+        h.export()
+    assert ei.value.status == 1
+    h.free()
 
 
 def test_empty_and_invalid(wt):
