@@ -19,7 +19,8 @@
 // words form one list, written by lanes in windows of 32 consecutive
 // entries.  Words copied whole are stored; the "boundary" words that several
 // tiles or nodes share (Section 4.2) are merged with atomicOr into the level
-// buffer, which the build zeroes first.  Finally the tile scatters its
+// buffer, which is zero before the pass (in a wavelet-matrix build each tile
+// zeroes its share of the next pass's levels).  Finally the tile scatters its
 // elements, narrowed to the bits still needed, to T_{a+t}: the stable
 // partition on the t-bit digit (big nodes, Section 3).
 #pragma once
