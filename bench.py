@@ -348,18 +348,20 @@ def run_native(args):
     torch.cuda.synchronize()
     sampler.start()
     wt.prof_enable(True)
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
+    # an event between consecutive builds gives every step's own time
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    e0, e1 = evs[0], evs[-1]
     e0.record(stream)
-    for _ in range(args.steps):
+    for i in range(args.steps):
         handles.append(wt.wm_build(d, SIGMA))
-    e1.record(stream)
+        evs[i + 1].record(stream)
     torch.cuda.synchronize()
     barrier()
     clocks = sampler.stop()
     launches, pass_launches, pass_ms = wt.prof_read()
     wt.prof_enable(False)
     ms = e0.elapsed_time(e1) / args.steps
+    step_ms = [evs[i].elapsed_time(evs[i + 1]) for i in range(args.steps)]
     for h in handles:
         h.sync()
     handles[0].export()  # completes without error
@@ -419,30 +421,9 @@ def run_native(args):
         sbs = [torch.cuda.Stream(), torch.cuda.Stream()]
         copied = [torch.cuda.Event(), torch.cuda.Event()]
         built = [torch.cuda.Event(), torch.cuda.Event()]
-        barrier()
-        torch.cuda.synchronize()
-        f0 = torch.cuda.Event(enable_timing=True)
-        f1 = torch.cuda.Event(enable_timing=True)
-        f0.record(sbs[0])
-        sc.wait_stream(sbs[0])
-        sbs[1].wait_stream(sbs[0])
         lib = wt.load_library()
         view = wt.ExportView()
-
-        # per-step events: the copy on the copy stream, the build on its stream
         ev = lambda: torch.cuda.Event(enable_timing=True)
-        cs, ce = [ev() for _ in range(k)], [ev() for _ in range(k)]
-        bs, be = [ev() for _ in range(k)], [ev() for _ in range(k)]
-
-        def copy_in(i):
-            b = i % 2
-            with torch.cuda.stream(sc):
-                if i >= 2:
-                    sc.wait_event(built[b])
-                cs[i].record(sc)
-                dbufs[b].copy_(pin, non_blocking=True)
-                ce[i].record(sc)
-                copied[b].record(sc)
 
         def finish(h):
             # the step's result read on the host: wt_export waits for the
@@ -453,22 +434,53 @@ def run_native(args):
             hz.numpy()[:] = np.ctypeslib.as_array(view.zeros, shape=(L,)).view(np.int64)
             h.free()
 
-        copy_in(0)
-        prev = None
-        for i in range(k):
-            if i + 1 < k:
-                copy_in(i + 1)
-            b = i % 2
-            sbs[b].wait_event(copied[b])
-            bs[i].record(sbs[b])
-            h = wt.wm_build(dbufs[b], SIGMA, stream=sbs[b])
-            be[i].record(sbs[b])
-            built[b].record(sbs[b])
-            if prev is not None:
-                finish(prev)
-            prev = h
-        finish(prev)
-        sbs[0].wait_stream(sbs[1])
+        def pipeline(k):
+            """k steps; returns the first event and the per-step copy and
+            build events (the copy on the copy stream, the build on its
+            stream)"""
+            f0 = ev()
+            f0.record(sbs[0])
+            sc.wait_stream(sbs[0])
+            sbs[1].wait_stream(sbs[0])
+            cs, ce = [ev() for _ in range(k)], [ev() for _ in range(k)]
+            bs, be = [ev() for _ in range(k)], [ev() for _ in range(k)]
+
+            def copy_in(i):
+                b = i % 2
+                with torch.cuda.stream(sc):
+                    if i >= 2:
+                        sc.wait_event(built[b])
+                    cs[i].record(sc)
+                    dbufs[b].copy_(pin, non_blocking=True)
+                    ce[i].record(sc)
+                    copied[b].record(sc)
+
+            copy_in(0)
+            prev = None
+            for i in range(k):
+                if i + 1 < k:
+                    copy_in(i + 1)
+                b = i % 2
+                sbs[b].wait_event(copied[b])
+                bs[i].record(sbs[b])
+                h = wt.wm_build(dbufs[b], SIGMA, stream=sbs[b])
+                be[i].record(sbs[b])
+                built[b].record(sbs[b])
+                if prev is not None:
+                    finish(prev)
+                prev = h
+            finish(prev)
+            sbs[0].wait_stream(sbs[1])
+            return f0, cs, ce, bs, be
+
+        # the same pipeline untimed first (W steps), so that first uses of
+        # the buffers and the copy path fall outside the timed steps
+        pipeline(max(args.warmup, 2))
+        torch.cuda.synchronize()
+        barrier()
+        torch.cuda.synchronize()
+        f0, cs, ce, bs, be = pipeline(k)
+        f1 = ev()
         f1.record(sbs[0])
         torch.cuda.synchronize()
         barrier()
@@ -487,7 +499,8 @@ def run_native(args):
         e2e = {"value": ws * n * L / (float(te.item()) * 1e-3) / 1e9, "unit": UNIT,
                "h2d_bytes_per_step": 2 * n, "d2h_bytes_per_step": 8 * L, "steps": k,
                "ms_per_step": e_ms,
-               "timeline": {"copy_ms_median": statistics.median(cms), "copy_ms_max": max(cms),
+               "timeline": {"copy_ms": [round(x, 3) for x in cms],
+                            "copy_ms_median": statistics.median(cms), "copy_ms_max": max(cms),
                             "h2d_GBps_median": 2 * n / (statistics.median(cms) * 1e-3) / 1e9,
                             "build_ms_median": statistics.median(bms),
                             "copy_overlapped_with_build_frac": statistics.median(ov) if ov else None,
@@ -520,6 +533,8 @@ def run_native(args):
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "u16", "data": "synthetic",
+                "step_ms": {"min": min(step_ms), "median": statistics.median(step_ms),
+                            "max": max(step_ms)},
                 "config": cfg, "roofline": roof, "cpu_baseline": cpu,
                 "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
                 "parallelism": f"replicas x{ws} (independent builds, no collective)",
@@ -662,23 +677,29 @@ def batch_measure(wt, pin, offs, ln, sig, total, reps=3, e2e_steps=4):
                 dbufs[i % 2].copy_(pin, non_blocking=True)
                 copied[i % 2].record(sc)
 
+        def pipeline(k):
+            copy_in(0)
+            prev = None
+            for i in range(k):
+                if i + 1 < k:
+                    copy_in(i + 1)
+                sbs[i % 2].wait_event(copied[i % 2])
+                cur = wt.wm_batch_build_one(items=its[i % 2], stream=sbs[i % 2])
+                built[i % 2].record(sbs[i % 2])
+                if prev is not None:
+                    assert not prev.sync().any()
+                    prev.free()
+                prev = cur
+            assert not prev.sync().any()
+            prev.free()
+            torch.cuda.synchronize()
+
+        # untimed first (first uses of the buffers and the copy path), then
+        # the timed steps
+        pipeline(2)
         k = e2e_steps
         t0 = time.perf_counter()
-        copy_in(0)
-        prev = None
-        for i in range(k):
-            if i + 1 < k:
-                copy_in(i + 1)
-            sbs[i % 2].wait_event(copied[i % 2])
-            cur = wt.wm_batch_build_one(items=its[i % 2], stream=sbs[i % 2])
-            built[i % 2].record(sbs[i % 2])
-            if prev is not None:
-                assert not prev.sync().any()
-                prev.free()
-            prev = cur
-        assert not prev.sync().any()
-        prev.free()
-        torch.cuda.synchronize()
+        pipeline(k)
         te = (time.perf_counter() - t0) / k
         out["e2e"] = {"value": sl / te / 1e9, "unit": UNIT, "ms_per_step": 1e3 * te,
                       "h2d_bytes_per_step": int(2 * offs[-1]), "d2h_bytes_per_step": 4 * m,

@@ -18,8 +18,10 @@
  *    (wt_sync, wt_export, wt_export_select, wt_dd_merge for its parts,
  *    wt_free, wm_autotune, wm_autotune_config) synchronise the handle's stream themselves.  Device-side errors found during
  *    a build (a symbol >= sigma: WT_ERR_SYMBOL_GE_SIGMA; an internal table
- *    that disagrees with the data, which leaves the affected bits unwritten:
- *    WT_ERR_CUDA) are reported by wt_sync() or by the next call on the handle.
+ *    that disagrees with the data, which leaves the affected bits unwritten,
+ *    or a tile's bulk copy into shared memory that did not complete within
+ *    about a second, after which the waiting block stops: WT_ERR_CUDA) are
+ *    reported by wt_sync() or by the next call on the handle.
  *  * Symbol sequences are contiguous arrays of width_bytes = 1, 2 or 4
  *    (little-endian unsigned), read-only, borrowed for the duration of the
  *    call and never retained.  n must be below 2^40; longer sequences return

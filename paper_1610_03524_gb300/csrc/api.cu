@@ -106,7 +106,9 @@ wt_status sync_handle(wt_struct* h) {
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
   if (e != cudaSuccess) return h->deferred = WT_ERR_CUDA;
   if (err & ERR_SYMBOL) return h->deferred = WT_ERR_SYMBOL_GE_SIGMA;
-  if (err) return h->deferred = WT_ERR_CUDA;  // ERR_INTERNAL: a table disagreed with a tile
+  // ERR_INTERNAL (a table disagreed with a tile) or ERR_STALL (a tile load
+  // that did not complete in time)
+  if (err) return h->deferred = WT_ERR_CUDA;
   if (!h->zeros_valid) {
     h->zeros.assign(h->levels, 0);
     if (h->levels && h->bpe == 1) {

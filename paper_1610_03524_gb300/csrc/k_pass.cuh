@@ -1,8 +1,9 @@
 // k_pass.cuh -- the level-group partition kernel (one pass = t levels).
 //
 // One CTA processes one tile of T_a at a time (tiles taken from an atomic
-// ticket; no CTA waits on another).  For a tile it computes, in shared
-// memory:
+// ticket; no CTA waits on another).  A whole, aligned tile arrives by one
+// bulk copy (TMA) into shared memory, issued while the previous tile is still
+// being processed.  For a tile it computes, in shared memory:
 //   * the tile's bits of levels a..a+t-1, each in the order that level has
 //     inside the tile, by t stable 1-bit splits of the tile (Section 4.1: the
 //     descendants' sub-sequences are a stable integer sort on the next tau
@@ -103,6 +104,13 @@ __device__ __forceinline__ void class_range(const PassParams& P, int j, uint32_t
   ce = P.hf_node[off + (q - first) + 1];
 }
 
+// store the low sizeof(E) bytes of v at shared-memory byte address a
+template <typename E>
+__device__ __forceinline__ void st_shared(uint32_t a, uint32_t v) {
+  if (sizeof(E) == 2) asm volatile("st.shared.u16 [%0], %1;" ::"r"(a), "h"((unsigned short)v));
+  else asm volatile("st.shared.u32 [%0], %1;" ::"r"(a), "r"(v));
+}
+
 __device__ __forceinline__ uint64_t spread32(uint32_t v) {
   uint64_t x = v;
   x = (x | (x << 16)) & 0x0000FFFF0000FFFFull;
@@ -170,8 +178,8 @@ __global__ void __launch_bounds__(NT + 32, PassCtas<T, NT>::value) k_pass(const 
   static_assert(T % 64 == 0 && NT >= (1 << TAU_MAX), "tile geometry");
   using SM = PassSmem<E, T, NT, DIG>;
   extern __shared__ __align__(16) unsigned char smem[];
-  E* const bufA = (E*)(smem + SM::off_buf);
-  E* const bufB = bufA + T;
+  E* const buf0 = (E*)(smem + SM::off_buf);
+  E* const buf1 = buf0 + T;
   // per level and row: (ballot of the level's bit = the level's bits in its
   // order, ones before the row inside its warp)
   uint2* const rowq = (uint2*)(smem + SM::off_lbits);
@@ -183,6 +191,13 @@ __global__ void __launch_bounds__(NT + 32, PassCtas<T, NT>::value) k_pass(const 
   uint64_t* const sbase = cls_cs;  // reused by the scatter
 
   __shared__ uint32_t s_tile;
+  // the buffer holding this tile's elements as loaded (0: the first of the
+  // two) and whether they came by a bulk copy that completes on s_bar; the
+  // same for the next tile (set during this one)
+  __shared__ int s_ib, s_stg, s_nib, s_nstg, s_stall;
+  __shared__ uint32_t s_phase, s_nxt;           // s_bar's open phase; the next tile
+  __shared__ const unsigned char* s_nsrc;       // its elements if copied in bulk
+  __shared__ __align__(8) uint64_t s_bar;
   __shared__ int s_ones[W];
   __shared__ int s_scan[W + 1];
   __shared__ int wst[1 << TAU_MAX];
@@ -218,27 +233,71 @@ __global__ void __launch_bounds__(NT + 32, PassCtas<T, NT>::value) k_pass(const 
     }
     if (lane == 31) s_scan[warp] = si;
     __syncthreads();
-    int base = 0, tot = 0;
-#pragma unroll
-    for (int w2 = 0; w2 <= W; w2++) {
-      const int x = s_scan[w2];
-      base += (w2 < warp) ? x : 0;
-      tot += x;
-    }
+    const int x = lane <= W ? s_scan[lane] : 0;
+    const int base = __reduce_add_sync(FULL, lane < warp ? x : 0);
+    total = __reduce_add_sync(FULL, x);
     __syncthreads();
-    total = tot;
     return base + si - v;
   };
 
+  // Tile loads by the bulk-copy unit (TMA): tile ti+1's elements are copied
+  // into the buffer tile ti no longer reads while tile ti is still being
+  // processed, so a tile's load latency hides behind the previous tile.
+  // Used for whole tiles at 16-byte aligned addresses whose elements have the
+  // buffer's width (copied as they are) or are bytes in 16-bit buffers
+  // (copied into the buffer's upper half, where the first split reads them
+  // as bytes); other tiles, and batched passes, are loaded by the threads.
+  // tile nx's elements if they can come by one bulk copy, else nullptr
+  auto stage_src = [&](uint32_t nx) -> const unsigned char* {
+    if (BATCH || nx >= ntiles || P0.code_map) return nullptr;
+    const int iw = P0.in_w;
+    if (!(iw == (int)sizeof(E) || (iw == 1 && sizeof(E) == 2))) return nullptr;
+    uint64_t s0;
+    if (P0.tiles) {
+      const TileDesc d = P0.tiles[nx];
+      if (d.count != (uint32_t)T) return nullptr;
+      s0 = d.start;
+    } else {
+      s0 = (uint64_t)(nx - P0.tile0) * T;
+      if (s0 + T > P0.n_in) return nullptr;
+    }
+    const unsigned char* src = (const unsigned char*)P0.in + s0 * (uint64_t)iw;
+    return ((uintptr_t)src & 15) ? nullptr : src;
+  };
+  // copy them into buffer X (bytes narrower than E into its upper part)
+  auto stage = [&](const unsigned char* src, E* X) {
+    const int iw = P0.in_w;
+    bulk_load((unsigned char*)X + (size_t)T * (sizeof(E) - iw), src, (uint32_t)(T * iw), &s_bar);
+  };
+  if (tid == 0) {
+    s_stall = 0;
+    s_nib = 0;
+    s_phase = 0;
+    const uint32_t nx = atomicAdd(P0.ticket, 1u);
+    s_nxt = nx;
+    if (!BATCH) mbar_init1(&s_bar);
+    const unsigned char* src = stage_src(nx);
+    if (src) stage(src, buf0);
+    s_nstg = src != nullptr;
+  }
+
   for (;;) {
     if (tid == 0) {
-      uint32_t ti = atomicAdd(P0.ticket, 1u);
-      s_tile = ti;
-      if (BATCH && ti < ntiles) fill_seg(s_P, P0, ti);
+      const uint32_t nx = s_nxt;
+      s_tile = nx;
+      s_ib = s_nib;
+      s_stg = s_nstg;
+      if (BATCH && nx < ntiles) fill_seg(s_P, P0, nx);
     }
     __syncthreads();
     const uint32_t ti = s_tile;
     if (ti >= ntiles) break;
+    // the tile's elements as loaded (k = 0) and the other buffer (k = 1),
+    // both from one register: the byte offset of the first of them
+    const uint32_t boff = s_ib ? (uint32_t)(T * sizeof(E)) : 0u;
+    auto buf = [&](int k) -> E* {
+      return (E*)((unsigned char*)buf0 + (boff ^ (k ? (uint32_t)(T * sizeof(E)) : 0u)));
+    };
     // this tile's share of the zeroing of a later pass's levels (stores that
     // use the DRAM bandwidth the tile's compute leaves idle)
     if (!BATCH && P0.clear) clear_share(P0.clear, P0.clear_units, P0.clear_per, ti, tid, NB);
@@ -263,7 +322,10 @@ __global__ void __launch_bounds__(NT + 32, PassCtas<T, NT>::value) k_pass(const 
     const bool full = cnt == T;
 
     // ---- 1. load the tile (its digit counts were taken before the pass) --
-    {
+    if (s_stg) {
+      if (!mbar_wait(&s_bar, s_phase)) s_stall = 1;
+    } else {
+      E* const bufA = buf(0);
       if (P.code_map) {
         for (int i = tid; i < cnt; i += NB) bufA[i] = (E)P.code_map[load_elem(P.in, P.in_w, ts + i)];
       } else if (P.in_w == 2 && sizeof(E) == 2 && full &&
@@ -291,12 +353,19 @@ __global__ void __launch_bounds__(NT + 32, PassCtas<T, NT>::value) k_pass(const 
       }
     }
     __syncthreads();
+    if (s_stall) {  // uniform: a bulk copy that never completed
+      if (tid == 0) atomicOr(P.err, ERR_STALL);
+      return;
+    }
 
     int cur;
     if (warp == CW) {
       // ---- 3 (control warp). class counts of every level from the tile's
       //      digit counts; counts of all earlier tiles from their prefix
       //      sums; exclusive counts of every level -------------------------
+      // the CTA's next tile, taken now so that its latency hides behind
+      // this tile's work, and where its elements are
+      const uint32_t nx = lane == 0 ? atomicAdd(P0.ticket, 1u) : 0u;
       const int nd = 1 << t;
       // this tile's count of every digit value in the earlier tiles of its
       // sequence or node: the prefix sums of the per-tile counts (Section
@@ -362,6 +431,10 @@ __global__ void __launch_bounds__(NT + 32, PassCtas<T, NT>::value) k_pass(const 
           ex_cnt[cls_idx(j, k)] = ex_cnt[cls_idx(j + 1, k)] + ex_cnt[cls_idx(j + 1, k + (1 << j))];
         __syncwarp();
       }
+      if (lane == 0) {
+        s_nxt = nx;
+        s_nsrc = stage_src(nx);
+      }
     } else {
       // ---- 4 (worker warps). t stable 1-bit splits in shared memory -------
       // Warp w holds rows 16w..16w+15 of the tile (row = 32 consecutive
@@ -371,12 +444,15 @@ __global__ void __launch_bounds__(NT + 32, PassCtas<T, NT>::value) k_pass(const 
       // are a running sum in uniform registers.  After one exchange of the
       // warps' one counts, an element at position p with k ones before it
       // goes to Z + k if its bit is 1 and to p - k otherwise.
+      // a staged tile of bytes bound for a 16-bit buffer sits, as bytes, in
+      // the buffer's upper half; the first split reads it there
+      const bool bytes0 = sizeof(E) == 2 && s_stg && P.in_w == 1;
       auto splits = [&](auto full_c) {
         constexpr bool F = decltype(full_c)::value;
         const int nmove = P.out != nullptr ? t : t - 1;
         for (int j = 0; j < t; j++) {
-          const E* src = (j & 1) ? bufB : bufA;
-          E* dst = (j & 1) ? bufA : bufB;
+          const E* src = buf(j & 1);
+          E* dst = buf((j & 1) ^ 1);
           const uint32_t m = 1u << (P.rbits - 1 - j);
           const bool two = DIG && (((P.a + j) & 1) == 0) && (P.a + j + 1 < P.L);
           uint2* const Rw = rowq + j * TWS + warp * EPW;
@@ -384,40 +460,52 @@ __global__ void __launch_bounds__(NT + 32, PassCtas<T, NT>::value) k_pass(const 
           uint32_t xr[EPW];
 #endif
           int ones = 0;
+          // ballots of the level's bit over the warp's rows, reading the
+          // elements through sp (bytes for a staged byte tile's first split)
+          auto phase1 = [&](auto* sp) {
 #pragma unroll
-          for (int e = 0; e < EPW; e++) {
-            const int p = wbase + e * 32 + lane;
-            const uint32_t x = (F || p < cnt) ? (uint32_t)src[p] : 0u;
+            for (int e = 0; e < EPW; e++) {
+              const int p = wbase + e * 32 + lane;
+              const uint32_t x = (F || p < cnt) ? (uint32_t)sp[p] : 0u;
 #if WT_PASS_KEEP_X
-            xr[e] = x;
+              xr[e] = x;
 #endif
-            const uint32_t B = __ballot_sync(FULL, x & m);
-            if (lane == 0) Rw[e] = make_uint2(B, (uint32_t)ones);
-            ones += __popc(B);
-            if (DIG && two) {
-              const uint32_t B2 = __ballot_sync(FULL, x & (m >> 1));
-              if (lane == 0) pb1[(j >> 1) * TW + warp * EPW + e] = B2;
+              const uint32_t B = __ballot_sync(FULL, x & m);
+              if (lane == 0) Rw[e] = make_uint2(B, (uint32_t)ones);
+              ones += (int)sizeof(E) * __popc(B);
+              if (DIG && two) {
+                const uint32_t B2 = __ballot_sync(FULL, x & (m >> 1));
+                if (lane == 0) pb1[(j >> 1) * TW + warp * EPW + e] = B2;
+              }
             }
-          }
+          };
+          if (sizeof(E) == 2 && j == 0 && bytes0)
+            phase1((const uint8_t*)src + T);
+          else
+            phase1(src);
           if (j < nmove) {
             if (lane == 0) s_ones[warp] = ones;
             bar_workers();
             const int v = lane < W ? s_ones[lane] : 0;
             const int T1 = __reduce_add_sync(FULL, v);
             const int ob = __reduce_add_sync(FULL, lane < warp ? v : 0);
-            const int zb = cnt - T1 + ob;      // destination of this warp's first one
-            const int pl = wbase + lane - ob;  // position minus ones before the warp
+            // shared-memory byte addresses: of this warp's first one's
+            // destination, and of the lane's position minus the ones before
+            // the warp
+            const uint32_t ds = smem_addr(dst);
+            const uint32_t zb = ds + (uint32_t)((int)sizeof(E) * cnt - T1 + ob);
+            const uint32_t pl = ds + (uint32_t)((int)sizeof(E) * (wbase + lane) - ob);
 #pragma unroll
             for (int e = 0; e < EPW; e++) {
               const uint2 R = Rw[e];
-              const int q = (int)R.y + __popc(R.x & lt);
+              const uint32_t q = R.y + (uint32_t)sizeof(E) * __popc(R.x & lt);
 #if WT_PASS_KEEP_X
               const uint32_t x = xr[e];
 #else
               const uint32_t x = (F || wbase + e * 32 + lane < cnt) ? (uint32_t)src[wbase + e * 32 + lane] : 0u;
 #endif
-              const int dest = (x & m) ? zb + q : pl + 32 * e - q;
-              if (F || wbase + e * 32 + lane < cnt) dst[dest] = (E)x;
+              const uint32_t dest = (x & m) ? zb + q : pl + (uint32_t)(sizeof(E) * 32 * e) - q;
+              if (F || wbase + e * 32 + lane < cnt) st_shared<E>(dest, x);
             }
             bar_workers();
           }
@@ -426,9 +514,20 @@ __global__ void __launch_bounds__(NT + 32, PassCtas<T, NT>::value) k_pass(const 
       if (full) splits(std::true_type{});
       else splits(std::false_type{});
     }
+    if (!BATCH) fence_async_smem();  // the splits' accesses before the next bulk copy
     __syncthreads();
-    // the final element order is in bufB after an odd number of moves
+    // the final element order is in buf(1) after an odd number of moves
     cur = (P.out != nullptr ? t : t - 1) & 1;
+    // the next tile goes to the buffer that does not hold the final order;
+    // a bulk copy consumed by this tile has closed s_bar's phase
+    if (tid == 0) {
+      const int nib = cur ? s_ib : 1 - s_ib;
+      const unsigned char* src = s_nsrc;
+      s_phase ^= (uint32_t)s_stg;
+      s_nib = nib;
+      s_nstg = src != nullptr;
+      if (src) stage(src, nib ? buf1 : buf0);
+    }
 
     if (s_bad) continue;  // uniform: read after the barrier above
 
@@ -517,13 +616,15 @@ __global__ void __launch_bounds__(NT + 32, PassCtas<T, NT>::value) k_pass(const 
 
     // ---- 6. scatter T_{a+t}, narrowed ------------------------------------
     if (P.out) {
-      const E* fin = cur ? bufB : bufA;
+      const E* fin = buf(cur);
       if (tid < 8) s_dead[tid] = 0;
       if (tid == 0) s_oob = 0;
       __syncthreads();
       // per digit value d (the t bits above the ones still needed, i.e. the
-      // class key reversed): the output index of the tile's first element
-      // minus the tile-local start of its class (modular: may wrap)
+      // class key reversed): the byte address that tile-local position 0
+      // would have in d's output range, so that position p goes to that
+      // address + p * width (modular arithmetic: the base itself may lie
+      // outside the output)
       for (int r = tid; r < (1 << t); r += NB) {
         uint64_t cs, ce;
         bool dead;
@@ -531,7 +632,7 @@ __global__ void __launch_bounds__(NT + 32, PassCtas<T, NT>::value) k_pass(const 
         const int ci = cls_idx(t, r);
         const uint32_t d = rev_bits((uint32_t)r, t);
         const uint64_t b0 = cs + ex_cnt[ci];
-        sbase[d] = b0 - cstart[ci];
+        sbase[d] = (uint64_t)(uintptr_t)P.out + (b0 - cstart[ci]) * (uint64_t)P.out_w;
         if (dead) atomicOr(&s_dead[d >> 5], 1u << (d & 31));
         else if (ccnt[ci] && b0 + ccnt[ci] > P.n_in) s_oob = 1;  // never for consistent tables
       }
@@ -543,12 +644,20 @@ __global__ void __launch_bounds__(NT + 32, PassCtas<T, NT>::value) k_pass(const 
       auto scatter = [&](auto out_t, auto huff_c) {
         using O = decltype(out_t);
         constexpr bool HF = decltype(huff_c)::value;
-        O* const out = (O*)P.out;
-        for (int p = tid; p < cnt; p += NB) {
+        auto one = [&](int p) {
           const uint32_t x = fin[p];
           const uint32_t d = (x >> nb) & dmask;
-          if (HF && ((s_dead[d >> 5] >> (d & 31)) & 1u)) continue;
-          out[sbase[d] + (uint64_t)p] = (O)(x & mask);
+          if (HF && ((s_dead[d >> 5] >> (d & 31)) & 1u)) return;
+          *(O*)(uintptr_t)(sbase[d] + (uint64_t)p * sizeof(O)) = (O)(x & mask);
+        };
+        if (full) {
+          // a whole tile: T / NT elements per worker thread, unrolled
+          if (tid < NT) {
+#pragma unroll
+            for (int k = 0; k < T / NT; k++) one(tid + k * NT);
+          }
+        } else {
+          for (int p = tid; p < cnt; p += NB) one(p);
         }
       };
       if (s_oob) {

@@ -12,7 +12,8 @@ constexpr uint32_t FULL = 0xffffffffu;
 
 // device error word bits
 // (ERR_INTERNAL: a prefix table disagreed with a tile; never for correct tables)
-enum : uint32_t { ERR_SYMBOL = 1u, ERR_INTERNAL = 4u };
+// (ERR_STALL: a staged tile load did not complete within its time limit)
+enum : uint32_t { ERR_SYMBOL = 1u, ERR_INTERNAL = 4u, ERR_STALL = 8u };
 
 // structure shapes handled by the partition pass
 enum Shape : int { SHAPE_WM = 0, SHAPE_WT = 1, SHAPE_HUFF = 2 };
@@ -142,6 +143,64 @@ __device__ __forceinline__ uint32_t lanemask_lt() {
   uint32_t m;
   asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
   return m;
+}
+
+// ---- bulk copies (TMA) into shared memory, completed on an mbarrier -------
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// an mbarrier for one arriving thread, visible to the bulk-copy unit
+__device__ __forceinline__ void mbar_init1(uint64_t* bar) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(bar)) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// Copy `bytes` (a multiple of 16; both addresses 16-byte aligned) from global
+// memory to shared memory with the bulk-copy unit; the barrier's current
+// phase completes when the bytes have landed.  One thread issues it.
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
+               "r"(bytes)
+               : "memory");
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_addr(dst)),
+      "l"(src), "r"(bytes), "r"(smem_addr(bar))
+      : "memory");
+}
+
+// order this thread's earlier shared-memory accesses before later bulk copies
+__device__ __forceinline__ void fence_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Wait for the phase of `bar` with parity `parity` to complete: false if it
+// has not after about one second (or 2^24 polls), which a bulk copy of a few
+// KB from valid memory never takes.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  const uint32_t a = smem_addr(bar);
+  uint64_t t0 = 0;
+  for (uint32_t it = 0; it < (1u << 24); it++) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (ok) return true;
+    if (it == 0) t0 = global_ns();
+    else if (global_ns() - t0 > 1000000000ull) return false;
+  }
+  return false;
 }
 
 
