@@ -670,21 +670,32 @@ def batch_measure(wt, pin, offs, ln, sig, total, reps=3, e2e_steps=4):
         built = [torch.cuda.Event(), torch.cuda.Event()]
         torch.cuda.synchronize()
 
-        def copy_in(i):
-            with torch.cuda.stream(sc):
-                if i >= 2:
-                    sc.wait_event(built[i % 2])
-                dbufs[i % 2].copy_(pin, non_blocking=True)
-                copied[i % 2].record(sc)
+        ev = lambda: torch.cuda.Event(enable_timing=True)
 
         def pipeline(k):
+            # per-step events: the copy on the copy stream, the build on its
+            # stream
+            cs, ce = [ev() for _ in range(k)], [ev() for _ in range(k)]
+            bs, be = [ev() for _ in range(k)], [ev() for _ in range(k)]
+
+            def copy_in(i):
+                with torch.cuda.stream(sc):
+                    if i >= 2:
+                        sc.wait_event(built[i % 2])
+                    cs[i].record(sc)
+                    dbufs[i % 2].copy_(pin, non_blocking=True)
+                    ce[i].record(sc)
+                    copied[i % 2].record(sc)
+
             copy_in(0)
             prev = None
             for i in range(k):
                 if i + 1 < k:
                     copy_in(i + 1)
                 sbs[i % 2].wait_event(copied[i % 2])
+                bs[i].record(sbs[i % 2])
                 cur = wt.wm_batch_build_one(items=its[i % 2], stream=sbs[i % 2])
+                be[i].record(sbs[i % 2])
                 built[i % 2].record(sbs[i % 2])
                 if prev is not None:
                     assert not prev.sync().any()
@@ -693,17 +704,19 @@ def batch_measure(wt, pin, offs, ln, sig, total, reps=3, e2e_steps=4):
             assert not prev.sync().any()
             prev.free()
             torch.cuda.synchronize()
+            return ([round(cs[i].elapsed_time(ce[i]), 3) for i in range(k)],
+                    [round(bs[i].elapsed_time(be[i]), 3) for i in range(k)])
 
         # untimed first (first uses of the buffers and the copy path), then
         # the timed steps
         pipeline(2)
         k = e2e_steps
         t0 = time.perf_counter()
-        pipeline(k)
+        cms, bms = pipeline(k)
         te = (time.perf_counter() - t0) / k
         out["e2e"] = {"value": sl / te / 1e9, "unit": UNIT, "ms_per_step": 1e3 * te,
                       "h2d_bytes_per_step": int(2 * offs[-1]), "d2h_bytes_per_step": 4 * m,
-                      "steps": k}
+                      "steps": k, "timeline": {"copy_ms": cms, "build_ms": bms}}
         del dbufs
     del d, seqs
     torch.cuda.empty_cache()

@@ -45,16 +45,21 @@ __device__ __forceinline__ void store_elem(void* p, int w, uint64_t i, uint32_t 
   else ((uint32_t*)p)[i] = v;
 }
 
-// Batched builds: the part of the parameters that belongs to tile ti's
-// sequence (the last segment with tile0 <= ti) into D.
-__device__ __forceinline__ void fill_seg(PassParams& D, const PassParams& P0, uint32_t ti) {
+// Batched builds: tile ti's sequence, the last segment with tile0 <= ti.
+__device__ __forceinline__ const SegDesc& seg_of(const PassParams& P0, uint32_t ti) {
   uint32_t lo = 0, hi = P0.nsegs - 1;
   while (lo < hi) {
     const uint32_t mid = (lo + hi + 1) >> 1;
     if (P0.segs[mid].tile0 <= ti) lo = mid;
     else hi = mid - 1;
   }
-  const SegDesc& d = P0.segs[lo];
+  return P0.segs[lo];
+}
+
+// Batched builds: the part of the parameters that belongs to tile ti's
+// sequence into D.
+__device__ __forceinline__ void fill_seg(PassParams& D, const PassParams& P0, uint32_t ti) {
+  const SegDesc& d = seg_of(P0, ti);
   D.in = d.in;
   D.in_w = d.in_w;
   D.out = d.out;
@@ -152,24 +157,26 @@ struct PassSmem {
   static constexpr size_t bytes = off_clscs + (size_t)(1 << TAU_MAX) * 8;
 };
 
-// resident CTAs per SM the register budget is sized for (40 registers a
-// thread at 288 threads a CTA; the 8192-symbol tile runs 544 threads a CTA,
-// 2 CTAs an SM at 60 registers),
-// and whether a split keeps its elements in registers between its two
-// phases (else it reads them from shared memory again)
+// resident CTAs per SM the register budget is sized for: 5 for 16-bit
+// elements (40 registers a thread at 288 threads a CTA); 4 for 32-bit
+// elements, whose buffers let only 4 CTAs share an SM's shared memory, and
+// for batched passes, whose per-sequence state would spill at 40 registers
+// (56 at 4); 2 for the 8192-symbol tile (544 threads a CTA).  And whether a
+// split keeps its elements in registers between its two phases (else it
+// reads them from shared memory again).
 #ifndef WT_PASS_MIN_CTAS
 #define WT_PASS_MIN_CTAS 5
 #endif
-template <int T, int NT>
+template <typename E, int T, bool BATCH>
 struct PassCtas {
-  static constexpr int value = T >= 8192 ? 2 : WT_PASS_MIN_CTAS;
+  static constexpr int value = T >= 8192 ? 2 : (BATCH || sizeof(E) == 4) ? 4 : WT_PASS_MIN_CTAS;
 };
 #ifndef WT_PASS_KEEP_X
 #define WT_PASS_KEEP_X 1
 #endif
 
 template <typename E, int T, int NT, bool DIG, bool BATCH>
-__global__ void __launch_bounds__(NT + 32, PassCtas<T, NT>::value) k_pass(const __grid_constant__ PassParams P0) {
+__global__ void __launch_bounds__(NT + 32, PassCtas<E, T, BATCH>::value) k_pass(const __grid_constant__ PassParams P0) {
   __shared__ PassParams s_P;
   const PassParams& P = BATCH ? s_P : P0;
   constexpr int W = NT / 32, PW = T / W, EPW = PW / 32, TW = T / 32, NB = NT + 32, CW = W;
@@ -197,6 +204,7 @@ __global__ void __launch_bounds__(NT + 32, PassCtas<T, NT>::value) k_pass(const 
   __shared__ int s_ib, s_stg, s_nib, s_nstg, s_stall;
   __shared__ uint32_t s_phase, s_nxt;           // s_bar's open phase; the next tile
   __shared__ const unsigned char* s_nsrc;       // its elements if copied in bulk
+  __shared__ int s_niw;                         // and their width
   __shared__ __align__(8) uint64_t s_bar;
   __shared__ int s_ones[W];
   __shared__ int s_scan[W + 1];
@@ -246,14 +254,21 @@ __global__ void __launch_bounds__(NT + 32, PassCtas<T, NT>::value) k_pass(const 
   // Used for whole tiles at 16-byte aligned addresses whose elements have the
   // buffer's width (copied as they are) or are bytes in 16-bit buffers
   // (copied into the buffer's upper half, where the first split reads them
-  // as bytes); other tiles, and batched passes, are loaded by the threads.
+  // as bytes); other tiles are loaded by the threads.
   // tile nx's elements if they can come by one bulk copy, else nullptr
-  auto stage_src = [&](uint32_t nx) -> const unsigned char* {
-    if (BATCH || nx >= ntiles || P0.code_map) return nullptr;
-    const int iw = P0.in_w;
-    if (!(iw == (int)sizeof(E) || (iw == 1 && sizeof(E) == 2))) return nullptr;
+  // (and its element width into iw)
+  auto stage_src = [&](uint32_t nx, int& iw) -> const unsigned char* {
+    if (nx >= ntiles || P0.code_map) return nullptr;
+    const void* in = P0.in;
+    iw = P0.in_w;
     uint64_t s0;
-    if (P0.tiles) {
+    if (BATCH) {
+      const SegDesc& sd = seg_of(P0, nx);
+      in = sd.in;
+      iw = sd.in_w;
+      s0 = (uint64_t)(nx - sd.tile0) * T;
+      if (s0 + T > sd.n) return nullptr;
+    } else if (P0.tiles) {
       const TileDesc d = P0.tiles[nx];
       if (d.count != (uint32_t)T) return nullptr;
       s0 = d.start;
@@ -261,12 +276,12 @@ __global__ void __launch_bounds__(NT + 32, PassCtas<T, NT>::value) k_pass(const 
       s0 = (uint64_t)(nx - P0.tile0) * T;
       if (s0 + T > P0.n_in) return nullptr;
     }
-    const unsigned char* src = (const unsigned char*)P0.in + s0 * (uint64_t)iw;
+    if (!(iw == (int)sizeof(E) || (iw == 1 && sizeof(E) == 2))) return nullptr;
+    const unsigned char* src = (const unsigned char*)in + s0 * (uint64_t)iw;
     return ((uintptr_t)src & 15) ? nullptr : src;
   };
   // copy them into buffer X (bytes narrower than E into its upper part)
-  auto stage = [&](const unsigned char* src, E* X) {
-    const int iw = P0.in_w;
+  auto stage = [&](const unsigned char* src, int iw, E* X) {
     bulk_load((unsigned char*)X + (size_t)T * (sizeof(E) - iw), src, (uint32_t)(T * iw), &s_bar);
   };
   if (tid == 0) {
@@ -275,9 +290,10 @@ __global__ void __launch_bounds__(NT + 32, PassCtas<T, NT>::value) k_pass(const 
     s_phase = 0;
     const uint32_t nx = atomicAdd(P0.ticket, 1u);
     s_nxt = nx;
-    if (!BATCH) mbar_init1(&s_bar);
-    const unsigned char* src = stage_src(nx);
-    if (src) stage(src, buf0);
+    mbar_init1(&s_bar);
+    int iw;
+    const unsigned char* src = stage_src(nx, iw);
+    if (src) stage(src, iw, buf0);
     s_nstg = src != nullptr;
   }
 
@@ -433,7 +449,9 @@ __global__ void __launch_bounds__(NT + 32, PassCtas<T, NT>::value) k_pass(const 
       }
       if (lane == 0) {
         s_nxt = nx;
-        s_nsrc = stage_src(nx);
+        int iw;
+        s_nsrc = stage_src(nx, iw);
+        s_niw = iw;
       }
     } else {
       // ---- 4 (worker warps). t stable 1-bit splits in shared memory -------
@@ -514,7 +532,7 @@ __global__ void __launch_bounds__(NT + 32, PassCtas<T, NT>::value) k_pass(const 
       if (full) splits(std::true_type{});
       else splits(std::false_type{});
     }
-    if (!BATCH) fence_async_smem();  // the splits' accesses before the next bulk copy
+    fence_async_smem();  // the splits' accesses before the next bulk copy
     __syncthreads();
     // the final element order is in buf(1) after an odd number of moves
     cur = (P.out != nullptr ? t : t - 1) & 1;
@@ -526,7 +544,7 @@ __global__ void __launch_bounds__(NT + 32, PassCtas<T, NT>::value) k_pass(const 
       s_phase ^= (uint32_t)s_stg;
       s_nib = nib;
       s_nstg = src != nullptr;
-      if (src) stage(src, nib ? buf1 : buf0);
+      if (src) stage(src, s_niw, nib ? buf1 : buf0);
     }
 
     if (s_bad) continue;  // uniform: read after the barrier above
