@@ -26,9 +26,6 @@ namespace wtk {
 
 wt_status launch_pass_batch(const PassParams& P, bool wide, const wt_build_opts* o,
                             cudaStream_t st);
-wt_status launch_hist_batch(const HistSeg* d_segs, uint32_t nsegs, uint64_t nchunks,
-                            uint64_t* hist, cudaStream_t st);
-wt_status launch_plan_batch(const PlanSeg* d_ps, uint32_t m, cudaStream_t st);
 wt_status dir_build_levels(const uint64_t* bits, const LevelMeta* d_meta, uint32_t nlev,
                            const std::vector<uint64_t>& sb_first, uint64_t* dir, uint64_t* samp,
                            uint64_t* zeros, int write_zeros, cudaStream_t st,
@@ -110,7 +107,7 @@ struct SeqPlan {
   // arena offsets (u64 units inside each region)
   uint64_t bits_base, dir_base, samp_base, zeros_base, meta_base;
   // workspace offsets
-  uint64_t hist_off, cls_off, lvl_base, seq_off;  // seq_off: bytes in each ping-pong buffer
+  uint64_t cls_off, lvl_base, seq_off;  // seq_off: bytes in each ping-pong buffer
   uint64_t seq_bytes;
 };
 
@@ -160,8 +157,8 @@ wt_status batch_build_wm(const wt_batch_item* items, uint32_t m, const wt_build_
                          cudaStream_t st, wt_struct** hs) {
   std::vector<SeqPlan> sp(m);
   uint64_t nbits = 0, ndir = 0, nsamp = 0, nzeros = 0, nmeta = 0;
-  uint64_t nhist = 0, ncls = 0, nlvl = 0, nseq = 0;
-  uint64_t nchunks = 0, nlev_tot = 0;
+  uint64_t ncls = 0, nlvl = 0, nseq = 0;
+  uint64_t nlev_tot = 0;
   int Gmax = 0;
   for (uint32_t i = 0; i < m; i++) {
     SeqPlan& p = sp[i];
@@ -179,17 +176,12 @@ wt_status batch_build_wm(const wt_batch_item* items, uint32_t m, const wt_build_
     nsamp += samp_u64(p);
     nzeros += p.L;
     nmeta += p.L;
-    p.hist_off = nhist;
     p.cls_off = ncls;
-    for (const Pass1& q : p.ps) {
-      nhist += 1u << q.t;
-      ncls += (2u << q.t) + q.t + 1;
-    }
+    for (const Pass1& q : p.ps) ncls += (2u << q.t) + q.t + 1;
     p.lvl_base = nlvl;
     nlvl += 2 * (uint64_t)p.L + 1;  // L+1 word offsets, then L lengths
     p.seq_off = nseq;
     nseq += p.G > 1 ? p.seq_bytes : 0;
-    if (p.n) nchunks += (p.n + HIST_CH - 1) / HIST_CH;
     nlev_tot += p.L;
     Gmax = std::max(Gmax, p.n ? p.G : 0);
   }
@@ -255,19 +247,14 @@ wt_status batch_build_wm(const wt_batch_item* items, uint32_t m, const wt_build_
     }
   }
   // ---- workspace ----------------------------------------------------------
-  uint32_t nh = 0;
-  for (uint32_t i = 0; i < m; i++) nh += sp[i].n ? 1 : 0;
   uint64_t nsegs_tot = 0;
   for (int g = 0; g < Gmax; g++)
     for (uint32_t i = 0; i < m; i++)
       if (sp[i].n && g < sp[i].G) nsegs_tot++;
-  const uint64_t w_hist = 0;
-  const uint64_t w_cls = up(w_hist + 8 * nhist, 256);
+  const uint64_t w_cls = 0;
   const uint64_t w_lvl = up(w_cls + 8 * ncls, 256);
   const uint64_t w_gmeta = up(w_lvl + 8 * nlvl, 256);
-  const uint64_t w_hseg = up(w_gmeta + sizeof(LevelMeta) * nlev_tot, 256);
-  const uint64_t w_pseg = up(w_hseg + sizeof(HistSeg) * std::max<uint32_t>(nh, 1), 256);
-  const uint64_t w_sseg = up(w_pseg + sizeof(PlanSeg) * std::max<uint32_t>(m, 1), 256);
+  const uint64_t w_sseg = up(w_gmeta + sizeof(LevelMeta) * nlev_tot, 256);
   const uint64_t w_tab_end = up(w_sseg + sizeof(SegDesc) * std::max<uint64_t>(nsegs_tot, 1), 256);
   const uint64_t w_tick = w_tab_end;
   const uint64_t w_seq0 = up(w_tick + 4 * 64, 256);
@@ -276,12 +263,9 @@ wt_status batch_build_wm(const wt_batch_item* items, uint32_t m, const wt_build_
   void* wsv = nullptr;
   CK(dmalloc(&wsv, ws_bytes, st));
   uint8_t* Wd = (uint8_t*)wsv;
-  uint64_t* d_hist = (uint64_t*)(Wd + w_hist);
   uint64_t* d_cls = (uint64_t*)(Wd + w_cls);
   uint64_t* d_lvl = (uint64_t*)(Wd + w_lvl);
   LevelMeta* d_gmeta = (LevelMeta*)(Wd + w_gmeta);
-  HistSeg* d_hseg = (HistSeg*)(Wd + w_hseg);
-  PlanSeg* d_pseg = (PlanSeg*)(Wd + w_pseg);
   SegDesc* d_sseg = (SegDesc*)(Wd + w_sseg);
   uint32_t* d_tick = (uint32_t*)(Wd + w_tick);
   uint8_t* d_seq[2] = {Wd + w_seq0, Wd + w_seq1};
@@ -291,14 +275,11 @@ wt_status batch_build_wm(const wt_batch_item* items, uint32_t m, const wt_build_
   auto at = [&](uint64_t off) { return img.data() + (off - w_lvl); };
   uint64_t* h_lvl = (uint64_t*)at(w_lvl);
   LevelMeta* h_gmeta = (LevelMeta*)at(w_gmeta);
-  HistSeg* h_hseg = (HistSeg*)at(w_hseg);
-  PlanSeg* h_pseg = (PlanSeg*)at(w_pseg);
   SegDesc* h_sseg = (SegDesc*)at(w_sseg);
   std::vector<uint64_t> sb_first(nlev_tot + 1, 0);
   std::vector<LevelMeta> h_meta_all(nmeta);
   {
-    uint64_t lev = 0, chunk = 0;
-    uint32_t hi = 0;
+    uint64_t lev = 0;
     for (uint32_t i = 0; i < m; i++) {
       const SeqPlan& p = sp[i];
       uint64_t* lo = h_lvl + p.lvl_base;
@@ -315,26 +296,6 @@ wt_status batch_build_wm(const wt_batch_item* items, uint32_t m, const wt_build_
         h_gmeta[lev] = mt;
         sb_first[lev + 1] = sb_first[lev] + p.nsb;
       }
-      if (p.n) {
-        HistSeg& d = h_hseg[hi++];
-        d.seq = items[i].d_seq;
-        d.n = p.n;
-        d.chunk0 = chunk;
-        d.hist_off = p.hist_off;
-        d.err = a_err + i;
-        d.sigma = p.sigma;
-        d.w = p.w;
-        d.L = p.L;
-        d.tau = p.tau;
-        chunk += (p.n + HIST_CH - 1) / HIST_CH;
-      }
-      PlanSeg& q = h_pseg[i];
-      q.hist = d_hist + p.hist_off;
-      q.cls = d_cls + p.cls_off;
-      q.zeros = a_zeros + p.zeros_base;
-      q.L = p.L;
-      q.tau = p.tau;
-      q.G = p.n ? p.G : 0;
     }
   }
   // per-launch segment lists: pass g, narrow (E = u16) then wide (E = u32)
@@ -364,9 +325,11 @@ wt_status batch_build_wm(const wt_batch_item* items, uint32_t m, const wt_build_
           d.lvl_off = d_lvl + p.lvl_base;
           d.lvl_len = d_lvl + p.lvl_base + p.L + 1;
           d.wm_cls = d_cls + coff;
+          d.zeros = a_zeros + p.zeros_base;
           d.err = a_err + i;
           d.n = p.n;
           d.tile0 = tiles;
+          d.sigma = g == 0 ? p.sigma : 0u;
           d.in_w = q.in_w;
           d.out_w = q.out_w;
           d.L = p.L;
@@ -386,12 +349,9 @@ wt_status batch_build_wm(const wt_batch_item* items, uint32_t m, const wt_build_
   if (nbits) CK(cudaMemsetAsync(a_bits, 0, 8 * nbits, st));
   CK(cudaMemsetAsync(a_err, 0, 4 * (uint64_t)m, st));
   if (nzeros) CK(cudaMemsetAsync(a_zeros, 0, 8 * nzeros, st));  // empty sequences plan nothing
-  if (nhist) CK(cudaMemsetAsync(d_hist, 0, 8 * nhist, st));
   CK(cudaMemsetAsync(d_tick, 0, 4 * 64, st));
   wt_status s = nmeta ? upload(a_meta, h_meta_all.data(), sizeof(LevelMeta) * nmeta, st) : WT_OK;
   if (s == WT_OK) s = upload(Wd + w_lvl, img.data(), img.size(), st);
-  if (s == WT_OK) s = launch_hist_batch(d_hseg, nh, nchunks, d_hist, st);
-  if (s == WT_OK) s = launch_plan_batch(d_pseg, m, st);
   for (size_t li = 0; li < launches.size() && s == WT_OK; li++) {
     const Launch& L0 = launches[li];
     PassParams P;

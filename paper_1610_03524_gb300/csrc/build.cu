@@ -473,6 +473,26 @@ __global__ void k_plan_wm_pass(const uint64_t* totals, int a, int t, uint64_t* c
   plan_wm_pass(totals, 1, a, t, cls, zeros);
 }
 
+// Batched builds, one block per sequence of the launch: the plan of its pass
+// from the totals of its own tiles' digit counts, i.e. the difference of the
+// scanned tables' prefixes at its last and first tile (tcnt exclusive
+// within chunks of TCHUNK tiles, tchunk the chunks' exclusive prefixes with
+// the total after the last chunk).
+__global__ void k_plan_batch_pass(const SegDesc* segs, const uint32_t* tcnt,
+                                  const uint64_t* tchunk, uint32_t tcs, uint32_t ntiles) {
+  __shared__ uint64_t tot[TC_STRIDE];
+  const SegDesc& d = segs[blockIdx.x];
+  const uint32_t t0 = d.tile0, t1 = t0 + (uint32_t)((d.n + PASS_T - 1) / PASS_T);
+  const uint64_t last = (uint64_t)((ntiles + TCHUNK - 1) / TCHUNK) * tcs;
+  auto prefix = [&](uint32_t ti, uint32_t r) -> uint64_t {
+    if (ti >= ntiles) return tchunk[last + r];
+    return tchunk[(uint64_t)(ti / TCHUNK) * tcs + r] + tcnt[(uint64_t)ti * tcs + r];
+  };
+  for (uint32_t r = threadIdx.x; r < (1u << d.t); r += blockDim.x) tot[r] = prefix(t1, r) - prefix(t0, r);
+  __syncthreads();
+  plan_wm_pass(tot, 1, d.a, d.t, d.wm_cls, d.zeros);
+}
+
 // Wavelet-matrix plan, one block: class starts and zero counts; reset of the
 // tile tickets.
 __global__ void k_plan_wm(const uint64_t* hist, int L, int tau, int G, uint64_t* cls,
@@ -598,7 +618,14 @@ __global__ void __launch_bounds__(256) k_tile_counts(const __grid_constant__ Pas
     }
     const uint32_t rmask = (1u << P.t) - 1u;
     const int rsh = 32 - P.rbits;
-    auto count = [&](uint32_t x) { atomicAdd(&h[(__brev(x) >> rsh) & rmask], 1u); };
+    // batched first passes also check the symbols (the single builds check
+    // them in their histogram kernel)
+    const uint32_t sigma = BATCH ? P.sigma : 0u;
+    bool bad = false;
+    auto count = [&](uint32_t x) {
+      if (BATCH) bad |= sigma != 0u && x >= sigma;
+      atomicAdd(&h[(__brev(x) >> rsh) & rmask], 1u);
+    };
     const uintptr_t a = (uintptr_t)P.in + ts * (uint64_t)P.in_w;
     if (P.code_map) {
       for (int i = tid; i < cnt; i += 256) count(P.code_map[load_elem(P.in, P.in_w, ts + i)]);
@@ -626,6 +653,7 @@ __global__ void __launch_bounds__(256) k_tile_counts(const __grid_constant__ Pas
     } else {
       for (int i = tid; i < cnt; i += 256) count(load_elem(P.in, P.in_w, ts + i));
     }
+    if (BATCH && bad) atomicOr(P.err, ERR_SYMBOL);
     __syncthreads();
     if (tid < (int)P0.tcs) tcnt[(uint64_t)ti * P0.tcs + tid] = h[tid];
     __syncthreads();
@@ -727,6 +755,10 @@ static wt_status launch_pass_t(const PassParams& P, uint64_t max_tiles, const wt
   if (plan) {
     k_plan_wm_pass<<<1, 256, 0, st>>>(tchunk + (uint64_t)nchunk * Q.tcs, P.a, P.t, plan->cls,
                                       plan->zeros);
+    count_launch();
+  }
+  if (BATCH) {
+    k_plan_batch_pass<<<P.nsegs, 256, 0, st>>>(P.segs, tcnt, tchunk, Q.tcs, (uint32_t)mt);
     count_launch();
   }
   Q.tcnt = tcnt;
@@ -1389,100 +1421,6 @@ wt_status build_huff(const void* d_seq, uint64_t n, uint32_t sigma, int w, const
   return build_directories(h);
 }
 
-
-}  // namespace wtk
-
-namespace wtk {
-
-// ---------------------------------------------------------------------------
-// batched wavelet matrices: histograms and plans of many sequences per launch
-// ---------------------------------------------------------------------------
-template <int WB>
-__device__ __forceinline__ void hist_chunk(const HistSeg& d, uint64_t i0, uint64_t i1,
-                                           uint32_t* sh, const int* off, const int* tt,
-                                           const int* shf, int G, bool& bad) {
-  using T = typename std::conditional<WB == 1, uint8_t,
-                                      typename std::conditional<WB == 2, uint16_t, uint32_t>::type>::type;
-  const T* s = (const T*)d.seq;
-  for (uint64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
-    const uint32_t x = (uint32_t)__ldcs(s + i);
-    bad |= x >= d.sigma;
-    for (int g = 0; g < G; g++) {
-      const uint32_t dg = (x >> shf[g]) & ((1u << tt[g]) - 1u);
-      atomicAdd(&sh[off[g] + dg], 1u);
-    }
-  }
-}
-
-// Digit histograms of every pass of every sequence (the per-sequence
-// counterpart of k_hist_digits), with the symbol check.  The launch walks
-// chunks of HIST_CH symbols; segs are sorted by chunk0.
-__global__ void k_hist_batch(const HistSeg* segs, uint32_t nsegs, uint64_t nchunks,
-                             uint64_t* hist) {
-  __shared__ uint32_t sh[1024];
-  __shared__ int off[33], tt[32], shf[32];
-  __shared__ HistSeg d;
-  __shared__ int sG;
-  for (uint64_t c = blockIdx.x; c < nchunks; c += gridDim.x) {
-    if (threadIdx.x == 0) {
-      uint32_t lo = 0, hi = nsegs - 1;
-      while (lo < hi) {
-        const uint32_t mid = (lo + hi + 1) >> 1;
-        if (segs[mid].chunk0 <= c) lo = mid;
-        else hi = mid - 1;
-      }
-      d = segs[lo];
-      int o = 0, G = 0;
-      for (int a = 0; a < d.L && G < 32; a += d.tau, G++) {
-        tt[G] = min(d.tau, d.L - a);
-        shf[G] = d.L - a - tt[G];
-        off[G] = o;
-        o += 1 << tt[G];
-      }
-      off[G] = o;
-      sG = G;
-    }
-    __syncthreads();
-    const int G = sG, nb = off[G];
-    for (int i = threadIdx.x; i < nb; i += blockDim.x) sh[i] = 0;
-    __syncthreads();
-    const uint64_t i0 = (c - d.chunk0) * HIST_CH;
-    const uint64_t i1 = min(i0 + HIST_CH, d.n);
-    bool bad = false;
-    if (d.w == 1) hist_chunk<1>(d, i0, i1, sh, off, tt, shf, G, bad);
-    else if (d.w == 2) hist_chunk<2>(d, i0, i1, sh, off, tt, shf, G, bad);
-    else hist_chunk<4>(d, i0, i1, sh, off, tt, shf, G, bad);
-    if (bad) atomicOr(d.err, ERR_SYMBOL);
-    __syncthreads();
-    for (int i = threadIdx.x; i < nb; i += blockDim.x)
-      if (sh[i]) atomicAdd((unsigned long long*)&hist[d.hist_off + i], (unsigned long long)sh[i]);
-    __syncthreads();
-  }
-}
-
-// One block per sequence: class starts and zero counts (plan_wm_classes).
-__global__ void k_plan_batch(const PlanSeg* ps) {
-  const PlanSeg p = ps[blockIdx.x];
-  plan_wm_classes(p.hist, p.L, p.tau, p.G, p.cls, p.zeros);
-}
-
-wt_status launch_hist_batch(const HistSeg* d_segs, uint32_t nsegs, uint64_t nchunks,
-                            uint64_t* hist, cudaStream_t st) {
-  if (!nchunks) return WT_OK;
-  const uint32_t blocks = (uint32_t)std::min<uint64_t>((uint64_t)num_sms() * 4, nchunks);
-  k_hist_batch<<<blocks, 512, 0, st>>>(d_segs, nsegs, nchunks, hist);
-  count_launch();
-  CK(cudaGetLastError());
-  return WT_OK;
-}
-
-wt_status launch_plan_batch(const PlanSeg* d_ps, uint32_t m, cudaStream_t st) {
-  if (!m) return WT_OK;
-  k_plan_batch<<<m, 256, 0, st>>>(d_ps);
-  count_launch();
-  CK(cudaGetLastError());
-  return WT_OK;
-}
 
 }  // namespace wtk
 

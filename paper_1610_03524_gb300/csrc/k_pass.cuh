@@ -75,6 +75,7 @@ __device__ __forceinline__ void fill_seg(PassParams& D, const PassParams& P0, ui
   D.err = d.err;
   D.n_in = d.n;
   D.tile0 = d.tile0;
+  D.sigma = d.sigma;
 }
 
 // Global class range [cs, ce) of level a+j, class k (k = the tile-local key

@@ -47,38 +47,23 @@ constexpr int PASS_T = WT_PASS_T;
 // Batched builds: the per-sequence part of a pass, one entry per sequence
 // taking part in the launch.  Its tiles are tile0 .. tile0 + ceil(n/T) - 1 of
 // the launch's tile numbering.
+// The pass's class starts (wm_cls) and the sequence's zero counts (zeros) are
+// planned on the device from the totals of the pass's own tile counts;
+// sigma (first pass only, else 0) is the bound the tile counts check the
+// symbols against.
 struct SegDesc {
   const void* in;
   void* out;
   uint64_t* bits;
   const uint64_t* lvl_off;
   const uint64_t* lvl_len;
-  const uint64_t* wm_cls;
+  uint64_t* wm_cls;
+  uint64_t* zeros;
   uint32_t* err;
   uint64_t n;
   uint32_t tile0;
-  int in_w, out_w, L, a, t, rbits;
-};
-
-// Batched histogram: one entry per sequence, sorted by chunk0 (its first
-// chunk of HIST_CH symbols in the launch's chunk numbering).
-constexpr uint64_t HIST_CH = 16384;
-struct HistSeg {
-  const void* seq;
-  uint64_t n;
-  uint64_t chunk0;
-  uint64_t hist_off;   // first histogram entry of the sequence
-  uint32_t* err;
   uint32_t sigma;
-  int w, L, tau;
-};
-
-// Batched plan: one entry per sequence.
-struct PlanSeg {
-  const uint64_t* hist;
-  uint64_t* cls;
-  uint64_t* zeros;
-  int L, tau, G;
+  int in_w, out_w, L, a, t, rbits;
 };
 
 struct PassParams {
@@ -110,6 +95,7 @@ struct PassParams {
   uint32_t ntiles;
   uint64_t n_in;
   uint32_t tile0;           // first tile of the sequence (0 unless batched)
+  uint32_t sigma;           // batched first passes: the tile counts check S[i] < sigma
   // batched builds: per-sequence parts, sorted by tile0
   const SegDesc* segs;
   uint32_t nsegs;
