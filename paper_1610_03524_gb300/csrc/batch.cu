@@ -208,7 +208,19 @@ wt_status batch_build_wm(const wt_batch_item* items, uint32_t m, const wt_build_
   uint64_t* a_zeros = (uint64_t*)(A + off_zeros);
   LevelMeta* a_meta = (LevelMeta*)(A + off_meta);
   uint32_t* a_err = (uint32_t*)(A + off_err);
-  // handles own the arena from here on (a failure below frees it through them)
+  // level l of a sequence inside its own arrays
+  auto meta_of = [](const SeqPlan& p, int l) {
+    LevelMeta mt{};
+    mt.bit_off = (uint64_t)l * p.W;
+    mt.dir_off = (uint64_t)l * 2 * (p.nsb + 1);
+    mt.s0_off = (uint64_t)(2 * l) * p.cap;
+    mt.s1_off = (uint64_t)(2 * l + 1) * p.cap;
+    mt.n = p.n;
+    mt.nsb = p.nsb;
+    return mt;
+  };
+  // handles own the arena from here on (a failure below frees it through
+  // them); their host-side tables are filled once the work is enqueued
   for (uint32_t i = 0; i < m; i++) {
     wt_struct* h = hs[i];
     const SeqPlan& p = sp[i];
@@ -227,24 +239,6 @@ wt_status batch_build_wm(const wt_batch_item* items, uint32_t m, const wt_build_
     h->d_zeros = a_zeros + p.zeros_base;
     h->d_meta = a_meta + p.meta_base;
     h->d_err = a_err + i;
-    h->level_len.assign(p.L, p.n);
-    h->level_off.assign(p.L + 1, 0);
-    h->dir_off.assign(p.L + 1, 0);
-    h->samp_off.assign(2 * p.L + 1, 0);
-    h->meta.assign(p.L, LevelMeta{});
-    for (int l = 0; l < p.L; l++) {
-      h->level_off[l + 1] = (uint64_t)(l + 1) * p.W;
-      h->dir_off[l + 1] = (uint64_t)(l + 1) * 2 * (p.nsb + 1);
-      h->samp_off[2 * l + 1] = (uint64_t)(2 * l + 1) * p.cap;
-      h->samp_off[2 * l + 2] = (uint64_t)(2 * l + 2) * p.cap;
-      LevelMeta& mt = h->meta[l];
-      mt.bit_off = (uint64_t)l * p.W;
-      mt.dir_off = h->dir_off[l];
-      mt.s0_off = h->samp_off[2 * l];
-      mt.s1_off = h->samp_off[2 * l + 1];
-      mt.n = p.n;
-      mt.nsb = p.nsb;
-    }
   }
   // ---- workspace ----------------------------------------------------------
   uint64_t nsegs_tot = 0;
@@ -287,7 +281,7 @@ wt_status batch_build_wm(const wt_batch_item* items, uint32_t m, const wt_build_
       for (int l = 0; l <= p.L; l++) lo[l] = (uint64_t)l * p.W;
       for (int l = 0; l < p.L; l++) ll[l] = p.n;
       for (int l = 0; l < p.L; l++, lev++) {
-        LevelMeta mt = hs[i]->meta[l];
+        LevelMeta mt = meta_of(p, l);
         h_meta_all[p.meta_base + l] = mt;
         mt.bit_off += p.bits_base;
         mt.dir_off += p.dir_base;
@@ -371,6 +365,26 @@ wt_status batch_build_wm(const wt_batch_item* items, uint32_t m, const wt_build_
   dfree(wsv, st);
   if (s != WT_OK) return s;
   CK(cudaGetLastError());
+  // the handles' host-side tables, while the device works
+  for (uint32_t i = 0; i < m; i++) {
+    wt_struct* h = hs[i];
+    const SeqPlan& p = sp[i];
+    h->level_len.assign(p.L, p.n);
+    h->level_off.resize(p.L + 1);
+    h->dir_off.resize(p.L + 1);
+    h->samp_off.resize(2 * p.L + 1);
+    h->meta.resize(p.L);
+    for (int l = 0; l <= p.L; l++) {
+      const LevelMeta mt = meta_of(p, l);
+      h->level_off[l] = mt.bit_off;
+      h->dir_off[l] = mt.dir_off;
+      h->samp_off[2 * l] = mt.s0_off;
+      if (l < p.L) {
+        h->samp_off[2 * l + 1] = mt.s1_off;
+        h->meta[l] = mt;
+      }
+    }
+  }
   return WT_OK;
 }
 
