@@ -349,7 +349,7 @@ wt_status upload_meta(wt_struct* h) {
 
 // Binary directories and select samples of nlev levels described by d_meta
 // (offsets relative to bits / dir / samp); sb_first: first superblock of each
-// level in one numbering, nlev + 1 entries.  write_zeros: also store each
+// level in one numbering, its first nlev + 1 entries used.  write_zeros: also store each
 // level's zero count in zeros[l].
 wt_status dir_build_levels(const uint64_t* bits, const LevelMeta* d_meta, uint32_t nlev,
                            const std::vector<uint64_t>& sb_first, uint64_t* dir, uint64_t* samp,
@@ -359,7 +359,7 @@ wt_status dir_build_levels(const uint64_t* bits, const LevelMeta* d_meta, uint32
   const uint64_t total_sb = sb_first[nlev];
   // blocks of the counting kernel: DIR_SB_PER_BLOCK superblocks of one level each
   std::vector<uint64_t> firsts(2 * ((size_t)nlev + 1), 0);
-  std::copy(sb_first.begin(), sb_first.end(), firsts.begin());
+  std::copy(sb_first.begin(), sb_first.begin() + nlev + 1, firsts.begin());
   uint64_t* blk_first = firsts.data() + nlev + 1;
   for (uint32_t l = 0; l < nlev; l++) {
     const uint64_t nsb = sb_first[l + 1] - sb_first[l];
