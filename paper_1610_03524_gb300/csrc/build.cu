@@ -197,6 +197,62 @@ __global__ void __launch_bounds__(256) k_hist_digits_tiles(const void* seq, uint
 }
 
 
+// Histogram of a byte sequence over sigma = NV + 1 <= 8 values, four bytes
+// at a time in a 32-bit word: a byte equals v exactly when w ^ (v x
+// 0x01010101) has a zero byte there, which ((t & 0x7F7F7F7F) + 0x7F7F7F7F)
+// finds without carries between bytes; the count of the last value is the
+// bytes seen minus the others.  No atomics per symbol.
+template <int NV>
+__device__ __forceinline__ void hist_bytes_swar(const void* seq, uint64_t n, uint64_t* hist,
+                                                uint32_t* err) {
+  constexpr uint32_t sigma = NV + 1;
+  uint32_t cnt[NV > 0 ? NV : 1] = {};
+  uint64_t seen = 0;
+  bool bad = false;
+  constexpr uint32_t ge = (0x80u - sigma) * 0x01010101u;  // + low 7 bits: bit 7 iff byte >= sigma
+  auto word = [&](uint32_t w) {
+    bad |= ((((w & 0x7F7F7F7Fu) + ge) | w) & 0x80808080u) != 0u;
+#pragma unroll
+    for (int v = 0; v < NV; v++) {
+      const uint32_t t = w ^ ((uint32_t)v * 0x01010101u);
+      const uint32_t y = (t & 0x7F7F7F7Fu) + 0x7F7F7F7Fu;
+      cnt[v] += __popc(~(y | t) & 0x80808080u);
+    }
+  };
+  const uint8_t* sb = (const uint8_t*)seq;
+  const uint64_t gt = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const uint64_t gs = (uint64_t)gridDim.x * blockDim.x;
+  const uint64_t nvec = ((((uintptr_t)seq) & 15) == 0) ? n / 16 : 0;
+  const uint4* vp = (const uint4*)seq;
+  for (uint64_t i = gt; i < nvec; i += gs) {
+    const uint4 q = __ldcs(vp + i);
+    word(q.x);
+    word(q.y);
+    word(q.z);
+    word(q.w);
+    seen += 16;
+  }
+  for (uint64_t i = nvec * 16 + gt; i < n; i += gs) {
+    const uint32_t x = sb[i];
+    bad |= x >= sigma;
+#pragma unroll
+    for (int v = 0; v < NV; v++) cnt[v] += x == (uint32_t)v ? 1u : 0u;
+    seen++;
+  }
+  if (bad) atomicOr(err, ERR_SYMBOL);
+  const int lane = threadIdx.x & 31;
+  uint64_t rest = seen;
+#pragma unroll
+  for (int v = 0; v < NV; v++) rest -= cnt[v];
+#pragma unroll
+  for (int v = 0; v <= NV; v++) {
+    uint64_t c = v < NV ? (uint64_t)cnt[v] : rest;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(FULL, c, o);
+    if (lane == 0 && c) atomicAdd((unsigned long long*)&hist[v], (unsigned long long)c);
+  }
+}
+
 // Full symbol histogram (balanced / Huffman / 4-ary trees).
 // (large alphabets: block b adds into copy b % ncopy of the histogram, at
 // hist + (b % ncopy) * sigma, so that the frequent symbols of a skewed
@@ -212,23 +268,18 @@ __global__ void k_hist_full(const void* seq, uint64_t n, uint32_t sigma, uint64_
   }
   bool bad = false;
   const int lane = threadIdx.x & 31;
-  if (sigma <= 8) {
-    // tiny alphabets (DNA-like text): counters in registers, no atomics per symbol
-    uint32_t cnt[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-    for_each_symbol<WB>(seq, n, (uint64_t)blockIdx.x * blockDim.x + threadIdx.x,
-                        (uint64_t)gridDim.x * blockDim.x, [&](uint32_t x) {
-                          bad |= x >= sigma;
-#pragma unroll
-                          for (int k = 0; k < 8; k++) cnt[k] += (x == (uint32_t)k) ? 1u : 0u;
-                        });
-    if (bad) atomicOr(err, ERR_SYMBOL);
-#pragma unroll
-    for (int k = 0; k < 8; k++) {
-      const uint32_t c = __reduce_add_sync(FULL, cnt[k]);
-      if (lane == 0 && c && (uint32_t)k < sigma)
-        atomicAdd((unsigned long long*)&hist[k], (unsigned long long)c);
+  if (WB == 1 && sigma <= 8) {
+    // byte sequences over tiny alphabets (DNA-like text)
+    switch (sigma) {
+      case 1: hist_bytes_swar<0>(seq, n, hist, err); return;
+      case 2: hist_bytes_swar<1>(seq, n, hist, err); return;
+      case 3: hist_bytes_swar<2>(seq, n, hist, err); return;
+      case 4: hist_bytes_swar<3>(seq, n, hist, err); return;
+      case 5: hist_bytes_swar<4>(seq, n, hist, err); return;
+      case 6: hist_bytes_swar<5>(seq, n, hist, err); return;
+      case 7: hist_bytes_swar<6>(seq, n, hist, err); return;
+      default: hist_bytes_swar<7>(seq, n, hist, err); return;
     }
-    return;
   }
   for_each_symbol<WB>(seq, n, (uint64_t)blockIdx.x * blockDim.x + threadIdx.x,
                       (uint64_t)gridDim.x * blockDim.x, [&](uint32_t x) {
@@ -274,7 +325,7 @@ static wt_status launch_hist_full(const void* seq, int w, uint64_t n, uint32_t s
   uint32_t ncopy = 1;
   uint64_t* dst = hist;
   Work wk{st, {}};
-  if (!use_smem && sigma > 8) {
+  if (!use_smem) {
     ncopy = (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>(16, (256ull << 20) / (8ull * sigma)));
     if (ncopy > 1) {
       TRY(wk.get(&dst, (size_t)ncopy * sigma));

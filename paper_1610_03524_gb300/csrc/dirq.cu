@@ -239,6 +239,69 @@ __device__ __forceinline__ uint64_t digit_match(uint64_t w, uint32_t d) {
   return ~(x | (x >> 1)) & 0x5555555555555555ull;
 }
 
+// The same counts, laid out like k_dir_count for up to DIR_SMALL levels:
+// DIR_SB_PER_BLOCK superblocks of one level per block, two superblocks per
+// warp step (each half-warp one: 16 lanes x two words = 1024 digits), 16-byte
+// loads.  A lane holds 64 digits, so the 256-digit blocks end at lanes 3, 7,
+// 11 of its half.
+__global__ void __launch_bounds__(256) k_mdir_count_blk(const uint64_t* bits, uint64_t total_sb,
+                                                        uint64_t* dir, uint64_t* sbz,
+                                                        const __grid_constant__ DirLevels dl) {
+  int l = 0;
+  while (l + 1 < dl.nlev && dl.blk_first[l + 1] <= blockIdx.x) l++;
+  const LevelMeta m = dl.meta[l];
+  const uint64_t sb0 = (blockIdx.x - dl.blk_first[l]) * DIR_SB_PER_BLOCK;
+  const uint64_t g0 = dl.sb_first[l];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int hl = lane & 15, half = lane >> 4;
+  const uint64_t s0 = sb0 + (uint64_t)warp * DIR_SB_PER_WARP;
+  const uint64_t* lb = bits + m.bit_off;
+  const bool vec = (((uintptr_t)lb) & 15) == 0;
+  constexpr int NP = DIR_SB_PER_WARP / 2;
+  uint64_t w0[NP], w1[NP];
+  int v0[NP], v1[NP];  // valid digits of the two words
+#pragma unroll
+  for (int u = 0; u < NP; u++) {
+    const uint64_t s = s0 + 2 * u + half;
+    const int64_t rem = (int64_t)m.n - (int64_t)(1024 * s + 64 * (uint64_t)hl);
+    const bool live = s < m.nsb && rem > 0;
+    v0[u] = !live ? 0 : (rem >= 32 ? 32 : (int)rem);
+    v1[u] = (!live || rem <= 32) ? 0 : (rem >= 64 ? 32 : (int)(rem - 32));
+    const uint64_t* p = lb + 32 * s + 2 * hl;
+    if (v1[u] && vec) {
+      const ulonglong2 q = __ldcs((const ulonglong2*)p);
+      w0[u] = q.x;
+      w1[u] = q.y;
+    } else {
+      w0[u] = v0[u] ? __ldcs(p) : 0ull;
+      w1[u] = v1[u] ? __ldcs(p + 1) : 0ull;
+    }
+  }
+#pragma unroll
+  for (int u = 0; u < NP; u++) {
+    const uint64_t s = s0 + 2 * u + half;
+    const uint64_t vm0 = v0[u] >= 32 ? ~0ull : ((1ull << (2 * v0[u])) - 1ull);
+    const uint64_t vm1 = v1[u] >= 32 ? ~0ull : ((1ull << (2 * v1[u])) - 1ull);
+    uint64_t rec = 0;  // lane hl < 4: the four values' counts before block hl
+#pragma unroll
+    for (int d = 0; d < 4; d++) {
+      int ci = __popcll(digit_match(w0[u], d) & vm0) + __popcll(digit_match(w1[u], d) & vm1);
+#pragma unroll
+      for (int o = 1; o < 16; o <<= 1) {
+        const int y = __shfl_up_sync(FULL, ci, o, 16);
+        if (hl >= o) ci += y;
+      }
+      const uint32_t r1 = (uint32_t)__shfl_sync(FULL, ci, 3, 16);
+      const uint32_t r2 = (uint32_t)__shfl_sync(FULL, ci, 7, 16);
+      const uint32_t r3 = (uint32_t)__shfl_sync(FULL, ci, 11, 16);
+      const uint32_t rb = hl == 1 ? r1 : (hl == 2 ? r2 : (hl == 3 ? r3 : 0u));
+      rec |= (uint64_t)rb << (16 * d);
+      if (hl == 15 && s < m.nsb) sbz[(uint64_t)d * total_sb + g0 + s] = (uint64_t)ci;
+    }
+    if (hl < 4 && s < m.nsb) dir[m.dir_off + 8 * s + 4 + hl] = rec;
+  }
+}
+
 __global__ void k_mdir_count(const uint64_t* bits, const LevelMeta* meta, int nlev,
                              const uint64_t* sb_first, uint64_t total_sb, uint64_t* dir,
                              uint64_t* sbz /* 4 x total_sb */) {
@@ -749,10 +812,25 @@ wt_status build_directories(wt_struct* h) {
   TRY(wk.get(&sbx, (total_sb + 1) * 4));
   TRY(wk.get(&scr, scan_scratch_pub(total_sb)));
   TRY(upload(d_first, sb_first.data(), (nlev + 1) * 8, st));
-  // one warp per superblock: enough loads in flight to stream the bitmaps
-  const unsigned cgrid = (unsigned)std::min<uint64_t>((total_sb * 32 + 255) / 256 + 1, 1u << 24);
   const unsigned fgrid = (unsigned)((total_sb + nlev + 255) / 256);
-  if (total_sb) {
+  if (total_sb && nlev <= (uint32_t)DIR_SMALL) {
+    // blocks of DIR_SB_PER_BLOCK superblocks of one level, the level tables
+    // in the parameters
+    DirLevels dl;
+    memset(&dl, 0, sizeof(dl));
+    dl.nlev = (int)nlev;
+    for (uint32_t l = 0; l < nlev; l++) {
+      dl.blk_first[l + 1] =
+          dl.blk_first[l] + (h->meta[l].nsb + DIR_SB_PER_BLOCK - 1) / DIR_SB_PER_BLOCK;
+      dl.sb_first[l + 1] = sb_first[l + 1];
+      dl.meta[l] = h->meta[l];
+    }
+    k_mdir_count_blk<<<(unsigned)dl.blk_first[nlev], 256, 0, st>>>(h->d_bits_ro, total_sb,
+                                                                  h->d_dir, sbz, dl);
+    count_launch();
+  } else if (total_sb) {
+    // one warp per superblock: enough loads in flight to stream the bitmaps
+    const unsigned cgrid = (unsigned)std::min<uint64_t>((total_sb * 32 + 255) / 256 + 1, 1u << 24);
     k_mdir_count<<<cgrid, 256, 0, st>>>(h->d_bits_ro, h->d_meta, nlev, d_first, total_sb,
                                         h->d_dir, sbz);
     count_launch();

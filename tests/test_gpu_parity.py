@@ -353,6 +353,27 @@ def test_huffman_tau_levels(wt, tau, seed, n, sigma):
     h.free()
 
 
+@pytest.mark.parametrize("sigma,off", [(5, 3), (2, 0), (8, 7), (3, 1)])
+def test_tiny_alphabet_histogram(wt, sigma, off):
+    """Byte sequences over at most 8 values (counted four bytes to a word
+    where the start is 16-byte aligned, one by one elsewhere): the balanced
+    tree, which plans from the full histogram, equals the oracle's, aligned
+    and not; a byte >= sigma in the tail is reported."""
+    S = synth.uniform(310 + sigma, 70001 + off, sigma, 1)
+    Sv = S[off:]
+    h = wt.wt_build(to_dev(S)[off:], sigma)
+    ob = oracle.wt_build(Sv, sigma)
+    assert np.array_equal(h.export().bits.reshape(ob.shape), ob)
+    h.free()
+    bad = S.copy()
+    bad[-2] = sigma
+    h = wt.wt_build(to_dev(bad), sigma)
+    with pytest.raises(wt.WaveletError) as ei:
+        h.sync()
+    assert ei.value.status == 2
+    h.free()
+
+
 @pytest.mark.parametrize("width,off", [(1, 5), (2, 3), (4, 1)])
 def test_unaligned_input_pointer(wt, width, off):
     """A sequence that starts at an address not 16-byte aligned (a slice of a
