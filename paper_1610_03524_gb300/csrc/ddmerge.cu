@@ -126,6 +126,26 @@ __global__ void k_dd_dest(const uint64_t* cnt, const uint64_t* X, uint32_t R, ui
   }
 }
 
+// The copy stores the words a run covers whole and ORs the others, so the
+// words a run shares (its first and last when not word-aligned) and every
+// level's words from its last partial one on start at zero: one thread per
+// run, and per level the words [n / 64, W).
+__global__ void k_dd_zero_edges(const uint64_t* cnt, const uint64_t* dst, uint64_t nseg,
+                                uint64_t stride, uint64_t* out, uint64_t W, int L, uint64_t n) {
+  const uint64_t g = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g < nseg) {
+    const uint64_t k = cnt[g];
+    if (k) {
+      uint64_t* const ol = out + (uint64_t)dd_level_of(g % stride) * W;
+      const uint64_t d = dst[g];
+      if (d & 63) ol[d >> 6] = 0;
+      if ((d + k) & 63) ol[(d + k - 1) >> 6] = 0;
+    }
+  }
+  const uint64_t pw = W - (n >> 6);
+  if (g < (uint64_t)L * pw) out[(g / pw) * W + (n >> 6) + g % pw] = 0;
+}
+
 // run of every piece: one warp per run writes its index over its pieces
 __global__ void k_dd_map(const uint64_t* PS, uint64_t nseg, uint32_t* map) {
   const int lane = threadIdx.x & 31;
@@ -193,7 +213,6 @@ wt_status dd_merge(wt_struct* const* parts, uint32_t R, wt_struct* h) {
   for (int l = 0; l < L; l++) h->level_off[l + 1] = h->level_off[l] + W;
   CK(dmalloc((void**)&h->d_bits, std::max<uint64_t>(W * L, 1) * 8, st));
   h->d_bits_ro = h->d_bits;
-  CK(cudaMemsetAsync(h->d_bits, 0, std::max<uint64_t>(W * L, 1) * 8, st));
   CK(dmalloc((void**)&h->d_zeros, std::max(L, 1) * 8, st));
   // zero counts: the parts' sums
   h->zeros.assign(L, 0);
@@ -240,6 +259,12 @@ wt_status dd_merge(wt_struct* const* parts, uint32_t R, wt_struct* h) {
   if (s == WT_OK) {
     k_dd_dest<<<(unsigned)((stride + 255) / 256), 256, 0, st>>>(cnt, X, R, stride, dst, npc);
     count_launch();
+    const uint64_t nz = std::max<uint64_t>(nseg, (uint64_t)L * (W - (n >> 6)));
+    if (nz) {
+      k_dd_zero_edges<<<(unsigned)((nz + 255) / 256), 256, 0, st>>>(cnt, dst, nseg, stride,
+                                                                    h->d_bits, W, L, n);
+      count_launch();
+    }
     s = scan_excl_u64_pub(npc, PS, nseg, scr, st);
   }
   uint64_t npieces = 0;
