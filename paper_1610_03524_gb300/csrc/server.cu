@@ -44,6 +44,7 @@ struct Request {
   // queries
   uint64_t q = 0;
   std::vector<uint64_t> sid, x, out;
+  std::vector<uint64_t> uniq;  // the distinct structures the queries name
   std::vector<uint8_t> op;
   std::vector<uint32_t> c;
 };
@@ -228,6 +229,7 @@ void wt_server_s::query_loop() {
   Pinned pin_in, pin_out;
   void* d_buf = nullptr;
   size_t d_cap = 0;
+  std::vector<uint32_t> dense;
   for (;;) {
     std::vector<std::shared_ptr<Request>> take;
     std::vector<wt_handle> tab;
@@ -248,9 +250,12 @@ void wt_server_s::query_loop() {
         for (auto it = pend_query.begin(); it != pend_query.end();) {
           auto& r = *it;
           bool ready = true;
-          for (uint64_t i = 0; i < r->q && ready; i++) {
-            auto f = structs.find(r->sid[i]);
-            if (f != structs.end() && !f->second.ready && !f->second.failed) ready = false;
+          for (uint64_t id : r->uniq) {
+            auto f = structs.find(id);
+            if (f != structs.end() && !f->second.ready && !f->second.failed) {
+              ready = false;
+              break;
+            }
           }
           if (!ready || (qtot && qtot + r->q > opts.max_batch_queries)) {
             ++it;
@@ -264,10 +269,10 @@ void wt_server_s::query_loop() {
         cv_query.wait(lk);
       }
       for (auto& r : take)
-        for (uint64_t i = 0; i < r->q; i++) {
-          auto f = structs.find(r->sid[i]);
+        for (uint64_t id : r->uniq) {
+          auto f = structs.find(id);
           if (f == structs.end() || !f->second.ready) continue;
-          if (slot.emplace(r->sid[i], (uint32_t)tab.size()).second) tab.push_back(f->second.h);
+          if (slot.emplace(id, (uint32_t)tab.size()).second) tab.push_back(f->second.h);
         }
       // the handles stay valid: wt_server_release waits for this launch
       for (auto& kv : slot) structs[kv.first].inflight++;
@@ -292,15 +297,20 @@ void wt_server_s::query_loop() {
       uint8_t* hop = P + b_op;
       uint32_t* hc = (uint32_t*)(P + b_c);
       uint64_t* hx = (uint64_t*)(P + b_x);
+      // structure id -> table index in a flat array over the ids in use
+      // (ids are small consecutive request numbers)
+      const uint64_t top = slot.empty() ? 0 : slot.rbegin()->first + 1;
+      dense.assign(top, 0xffffffffu);
+      for (auto& kv : slot) dense[kv.first] = kv.second;
       uint64_t k = 0;
-      for (auto& r : take)
-        for (uint64_t i = 0; i < r->q; i++, k++) {
-          auto f = slot.find(r->sid[i]);
-          hsid[k] = f == slot.end() ? 0xffffffffu : f->second;  // unknown -> UINT64_MAX
-          hop[k] = r->op[i];
-          hc[k] = r->c[i];
-          hx[k] = r->x[i];
-        }
+      for (auto& r : take) {
+        const uint64_t* rs = r->sid.data();
+        for (uint64_t i = 0; i < r->q; i++, k++)
+          hsid[k] = rs[i] < top ? dense[rs[i]] : 0xffffffffu;  // unknown -> UINT64_MAX
+        memcpy(hop + (k - r->q), r->op.data(), r->q);
+        memcpy(hc + (k - r->q), r->c.data(), 4 * r->q);
+        memcpy(hx + (k - r->q), r->x.data(), 8 * r->q);
+      }
       uint8_t* D = (uint8_t*)d_buf;
       if (cudaMemcpyAsync(D, P, b_end, cudaMemcpyHostToDevice, s_query) != cudaSuccess)
         s = WT_ERR_CUDA;
@@ -341,8 +351,13 @@ wt_status wt_server_create(const wt_server_opts* opts, wt_server* out) {
   if (!s->opts.max_batch_builds) s->opts.max_batch_builds = 4096;
   if (!s->opts.max_batch_queries) s->opts.max_batch_queries = 1u << 22;
   cudaGetDevice(&s->device);
+  // queries on the highest-priority stream: when both streams have work
+  // waiting, the query kernels' blocks are scheduled first
+  int prio_least = 0, prio_greatest = 0;
+  cudaDeviceGetStreamPriorityRange(&prio_least, &prio_greatest);
   if (cudaStreamCreateWithFlags(&s->s_build, cudaStreamNonBlocking) != cudaSuccess ||
-      cudaStreamCreateWithFlags(&s->s_query, cudaStreamNonBlocking) != cudaSuccess) {
+      cudaStreamCreateWithPriority(&s->s_query, cudaStreamNonBlocking, prio_greatest) !=
+          cudaSuccess) {
     if (s->s_build) cudaStreamDestroy(s->s_build);
     delete s;
     return WT_ERR_CUDA;
@@ -390,6 +405,24 @@ wt_status wt_server_submit_queries(wt_server s, uint64_t q, const uint64_t* h_si
   r->c.assign(h_c, h_c + q);
   r->x.assign(h_x, h_x + q);
   r->submit_ns = now_ns();
+  // the distinct structures named (a flat marker over the ids when they are
+  // small, as request ids are; else a sort)
+  {
+    uint64_t mx = 0;
+    for (uint64_t i = 0; i < q; i++) mx = std::max(mx, h_sid[i]);
+    if (mx < (1ull << 24)) {
+      std::vector<uint8_t> seen(mx + 1, 0);
+      for (uint64_t i = 0; i < q; i++)
+        if (!seen[h_sid[i]]) {
+          seen[h_sid[i]] = 1;
+          r->uniq.push_back(h_sid[i]);
+        }
+    } else {
+      r->uniq = r->sid;
+      std::sort(r->uniq.begin(), r->uniq.end());
+      r->uniq.erase(std::unique(r->uniq.begin(), r->uniq.end()), r->uniq.end());
+    }
+  }
   {
     std::lock_guard<std::mutex> lk(s->mu);
     r->id = s->next_id++;
