@@ -1263,17 +1263,57 @@ wt_status build_huff(const void* d_seq, uint64_t n, uint32_t sigma, int w, const
   h->max_code_len = maxlen;
   const int Lm = (int)maxlen;
   h->L = h->levels = (uint32_t)Lm;
+  // The sweeps below run on up to 16 host threads, each over a contiguous
+  // chunk of symbols (or of `order`), with per-thread partial results
+  // combined in a fixed order, so the result does not depend on the thread
+  // count.
+  const uint32_t hw = std::max(1u, std::thread::hardware_concurrency());
+  auto par = [&](uint64_t items, auto&& f) {
+    const int nt = (int)std::max<uint64_t>(1, std::min<uint64_t>({16, hw, items / 65536 + 1}));
+    std::vector<std::thread> th;
+    for (int t = 1; t < nt; t++) th.emplace_back(f, t, nt);
+    f(0, nt);
+    for (auto& x : th) x.join();
+    return nt;
+  };
+  auto chunk = [](uint64_t items, int t, int nt, uint64_t& b, uint64_t& e) {
+    b = items * (uint64_t)t / (uint64_t)nt;
+    e = items * (uint64_t)(t + 1) / (uint64_t)nt;
+  };
+  constexpr int MAXT = 16;
   // symbols in canonical order (= order of the left-aligned codewords):
-  // by (length, symbol), a counting sort on the length
+  // by (length, symbol), a counting sort on the length, stable across the
+  // threads' symbol ranges
   std::vector<uint32_t> order;
   uint64_t lcount[34] = {0};
+  uint64_t lpos[34] = {0};  // first index in `order` of each length
   {
-    for (uint32_t s = 0; s < sigma; s++) lcount[h->code_len[s]]++;
-    uint64_t lpos[34] = {0};
+    uint64_t tc[MAXT][34] = {};
+    const int nt = par(sigma, [&](int t, int n_t) {
+      uint64_t b, e;
+      chunk(sigma, t, n_t, b, e);
+      for (uint64_t s = b; s < e; s++) tc[t][h->code_len[s]]++;
+    });
+    for (int t = 0; t < nt; t++)
+      for (int ln = 0; ln <= 33; ln++) lcount[ln] += tc[t][ln];
     for (int ln = 2; ln <= 33; ln++) lpos[ln] = lpos[ln - 1] + (ln - 1 >= 1 ? lcount[ln - 1] : 0);
+    // each thread's first slot per length: after the earlier threads'
+    uint64_t at[MAXT][34];
+    for (int ln = 1; ln <= 33; ln++) {
+      uint64_t p0 = lpos[ln];
+      for (int t = 0; t < nt; t++) {
+        at[t][ln] = p0;
+        p0 += tc[t][ln];
+      }
+    }
     order.resize(lpos[33]);
-    for (uint32_t s = 0; s < sigma; s++)
-      if (h->code_len[s]) order[lpos[h->code_len[s]]++] = s;
+    par(sigma, [&](int t, int n_t) {
+      uint64_t b, e;
+      chunk(sigma, t, n_t, b, e);
+      uint64_t* w = at[t];
+      for (uint64_t s = b; s < e; s++)
+        if (h->code_len[s]) order[w[h->code_len[s]]++] = (uint32_t)s;
+    });
   }
   // level sizes, internal nodes of every level and their start positions,
   // and zero counts.  `order` is sorted by length, so the elements still on
@@ -1283,29 +1323,66 @@ wt_status build_huff(const void* d_seq, uint64_t n, uint32_t sigma, int w, const
   // symbol to the next (the next codeword adds 2^(Lm - len) to the left-
   // aligned value, len > l).  So symbol i opens a node on level l exactly
   // when l < len(i) and l exceeds the common prefix of codewords i-1 and i
-  // (every level below len(0) for i = 0), and the node starts at the
-  // elements before i on that level: S[i] - S[first_gt[l]], S = prefix sums
-  // of the symbol counts along `order`.  One sweep over the symbols.
+  // (every level below len(0) for i = 0); that node's index on level l is
+  // its prefix minus the level's first one, and it starts at the elements
+  // before i on that level: S[i] - S[first_gt[l]], S = prefix sums of the
+  // symbol counts along `order`.
   const size_t np = order.size();
   const int Lw = std::max(Lm, 1);
-  std::vector<uint64_t> S(np + 1, 0), lc(np);
-  std::vector<uint8_t> ln(np), lo(np);
+  // canonical codes: consecutive values within a length, the first of each
+  // length the last of the previous length plus one, shifted left
+  uint64_t fcode[34] = {0};
+  {
+    uint64_t c = 0;
+    int prev = 0;
+    for (int ln = 1; ln <= 33; ln++) {
+      if (!lcount[ln]) continue;
+      if (prev) c = (c + lcount[prev]) << (ln - prev);
+      fcode[ln] = c;
+      prev = ln;
+    }
+  }
+  auto lcode = [&](uint64_t i, int& ln_i) -> uint64_t {  // left-aligned code of order[i]
+    ln_i = h->code_len[order[i]];
+    return (fcode[ln_i] + (i - lpos[ln_i])) << (Lm - ln_i);
+  };
+  auto first_open = [&](uint64_t i, uint64_t lci) -> int {  // first level symbol i opens a node on
+    if (i == 0) return 0;
+    int lp;
+    const uint64_t prev = lcode(i - 1, lp);
+    return __builtin_clzll((prev ^ lci) << (64 - Lm)) + 1;
+  };
+  std::vector<uint64_t> S(np + 1, 0);
   std::vector<uint64_t> nn(Lw, 0);
   {
-    // canonical codes along the order (consecutive values, shifted left
-    // when the length grows), with the per-symbol arrays above
-    uint64_t c = 0;
-    for (size_t i = 0; i < np; i++) {
-      const uint32_t sy = order[i];
-      ln[i] = h->code_len[sy];
-      if (i) c = (c + 1) << (ln[i] - ln[i - 1]);
-      h->code[sy] = (uint32_t)c;
-      lc[i] = c << (Lm - ln[i]);
-      S[i + 1] = S[i] + hh[sy];
-      // first level on which symbol i opens a node
-      lo[i] = i == 0 ? 0 : (uint8_t)(__builtin_clzll((lc[i - 1] ^ lc[i]) << (64 - Lm)) + 1);
-      for (int l = lo[i]; l < ln[i]; l++) nn[l]++;
-    }
+    // chunk sums of the counts, then the prefix sums, the codes and the
+    // nodes opened per level
+    uint64_t csum[MAXT + 1] = {0};
+    uint64_t topen[MAXT][33] = {};
+    const int nt = par(np, [&](int t, int n_t) {
+      uint64_t b, e, acc = 0;
+      chunk(np, t, n_t, b, e);
+      for (uint64_t i = b; i < e; i++) acc += hh[order[i]];
+      csum[t + 1] = acc;
+    });
+    for (int t = 0; t < nt; t++) csum[t + 1] += csum[t];
+    par(np, [&](int t, int n_t) {
+      uint64_t b, e;
+      chunk(np, t, n_t, b, e);
+      uint64_t acc = csum[t];
+      for (uint64_t i = b; i < e; i++) {
+        const uint32_t sy = order[i];
+        int ln_i;
+        const uint64_t lci = lcode(i, ln_i);
+        h->code[sy] = (uint32_t)(lci >> (Lm - ln_i));
+        S[i] = acc;
+        acc += hh[sy];
+        for (int l = first_open(i, lci); l < ln_i; l++) topen[t][l]++;
+      }
+      if (t + 1 == n_t) S[np] = acc;
+    });
+    for (int t = 0; t < nt; t++)
+      for (int l = 0; l < Lm; l++) nn[l] += topen[t][l];
   }
   std::vector<uint64_t> first_gt(Lw + 1, np);
   {
@@ -1323,39 +1400,52 @@ wt_status build_huff(const void* d_seq, uint64_t n, uint32_t sigma, int w, const
   {
     uint64_t tot = 0;
     for (int l = 0; l < Lm; l++) {
+      int lf;
       node_lvl[3 * l] = tot;
-      node_lvl[3 * l + 1] = first_gt[l] < np ? lc[first_gt[l]] >> (Lm - l) : 0;
+      node_lvl[3 * l + 1] = first_gt[l] < np ? lcode(first_gt[l], lf) >> (Lm - l) : 0;
       node_lvl[3 * l + 2] = nn[l];
       tot += nn[l] + 1;  // with the sentinel
       h->level_len[l] = S[np] - S[first_gt[l]];
     }
     node.resize(tot);
   }
-  // node starts, and the ones of every level as runs: bit l of symbol i
-  // (the last bit of its (l+1)-bit prefix) can differ from symbol i-1's
-  // only where that prefix changes, i.e. from level lo[i] - 1 up
-  std::vector<uint64_t> fill(Lw, 0), ones(Lw, 0), run0(Lw, 0);
-  std::vector<uint8_t> cur(Lw, 0);
-  for (size_t i = 0; i < np; i++) {
-    const int l0 = lo[i] > 0 ? lo[i] - 1 : 0;
-    for (int l = l0; l < ln[i]; l++) {
-      if (l >= lo[i]) node[node_lvl[3 * l] + fill[l]++] = S[i] - S[first_gt[l]];
-      const uint8_t b = (uint8_t)((lc[i] >> (Lm - 1 - l)) & 1u);
-      if (i == first_gt[l]) {
-        cur[l] = b;
-        run0[l] = S[i];
-      } else if (b != cur[l]) {
-        if (cur[l]) ones[l] += S[i] - run0[l];
-        cur[l] = b;
-        run0[l] = S[i];
+  // node starts at their indices, the ones of every level (the counts of the
+  // symbols whose code bit l is 1), and the left-aligned codes the first
+  // pass maps the symbols to
+  std::vector<uint32_t> left(sigma, 0u);
+  std::vector<uint64_t> ones(Lw, 0);
+  {
+    uint64_t tones[MAXT][33] = {};
+    int tbad[MAXT] = {0};
+    const int nt = par(np, [&](int t, int n_t) {
+      uint64_t b, e;
+      chunk(np, t, n_t, b, e);
+      for (uint64_t i = b; i < e; i++) {
+        const uint32_t sy = order[i];
+        int ln_i;
+        const uint64_t lci = lcode(i, ln_i);
+        left[sy] = (uint32_t)lci;
+        const uint64_t w = hh[sy];
+        for (int l = first_open(i, lci); l < ln_i; l++) {
+          const uint64_t k = (lci >> (Lm - l)) - node_lvl[3 * l + 1];
+          if (k >= nn[l]) {  // never for a prefix code
+            tbad[t] = 1;
+            continue;
+          }
+          node[node_lvl[3 * l] + k] = S[i] - S[first_gt[l]];
+        }
+        for (int l = 0; l < ln_i; l++)
+          if ((lci >> (Lm - 1 - l)) & 1u) tones[t][l] += w;
       }
+    });
+    for (int t = 0; t < nt; t++) {
+      if (tbad[t]) return WT_ERR_INVALID_ARG;  // not a prefix code
+      for (int l = 0; l < Lm; l++) ones[l] += tones[t][l];
     }
   }
   for (int l = 0; l < Lm; l++) {
-    if (cur[l]) ones[l] += S[np] - run0[l];
     zc[l] = h->level_len[l] - ones[l];
     node[node_lvl[3 * l] + nn[l]] = h->level_len[l];  // sentinel = level length
-    if (fill[l] != nn[l]) return WT_ERR_INVALID_ARG;   // not a prefix code
   }
   h->level_off.assign(Lm + 1, 0);
   for (int l = 0; l < Lm; l++) h->level_off[l + 1] = h->level_off[l] + level_words(h->level_len[l]);
@@ -1365,9 +1455,6 @@ wt_status build_huff(const void* d_seq, uint64_t n, uint32_t sigma, int w, const
   if (Lm) CK(cudaMemcpyAsync(h->d_zeros, h->zeros.data(), Lm * 8, cudaMemcpyHostToDevice, st));
   h->zeros_valid = true;
   // device tables
-  std::vector<uint32_t> left(sigma);
-  for (uint32_t s = 0; s < sigma; s++)
-    left[s] = h->code_len[s] ? (uint32_t)((uint64_t)h->code[s] << (Lm - h->code_len[s])) : 0;
   // per length: first canonical code, its index in `order`, symbol count
   std::vector<uint64_t> lentab(3 * 34, 0);
   {
