@@ -79,6 +79,19 @@ def test_no_cpu_fallback(lib, monkeypatch):
         lib.load_library(os.path.join(ROOT, "no_such_libwavelet.so"))
 
 
+@pytest.mark.parametrize("seed,sigma,hi", [(11, 1 << 19, 7), (12, 300001, 2000)])
+def test_library_huffman_large_alphabet_matches_oracle(lib, seed, sigma, hi):
+    """Alphabets large enough for the length computation's counting sort to
+    split its symbols over several threads, with many equal weights: the
+    order of equal weights, and so every length, stays the definition's."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    hist = rng.integers(0, hi + 1, size=sigma).astype(np.uint64)
+    hist[rng.integers(0, sigma, size=50)] = rng.integers(1 << 16, 1 << 20, size=50).astype(np.uint64)
+    la, ma = lib.huffman_lengths(hist, 32)
+    lo, mo = oracle.huffman_lengths(hist, 32)
+    assert ma == mo and np.array_equal(la, lo)
+
+
 @pytest.mark.parametrize("seed,sigma,hi", [(7, 1000, 3), (8, 4096, 1), (9, 300, 40), (10, 70000, 5)])
 def test_library_huffman_ties_match_oracle(lib, seed, sigma, hi):
     """Many equal weights (and zero counts): the library's merge order must
