@@ -381,7 +381,13 @@ def run_native(args):
     alg_bytes = args.steps * sum(pass_bytes(n, L, 2, tau))
     achieved = alg_bytes / (pass_ms * 1e-3) / 1e9 if pass_ms > 0 else None
     peak, peak_kind = measured_peak_hbm()
+    # (the committed figure is per launch at n = 2^30: scaled to this n, as
+    # a tile's traffic is its own data and two table rows)
     traffic = profiled_traffic()
+    if traffic is not None and tau == 8:
+        traffic = traffic * n / float(1 << 30)
+    elif traffic is not None:
+        traffic = None  # taken at tau = 8 only
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": (achieved / peak) if achieved else None,
             "traffic": traffic, "kernel": "k_pass (level-group partition pass)",
