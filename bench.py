@@ -411,22 +411,19 @@ def run_native(args):
     roof["whole_step_frac_of_B_tau"] = (step_bytes(n, L, 2, tau) / (ms * 1e-3) / 1e9) / peak
     roof["whole_step_frac_of_Bmin"] = ((2 + 2 + 16 / 128 + 16 / 512) * n / (ms * 1e-3) / 1e9) / peak
 
-    # end to end through the C ABI: every step copies its input from pinned
-    # host memory, builds, and reads its zero counts back on the host.  Two
-    # device buffers, one copy stream and two build streams taken in turn:
-    # the copy of step i + 1 runs while step i builds (the copy into a buffer
-    # waits for the build that last read it), and step i + 1's build is
-    # queued before the host waits for step i's result, so the GPU never
-    # waits for the host between builds
+    # end to end through the C ABI with host memory: every step hands the
+    # pinned host sequence to wm_build_host (the library copies it in on its
+    # host-copy stream and builds on the step's stream) and reads the
+    # structure's zero counts back on the host.  Three build streams taken in
+    # turn; the host reads step i - 2's result after queueing step i (its
+    # release synchronises only step i - 2's stream), so the copies of later
+    # steps run while earlier steps build and the GPU never waits for the
+    # host between builds
     e2e = None
     if not args.no_e2e:
-        dbufs = [torch.empty_like(d), torch.empty_like(d)]
         hz = torch.empty(L, dtype=torch.int64).pin_memory()
         k = max(1, args.steps)
-        sc = torch.cuda.Stream()
-        sbs = [torch.cuda.Stream(), torch.cuda.Stream()]
-        copied = [torch.cuda.Event(), torch.cuda.Event()]
-        built = [torch.cuda.Event(), torch.cuda.Event()]
+        sbs = [torch.cuda.Stream() for _ in range(3)]
         lib = wt.load_library()
         view = wt.ExportView()
         ev = lambda: torch.cuda.Event(enable_timing=True)
@@ -441,51 +438,34 @@ def run_native(args):
             h.free()
 
         def pipeline(k):
-            """k steps; returns the first event and the per-step copy and
-            build events (the copy on the copy stream, the build on its
-            stream)"""
+            """k steps; returns the first event and each step's events on its
+            stream (before the call, and after its build)"""
             f0 = ev()
             f0.record(sbs[0])
-            sc.wait_stream(sbs[0])
-            sbs[1].wait_stream(sbs[0])
-            cs, ce = [ev() for _ in range(k)], [ev() for _ in range(k)]
+            for x in sbs[1:]:
+                x.wait_stream(sbs[0])
             bs, be = [ev() for _ in range(k)], [ev() for _ in range(k)]
-
-            def copy_in(i):
-                b = i % 2
-                with torch.cuda.stream(sc):
-                    if i >= 2:
-                        sc.wait_event(built[b])
-                    cs[i].record(sc)
-                    dbufs[b].copy_(pin, non_blocking=True)
-                    ce[i].record(sc)
-                    copied[b].record(sc)
-
-            copy_in(0)
-            prev = None
+            pend = []
             for i in range(k):
-                if i + 1 < k:
-                    copy_in(i + 1)
-                b = i % 2
-                sbs[b].wait_event(copied[b])
-                bs[i].record(sbs[b])
-                h = wt.wm_build(dbufs[b], SIGMA, stream=sbs[b])
-                be[i].record(sbs[b])
-                built[b].record(sbs[b])
-                if prev is not None:
-                    finish(prev)
-                prev = h
-            finish(prev)
-            sbs[0].wait_stream(sbs[1])
-            return f0, cs, ce, bs, be
+                s = sbs[i % 3]
+                bs[i].record(s)
+                pend.append(wt.wm_build_host(pin, SIGMA, stream=s))
+                be[i].record(s)
+                if len(pend) > 2:
+                    finish(pend.pop(0))
+            for h in pend:
+                finish(h)
+            for x in sbs[1:]:
+                sbs[0].wait_stream(x)
+            return f0, bs, be
 
         # the same pipeline untimed first (W steps), so that first uses of
-        # the buffers and the copy path fall outside the timed steps
-        pipeline(max(args.warmup, 2))
+        # the pool's memory and of the copy path fall outside the timed steps
+        pipeline(max(args.warmup, 3))
         torch.cuda.synchronize()
         barrier()
         torch.cuda.synchronize()
-        f0, cs, ce, bs, be = pipeline(k)
+        f0, bs, be = pipeline(k)
         f1 = ev()
         f1.record(sbs[0])
         torch.cuda.synchronize()
@@ -494,22 +474,15 @@ def run_native(args):
         te = torch.tensor([e_ms], dtype=torch.float64, device=dev)
         if ws > 1:
             dist.all_reduce(te, op=dist.ReduceOp.MAX)
-        cms = [cs[i].elapsed_time(ce[i]) for i in range(k)]
-        bms = [bs[i].elapsed_time(be[i]) for i in range(k)]
-        # overlap of step i+1's copy with step i's build
-        ov = []
-        for i in range(k - 1):
-            a0, a1 = f0.elapsed_time(cs[i + 1]), f0.elapsed_time(ce[i + 1])
-            b0, b1 = f0.elapsed_time(bs[i]), f0.elapsed_time(be[i])
-            ov.append(max(0.0, min(a1, b1) - max(a0, b0)) / max(a1 - a0, 1e-9))
+        # a step's time on its stream: from the end of the build three steps
+        # earlier (or the start) through its copy and build
+        sms = [bs[i].elapsed_time(be[i]) for i in range(k)]
         e2e = {"value": ws * n * L / (float(te.item()) * 1e-3) / 1e9, "unit": UNIT,
                "h2d_bytes_per_step": 2 * n, "d2h_bytes_per_step": 8 * L, "steps": k,
                "ms_per_step": e_ms,
-               "timeline": {"copy_ms": [round(x, 3) for x in cms],
-                            "copy_ms_median": statistics.median(cms), "copy_ms_max": max(cms),
-                            "h2d_GBps_median": 2 * n / (statistics.median(cms) * 1e-3) / 1e9,
-                            "build_ms_median": statistics.median(bms),
-                            "copy_overlapped_with_build_frac": statistics.median(ov) if ov else None,
+               "api": "wm_build_host (host sequence in) + wt_export (zero counts out)",
+               "timeline": {"stream_ms": [round(x, 3) for x in sms],
+                            "stream_ms_median": statistics.median(sms),
                             "exposed_ms_per_step": e_ms - ms}}
 
     # the batched and the serving workloads, bounded, beside the headline

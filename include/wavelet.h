@@ -131,6 +131,23 @@ wt_status wt_build(const void* d_seq, uint64_t n, uint32_t sigma, uint32_t width
 wt_status wm_build(const void* d_seq, uint64_t n, uint32_t sigma, uint32_t width_bytes,
                    const wt_build_opts* opts, wt_stream stream, wt_handle* out);
 
+/* The same wavelet matrix from a sequence in HOST memory: the call enqueues
+ * a copy of the n * width_bytes bytes at h_seq into a device buffer of its
+ * own (from the library's memory pool), then on `stream` the build wm_build
+ * makes of that buffer and the buffer's release, and returns.  The copies
+ * of all host-memory builds on a device go, in call order, through one
+ * stream of the library's, which `stream` waits for, so that calls on
+ * several streams copy one after another while earlier builds run.  h_seq
+ * is borrowed until that copy has finished (wt_sync on the handle, or any
+ * later synchronisation of `stream`, passes that point); the copy runs
+ * asynchronously from page-locked memory, while the driver copies pageable
+ * memory before the call returns.  Arguments, result and errors
+ * are those of wm_build; in addition, WT_ERR_NO_MEMORY when the device
+ * buffer cannot be had and WT_ERR_CUDA when the copy cannot be enqueued,
+ * both with *out left NULL. */
+wt_status wm_build_host(const void* h_seq, uint64_t n, uint32_t sigma, uint32_t width_bytes,
+                        const wt_build_opts* opts, wt_stream stream, wt_handle* out);
+
 /* Huffman-shaped binary wavelet tree (Section 4.3, arbitrarily-shaped
  * trees).  h_code_len: sigma code lengths (0 = absent symbol), or NULL to
  * derive Huffman lengths from the sequence's histogram, limited to 32 bits.

@@ -25,7 +25,7 @@ FLAG_NO_DIRECTORY = 1
 FLAG_SELECT_O1 = 2
 
 #: every entry point declared in include/wavelet.h
-ABI_SYMBOLS = ("wt_build", "wm_build", "huff_wt_build", "multiary_build", "rs_build",
+ABI_SYMBOLS = ("wt_build", "wm_build", "wm_build_host", "huff_wt_build", "multiary_build", "rs_build",
                "wt_access", "wt_rank", "wt_select", "wt_sync", "wt_export", "wt_free",
                "wt_symbol_levels", "wt_status_str", "wt_memcpy_d2h", "wt_huffman_lengths",
                "wt_canonical_codes", "wt_prof_enable", "wt_prof_read", "rs_dir_build_static",
@@ -115,7 +115,7 @@ def load_library(path: str = LIB_PATH):
     c = ctypes
     vp, u64, u32 = c.c_void_p, c.c_uint64, c.c_uint32
     hp = c.POINTER(c.c_void_p)
-    for name in ("wt_build", "wm_build"):
+    for name in ("wt_build", "wm_build", "wm_build_host"):
         f = getattr(lib, name)
         f.restype = c.c_int
         f.argtypes = [vp, u64, u32, u32, c.POINTER(BuildOpts), vp, hp]
@@ -379,6 +379,25 @@ def wm_build(seq, sigma: int, n: int | None = None, tau: int = 0, ctas_per_sm: i
     n = seq.numel() if n is None else n
     o = _opts(tau, ctas_per_sm, flags, tile_symbols)
     return _build(load_library().wm_build, "wm_build", _ptr(seq), n, sigma, _width(seq),
+                  ctypes.byref(o), _stream_ptr(stream))
+
+
+def wm_build_host(seq, sigma: int, n: int | None = None, tau: int = 0, ctas_per_sm: int = 0,
+                  flags: int = 0, stream=None, tile_symbols: int = 0) -> Handle:
+    """Wavelet matrix of a host tensor (ideally pinned) or numpy array of
+    uint8/int16/int32 symbols: the library copies it to the device on the
+    stream and builds there."""
+    if isinstance(seq, np.ndarray):
+        ptr, width, count = seq.ctypes.data, seq.itemsize, seq.size
+    else:
+        if seq.is_cuda:
+            raise ValueError("wm_build_host takes host memory; use wm_build for device tensors")
+        ptr, width, count = seq.data_ptr(), seq.element_size(), seq.numel()
+    n = count if n is None else n
+    if n > count:
+        raise ValueError(f"n = {n} exceeds the {count} host elements")
+    o = _opts(tau, ctas_per_sm, flags, tile_symbols)
+    return _build(load_library().wm_build_host, "wm_build_host", ptr, n, sigma, width,
                   ctypes.byref(o), _stream_ptr(stream))
 
 

@@ -3,6 +3,7 @@
 // dirq.cu.
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 
 #include "wt_host.h"
@@ -207,6 +208,27 @@ wt_status huff_async(const void* d_seq, uint64_t n, uint32_t sigma, uint32_t wid
   return WT_OK;
 }
 
+// One stream per device for the copies of host-memory builds, created on
+// first use and kept for the life of the process.
+cudaError_t host_copy_stream(cudaStream_t* out) {
+  static std::mutex mu;
+  static cudaStream_t streams[64] = {};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> g(mu);
+  if (!streams[dev]) {
+    e = cudaStreamCreateWithFlags(&streams[dev], cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+      streams[dev] = nullptr;
+      return e;
+    }
+  }
+  *out = streams[dev];
+  return cudaSuccess;
+}
+
 wt_status seq_build(int kind, const void* d_seq, uint64_t n, uint32_t sigma, uint32_t width,
                     const uint8_t* h_len, uint32_t degree, const wt_build_opts* opts,
                     wt_stream stream, wt_handle* out) {
@@ -255,6 +277,49 @@ wt_status wt_build(const void* d_seq, uint64_t n, uint32_t sigma, uint32_t width
 wt_status wm_build(const void* d_seq, uint64_t n, uint32_t sigma, uint32_t width_bytes,
                    const wt_build_opts* opts, wt_stream stream, wt_handle* out) {
   return seq_build(WT_KIND_WM, d_seq, n, sigma, width_bytes, nullptr, 2, opts, stream, out);
+}
+
+wt_status wm_build_host(const void* h_seq, uint64_t n, uint32_t sigma, uint32_t width_bytes,
+                        const wt_build_opts* opts, wt_stream stream, wt_handle* out) {
+  if (!out) return WT_ERR_INVALID_ARG;
+  *out = nullptr;
+  if ((!h_seq && n) || sigma == 0 || !valid_width(width_bytes)) return WT_ERR_INVALID_ARG;
+  wt_status s = check_opts(opts);
+  if (s != WT_OK) return s;
+  if (n >= ((uint64_t)1 << 40)) return WT_ERR_UNSUPPORTED;
+  cudaStream_t cs = (cudaStream_t)stream;
+  const uint64_t bytes = n * (uint64_t)width_bytes;
+  void* d = nullptr;
+  if (bytes) {
+    // the copy goes on the device's host-copy stream, so that the copies of
+    // calls on different streams follow one another at the link's full rate
+    // (each while earlier builds run) instead of sharing it; the caller's
+    // stream waits for it
+    cudaStream_t xs = nullptr;
+    cudaEvent_t copied = nullptr;
+    if (host_copy_stream(&xs) != cudaSuccess) {
+      cudaGetLastError();
+      return WT_ERR_CUDA;
+    }
+    if (dmalloc(&d, bytes, xs) != cudaSuccess) {
+      cudaGetLastError();
+      return WT_ERR_NO_MEMORY;
+    }
+    const bool ok = cudaMemcpyAsync(d, h_seq, bytes, cudaMemcpyHostToDevice, xs) == cudaSuccess &&
+                    cudaEventCreateWithFlags(&copied, cudaEventDisableTiming) == cudaSuccess &&
+                    cudaEventRecord(copied, xs) == cudaSuccess &&
+                    cudaStreamWaitEvent(cs, copied, 0) == cudaSuccess;
+    if (copied) cudaEventDestroy(copied);
+    if (!ok) {
+      dfree(d, xs);
+      cudaGetLastError();
+      return WT_ERR_CUDA;
+    }
+  }
+  s = seq_build(WT_KIND_WM, d, n, sigma, width_bytes, nullptr, 2, opts, stream, out);
+  // every step of the build is on `stream`: the release follows them
+  if (d) dfree(d, cs);
+  return s;
 }
 
 wt_status huff_wt_build(const void* d_seq, uint64_t n, uint32_t sigma, uint32_t width_bytes,

@@ -39,7 +39,11 @@ namespace wtk {
 // Device memory comes from the device's stream-ordered pool.  The pool keeps
 // up to POOL_KEEP bytes of freed memory reserved instead of returning it to
 // the driver at every synchronisation, so repeated builds do not map and
-// unmap their multi-GB buffers each time.
+// unmap their multi-GB buffers each time.  It reuses memory freed on another
+// stream only once that free has completed (or the allocating stream already
+// waits for it): it never makes one stream wait for another's work to hand
+// memory over, which would serialise builds and copies queued on different
+// streams; it takes more memory from the device instead.
 constexpr uint64_t POOL_KEEP = 32ull << 30;
 
 cudaError_t dmalloc(void** p, size_t bytes, cudaStream_t s) {
@@ -53,6 +57,8 @@ cudaError_t dmalloc(void** p, size_t bytes, cudaStream_t s) {
       if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
         uint64_t keep = POOL_KEEP;
         cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+        int no = 0;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolReuseAllowInternalDependencies, &no);
       }
       done[dev] = true;
     }

@@ -1,9 +1,11 @@
 /* A plain C consumer of include/wavelet.h: builds a wavelet matrix of a small
- * sequence on the current GPU and answers rank queries, using only the C ABI
- * and the CUDA runtime for device memory.  The CPU test suite compiles it as
+ * sequence on the current GPU, once from a device copy (wm_build) and once
+ * from the host array itself (wm_build_host, pageable memory), and answers
+ * rank queries on both, using only the C ABI and the CUDA runtime for device
+ * memory.  The CPU test suite compiles it as
  * C99 and as C++ and links it against the library (every call it makes must
  * resolve); it is not run there.  Run on a GPU it prints "abi client ok" and
- * exits 0 when every rank answer equals a count on the host. */
+ * exits 0 when every rank answer of both equals a count on the host. */
 #include <stdint.h>
 #include <stdio.h>
 #include <stdlib.h>
@@ -23,10 +25,10 @@ static int fail(const char* what, int s) {
 
 int main(void) {
   uint16_t* h_seq = (uint16_t*)malloc(N * sizeof(uint16_t));
-  uint64_t h_i[Q], h_out[Q];
+  uint64_t h_i[Q], h_out[Q], h_out2[Q];
   uint32_t h_c[Q];
   void *d_seq = NULL, *d_i = NULL, *d_c = NULL, *d_out = NULL;
-  wt_handle h = NULL;
+  wt_handle h = NULL, h2 = NULL;
   wt_status s;
   uint32_t x = 12345u, q;
   uint64_t k;
@@ -55,12 +57,21 @@ int main(void) {
   s = wt_sync(h);
   if (s != WT_OK) return fail("wt_sync", s);
   if (wt_memcpy_d2h(h_out, d_out, sizeof h_out) != WT_OK) return fail("wt_memcpy_d2h", 0);
+  s = wm_build_host(h_seq, N, SIGMA, 2, NULL, NULL, &h2);
+  if (s != WT_OK) return fail("wm_build_host", s);
+  s = wt_rank(h2, (const uint32_t*)d_c, (const uint64_t*)d_i, Q, (uint64_t*)d_out, NULL);
+  if (s != WT_OK) return fail("wt_rank (host build)", s);
+  s = wt_sync(h2);
+  if (s != WT_OK) return fail("wt_sync (host build)", s);
+  if (wt_memcpy_d2h(h_out2, d_out, sizeof h_out2) != WT_OK) return fail("wt_memcpy_d2h", 0);
   for (q = 0; q < Q; q++) {  /* rank(c, i): occurrences of c in S[0..i] */
     uint64_t cnt = 0;
     for (k = 0; k <= h_i[q]; k++) cnt += h_seq[k] == h_c[q];
     if (cnt != h_out[q]) bad++;
+    if (cnt != h_out2[q]) bad++;
   }
   wt_free(h);
+  wt_free(h2);
   cudaFree(d_seq);
   cudaFree(d_i);
   cudaFree(d_c);

@@ -393,3 +393,47 @@ def test_unaligned_input_pointer(wt, width, off):
     assert np.array_equal(hs[0].export().bits.reshape(ob.shape), ob)
     ob, _ = oracle.wm_build(S[1:], sigma)
     assert np.array_equal(hs[1].export().bits.reshape(ob.shape), ob)
+
+
+@pytest.mark.parametrize("case", [("zipf", 81, 12289, 65536, 2), ("uniform", 82, 4097, 200, 1),
+                                  ("uniform", 83, 30001, 1 << 20, 4), ("zipf", 84, 1, 7, 2)],
+                         ids=lambda c: f"{c[0]}-n{c[2]}-s{c[3]}-w{c[4]}")
+@pytest.mark.parametrize("pinned", [True, False])
+def test_wm_build_host_parity(wt, case, pinned):
+    """The host-memory build (the library copies the sequence in on the
+    stream) gives the oracle's wavelet matrix, from page-locked and from
+    pageable memory."""
+    import torch
+    kind, seed, n, sigma, width = case
+    S = gen(kind, seed, n, sigma, width)
+    t = torch.from_numpy(S.view({1: np.uint8, 2: np.int16, 4: np.int32}[width]))
+    if pinned:
+        t = t.pin_memory()
+    h = wt.wm_build_host(t, sigma)
+    ex = h.export()
+    ob, oz = oracle.wm_build(S, sigma)
+    assert ex.levels == ob.shape[0]
+    assert np.array_equal(ex.bits.reshape(ob.shape), ob)
+    assert np.array_equal(ex.zeros, oz)
+    check_binary_dirs(ex, list(ob), [S.size] * ob.shape[0])
+    h.free()
+
+
+def test_wm_build_host_errors(wt):
+    import torch
+    S = synth.uniform(85, 5000, 100, 2)
+    # a symbol >= sigma: reported by the handle, as for wm_build
+    h = wt.wm_build_host(S, 50)
+    with pytest.raises(wt.WaveletError) as e:
+        h.sync()
+    assert e.value.status == 2
+    h.free()
+    with pytest.raises(wt.WaveletError):
+        wt.wm_build_host(S, 0)
+    with pytest.raises(ValueError):
+        wt.wm_build_host(S, 100, n=S.size + 1)
+    with pytest.raises(ValueError):
+        wt.wm_build_host(torch.zeros(4, dtype=torch.int16, device="cuda"), 10)
+    h = wt.wm_build_host(np.empty(0, dtype=np.uint16), 10)
+    assert h.export().n == 0
+    h.free()
