@@ -159,18 +159,19 @@ struct PassSmem {
 };
 
 // resident CTAs per SM the register budget is sized for: 5 for 16-bit
-// elements (40 registers a thread at 288 threads a CTA); 4 for 32-bit
-// elements, whose buffers let only 4 CTAs share an SM's shared memory, and
-// for batched passes, whose per-sequence state would spill at 40 registers
-// (56 at 4); 2 for the 8192-symbol tile (544 threads a CTA).  And whether a
-// split keeps its elements in registers between its two phases (else it
-// reads them from shared memory again).
+// elements (40 registers a thread at 288 threads a CTA; batched passes keep
+// their per-sequence state in shared memory and spill 12 bytes at 40, which
+// costs less than a fifth of the CTAs would); 4 for 32-bit elements, whose
+// buffers let only 4 CTAs share an SM's shared memory (56 registers); 2 for
+// the 8192-symbol tile (544 threads a CTA).  And whether a split keeps its
+// elements in registers between its two phases (else it reads them from
+// shared memory again).
 #ifndef WT_PASS_MIN_CTAS
 #define WT_PASS_MIN_CTAS 5
 #endif
 template <typename E, int T, bool BATCH>
 struct PassCtas {
-  static constexpr int value = T >= 8192 ? 2 : (BATCH || sizeof(E) == 4) ? 4 : WT_PASS_MIN_CTAS;
+  static constexpr int value = T >= 8192 ? 2 : sizeof(E) == 4 ? 4 : WT_PASS_MIN_CTAS;
 };
 #ifndef WT_PASS_KEEP_X
 #define WT_PASS_KEEP_X 1
