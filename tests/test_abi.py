@@ -132,6 +132,20 @@ def test_unsupported_options_are_rejected_before_device_work(lib):
     assert so.wm_build(None, 0, 4, 3, None, None, ctypes.byref(h)) == 1
     assert so.wm_build(None, 0, 0, 2, None, None, ctypes.byref(h)) == 1
     assert so.wm_build(None, 5, 4, 2, None, None, ctypes.byref(h)) == 1
+    # the host-memory build checks the same before its copy is enqueued
+    for b in bad:
+        o = lib.BuildOpts()
+        for f in ("tau", "tile_symbols", "k_chunks", "select_sample"):
+            setattr(o, f, b.get(f, 0))
+        assert so.wm_build_host(None, 0, 4, 2, ctypes.byref(o), None, ctypes.byref(h)) == b["status"], b
+        assert not h.value
+    assert so.wm_build_host(None, 0, 4, 3, None, None, ctypes.byref(h)) == 1
+    assert so.wm_build_host(None, 0, 0, 2, None, None, ctypes.byref(h)) == 1
+    assert so.wm_build_host(None, 5, 4, 2, None, None, ctypes.byref(h)) == 1
+    assert so.wm_build_host(None, 0, 4, 2, None, None, None) == 1
+    # the binding refuses a length beyond the host array before any call
+    with pytest.raises(ValueError):
+        lib.wm_build_host(np.zeros(4, dtype=np.uint16), 10, n=5)
 
 
 @pytest.mark.parametrize("compiler,std", [("gcc", "-std=c99"), ("g++", "-std=c++17")])
