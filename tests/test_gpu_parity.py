@@ -437,3 +437,23 @@ def test_wm_build_host_errors(wt):
     h = wt.wm_build_host(np.empty(0, dtype=np.uint16), 10)
     assert h.export().n == 0
     h.free()
+
+
+def test_wm_build_host_concurrent_streams(wt):
+    """Host-memory builds queued on several streams at once (their copies
+    share the library's copy stream, their staging buffers the pool) give
+    the same structures as device builds, with and without options."""
+    import torch
+    S = synth.zipf(86, 200003, 65536, 1.1, 2)
+    pin = torch.from_numpy(S.view(np.int16)).pin_memory()
+    ref = wt.wm_build(pin.to("cuda"), 65536)
+    rb, rz = ref.export().bits.copy(), ref.export().zeros.copy()
+    ref.free()
+    streams = [torch.cuda.Stream() for _ in range(4)]
+    opts = [dict(), dict(tau=4), dict(tile_symbols=2048), dict(tau=8, tile_symbols=8192)]
+    hs = [wt.wm_build_host(pin, 65536, stream=s, **o) for s, o in zip(streams, opts)]
+    for h in hs:
+        ex = h.export()
+        assert np.array_equal(ex.bits, rb)
+        assert np.array_equal(ex.zeros, rz)
+        h.free()
