@@ -198,6 +198,33 @@ __device__ uint32_t find_in_sb(const uint64_t* lbits, const uint64_t* ldir, uint
   return 2047;
 }
 
+// The same for the sample kernel, with the target block's eight words loaded
+// together (one round of loads instead of one per word visited); words at
+// or past nw, the level's word count, are not read.
+__device__ uint32_t find_in_sb_blk(const uint64_t* lbits, const uint64_t* ldir, uint64_t s,
+                                   int bv, uint32_t r, uint64_t nw) {
+  const uint64_t rel = ldir[2 * s + 1];
+  int b = 3;
+  for (; b > 0; b--) {
+    const uint32_t z = (uint32_t)((rel >> (16 * b)) & 0xffffu);
+    const uint32_t before = bv ? 512u * b - z : z;
+    if (before <= r) break;
+  }
+  const uint32_t z = b ? (uint32_t)((rel >> (16 * b)) & 0xffffu) : 0u;
+  r -= bv ? 512u * b - z : z;
+  const uint64_t w0 = 32 * s + 8 * (uint64_t)b;
+  uint64_t v[8];
+#pragma unroll
+  for (int i = 0; i < 8; i++) v[i] = w0 + i < nw ? lbits[w0 + i] : 0ull;
+#pragma unroll
+  for (int i = 0; i < 8; i++) {
+    const uint32_t c = bv ? __popcll(v[i]) : 64 - __popcll(v[i]);
+    if (c > r) return (uint32_t)((8 * b + i) * 64) + sel64(bv ? v[i] : ~v[i], r);
+    r -= c;
+  }
+  return 2047;
+}
+
 template <bool SMALL>
 __global__ void k_select_samples(const uint64_t* bits, const LevelMeta* meta, int nlev,
                                  const uint64_t* sb_first, uint64_t total_sb,
@@ -223,12 +250,13 @@ __global__ void k_select_samples(const uint64_t* bits, const LevelMeta* meta, in
   const uint64_t zs = ze - zb;
   const uint64_t nvalid = std::min<uint64_t>(2048, m.n - 2048 * s);
   const uint64_t ob = 2048 * s - zb, os = nvalid - zs;
+  const uint64_t nw = (m.n + 63) / 64;
   const uint64_t k0 = (zb + 4095) / 4096;
   if (4096 * k0 < zb + zs)
-    samp[m.s0_off + k0] = 2048 * s + find_in_sb(lb, ld, s, 0, (uint32_t)(4096 * k0 - zb));
+    samp[m.s0_off + k0] = 2048 * s + find_in_sb_blk(lb, ld, s, 0, (uint32_t)(4096 * k0 - zb), nw);
   const uint64_t k1 = (ob + 4095) / 4096;
   if (4096 * k1 < ob + os)
-    samp[m.s1_off + k1] = 2048 * s + find_in_sb(lb, ld, s, 1, (uint32_t)(4096 * k1 - ob));
+    samp[m.s1_off + k1] = 2048 * s + find_in_sb_blk(lb, ld, s, 1, (uint32_t)(4096 * k1 - ob), nw);
 }
 
 // ---------------------------------------------------------------------------
