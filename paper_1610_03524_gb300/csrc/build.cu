@@ -261,12 +261,15 @@ __device__ __forceinline__ void hist_bytes_swar(const void* seq, uint64_t n, uin
 
 // Full symbol histogram (balanced / Huffman / 4-ary trees).
 // (large alphabets: block b adds into copy b % ncopy of the histogram, at
-// hist + (b % ncopy) * sigma, so that the frequent symbols of a skewed
-// alphabet spread their atomics over several addresses; the copies are
-// summed afterwards)
+// (b % ncopy) * sigma, so that the frequent symbols of a skewed alphabet
+// spread their atomics over several addresses; the copies are summed
+// afterwards.  The copies are 32-bit (hist32) while no count can reach
+// 2^32, so that 16 copies of a 2^20-symbol alphabet, 64 MB, stay in L2: as
+// 64-bit copies they took 128 MB and their atomics went to DRAM)
 template <int WB>
 __global__ void k_hist_full(const void* seq, uint64_t n, uint32_t sigma, uint64_t* hist,
-                            uint32_t* err, int use_smem, uint32_t ncopy = 1) {
+                            uint32_t* err, int use_smem, uint32_t ncopy = 1,
+                            uint32_t* hist32 = nullptr) {
   extern __shared__ uint32_t shh[];
   if (use_smem) {
     for (uint32_t i = threadIdx.x; i < sigma; i += blockDim.x) shh[i] = 0;
@@ -298,9 +301,11 @@ __global__ void k_hist_full(const void* seq, uint64_t n, uint32_t sigma, uint64_
                           // alphabets put many lanes on the frequent ones)
                           const uint32_t act = __activemask();
                           const uint32_t peers = __match_any_sync(act, x);
-                          if (ok && lane == __ffs(peers) - 1)
-                            atomicAdd((unsigned long long*)&hist[(uint64_t)(blockIdx.x % ncopy) * sigma + x],
-                                      (unsigned long long)__popc(peers));
+                          if (ok && lane == __ffs(peers) - 1) {
+                            const uint64_t at = (uint64_t)(blockIdx.x % ncopy) * sigma + x;
+                            if (hist32) atomicAdd(&hist32[at], (uint32_t)__popc(peers));
+                            else atomicAdd((unsigned long long*)&hist[at], (unsigned long long)__popc(peers));
+                          }
                         }
                       });
   if (bad) atomicOr(err, ERR_SYMBOL);
@@ -311,8 +316,8 @@ __global__ void k_hist_full(const void* seq, uint64_t n, uint32_t sigma, uint64_
   }
 }
 
-__global__ void k_hist_sum_copies(const uint64_t* copies, uint32_t sigma, uint32_t ncopy,
-                                  uint64_t* hist) {
+template <typename C>
+__global__ void k_hist_sum_copies(const C* copies, uint32_t sigma, uint32_t ncopy, uint64_t* hist) {
   for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < sigma;
        i += (uint64_t)gridDim.x * blockDim.x) {
     uint64_t a = 0;
@@ -321,31 +326,48 @@ __global__ void k_hist_sum_copies(const uint64_t* copies, uint32_t sigma, uint32
   }
 }
 
+#ifndef WT_HIST_COPY_MB
+#define WT_HIST_COPY_MB 64
+#endif
+constexpr uint64_t HIST_COPY_BYTES = (uint64_t)WT_HIST_COPY_MB << 20;
+
 static wt_status launch_hist_full(const void* seq, int w, uint64_t n, uint32_t sigma,
                                   uint64_t* hist, uint32_t* err, cudaStream_t st) {
   if (n == 0) return WT_OK;
   const int use_smem = sigma <= 12288;
   const size_t shb = use_smem ? sigma * 4 : 0;
   const uint32_t blocks = std::min<uint64_t>(num_sms() * 4, (n + 4095) / 4096 + 1);
-  // global counters: 16 copies while they take at most 256 MB
+  // global counters: up to 16 copies (32-bit while no count can reach 2^32),
+  // taking at most HIST_COPY_BYTES so that they stay in L2
   uint32_t ncopy = 1;
   uint64_t* dst = hist;
+  uint32_t* dst32 = nullptr;
   Work wk{st, {}};
+  const bool narrow = n < (1ull << 32);
   if (!use_smem) {
-    ncopy = (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>(16, (256ull << 20) / (8ull * sigma)));
-    if (ncopy > 1) {
+    const uint64_t c32 = HIST_COPY_BYTES / (4ull * sigma);
+    if (narrow && c32 >= 2) {
+      ncopy = (uint32_t)std::min<uint64_t>(16, c32);
+      TRY(wk.get(&dst32, (size_t)ncopy * sigma));
+      CK(cudaMemsetAsync(dst32, 0, (size_t)ncopy * sigma * 4, st));
+    } else if ((ncopy = (uint32_t)std::max<uint64_t>(
+                    1, std::min<uint64_t>(16, HIST_COPY_BYTES / (8ull * sigma)))) > 1) {
       TRY(wk.get(&dst, (size_t)ncopy * sigma));
       CK(cudaMemsetAsync(dst, 0, (size_t)ncopy * sigma * 8, st));
     }
   }
-  if (w == 1) k_hist_full<1><<<blocks, 512, shb, st>>>(seq, n, sigma, dst, err, use_smem, ncopy);
-  else if (w == 2) k_hist_full<2><<<blocks, 512, shb, st>>>(seq, n, sigma, dst, err, use_smem, ncopy);
-  else k_hist_full<4><<<blocks, 512, shb, st>>>(seq, n, sigma, dst, err, use_smem, ncopy);
+  if (w == 1) k_hist_full<1><<<blocks, 512, shb, st>>>(seq, n, sigma, dst, err, use_smem, ncopy, dst32);
+  else if (w == 2) k_hist_full<2><<<blocks, 512, shb, st>>>(seq, n, sigma, dst, err, use_smem, ncopy, dst32);
+  else k_hist_full<4><<<blocks, 512, shb, st>>>(seq, n, sigma, dst, err, use_smem, ncopy, dst32);
   count_launch();
   CK(cudaGetLastError());
-  if (ncopy > 1) {
-    k_hist_sum_copies<<<(unsigned)std::min<uint64_t>((sigma + 255) / 256, (uint64_t)num_sms() * 8), 256, 0,
-                        st>>>(dst, sigma, ncopy, hist);
+  const unsigned sg = (unsigned)std::min<uint64_t>((sigma + 255) / 256, (uint64_t)num_sms() * 8);
+  if (dst32) {
+    k_hist_sum_copies<uint32_t><<<sg, 256, 0, st>>>(dst32, sigma, ncopy, hist);
+    count_launch();
+    CK(cudaGetLastError());
+  } else if (ncopy > 1) {
+    k_hist_sum_copies<uint64_t><<<sg, 256, 0, st>>>(dst, sigma, ncopy, hist);
     count_launch();
     CK(cudaGetLastError());
   }
