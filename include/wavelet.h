@@ -137,7 +137,10 @@ wt_status wm_build(const void* d_seq, uint64_t n, uint32_t sigma, uint32_t width
  * makes of that buffer and the buffer's release, and returns.  The copies
  * of all host-memory builds on a device go, in call order, through one
  * stream of the library's, which `stream` waits for, so that calls on
- * several streams copy one after another while earlier builds run.  h_seq
+ * several streams copy one after another while earlier builds run (the
+ * library creates that stream on the device's first host-memory build and
+ * keeps it for the life of the process: after cudaDeviceReset, host-memory
+ * builds on that device are not supported).  h_seq
  * is borrowed until that copy has finished (wt_sync on the handle, or any
  * later synchronisation of `stream`, passes that point); the copy runs
  * asynchronously from page-locked memory, while the driver copies pageable
